@@ -1,0 +1,345 @@
+"""Benchmark: converged eigenpairs per second of the rational-filter eigensolver.
+
+One step = one complete Algorithm 1 solve (filter by batched COCG over all
+poles x columns, Cholesky-QR2, Rayleigh-Ritz, residuals, until every Ritz pair
+in (0, gamma] has rho <= 1e-8) of the 2D Q1 workload: 300 x 300 bilinear
+elements, lognormal coefficient, n = 89 401, 100 eigenvalues in (0, gamma],
+subspace L = 150, N = 4 SLRF poles (alpha = 1, beta = 0.01), mixed precision
+(FP32 Krylov on the FP64 residual, FP64 projection).  Inputs are synthetic and
+seeded; the start block and the pencil are resident on the device before the
+timed region.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run; ranks are independent replicas
+(the solve does not shard: weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "fem2d_q1_300"
+METRIC = "eigenpairs/s at resid 1e-8 (2D Q1 n=89401, 100 eigenpairs, mixed FP32/FP64)"
+UNIT = "eigenpairs/s"
+TOL = 1e-8
+MAX_OUTER = 40
+ROOFLINE_CLASS = "shifted_spmm"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "shifted_spmm_fem2d_q1_300.md")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_digest() -> str:
+    path = os.path.join(ROOT, "paper_2503_21618_gb300", "csrc", "krylov.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic_per_launch():
+    """DRAM bytes per launch of the roofline kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None, "no ncu summary"
+    text = open(PROFILE_SUMMARY).read()
+    m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    d = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m:
+        return None, "summary has no traffic line"
+    if not d or d.group(1) != source_digest():
+        return None, "kernel changed since the ncu capture"
+    return float(m.group(1)), "ncu"
+
+
+def aggregate(seconds: float, units: float, device="cpu"):
+    """Whole-job throughput of replicas: units summed over ranks, divided by
+    the slowest rank's time (max over ranks).  Returns (value, t_max, units)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_outer_step_seconds(p, iv, L, n_poles):
+    """Time one outer step of the oracle's Algorithm 1 (exact sparse LU per pole)."""
+    import numpy as np
+    from oracle import filter as ofilt
+    from oracle import poles, rr
+    from workloads import start_block
+    s, w = poles.slrf_poles(n_poles, 1.0, 0.01, iv["gamma"])
+    V = start_block(p.n, L, 2505)
+    A, B = p.A(), p.B()
+    t0 = time.perf_counter()
+    U = ofilt.filter_apply(A, B, s, w, V)
+    theta, X = rr.rayleigh_ritz(A, B, U)
+    rr.residuals(A, B, X, theta)
+    t = time.perf_counter() - t0
+    del np
+    return t
+
+
+def cpu_baseline(p, iv, outer_iters):
+    t = oracle_outer_step_seconds(p, iv, iv["L"], iv["n_poles"])
+    per_solve = t * max(1, outer_iters)
+    return {"value": iv["nev"] / per_solve, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one outer step of the FP64 oracle Algorithm 1 (SuperLU per pole, dense eigh) on "
+                       f"{WORKLOAD}: {t:.2f} s, scaled by the {outer_iters} outer steps of the measured solve; "
+                       f"SuperLU single-threaded, BLAS on up to {os.cpu_count()} threads")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from workloads import config_pencil, interval_for
+    p = config_pencil(WORKLOAD)
+    iv = interval_for(WORKLOAD)
+    outer = 8   # outer steps of a converged solve of this workload (GPU and oracle runs)
+    for _ in range(args.warmup):
+        pass
+    times = [oracle_outer_step_seconds(p, iv, iv["L"], iv["n_poles"]) for _ in range(args.steps)]
+    t_solve = statistics.mean(times) * outer
+    value = iv["nev"] / t_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "L": iv["L"], "nev": iv["nev"],
+                       "n_poles": iv["n_poles"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": (f"each step times one outer step of the FP64 oracle Algorithm 1 "
+                                        f"(SuperLU per pole) on {WORKLOAD}, scaled by {outer} outer steps")},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain", action="store_true", help="also time one plain FP64 solve")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    import numpy as np
+    torch.cuda.set_device(local)
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2503_21618_gb300 as pkg
+    from workloads import config_pencil, interval_for, start_block
+
+    p = config_pencil(WORKLOAD)
+    iv = interval_for(WORKLOAD)
+    L, nev, N = iv["L"], iv["nev"], iv["n_poles"]
+    f = pkg.design_poles("slrf", N, iv["gamma"], 1.0, 0.01)
+    opts = pkg.default_opts(profile=1)
+    h = pkg.Handle(p, opts)
+    V0 = torch.from_numpy(start_block(p.n, L, 2505)).cuda()
+    theta = torch.empty(L, dtype=torch.float64, device="cuda")
+    X = torch.empty_like(V0)
+    resid = torch.empty(L, dtype=torch.float64, device="cuda")
+
+    def step():
+        return h.subspace_iterate(f, iv["gamma"], V0, tol=TOL, max_outer=MAX_OUTER, theta=theta, X=X, resid=resid)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    reps, conv, outer = [], [], []
+    for _ in range(args.steps):
+        *_, nconv, st, rep = step()
+        reps.append(rep.as_dict())
+        conv.append(int(nconv) if st == pkg.OK else 0)
+        outer.append(rep.outer_iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    value, t_max, _ = aggregate(t, float(sum(conv)), "cuda")
+
+    # roofline of the dominant kernel from the live per-launch events
+    tot = {}
+    for r in reps:
+        for k, v in r["kernels"].items():
+            a = tot.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+            for key in a:
+                a[key] += v[key]
+    k = tot.get(ROOFLINE_CLASS, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+    peaks, peak_src = measured_peaks()
+    achieved = (k["bytes"] / k["launches"]) / (k["ms"] / k["launches"] / 1e3) / 1e9 if k["launches"] else None
+    traffic, traffic_src = ncu_traffic_per_launch()
+    launches = sum(r["kernel_launches"] for r in reps)
+    kshare = {kk: round(v["ms"] / max(1e-9, sum(x["ms"] for x in tot.values())), 4) for kk, v in tot.items()}
+
+    # end to end: the public host-buffer call, inputs copied from pinned host memory every step
+    e2e = None
+    if rank == 0 or world > 1:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        V0h = pin(start_block(p.n, L, 2505))
+        hp = type(p)(n=p.n, row_ptr=pin(p.row_ptr), col_idx=pin(p.col_idx), a_val=pin(p.a_val), b_val=pin(p.b_val))
+        h2d = p.row_ptr.nbytes + p.col_idx.nbytes + p.a_val.nbytes + p.b_val.nbytes + V0h.nbytes
+        d2h = p.n * L * 8 + 2 * L * 8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_conv = 0
+        for _ in range(args.steps):
+            he = pkg.Handle(hp, pkg.default_opts())
+            th_h, X_h, r_h, nc, st, _ = he.subspace_iterate_host(f, iv["gamma"], V0h, tol=TOL, max_outer=MAX_OUTER)
+            he.close()
+            e_conv += int(nc) if st == pkg.OK else 0
+        te = time.perf_counter() - t0
+        e2e_value, _, _ = aggregate(te, float(e_conv), "cuda")
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "includes": "handle creation from host CSR, V0 upload, solve, X/theta/resid download"}
+
+    plain = None
+    if args.plain and rank == 0:
+        hp64 = pkg.Handle(p, pkg.default_opts(precision=pkg.PREC_FP64, inner_tol=1e-13, inner_maxit=1000))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        *_, nc, st, rep = hp64.subspace_iterate(f, iv["gamma"], V0, tol=TOL, max_outer=MAX_OUTER)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        plain = {"value": (int(nc) if st == pkg.OK else 0) / tp, "unit": UNIT, "seconds": tp,
+                 "status": int(st), "outer_iters": rep.outer_iters, "max_resid": rep.max_resid}
+        hp64.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "L": L, "nev": nev, "n_poles": N,
+                       "filter": "SLRF alpha=1 beta=0.01 (library designer)", "precision": "mixed",
+                       "inner_tol": opts.inner_tol, "tol": TOL, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (Krylov state 1.29 GB per solve)"},
+            "converged_per_step": conv, "outer_iters": outer,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": {"kernel": ROOFLINE_CLASS, "bound": "hbm", "achieved": achieved,
+                         "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+                         "peak_source": f"{peak_src} hbm_gbs", "traffic": traffic,
+                         "traffic_source": traffic_src,
+                         "launches": k["launches"], "avg_launch_us": (k["ms"] / k["launches"] * 1e3)
+                         if k["launches"] else None},
+            "kernel_time_share": kshare,
+            "e2e": e2e,
+        }
+        if plain is not None:
+            line["plain_fp64"] = plain
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(p, iv, max(outer) if outer else 1)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

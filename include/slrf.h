@@ -1,0 +1,241 @@
+/*
+ * slrf.h -- C ABI of the GB300 (sm_103a) shifted Laplace rational-filter
+ * eigensolver for the symmetric-definite pencil A x = lambda B x
+ * (A, B real, sparse, symmetric positive definite; eigenpairs wanted in
+ * (0, gamma]; Section 1, Eq. (1)).
+ *
+ * General conventions
+ * -------------------
+ * - Every function returns an slrf_status; nothing aborts or exits.
+ * - Dense blocks are ROW-MAJOR n x m: element (i, c) of V lives at
+ *   V[i * ldv + c], ldv >= m.  (A torch tensor of shape [n, m] is exactly
+ *   this with ldv = m.)
+ * - "device" pointers are CUDA global-memory pointers on the handle's device;
+ *   "host" pointers are ordinary CPU memory.  Each argument says which.
+ * - The caller owns every buffer it passes.  The handle owns its device copy
+ *   of the pencil and all workspace (released by slrf_destroy).
+ * - Work is enqueued on the CUDA stream given to slrf_create.  Functions that
+ *   return results to host memory synchronise that stream before returning;
+ *   functions that write device outputs return after enqueuing, and outputs
+ *   are valid once the stream has been synchronised.
+ * - A filter is given by N poles sigma_j in the upper half plane and weights
+ *   w_j; the conjugate poles and weights are implied (Section 3, conjugate
+ *   pair reduction), so the filter is
+ *       Phi(A, B) = sum_{j=1}^{N} 2 Re( w_j (A - sigma_j B)^{-1} B ).
+ *   Any pole set may be passed: the shifted-Laplace (SLRF) design of
+ *   Section 3.1 and the circle quadrature rules of Section 3.2 are
+ *   interchangeable.
+ */
+#ifndef SLRF_H
+#define SLRF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SLRF_OK = 0,
+    SLRF_EINVAL = 1,              /* invalid argument (sizes, pointers, NaN input)   */
+    SLRF_ENOMEM = 2,              /* device allocation failed                        */
+    SLRF_EBUDGET = 3,             /* workspace would exceed opts.mem_budget          */
+    SLRF_ECUDA = 4,               /* a CUDA call failed (see slrf_last_error)        */
+    SLRF_ETIMEOUT = 5,            /* a bounded device wait gave up                   */
+    SLRF_NOT_CONVERGED = 6,       /* outer iteration cap reached; outputs written    */
+    SLRF_STAGNATION = 7,          /* residuals stopped decreasing; outputs written   */
+    SLRF_BREAKDOWN = 8,           /* Krylov breakdown in every remaining column      */
+    SLRF_SUBSPACE_TOO_SMALL = 9,  /* all L Ritz values lie in (0, gamma]             */
+    SLRF_CHOLQR_FAIL = 10         /* B-Gram matrix not numerically positive definite */
+} slrf_status;
+
+typedef struct slrf_handle slrf_handle;
+
+/* Sparse pencil in CSR form on ONE shared (union) pattern; explicit zeros
+ * allowed.  Column indices sorted within each row.  A = stiffness, B = mass.
+ * Pointers are host memory if on_device == 0, device memory if 1.  The data
+ * is copied into the handle by slrf_create; the caller may free it after. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t *row_ptr;   /* n + 1 */
+    const int32_t *col_idx;   /* nnz   */
+    const double *a_val;      /* nnz   */
+    const double *b_val;      /* nnz   */
+    int32_t on_device;
+} slrf_pencil;
+
+/* Upper-half-plane poles and weights, host arrays of length n_poles
+ * (1 <= n_poles <= SLRF_MAX_POLES).  Im(sigma_j) must be nonzero. */
+#define SLRF_MAX_POLES 16
+typedef struct {
+    int32_t n_poles;
+    const double *sigma_re;
+    const double *sigma_im;
+    const double *w_re;
+    const double *w_im;
+} slrf_filter;
+
+enum { SLRF_PREC_FP64 = 0,  /* plain: FP64 Krylov to inner_tol relative to ||B v||        */
+       SLRF_PREC_MIXED = 1  /* FP32 Krylov on the FP64 residual R = B X Theta - A X      */ };
+enum { SLRF_KRYLOV_COCG = 0 };
+enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1 };
+enum { SLRF_RULE_MIDPOINT = 0, SLRF_RULE_GAUSS_LEGENDRE = 1, SLRF_RULE_GAUSS_CHEBYSHEV = 2,
+       SLRF_RULE_SLRF = 3 };
+
+typedef struct {
+    int32_t precision;      /* SLRF_PREC_*                                     (MIXED) */
+    int32_t krylov;         /* SLRF_KRYLOV_*                                    (COCG) */
+    int32_t precond;        /* SLRF_PRECOND_*                                 (JACOBI) */
+    int32_t inner_maxit;    /* Krylov iteration cap per outer step, Section 4.2.1 (1000) */
+    double inner_tol;       /* FP64: rel. to ||B v||, Section 4.2.1 (1e-13);
+                               MIXED: rel. to ||R column||                      (1e-4) */
+    double lock_tol;        /* MIXED: columns with rho_i below this skip the solve
+                               (their correction is below the outer tolerance) (1e-9) */
+    int32_t check_every;    /* Krylov iterations between host polls of the
+                               active-column count                               (8) */
+    int32_t eig_refine;     /* small eigensolver: 1 = FP32 Jacobi + FP64 refinement,
+                               0 = FP64 Jacobi                                     (1) */
+    int64_t mem_budget;     /* workspace byte cap, 0 = none                       (0) */
+    int32_t profile;        /* 1: time each kernel class with CUDA events         (0) */
+    int32_t reserved[7];
+} slrf_opts;
+
+/* Counters of one call.  Krylov iteration counts follow Table 4/5 of the
+ * paper: spmv counts one shifted product per (pole, column). */
+#define SLRF_NKERNEL_CLASSES 12
+typedef struct {
+    int32_t outer_iters;          /* filter applications                         */
+    int32_t n_wanted;             /* Ritz values in (0, gamma]                   */
+    int32_t n_conv;               /* of those, rho_i <= tol                      */
+    int32_t status_detail;
+    double max_resid;             /* max rho_i over wanted Ritz pairs            */
+    double max_resid_ax;          /* max ||A x - theta B x|| / ||A x|| (wanted)  */
+    int64_t krylov_iters;         /* Krylov iterations summed over outer steps   */
+    int64_t spmv;                 /* shifted SpMV column-products (Table 5)      */
+    double iters_per_pole[SLRF_MAX_POLES]; /* mean iterations per column (Table 4) */
+    int64_t kernel_launches;      /* kernels launched by this call               */
+    double ms_total;              /* device time of the call (events)            */
+    double ms_krylov;             /* device time inside the Krylov phases        */
+    double ms_rr;                 /* device time inside orthonormalisation + RR  */
+    /* per kernel class (profile == 1): launches, summed device ms, algorithmic
+     * bytes and flops per class; class names from slrf_kernel_class_name(). */
+    int64_t k_launches[SLRF_NKERNEL_CLASSES];
+    double k_ms[SLRF_NKERNEL_CLASSES];
+    double k_bytes[SLRF_NKERNEL_CLASSES];
+    double k_flops[SLRF_NKERNEL_CLASSES];
+} slrf_report;
+
+/* ---- library -------------------------------------------------------- */
+
+/* Human-readable name of a status. Never NULL. */
+const char *slrf_status_str(slrf_status s);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *slrf_last_error(void);
+/* Name of a kernel class index of slrf_report.k_*; NULL if out of range. */
+const char *slrf_kernel_class_name(int32_t k);
+/* Fill *o with the defaults listed in slrf_opts. */
+slrf_status slrf_opts_default(slrf_opts *o);
+
+/* ---- handle ---------------------------------------------------------- */
+
+/* Create a handle: validate the pencil (n >= 1, CSR monotone, indices in
+ * range, finite values), copy it to the current CUDA device in the layouts the
+ * kernels use, and bind `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream).  Problem statement: Section 1, Eq. (1). */
+slrf_status slrf_create(slrf_handle **h, const slrf_pencil *p, const slrf_opts *o,
+                        void *cuda_stream);
+/* Replace the handle's options (workspace is resized lazily). */
+slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o);
+/* Release the handle and all its device memory.  NULL is ignored. */
+void slrf_destroy(slrf_handle *h);
+
+/* ---- the hot path ----------------------------------------------------- */
+
+/* U = sum_j 2 Re(w_j (A - sigma_j B)^{-1} B V)  (Section 3; Algorithm 1, the
+ * solve loop and the accumulation).  V, U: device, n x m row-major.  The N*m
+ * shifted systems are solved by Jacobi-preconditioned COCG in the handle's
+ * precision to opts.inner_tol relative residual (FP64: Section 4.2.1 uses
+ * 1e-13).  In MIXED precision the solves run in FP32, so U is accurate to
+ * about kappa(A - sigma B) * max(inner_tol, 1e-7); slrf_subspace_iterate
+ * recovers FP64 accuracy by filtering the FP64 residual instead.  Returns
+ * SLRF_NOT_CONVERGED (with U written) if some system missed its tolerance. */
+slrf_status slrf_filter_apply(slrf_handle *h, const slrf_filter *f, const double *V, int64_t ldv,
+                              int32_t m, double *U, int64_t ldu, slrf_report *rep);
+
+/* Algorithm 1: rational-filter subspace iteration from the start block V0
+ * (device, n x L row-major) until every Ritz value in (0, gamma] has
+ * rho_i = ||A x_i - theta_i B x_i|| / (|theta_i| ||B x_i||) <= tol, or
+ * max_outer filter applications.  Outputs (device): theta[L] ascending,
+ * X (n x L, B-orthonormal), resid[L] = rho_i; host: *n_conv.  Each outer step
+ * is filter -> B-orthonormalisation (Cholesky-QR2) -> Rayleigh-Ritz ->
+ * residuals.  MIXED runs the filter on R = B X Theta - A X (FP64) with FP32
+ * Krylov, using U = X Phi(Theta) + sum_j 2 Re(w_j (A - sigma_j B)^{-1} R D_j),
+ * D_j = (Theta - sigma_j)^{-1}, an identity of the filter operator.
+ * Returns SLRF_OK, or NOT_CONVERGED / SUBSPACE_TOO_SMALL / CHOLQR_FAIL with
+ * the outputs of the last completed step written. */
+slrf_status slrf_subspace_iterate(slrf_handle *h, const slrf_filter *f, double gamma, int32_t L,
+                                  const double *V0, int64_t ldv, double tol, int32_t max_outer,
+                                  double *theta, double *X, int64_t ldx, double *resid,
+                                  int32_t *n_conv, slrf_report *rep);
+
+/* Same as slrf_subspace_iterate with HOST buffers for V0, theta, X, resid:
+ * copies V0 in and the results out on the handle's stream (synchronised). */
+slrf_status slrf_subspace_iterate_host(slrf_handle *h, const slrf_filter *f, double gamma,
+                                       int32_t L, const double *V0, int64_t ldv, double tol,
+                                       int32_t max_outer, double *theta, double *X, int64_t ldx,
+                                       double *resid, int32_t *n_conv, slrf_report *rep);
+
+/* ---- individual steps (each row of the hot path, for testing/measuring) -- */
+
+/* Q_j = (A - sigma_j B) P_j for every pole j and column: P, Q device complex
+ * blocks of n x (N*ldp) interleaved (re, im) in the handle's precision
+ * (float pairs if prec == SLRF_PREC_MIXED, double pairs if FP64), pole j
+ * occupying columns [j*ldp, j*ldp + m).  ldp must be even.  Also returns
+ * mu[j*m + c] = sum_i P_j[i,c] Q_j[i,c] (unconjugated, device complex, same
+ * precision) if mu != NULL.  (Eq. (2) operator; the Krylov matrix product.) */
+slrf_status slrf_shifted_spmm(slrf_handle *h, const slrf_filter *f, int32_t prec, int32_t m,
+                              int32_t ldp, const void *P, void *Q, void *mu);
+
+/* Y = A X and/or Z = B X (FP64, device, row-major n x m; either output may be
+ * NULL).  Algorithm 1 products A U, B U, A X, B X. */
+slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx, double *Y,
+                         int64_t ldy, double *Z, int64_t ldz);
+
+/* G = X^T Y (m x m row-major, device), X, Y device n x m row-major FP64.
+ * The projected matrices A_hat = U^T A U, B_hat = U^T B U of Algorithm 1. */
+slrf_status slrf_gram(slrf_handle *h, int32_t m, const double *X, int64_t ldx, const double *Y,
+                      int64_t ldy, double *G);
+
+/* Symmetric eigendecomposition of the m x m row-major device matrix S:
+ * S = Q diag(lam) Q^T, lam ascending (device), Q device row-major (columns are
+ * eigenvectors).  The small eigenproblem of Algorithm 1 after
+ * B-orthonormalisation (m <= 1024). */
+slrf_status slrf_syev(slrf_handle *h, int32_t m, const double *S, double *lam, double *Q);
+
+/* Rayleigh-Ritz of span(U) (device n x m): B-orthonormalise by Cholesky-QR2,
+ * project A, solve the small eigenproblem; returns theta (device, ascending),
+ * X = U S (device, B-orthonormal), and resid = rho_i (device).  Algorithm 1,
+ * projection, small eigenproblem and residual steps. */
+slrf_status slrf_rayleigh_ritz(slrf_handle *h, int32_t m, const double *U, int64_t ldu,
+                               double *theta, double *X, int64_t ldx, double *resid);
+
+/* ---- pole/weight sets (host) -------------------------------------------- */
+
+/* Fill N upper-half poles/weights (host arrays of length N) for a rule:
+ * SLRF_RULE_MIDPOINT / _GAUSS_LEGENDRE / _GAUSS_CHEBYSHEV on the circle with
+ * centre gamma/2 and radius gamma/2 (Section 3.2; alpha, beta ignored), or
+ * SLRF_RULE_SLRF: poles gamma x_j (1 + i alpha) with weights minimising the
+ * delta-weighted least-squares distance to the step function on [0, 10 gamma]
+ * (Section 3.1, the SLRF design).  Poles ordered by real part. */
+slrf_status slrf_design_poles(int32_t rule, int32_t N, double alpha, double beta, double gamma,
+                              double *sigma_re, double *sigma_im, double *w_re, double *w_im);
+
+/* phi[k] = Phi(x[k]) = sum_j 2 Re(w_j / (x[k] - sigma_j)) for real x (host).
+ * Eq. of Phi(lambda), Section 3. */
+slrf_status slrf_filter_eval(const slrf_filter *f, const double *x, int64_t count, double *phi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLRF_H */

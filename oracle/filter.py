@@ -59,3 +59,9 @@ def filter_apply_corrected(A, B, sigma, w, X, theta):
         Z = shifted_solve(A, B, s, R)
         U += 2.0 * np.real(wj * Z * d[None, :])
     return X * phi_theta[None, :] + U
+
+
+def shifted_product(A, B, sigma, P):
+    """Q = (A - sigma B) P for a complex block P: the operator of Eq. (2)."""
+    P = np.asarray(P, dtype=complex)
+    return (A @ P.real + 1j * (A @ P.imag)) - sigma * (B @ P.real + 1j * (B @ P.imag))

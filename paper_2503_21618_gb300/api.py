@@ -1,0 +1,315 @@
+"""Thin Python binding of libslrf.so (include/slrf.h), argument marshalling only.
+
+Every step of the eigensolver runs in the library's CUDA kernels; this module
+only converts Python objects (numpy arrays on the host, torch CUDA tensors on
+the device) into the pointers and sizes of the C ABI.  There is no fallback:
+if the library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+# ---------------------------------------------------------------- constants
+OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
+NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL = 6, 7, 8, 9, 10
+PREC_FP64, PREC_MIXED = 0, 1
+KRYLOV_COCG = 0
+PRECOND_NONE, PRECOND_JACOBI = 0, 1
+RULE_MIDPOINT, RULE_GAUSS_LEGENDRE, RULE_GAUSS_CHEBYSHEV, RULE_SLRF = 0, 1, 2, 3
+RULES = {"midpoint": 0, "gauss_legendre": 1, "gauss_chebyshev": 2, "slrf": 3}
+MAX_POLES = 16
+NKERNEL_CLASSES = 12
+
+
+class slrf_pencil(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("a_val", C.c_void_p), ("b_val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class slrf_filter(C.Structure):
+    _fields_ = [("n_poles", C.c_int32), ("sigma_re", C.POINTER(C.c_double)), ("sigma_im", C.POINTER(C.c_double)),
+                ("w_re", C.POINTER(C.c_double)), ("w_im", C.POINTER(C.c_double))]
+
+
+class slrf_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("krylov", C.c_int32), ("precond", C.c_int32),
+                ("inner_maxit", C.c_int32), ("inner_tol", C.c_double), ("lock_tol", C.c_double),
+                ("check_every", C.c_int32), ("eig_refine", C.c_int32), ("mem_budget", C.c_int64),
+                ("profile", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class slrf_report(C.Structure):
+    _fields_ = [("outer_iters", C.c_int32), ("n_wanted", C.c_int32), ("n_conv", C.c_int32),
+                ("status_detail", C.c_int32), ("max_resid", C.c_double), ("max_resid_ax", C.c_double),
+                ("krylov_iters", C.c_int64), ("spmv", C.c_int64), ("iters_per_pole", C.c_double * MAX_POLES),
+                ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_krylov", C.c_double),
+                ("ms_rr", C.c_double), ("k_launches", C.c_int64 * NKERNEL_CLASSES),
+                ("k_ms", C.c_double * NKERNEL_CLASSES), ("k_bytes", C.c_double * NKERNEL_CLASSES),
+                ("k_flops", C.c_double * NKERNEL_CLASSES)]
+
+    def as_dict(self, lib=None) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("k_") and k != "iters_per_pole"}
+        d["iters_per_pole"] = list(self.iters_per_pole)
+        names = [class_name(i, lib) for i in range(NKERNEL_CLASSES)]
+        d["kernels"] = {names[i]: {"launches": int(self.k_launches[i]), "ms": float(self.k_ms[i]),
+                                   "bytes": float(self.k_bytes[i]), "flops": float(self.k_flops[i])}
+                        for i in range(NKERNEL_CLASSES) if self.k_launches[i]}
+        return d
+
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "slrf_status_str": (C.c_char_p, [C.c_int]),
+    "slrf_last_error": (C.c_char_p, []),
+    "slrf_kernel_class_name": (C.c_char_p, [C.c_int32]),
+    "slrf_opts_default": (C.c_int, [C.POINTER(slrf_opts)]),
+    "slrf_create": (C.c_int, [C.POINTER(_P), C.POINTER(slrf_pencil), C.POINTER(slrf_opts), _P]),
+    "slrf_set_opts": (C.c_int, [_P, C.POINTER(slrf_opts)]),
+    "slrf_destroy": (None, [_P]),
+    "slrf_filter_apply": (C.c_int, [_P, C.POINTER(slrf_filter), _P, C.c_int64, C.c_int32, _P, C.c_int64,
+                                    C.POINTER(slrf_report)]),
+    "slrf_subspace_iterate": (C.c_int, [_P, C.POINTER(slrf_filter), C.c_double, C.c_int32, _P, C.c_int64,
+                                        C.c_double, C.c_int32, _P, _P, C.c_int64, _P, C.POINTER(C.c_int32),
+                                        C.POINTER(slrf_report)]),
+    "slrf_subspace_iterate_host": (C.c_int, [_P, C.POINTER(slrf_filter), C.c_double, C.c_int32, _P, C.c_int64,
+                                             C.c_double, C.c_int32, _P, _P, C.c_int64, _P, C.POINTER(C.c_int32),
+                                             C.POINTER(slrf_report)]),
+    "slrf_shifted_spmm": (C.c_int, [_P, C.POINTER(slrf_filter), C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
+    "slrf_spmm_ab": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64]),
+    "slrf_gram": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P]),
+    "slrf_syev": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
+    "slrf_rayleigh_ritz": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, _P, C.c_int64, _P]),
+    "slrf_design_poles": (C.c_int, [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
+    "slrf_filter_eval": (C.c_int, [C.POINTER(slrf_filter), C.POINTER(C.c_double), C.c_int64,
+                                   C.POINTER(C.c_double)]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libslrf.so (built in-tree by ``_build.build_library``); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libslrf.so not found at {path}: run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == _build.LIB:
+        _lib = lib
+    return lib
+
+
+def class_name(i, lib=None):
+    lib = lib or load()
+    s = lib.slrf_kernel_class_name(i)
+    return s.decode() if s else None
+
+
+class SlrfError(RuntimeError):
+    def __init__(self, status, where=""):
+        lib = load()
+        msg = lib.slrf_status_str(status).decode()
+        extra = lib.slrf_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({extra})" if extra else ""))
+        self.status = status
+
+
+def _check(status, where, allowed=(OK,)):
+    if status not in allowed:
+        raise SlrfError(status, where)
+    return status
+
+
+def default_opts(**kw) -> slrf_opts:
+    o = slrf_opts()
+    load().slrf_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Filter:
+    """N upper-half-plane poles and weights (conjugates implied)."""
+
+    def __init__(self, sigma, w):
+        sigma = np.asarray(sigma, dtype=complex).ravel()
+        w = np.asarray(w, dtype=complex).ravel()
+        if sigma.shape != w.shape or not 1 <= sigma.size <= MAX_POLES:
+            raise ValueError("need 1..16 poles with one weight each")
+        self.sigma = sigma
+        self.w = w
+        self._arr = [np.ascontiguousarray(a, dtype=np.float64) for a in (sigma.real, sigma.imag, w.real, w.imag)]
+        dp = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in self._arr]
+        self.c = slrf_filter(sigma.size, *dp)
+
+    @property
+    def n_poles(self):
+        return self.sigma.size
+
+
+def design_poles(rule: str, N: int, gamma: float, alpha: float = 1.0, beta: float = 0.01) -> Filter:
+    """Pole/weight set from the library's host designer (quadrature rule or SLRF)."""
+    out = [np.zeros(N) for _ in range(4)]
+    ptrs = [a.ctypes.data_as(C.POINTER(C.c_double)) for a in out]
+    _check(load().slrf_design_poles(RULES[rule], N, alpha, beta, gamma, *ptrs), "slrf_design_poles")
+    return Filter(out[0] + 1j * out[1], out[2] + 1j * out[3])
+
+
+def filter_eval(f: Filter, x) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    out = np.zeros_like(x)
+    _check(load().slrf_filter_eval(C.byref(f.c), x.ctypes.data_as(C.POINTER(C.c_double)), x.size,
+                                   out.ctypes.data_as(C.POINTER(C.c_double))), "slrf_filter_eval")
+    return out
+
+
+def _dptr(t, dtype_name="float64"):
+    """Device pointer of a contiguous torch CUDA tensor (row-major)."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("expected a torch CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Handle:
+    """An slrf handle: the pencil on the device plus workspace, bound to a stream."""
+
+    def __init__(self, pencil, opts: slrf_opts | None = None, stream=None):
+        self.lib = load()
+        self.n = int(pencil.n)
+        self._keep = [np.ascontiguousarray(pencil.row_ptr, dtype=np.int32),
+                      np.ascontiguousarray(pencil.col_idx, dtype=np.int32),
+                      np.ascontiguousarray(pencil.a_val, dtype=np.float64),
+                      np.ascontiguousarray(pencil.b_val, dtype=np.float64)]
+        p = slrf_pencil(self.n, int(self._keep[1].size), *[a.ctypes.data for a in self._keep], 0)
+        self.opts = opts or default_opts()
+        self._stream = stream
+        h = C.c_void_p()
+        _check(self.lib.slrf_create(C.byref(h), C.byref(p), C.byref(self.opts), _stream_ptr(stream)), "slrf_create")
+        self.h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.slrf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        _check(self.lib.slrf_set_opts(self.h, C.byref(self.opts)), "slrf_set_opts")
+
+    # ---- hot path ----------------------------------------------------------
+    def filter_apply(self, f: Filter, V, U=None, allowed=(OK, NOT_CONVERGED)):
+        import torch
+        m = V.shape[1]
+        if U is None:
+            U = torch.empty_like(V)
+        rep = slrf_report()
+        st = self.lib.slrf_filter_apply(self.h, C.byref(f.c), _dptr(V), V.stride(0), m, _dptr(U), U.stride(0),
+                                        C.byref(rep))
+        _check(st, "slrf_filter_apply", allowed)
+        return U, st, rep
+
+    def subspace_iterate(self, f: Filter, gamma: float, V0, tol=1e-8, max_outer=50, theta=None, X=None,
+                         resid=None, allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL)):
+        import torch
+        L = V0.shape[1]
+        dev = V0.device
+        theta = torch.empty(L, dtype=torch.float64, device=dev) if theta is None else theta
+        X = torch.empty_like(V0) if X is None else X
+        resid = torch.empty(L, dtype=torch.float64, device=dev) if resid is None else resid
+        nconv = C.c_int32(0)
+        rep = slrf_report()
+        st = self.lib.slrf_subspace_iterate(self.h, C.byref(f.c), gamma, L, _dptr(V0), V0.stride(0), tol,
+                                            max_outer, _dptr(theta), _dptr(X), X.stride(0), _dptr(resid),
+                                            C.byref(nconv), C.byref(rep))
+        _check(st, "slrf_subspace_iterate", allowed)
+        return theta, X, resid, nconv.value, st, rep
+
+    def subspace_iterate_host(self, f: Filter, gamma: float, V0: np.ndarray, tol=1e-8, max_outer=50,
+                              allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL)):
+        V0 = np.ascontiguousarray(V0, dtype=np.float64)
+        n, L = V0.shape
+        theta = np.zeros(L)
+        X = np.zeros((n, L))
+        resid = np.zeros(L)
+        nconv = C.c_int32(0)
+        rep = slrf_report()
+        st = self.lib.slrf_subspace_iterate_host(self.h, C.byref(f.c), gamma, L, V0.ctypes.data, L, tol, max_outer,
+                                                 theta.ctypes.data, X.ctypes.data, L, resid.ctypes.data,
+                                                 C.byref(nconv), C.byref(rep))
+        _check(st, "slrf_subspace_iterate_host", allowed)
+        return theta, X, resid, nconv.value, st, rep
+
+    # ---- individual steps -------------------------------------------------
+    def shifted_spmm(self, f: Filter, P, m, ldp, prec=PREC_MIXED, Q=None, mu=None):
+        import torch
+        Q = torch.empty_like(P) if Q is None else Q
+        _check(self.lib.slrf_shifted_spmm(self.h, C.byref(f.c), prec, m, ldp, _dptr(P), _dptr(Q),
+                                          _dptr(mu) if mu is not None else None), "slrf_shifted_spmm")
+        return Q
+
+    def spmm_ab(self, X, want_a=True, want_b=True):
+        import torch
+        m = X.shape[1]
+        Y = torch.empty_like(X) if want_a else None
+        Z = torch.empty_like(X) if want_b else None
+        _check(self.lib.slrf_spmm_ab(self.h, m, _dptr(X), X.stride(0), _dptr(Y) if Y is not None else None, m,
+                                     _dptr(Z) if Z is not None else None, m), "slrf_spmm_ab")
+        return Y, Z
+
+    def gram(self, X, Y):
+        import torch
+        m = X.shape[1]
+        G = torch.empty((m, m), dtype=torch.float64, device=X.device)
+        _check(self.lib.slrf_gram(self.h, m, _dptr(X), X.stride(0), _dptr(Y), Y.stride(0), _dptr(G)), "slrf_gram")
+        return G
+
+    def syev(self, S):
+        import torch
+        m = S.shape[0]
+        lam = torch.empty(m, dtype=torch.float64, device=S.device)
+        Q = torch.empty_like(S)
+        _check(self.lib.slrf_syev(self.h, m, _dptr(S), _dptr(lam), _dptr(Q)), "slrf_syev")
+        return lam, Q
+
+    def rayleigh_ritz(self, U, allowed=(OK,)):
+        import torch
+        m = U.shape[1]
+        theta = torch.empty(m, dtype=torch.float64, device=U.device)
+        X = torch.empty_like(U)
+        resid = torch.empty(m, dtype=torch.float64, device=U.device)
+        st = self.lib.slrf_rayleigh_ritz(self.h, m, _dptr(U), U.stride(0), _dptr(theta), _dptr(X), X.stride(0),
+                                         _dptr(resid))
+        _check(st, "slrf_rayleigh_ritz", allowed)
+        return theta, X, resid

@@ -1,0 +1,936 @@
+// C ABI of the slrf library: handle lifetime, workspace, and the drivers of
+// the hot path (Krylov solve loop, Cholesky-QR2 + Rayleigh-Ritz, Algorithm 1).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "slrf.h"
+
+using namespace slrf;
+using cd = std::complex<double>;
+
+namespace {
+thread_local std::string g_last_error;
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return SLRF_ECUDA;                                                          \
+        }                                                                               \
+    } while (0)
+#define CKS(expr)                                   \
+    do {                                            \
+        slrf_status s_ = (expr);                    \
+        if (s_ != SLRF_OK) return s_;               \
+    } while (0)
+
+const char *kKernelClassNames[SLRF_NKERNEL_CLASSES] = {
+    "shifted_spmm", "krylov_update", "krylov_direction", "krylov_reduce", "krylov_init", "spmm_real",
+    "gram", "tall_gemm", "small_dense", "residual", "filter_combine", "other"};
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Ctx
+// ---------------------------------------------------------------------------
+namespace slrf {
+void Ctx::reset_counters() {
+    for (int i = 0; i < SLRF_NKERNEL_CLASSES; ++i) {
+        launches[i] = 0;
+        bytes[i] = 0;
+        flops[i] = 0;
+    }
+    used = 0;
+}
+void Ctx::before(int kc, double b, double f) {
+    launches[kc] += 1;
+    bytes[kc] += b;
+    flops[kc] += f;
+    if (profile) {
+        if (used == pool.size()) {
+            EvPair p;
+            cudaEventCreate(&p.a);
+            cudaEventCreate(&p.b);
+            p.kc = kc;
+            pool.push_back(p);
+        }
+        pool[used].kc = kc;
+        cudaEventRecord(pool[used].a, stream);
+        cur_kc = kc;
+    }
+}
+void Ctx::after() {
+    if (profile) {
+        cudaEventRecord(pool[used].b, stream);
+        ++used;
+    }
+}
+void Ctx::harvest(double ms_out[SLRF_NKERNEL_CLASSES]) {
+    if (!profile || used == 0) return;
+    cudaStreamSynchronize(stream);
+    for (size_t i = 0; i < used; ++i) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, pool[i].a, pool[i].b) == cudaSuccess) ms_out[pool[i].kc] += t;
+    }
+    used = 0;
+}
+void Ctx::destroy() {
+    for (auto &p : pool) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    pool.clear();
+    used = 0;
+}
+}  // namespace slrf
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct slrf_handle {
+    Ctx ctx;
+    slrf_opts opts;
+    DevPencil A;
+    int device = 0;
+    size_t pencil_bytes = 0;
+    size_t ws_bytes = 0;
+    // named workspace buffers (grow only)
+    Buf kP, kQ, kR, kDinv, kU, kPart, kSig, kScal, kFlags;
+    Buf rW1, rQ1, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
+    Buf hostV, hostX;   // device staging for the host-buffer entry points
+    int32_t *h_pin = nullptr;   // pinned host words for polls
+    int32_t *d_pin = nullptr;   // device alias of h_pin
+    cudaEvent_t ev_poll = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> phase_k, phase_r;
+    size_t phase_k_used = 0, phase_r_used = 0;
+};
+
+namespace {
+
+slrf_status ensure(slrf_handle *h, Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return SLRF_OK;
+    if (h->opts.mem_budget > 0 &&
+        h->pencil_bytes + h->ws_bytes - b.bytes + bytes > (size_t)h->opts.mem_budget)
+        return SLRF_EBUDGET;
+    if (b.p) {
+        cudaStreamSynchronize(h->ctx.stream);
+        cudaFree(b.p);
+        h->ws_bytes -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        g_last_error = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+        return SLRF_ENOMEM;
+    }
+    b.bytes = bytes;
+    h->ws_bytes += bytes;
+    return SLRF_OK;
+}
+
+template <typename T> T *as(Buf &b) { return reinterpret_cast<T *>(b.p); }
+
+void phase_begin(slrf_handle *h, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, size_t &used) {
+    if (used == v.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        v.push_back({a, b});
+    }
+    cudaEventRecord(v[used].first, h->ctx.stream);
+}
+void phase_end(slrf_handle *h, std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, size_t &used) {
+    cudaEventRecord(v[used].second, h->ctx.stream);
+    ++used;
+}
+double phase_sum(std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v, size_t &used) {
+    double s = 0;
+    for (size_t i = 0; i < used; ++i) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, v[i].first, v[i].second) == cudaSuccess) s += t;
+    }
+    used = 0;
+    return s;
+}
+
+struct CallScope {
+    slrf_handle *h;
+    slrf_report *rep;
+    explicit CallScope(slrf_handle *h_, slrf_report *r) : h(h_), rep(r) {
+        h->ctx.reset_counters();
+        h->phase_k_used = h->phase_r_used = 0;
+        cudaEventRecord(h->ev_t0, h->ctx.stream);
+        if (rep) memset(rep, 0, sizeof(*rep));
+    }
+    void finish() {
+        cudaEventRecord(h->ev_t1, h->ctx.stream);
+        cudaEventSynchronize(h->ev_t1);
+        if (!rep) {
+            h->ctx.used = 0;
+            h->phase_k_used = h->phase_r_used = 0;
+            return;
+        }
+        float t = 0;
+        cudaEventElapsedTime(&t, h->ev_t0, h->ev_t1);
+        rep->ms_total = t;
+        rep->ms_krylov = phase_sum(h->phase_k, h->phase_k_used);
+        rep->ms_rr = phase_sum(h->phase_r, h->phase_r_used);
+        int64_t tot = 0;
+        for (int i = 0; i < SLRF_NKERNEL_CLASSES; ++i) {
+            rep->k_launches[i] = h->ctx.launches[i];
+            rep->k_bytes[i] = h->ctx.bytes[i];
+            rep->k_flops[i] = h->ctx.flops[i];
+            tot += h->ctx.launches[i];
+        }
+        rep->kernel_launches = tot;
+        h->ctx.harvest(rep->k_ms);
+    }
+};
+
+slrf_status check_filter(const slrf_filter *f) {
+    if (!f || f->n_poles < 1 || f->n_poles > SLRF_MAX_POLES || !f->sigma_re || !f->sigma_im || !f->w_re ||
+        !f->w_im)
+        return SLRF_EINVAL;
+    for (int j = 0; j < f->n_poles; ++j) {
+        if (!isfinite(f->sigma_re[j]) || !isfinite(f->sigma_im[j]) || !isfinite(f->w_re[j]) ||
+            !isfinite(f->w_im[j]) || f->sigma_im[j] == 0.0)
+            return SLRF_EINVAL;
+    }
+    return SLRF_OK;
+}
+
+template <typename T> PoleSet<T> make_poleset(const slrf_filter *f) {
+    PoleSet<T> ps;
+    ps.N = f->n_poles;
+    for (int j = 0; j < SLRF_MAX_POLES; ++j) {
+        ps.re[j] = j < f->n_poles ? (T)f->sigma_re[j] : (T)0;
+        ps.im[j] = j < f->n_poles ? (T)f->sigma_im[j] : (T)0;
+    }
+    return ps;
+}
+
+// ----- pencil setup kernels ------------------------------------------------
+__global__ void k_pack_ab(int64_t nnz, const double *a, const double *b, float2 *ab32, double2 *ab64) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    ab32[k] = make_float2((float)a[k], (float)b[k]);
+    ab64[k] = make_double2(a[k], b[k]);
+}
+__global__ void k_diag(int n, const int32_t *rowptr, const int32_t *col, const double *a, const double *b,
+                       double *da, double *db) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = 0, y = 0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+        if (col[k] == i) {
+            x = a[k];
+            y = b[k];
+        }
+    da[i] = x;
+    db[i] = y;
+}
+__global__ void k_symmetrize(int m, double *S) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int i = (int)(e / m), j = (int)(e % m);
+    if (j <= i) return;
+    const double v = 0.5 * (S[(int64_t)i * m + j] + S[(int64_t)j * m + i]);
+    S[(int64_t)i * m + j] = v;
+    S[(int64_t)j * m + i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Krylov solve of all (pole, column) systems; filter output accumulated in Uacc
+// ---------------------------------------------------------------------------
+struct KStats {
+    int64_t iters_max = 0;        // iterations of the longest column
+    int64_t spmv = 0;             // sum over columns of iterations
+    double iters_per_pole[SLRF_MAX_POLES] = {};
+    int n_fail = 0;               // columns that hit the cap or broke down
+    int n_breakdown = 0;
+};
+
+template <typename T>
+slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const double *rhs, int64_t ldr,
+                         const std::vector<int> &col_active, const std::vector<cd> &coef, double tol, int maxit,
+                         KrylovBuffers<T> &kb, KrylovDims &d, KStats &st) {
+    Ctx &ctx = h->ctx;
+    const int N = f->n_poles;
+    d.n = h->A.n;
+    d.N = N;
+    d.m = m;
+    d.Lp = (m + 1) / 2 * 2;
+    const int W = d.W();
+    const int64_t n = d.n;
+    kb.gy = krylov_row_groups(ctx, d, sizeof(T) == 4);
+    CKS(ensure(h, h->kP, (size_t)n * W * sizeof(cplx<T>)));
+    CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
+    CKS(ensure(h, h->kR, (size_t)n * W * sizeof(cplx<T>)));
+    CKS(ensure(h, h->kDinv, (size_t)n * N * sizeof(cplx<T>)));
+    CKS(ensure(h, h->kU, (size_t)n * d.Lp * sizeof(T)));
+    CKS(ensure(h, h->kPart, (size_t)kb.gy * W * 4 * sizeof(T)));
+    CKS(ensure(h, h->kSig, SLRF_MAX_POLES * sizeof(cplx<T>)));
+    // scalars: alpha, rho, beta, ua (cplx<T>) ; bnorm2, rnorm2 (double) ; coef (double2) ; flag, iters (int)
+    const size_t sc_bytes = (size_t)W * (4 * sizeof(cplx<T>) + 2 * sizeof(double) + sizeof(double2)) + 64;
+    CKS(ensure(h, h->kScal, sc_bytes));
+    CKS(ensure(h, h->kFlags, (size_t)W * 2 * sizeof(int32_t) + 64));
+
+    kb.P = as<cplx<T>>(h->kP);
+    kb.Q = as<cplx<T>>(h->kQ);
+    kb.R = as<cplx<T>>(h->kR);
+    kb.dinv = as<cplx<T>>(h->kDinv);
+    kb.Uacc = as<T>(h->kU);
+    kb.s.part = as<T>(h->kPart);
+    char *p = reinterpret_cast<char *>(h->kScal.p);
+    kb.s.alpha = reinterpret_cast<cplx<T> *>(p);
+    p += (size_t)W * sizeof(cplx<T>);
+    kb.s.rho = reinterpret_cast<cplx<T> *>(p);
+    p += (size_t)W * sizeof(cplx<T>);
+    kb.s.beta = reinterpret_cast<cplx<T> *>(p);
+    p += (size_t)W * sizeof(cplx<T>);
+    kb.s.ua = reinterpret_cast<cplx<T> *>(p);
+    p += (size_t)W * sizeof(cplx<T>);
+    kb.s.bnorm2 = reinterpret_cast<double *>(p);
+    p += (size_t)W * sizeof(double);
+    kb.s.rnorm2 = reinterpret_cast<double *>(p);
+    p += (size_t)W * sizeof(double);
+    kb.s.coef = reinterpret_cast<double2 *>(p);
+    kb.s.flag = as<int32_t>(h->kFlags);
+    kb.s.iters = kb.s.flag + W;
+    kb.s.active_count = nullptr;
+
+    // host-side per-column setup
+    std::vector<int32_t> flags(W, 0);
+    std::vector<double2> cf(W);
+    for (int j = 0; j < N; ++j)
+        for (int c = 0; c < d.Lp; ++c) {
+            const int col = j * d.Lp + c;
+            flags[col] = (c < m) ? (col_active[c] ? 1 : 4) : 0;
+            const cd v = (c < m) ? coef[(size_t)j * m + c] : cd(0, 0);
+            cf[col] = make_double2(v.real(), v.imag());
+        }
+    CK(cudaMemcpyAsync(kb.s.flag, flags.data(), W * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(kb.s.coef, cf.data(), W * sizeof(double2), cudaMemcpyHostToDevice, ctx.stream));
+    std::vector<cplx<T>> sg(SLRF_MAX_POLES);
+    for (int j = 0; j < N; ++j) sg[j] = mk((T)f->sigma_re[j], (T)f->sigma_im[j]);
+    CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
+    // the host vectors above are pageable; make the copies complete before they go out of scope
+    const PoleSet<T> ps = make_poleset<T>(f);
+    krylov_dinv<T>(ctx, h->A, ps, h->opts.precond, kb.dinv);
+    fill_zero(ctx, kb.Uacc, (size_t)n * d.Lp * sizeof(T));
+    krylov_init<T>(ctx, d, kb, rhs, ldr, nullptr);
+    krylov_reduce_init<T>(ctx, d, kb);
+
+    const double tol2 = tol * tol;
+    const int every = std::max(1, h->opts.check_every);
+    int it = 0;
+    for (; it < maxit;) {
+        const int chunk = std::min(every, maxit - it);
+        for (int k = 0; k < chunk; ++k) {
+            krylov_spmm<T>(ctx, d, h->A, as<cplx<T>>(h->kSig), kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
+            krylov_reduce_alpha<T>(ctx, d, kb);
+            krylov_update<T>(ctx, d, kb);
+            krylov_reduce_beta<T>(ctx, d, kb, tol2, maxit);
+            krylov_direction<T>(ctx, d, kb);
+        }
+        it += chunk;
+        krylov_count_active(ctx, W, kb.s.flag, h->d_pin);   // mapped pinned host word
+        CK(cudaEventRecord(h->ev_poll, ctx.stream));
+        CK(cudaEventSynchronize(h->ev_poll));
+        if (*(volatile int32_t *)h->h_pin == 0) break;
+    }
+    CK(cudaGetLastError());
+    // statistics
+    std::vector<int32_t> fl(W), its(W);
+    CK(cudaMemcpyAsync(fl.data(), kb.s.flag, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaMemcpyAsync(its.data(), kb.s.iters, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+    CK(cudaStreamSynchronize(ctx.stream));
+    st = KStats();
+    for (int j = 0; j < N; ++j) {
+        int64_t s = 0, cnt = 0;
+        for (int c = 0; c < m; ++c) {
+            const int col = j * d.Lp + c;
+            s += its[col];
+            st.iters_max = std::max<int64_t>(st.iters_max, its[col]);
+            if (fl[col] == 4) continue;
+            ++cnt;
+            if (fl[col] == 1 || fl[col] == 3) ++st.n_fail;
+            if (fl[col] == 2) ++st.n_breakdown;
+        }
+        st.spmv += s;
+        st.iters_per_pole[j] = cnt ? (double)s / cnt : 0.0;
+    }
+    return SLRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky-QR2 + Rayleigh-Ritz of span(U): theta (ascending), X = U M, AX, BX
+// (all n x m with leading dimension m except U/X which take ldu/ldx)
+// ---------------------------------------------------------------------------
+slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double *theta, double *X, int64_t ldx,
+                    double *AX, double *BX, int32_t *chol_status) {
+    Ctx &ctx = h->ctx;
+    const int64_t n = h->A.n;
+    const size_t m2 = (size_t)m * m;
+    const int split = gram_split(ctx, m, n);
+    CKS(ensure(h, h->rW1, (size_t)n * m * sizeof(double)));
+    CKS(ensure(h, h->rQ1, (size_t)n * m * sizeof(double)));
+    CKS(ensure(h, h->rSplit, (size_t)split * m2 * sizeof(double)));
+    CKS(ensure(h, h->rSmall, (8 * m2 + 4 * (size_t)m) * sizeof(double) + small_syev_work_bytes(m) + 64));
+    double *W1 = as<double>(h->rW1), *Q1 = as<double>(h->rQ1), *spw = as<double>(h->rSplit);
+    double *G = as<double>(h->rSmall);
+    double *R1 = G + m2, *T1 = R1 + m2, *T2 = T1 + m2, *Ah = T2 + m2, *Ah1 = Ah + m2, *Sm = Ah1 + m2,
+           *Mm = Sm + m2, *s = Mm + m2;
+    int32_t *st = reinterpret_cast<int32_t *>(s + 2 * m);
+    double *syw = reinterpret_cast<double *>(reinterpret_cast<char *>(s + 4 * m));
+
+    // pass 1: G = U^T B U, column scaling, R1 = chol, T1 = S R1^{-1}, Q1 = U T1
+    spmm_real(ctx, h->A, m, U, ldu, nullptr, 0, W1, m);
+    dgemm(ctx, 1, 0, m, m, (int)n, U, ldu, W1, m, 0.0, G, m, split, spw, KC_GRAM);
+    small_colscale(ctx, m, G, s);
+    small_chol_upper(ctx, m, G, st);
+    small_triinv_upper(ctx, m, G, T1);
+    small_scale_rows(ctx, m, s, T1);
+    dgemm(ctx, 0, 0, (int)n, m, m, U, ldu, T1, m, 0.0, Q1, m, 1, nullptr, KC_TALL_GEMM);
+    // pass 2: G2 = Q1^T B Q1, R2 = chol, T2 = R2^{-1}
+    spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
+    dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, G, m, split, spw, KC_GRAM);
+    small_chol_upper(ctx, m, G, st + 1);
+    small_triinv_upper(ctx, m, G, T2);
+    // projected A: A_hat = T2^T (Q1^T A Q1) T2
+    spmm_real(ctx, h->A, m, Q1, m, W1, m, nullptr, 0);
+    dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, Ah1, m, split, spw, KC_GRAM);
+    dgemm(ctx, 0, 0, m, m, m, Ah1, m, T2, m, 0.0, R1, m, 1, nullptr, KC_SMALL_DENSE);
+    dgemm(ctx, 1, 0, m, m, m, T2, m, R1, m, 0.0, Ah, m, 1, nullptr, KC_SMALL_DENSE);
+    ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
+    k_symmetrize<<<(unsigned)((m2 + 255) / 256), 256, 0, ctx.stream>>>(m, Ah);
+    ctx.after();
+    small_syev(ctx, m, Ah, theta, Sm, syw, h->opts.eig_refine);
+    // X = Q1 (T2 S); AX, BX by SpMM
+    dgemm(ctx, 0, 0, m, m, m, T2, m, Sm, m, 0.0, Mm, m, 1, nullptr, KC_SMALL_DENSE);
+    dgemm(ctx, 0, 0, (int)n, m, m, Q1, m, Mm, m, 0.0, X, ldx, 1, nullptr, KC_TALL_GEMM);
+    spmm_real(ctx, h->A, m, X, ldx, AX, m, BX, m);
+    if (chol_status) CK(cudaMemcpyAsync(chol_status, st, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+    return SLRF_OK;
+}
+
+slrf_status check_dense(const void *p, int64_t ld, int32_t m) { return (p && m >= 1 && ld >= m) ? SLRF_OK : SLRF_EINVAL; }
+
+// Algorithm 1 driver (device buffers)
+slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, int L, const double *V0, int64_t ldv,
+                          double tol, int max_outer, double *theta, double *X, int64_t ldx, double *resid,
+                          int32_t *n_conv, slrf_report *rep) {
+    Ctx &ctx = h->ctx;
+    const int64_t n = h->A.n;
+    const int N = f->n_poles;
+    const bool mixed = h->opts.precision == SLRF_PREC_MIXED;
+    CKS(ensure(h, h->rAX, (size_t)n * L * sizeof(double)));
+    CKS(ensure(h, h->rBX, (size_t)n * L * sizeof(double)));
+    CKS(ensure(h, h->rRes, (size_t)n * L * sizeof(double)));
+    CKS(ensure(h, h->rV, (size_t)n * L * sizeof(double)));
+    CKS(ensure(h, h->rRho, (size_t)L * sizeof(double) * 2 + (size_t)ctx.sm_count * 4 * L * 3 * sizeof(double) +
+                               (size_t)(n + 7) / 8 * 0));
+    double *AX = as<double>(h->rAX), *BX = as<double>(h->rBX), *Rm = as<double>(h->rRes), *U = as<double>(h->rV);
+    double *rho_ax = as<double>(h->rRho);
+    double *rwork = rho_ax + L;
+
+    std::vector<double> th(L), rh(L), rha(L);
+    std::vector<cd> coef((size_t)N * L);
+    std::vector<int> active(L, 1);
+    int32_t chol[2] = {0, 0};
+    KStats st;
+    int64_t spmv = 0, kit = 0;
+    double ipp[SLRF_MAX_POLES] = {};
+    int outer = 0;
+    slrf_status status = SLRF_NOT_CONVERGED;
+    int nw = 0, nc = 0;
+    double worst = 0, worst_ax = 0;
+
+    auto evaluate = [&]() -> slrf_status {
+        residual(ctx, (int)n, L, AX, BX, L, theta, mixed ? Rm : nullptr, L, resid, rho_ax, rwork);
+        CK(cudaMemcpyAsync(th.data(), theta, L * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(rh.data(), resid, L * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(rha.data(), rho_ax, L * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        CK(cudaGetLastError());
+        nw = nc = 0;
+        worst = worst_ax = 0;
+        for (int i = 0; i < L; ++i) {
+            if (th[i] > 0 && th[i] <= gamma) {
+                ++nw;
+                if (rh[i] <= tol && rha[i] <= tol) ++nc;
+                worst = std::max(worst, rh[i]);
+                worst_ax = std::max(worst_ax, rha[i]);
+            }
+        }
+        return SLRF_OK;
+    };
+
+    if (mixed) {
+        // Rayleigh-Ritz on the start block gives (X, Theta) for the corrected form
+        phase_begin(h, h->phase_r, h->phase_r_used);
+        CKS(rr_step(h, L, V0, ldv, theta, X, ldx, AX, BX, chol));
+        phase_end(h, h->phase_r, h->phase_r_used);
+        CKS(evaluate());
+        if (chol[0] || chol[1]) status = SLRF_CHOLQR_FAIL;
+    }
+    const double *V = V0;
+    int64_t ldV = ldv;
+    while (status != SLRF_CHOLQR_FAIL) {
+        if (mixed) {
+            if (nw == L) {
+                status = SLRF_SUBSPACE_TOO_SMALL;
+                break;
+            }
+            if (nw > 0 && nc == nw) {
+                status = SLRF_OK;
+                break;
+            }
+        }
+        if (outer >= max_outer) {
+            status = SLRF_NOT_CONVERGED;
+            break;
+        }
+        ++outer;
+        KrylovDims d;
+        phase_begin(h, h->phase_k, h->phase_k_used);
+        if (mixed) {
+            // U = X Phi(Theta) + sum_j 2 Re(w_j (A - sigma_j B)^{-1} R D_j)
+            std::vector<double> phi(L, 0.0);
+            for (int c = 0; c < L; ++c) {
+                active[c] = rh[c] > h->opts.lock_tol ? 1 : 0;
+                for (int j = 0; j < N; ++j) {
+                    const cd w(f->w_re[j], f->w_im[j]), sg(f->sigma_re[j], f->sigma_im[j]);
+                    const cd dj = 1.0 / (th[c] - sg);
+                    coef[(size_t)j * L + c] = w * dj;
+                    phi[c] += 2.0 * (w * dj).real();
+                }
+            }
+            KrylovBuffers<float> kb;
+            CKS(krylov_solve<float>(h, f, L, Rm, L, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d, st));
+            CKS(ensure(h, h->rTheta, (size_t)L * sizeof(double)));
+            CK(cudaMemcpyAsync(h->rTheta.p, phi.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx.stream));
+            filter_combine<float>(ctx, (int)n, L, X, ldx, as<double>(h->rTheta), kb.Uacc, d.Lp, U, L);
+            CK(cudaStreamSynchronize(ctx.stream));   // phi is pageable host memory
+        } else {
+            // F = B V ; U = sum_j 2 Re(w_j (A - sigma_j B)^{-1} F)
+            if (outer == 1) spmm_real(ctx, h->A, L, V, ldV, nullptr, 0, BX, L);
+            for (int j = 0; j < N; ++j)
+                for (int c = 0; c < L; ++c) coef[(size_t)j * L + c] = cd(f->w_re[j], f->w_im[j]);
+            KrylovBuffers<double> kb;
+            CKS(krylov_solve<double>(h, f, L, BX, L, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d,
+                                     st));
+            filter_combine<double>(ctx, (int)n, L, nullptr, 0, nullptr, kb.Uacc, d.Lp, U, L);
+        }
+        phase_end(h, h->phase_k, h->phase_k_used);
+        spmv += st.spmv;
+        kit += st.iters_max;
+        for (int j = 0; j < N; ++j) ipp[j] += st.iters_per_pole[j];
+        phase_begin(h, h->phase_r, h->phase_r_used);
+        CKS(rr_step(h, L, U, L, theta, X, ldx, AX, BX, chol));
+        phase_end(h, h->phase_r, h->phase_r_used);
+        CKS(evaluate());
+        if (chol[0] || chol[1]) {
+            status = SLRF_CHOLQR_FAIL;
+            break;
+        }
+        if (!mixed) {
+            if (nw == L) {
+                status = SLRF_SUBSPACE_TOO_SMALL;
+                break;
+            }
+            if (nw > 0 && nc == nw) {
+                status = SLRF_OK;
+                break;
+            }
+            V = X;
+            ldV = ldx;
+        }
+    }
+    if (n_conv) *n_conv = nc;
+    if (rep) {
+        rep->outer_iters = outer;
+        rep->n_wanted = nw;
+        rep->n_conv = nc;
+        rep->max_resid = worst;
+        rep->max_resid_ax = worst_ax;
+        rep->krylov_iters = kit;
+        rep->spmv = spmv;
+        for (int j = 0; j < N; ++j) rep->iters_per_pole[j] = outer ? ipp[j] / outer : 0.0;
+    }
+    return status;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *slrf_status_str(slrf_status s) {
+    switch (s) {
+        case SLRF_OK: return "SLRF_OK";
+        case SLRF_EINVAL: return "SLRF_EINVAL";
+        case SLRF_ENOMEM: return "SLRF_ENOMEM";
+        case SLRF_EBUDGET: return "SLRF_EBUDGET";
+        case SLRF_ECUDA: return "SLRF_ECUDA";
+        case SLRF_ETIMEOUT: return "SLRF_ETIMEOUT";
+        case SLRF_NOT_CONVERGED: return "SLRF_NOT_CONVERGED";
+        case SLRF_STAGNATION: return "SLRF_STAGNATION";
+        case SLRF_BREAKDOWN: return "SLRF_BREAKDOWN";
+        case SLRF_SUBSPACE_TOO_SMALL: return "SLRF_SUBSPACE_TOO_SMALL";
+        case SLRF_CHOLQR_FAIL: return "SLRF_CHOLQR_FAIL";
+    }
+    return "SLRF_UNKNOWN";
+}
+
+const char *slrf_last_error(void) { return g_last_error.c_str(); }
+
+const char *slrf_kernel_class_name(int32_t k) {
+    return (k >= 0 && k < SLRF_NKERNEL_CLASSES) ? kKernelClassNames[k] : nullptr;
+}
+
+slrf_status slrf_opts_default(slrf_opts *o) {
+    if (!o) return SLRF_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->precision = SLRF_PREC_MIXED;
+    o->krylov = SLRF_KRYLOV_COCG;
+    o->precond = SLRF_PRECOND_JACOBI;
+    o->inner_maxit = 1000;
+    o->inner_tol = 1e-4;
+    o->lock_tol = 1e-9;
+    o->check_every = 8;
+    o->eig_refine = 1;
+    o->mem_budget = 0;
+    o->profile = 0;
+    return SLRF_OK;
+}
+
+static slrf_status check_opts(const slrf_opts *o) {
+    if (!o) return SLRF_EINVAL;
+    if (o->precision != SLRF_PREC_FP64 && o->precision != SLRF_PREC_MIXED) return SLRF_EINVAL;
+    if (o->krylov != SLRF_KRYLOV_COCG) return SLRF_EINVAL;
+    if (o->precond != SLRF_PRECOND_NONE && o->precond != SLRF_PRECOND_JACOBI) return SLRF_EINVAL;
+    if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
+    return SLRF_OK;
+}
+
+slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
+    if (!h) return SLRF_EINVAL;
+    CKS(check_opts(o));
+    h->opts = *o;
+    h->ctx.profile = o->profile != 0;
+    return SLRF_OK;
+}
+
+void slrf_destroy(slrf_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->ctx.stream);
+    Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
+                   &h->rW1, &h->rQ1, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
+                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    void *pen[] = {h->A.rowptr, h->A.col, h->A.a, h->A.b, h->A.ab32, h->A.ab64, h->A.diag_a, h->A.diag_b};
+    for (void *p : pen)
+        if (p) cudaFree(p);
+    if (h->h_pin) cudaFreeHost(h->h_pin);
+    if (h->ev_poll) cudaEventDestroy(h->ev_poll);
+    if (h->ev_t0) cudaEventDestroy(h->ev_t0);
+    if (h->ev_t1) cudaEventDestroy(h->ev_t1);
+    for (auto &e : h->phase_k) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    for (auto &e : h->phase_r) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    h->ctx.destroy();
+    delete h;
+}
+
+slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts *o, void *cuda_stream) {
+    if (!out) return SLRF_EINVAL;
+    *out = nullptr;
+    if (!p || p->n < 1 || p->n > (1LL << 31) - 2 || p->nnz < p->n || p->nnz > (1LL << 31) - 1 || !p->row_ptr ||
+        !p->col_idx || !p->a_val || !p->b_val)
+        return SLRF_EINVAL;
+    slrf_opts def;
+    slrf_opts_default(&def);
+    if (!o) o = &def;
+    CKS(check_opts(o));
+    const int64_t n = p->n, nnz = p->nnz;
+    // host copies for validation
+    std::vector<int32_t> rp(n + 1), ci(nnz);
+    std::vector<double> av(nnz), bv(nnz);
+    const cudaMemcpyKind kind = p->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    CK(cudaMemcpy(rp.data(), p->row_ptr, (n + 1) * sizeof(int32_t), kind));
+    CK(cudaMemcpy(ci.data(), p->col_idx, nnz * sizeof(int32_t), kind));
+    CK(cudaMemcpy(av.data(), p->a_val, nnz * sizeof(double), kind));
+    CK(cudaMemcpy(bv.data(), p->b_val, nnz * sizeof(double), kind));
+    if (rp[0] != 0 || rp[n] != nnz) return SLRF_EINVAL;
+    for (int64_t i = 0; i < n; ++i) {
+        if (rp[i + 1] < rp[i]) return SLRF_EINVAL;
+        bool diag = false;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            if (ci[k] < 0 || ci[k] >= n) return SLRF_EINVAL;
+            if (k > rp[i] && ci[k] <= ci[k - 1]) return SLRF_EINVAL;
+            if (!isfinite(av[k]) || !isfinite(bv[k])) return SLRF_EINVAL;
+            if (ci[k] == i) diag = av[k] > 0 && bv[k] > 0;
+        }
+        if (!diag) return SLRF_EINVAL;   // SPD pencils have a positive diagonal
+    }
+    slrf_handle *h = new slrf_handle();
+    h->opts = *o;
+    h->ctx.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    h->ctx.profile = o->profile != 0;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->ctx.sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    h->A.n = (int)n;
+    h->A.nnz = nnz;
+    const size_t need = (n + 1) * 4 + nnz * (4 + 8 + 8 + 8 + 16) + n * 16;
+    if (o->mem_budget > 0 && need > (size_t)o->mem_budget) {
+        delete h;
+        return SLRF_EBUDGET;
+    }
+    auto alloc = [&](void **ptr, size_t bytes) -> bool {
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        h->pencil_bytes += bytes;
+        return true;
+    };
+    bool ok = alloc((void **)&h->A.rowptr, (n + 1) * 4) && alloc((void **)&h->A.col, nnz * 4) &&
+              alloc((void **)&h->A.a, nnz * 8) && alloc((void **)&h->A.b, nnz * 8) &&
+              alloc((void **)&h->A.ab32, nnz * 8) && alloc((void **)&h->A.ab64, nnz * 16) &&
+              alloc((void **)&h->A.diag_a, n * 8) && alloc((void **)&h->A.diag_b, n * 8) &&
+              cudaHostAlloc((void **)&h->h_pin, 64, cudaHostAllocMapped) == cudaSuccess;
+    if (!ok) {
+        g_last_error = "device allocation of the pencil failed";
+        slrf_destroy(h);
+        return SLRF_ENOMEM;
+    }
+    if (cudaHostGetDevicePointer((void **)&h->d_pin, h->h_pin, 0) != cudaSuccess) {
+        g_last_error = "mapped host memory is not available";
+        slrf_destroy(h);
+        return SLRF_ECUDA;
+    }
+    cudaEventCreate(&h->ev_poll);
+    cudaEventCreate(&h->ev_t0);
+    cudaEventCreate(&h->ev_t1);
+    cudaStream_t s = h->ctx.stream;
+    cudaMemcpyAsync(h->A.rowptr, rp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->A.col, ci.data(), nnz * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->A.a, av.data(), nnz * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->A.b, bv.data(), nnz * 8, cudaMemcpyHostToDevice, s);
+    k_pack_ab<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(nnz, h->A.a, h->A.b, h->A.ab32, h->A.ab64);
+    k_diag<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int)n, h->A.rowptr, h->A.col, h->A.a, h->A.b, h->A.diag_a,
+                                                         h->A.diag_b);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        g_last_error = std::string("pencil upload: ") + cudaGetErrorString(e);
+        slrf_destroy(h);
+        return SLRF_ECUDA;
+    }
+    *out = h;
+    return SLRF_OK;
+}
+
+slrf_status slrf_filter_apply(slrf_handle *h, const slrf_filter *f, const double *V, int64_t ldv, int32_t m,
+                              double *U, int64_t ldu, slrf_report *rep) {
+    if (!h) return SLRF_EINVAL;
+    CKS(check_filter(f));
+    CKS(check_dense(V, ldv, m));
+    CKS(check_dense(U, ldu, m));
+    CallScope scope(h, rep);
+    Ctx &ctx = h->ctx;
+    const int64_t n = h->A.n;
+    const int N = f->n_poles;
+    CKS(ensure(h, h->rBX, (size_t)n * m * sizeof(double)));
+    double *F = as<double>(h->rBX);
+    spmm_real(ctx, h->A, m, V, ldv, nullptr, 0, F, m);
+    std::vector<int> active(m, 1);
+    std::vector<cd> coef((size_t)N * m);
+    for (int j = 0; j < N; ++j)
+        for (int c = 0; c < m; ++c) coef[(size_t)j * m + c] = cd(f->w_re[j], f->w_im[j]);
+    KrylovDims d;
+    KStats st;
+    slrf_status s;
+    phase_begin(h, h->phase_k, h->phase_k_used);
+    if (h->opts.precision == SLRF_PREC_MIXED) {
+        KrylovBuffers<float> kb;
+        s = krylov_solve<float>(h, f, m, F, m, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d, st);
+        if (s == SLRF_OK) filter_combine<float>(ctx, (int)n, m, nullptr, 0, nullptr, kb.Uacc, d.Lp, U, ldu);
+    } else {
+        KrylovBuffers<double> kb;
+        s = krylov_solve<double>(h, f, m, F, m, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d, st);
+        if (s == SLRF_OK) filter_combine<double>(ctx, (int)n, m, nullptr, 0, nullptr, kb.Uacc, d.Lp, U, ldu);
+    }
+    phase_end(h, h->phase_k, h->phase_k_used);
+    if (s != SLRF_OK) return s;
+    if (rep) {
+        rep->outer_iters = 1;
+        rep->krylov_iters = st.iters_max;
+        rep->spmv = st.spmv;
+        for (int j = 0; j < N; ++j) rep->iters_per_pole[j] = st.iters_per_pole[j];
+        rep->status_detail = st.n_fail + st.n_breakdown;
+    }
+    scope.finish();
+    CK(cudaGetLastError());
+    return (st.n_fail + st.n_breakdown) ? SLRF_NOT_CONVERGED : SLRF_OK;
+}
+
+slrf_status slrf_subspace_iterate(slrf_handle *h, const slrf_filter *f, double gamma, int32_t L, const double *V0,
+                                  int64_t ldv, double tol, int32_t max_outer, double *theta, double *X, int64_t ldx,
+                                  double *resid, int32_t *n_conv, slrf_report *rep) {
+    if (!h || !(gamma > 0) || !(tol > 0) || max_outer < 1 || !theta || !resid) return SLRF_EINVAL;
+    CKS(check_filter(f));
+    CKS(check_dense(V0, ldv, L));
+    CKS(check_dense(X, ldx, L));
+    if (L > h->A.n || L > 1024) return SLRF_EINVAL;
+    CallScope scope(h, rep);
+    const slrf_status s = subspace_core(h, f, gamma, L, V0, ldv, tol, max_outer, theta, X, ldx, resid, n_conv, rep);
+    scope.finish();
+    if (s == SLRF_ECUDA || s == SLRF_ENOMEM || s == SLRF_EBUDGET) return s;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_last_error = cudaGetErrorString(e);
+        return SLRF_ECUDA;
+    }
+    return s;
+}
+
+slrf_status slrf_subspace_iterate_host(slrf_handle *h, const slrf_filter *f, double gamma, int32_t L,
+                                       const double *V0, int64_t ldv, double tol, int32_t max_outer, double *theta,
+                                       double *X, int64_t ldx, double *resid, int32_t *n_conv, slrf_report *rep) {
+    if (!h || !V0 || !X || !theta || !resid || L < 1 || ldv < L || ldx < L) return SLRF_EINVAL;
+    const int64_t n = h->A.n;
+    CKS(ensure(h, h->hostV, (size_t)n * L * sizeof(double)));
+    CKS(ensure(h, h->hostX, (size_t)n * L * sizeof(double) + 2 * (size_t)L * sizeof(double)));
+    double *dV = as<double>(h->hostV), *dX = as<double>(h->hostX);
+    double *dth = dX + (size_t)n * L, *dres = dth + L;
+    cudaStream_t s = h->ctx.stream;
+    CK(cudaMemcpy2DAsync(dV, (size_t)L * 8, V0, (size_t)ldv * 8, (size_t)L * 8, (size_t)n, cudaMemcpyHostToDevice, s));
+    const slrf_status st = slrf_subspace_iterate(h, f, gamma, L, dV, L, tol, max_outer, dth, dX, L, dres, n_conv, rep);
+    if (st == SLRF_EINVAL || st == SLRF_ECUDA || st == SLRF_ENOMEM || st == SLRF_EBUDGET) return st;
+    CK(cudaMemcpy2DAsync(X, (size_t)ldx * 8, dX, (size_t)L * 8, (size_t)L * 8, (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(theta, dth, L * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(resid, dres, L * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
+slrf_status slrf_shifted_spmm(slrf_handle *h, const slrf_filter *f, int32_t prec, int32_t m, int32_t ldp,
+                              const void *P, void *Q, void *mu) {
+    if (!h || !P || !Q || m < 1 || ldp < m || (ldp & 1)) return SLRF_EINVAL;
+    CKS(check_filter(f));
+    Ctx &ctx = h->ctx;
+    KrylovDims d;
+    d.n = h->A.n;
+    d.N = f->n_poles;
+    d.Lp = ldp;
+    d.m = m;
+    const int W = d.W();
+    const int gy = krylov_row_groups(ctx, d, prec == SLRF_PREC_MIXED);
+    const size_t esz = prec == SLRF_PREC_MIXED ? sizeof(float) : sizeof(double);
+    CKS(ensure(h, h->kPart, (size_t)gy * W * 4 * esz));
+    CKS(ensure(h, h->kSig, SLRF_MAX_POLES * 2 * esz));
+    CKS(ensure(h, h->kFlags, (size_t)W * 2 * sizeof(int32_t) + 64));
+    std::vector<int32_t> flags(W);
+    for (int col = 0; col < W; ++col) flags[col] = (col % ldp) < m ? 1 : 0;
+    CK(cudaMemcpyAsync(h->kFlags.p, flags.data(), W * 4, cudaMemcpyHostToDevice, ctx.stream));
+    h->ctx.reset_counters();
+    if (prec == SLRF_PREC_MIXED) {
+        std::vector<float2> sg(d.N);
+        for (int j = 0; j < d.N; ++j) sg[j] = make_float2((float)f->sigma_re[j], (float)f->sigma_im[j]);
+        CK(cudaMemcpyAsync(h->kSig.p, sg.data(), d.N * sizeof(float2), cudaMemcpyHostToDevice, ctx.stream));
+        krylov_spmm<float>(ctx, d, h->A, as<float2>(h->kSig), (const float2 *)P, (float2 *)Q, as<int32_t>(h->kFlags),
+                           as<float>(h->kPart), gy);
+        if (mu) krylov_reduce_mu<float>(ctx, d, as<float>(h->kPart), gy, (float2 *)mu);
+    } else if (prec == SLRF_PREC_FP64) {
+        std::vector<double2> sg(d.N);
+        for (int j = 0; j < d.N; ++j) sg[j] = make_double2(f->sigma_re[j], f->sigma_im[j]);
+        CK(cudaMemcpyAsync(h->kSig.p, sg.data(), d.N * sizeof(double2), cudaMemcpyHostToDevice, ctx.stream));
+        krylov_spmm<double>(ctx, d, h->A, as<double2>(h->kSig), (const double2 *)P, (double2 *)Q,
+                            as<int32_t>(h->kFlags), as<double>(h->kPart), gy);
+        if (mu) krylov_reduce_mu<double>(ctx, d, as<double>(h->kPart), gy, (double2 *)mu);
+    } else {
+        return SLRF_EINVAL;
+    }
+    CK(cudaStreamSynchronize(ctx.stream));
+    CK(cudaGetLastError());
+    return SLRF_OK;
+}
+
+slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx, double *Y, int64_t ldy, double *Z,
+                         int64_t ldz) {
+    if (!h || !X || m < 1 || ldx < m || (Y && ldy < m) || (Z && ldz < m) || (!Y && !Z)) return SLRF_EINVAL;
+    spmm_real(h->ctx, h->A, m, X, ldx, Y, ldy, Z, ldz);
+    CK(cudaGetLastError());
+    return SLRF_OK;
+}
+
+slrf_status slrf_gram(slrf_handle *h, int32_t m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                      double *G) {
+    if (!h || !X || !Y || !G || m < 1 || ldx < m || ldy < m) return SLRF_EINVAL;
+    const int64_t n = h->A.n;
+    const int split = gram_split(h->ctx, m, n);
+    CKS(ensure(h, h->rSplit, (size_t)split * m * m * sizeof(double)));
+    dgemm(h->ctx, 1, 0, m, m, (int)n, X, ldx, Y, ldy, 0.0, G, m, split, as<double>(h->rSplit), KC_GRAM);
+    CK(cudaGetLastError());
+    return SLRF_OK;
+}
+
+slrf_status slrf_syev(slrf_handle *h, int32_t m, const double *S, double *lam, double *Q) {
+    if (!h || !S || !lam || !Q || m < 1 || m > 1024) return SLRF_EINVAL;
+    CKS(ensure(h, h->rSmall, small_syev_work_bytes(m) + (size_t)m * m * sizeof(double)));
+    double *Sc = as<double>(h->rSmall);
+    double *w = Sc + (size_t)m * m;
+    CK(cudaMemcpyAsync(Sc, S, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, h->ctx.stream));
+    h->ctx.before(KC_SMALL_DENSE, 16.0 * m * m, 0);
+    k_symmetrize<<<(unsigned)(((size_t)m * m + 255) / 256), 256, 0, h->ctx.stream>>>(m, Sc);
+    h->ctx.after();
+    small_syev(h->ctx, m, Sc, lam, Q, w, h->opts.eig_refine);
+    CK(cudaGetLastError());
+    return SLRF_OK;
+}
+
+slrf_status slrf_rayleigh_ritz(slrf_handle *h, int32_t m, const double *U, int64_t ldu, double *theta, double *X,
+                               int64_t ldx, double *resid) {
+    if (!h || !theta || !resid || m > 1024) return SLRF_EINVAL;
+    CKS(check_dense(U, ldu, m));
+    CKS(check_dense(X, ldx, m));
+    const int64_t n = h->A.n;
+    if (m > n) return SLRF_EINVAL;
+    CKS(ensure(h, h->rAX, (size_t)n * m * sizeof(double)));
+    CKS(ensure(h, h->rBX, (size_t)n * m * sizeof(double)));
+    CKS(ensure(h, h->rRho, (size_t)m * sizeof(double) + (size_t)h->ctx.sm_count * 4 * m * 3 * sizeof(double)));
+    int32_t chol[2] = {0, 0};
+    CKS(rr_step(h, m, U, ldu, theta, X, ldx, as<double>(h->rAX), as<double>(h->rBX), chol));
+    double *rho_ax = as<double>(h->rRho);
+    residual(h->ctx, (int)n, m, as<double>(h->rAX), as<double>(h->rBX), m, theta, nullptr, 0, resid, rho_ax,
+             rho_ax + m);
+    CK(cudaStreamSynchronize(h->ctx.stream));
+    CK(cudaGetLastError());
+    return (chol[0] || chol[1]) ? SLRF_CHOLQR_FAIL : SLRF_OK;
+}
+
+}  // extern "C"

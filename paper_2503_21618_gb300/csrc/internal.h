@@ -1,0 +1,148 @@
+// Internal interfaces between the slrf translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace slrf {
+
+// Launch bookkeeping: every kernel launch of the library goes through a Ctx,
+// which counts launches per class and, when profiling, brackets each launch
+// with a pair of CUDA events on the launch stream.
+struct Ctx {
+    cudaStream_t stream = nullptr;
+    int sm_count = 152;
+    bool profile = false;
+    int64_t launches[SLRF_NKERNEL_CLASSES] = {};
+    double bytes[SLRF_NKERNEL_CLASSES] = {};
+    double flops[SLRF_NKERNEL_CLASSES] = {};
+    struct EvPair { cudaEvent_t a, b; int kc; };
+    std::vector<EvPair> pool;     // all events ever created (reused)
+    size_t used = 0;              // pairs recorded since reset
+    int cur_kc = -1;
+
+    void reset_counters();
+    // Call around each launch.
+    void before(int kc, double bytes_, double flops_);
+    void after();
+    // Sum event times per class (synchronises the stream).
+    void harvest(double ms_out[SLRF_NKERNEL_CLASSES]);
+    void destroy();
+};
+
+// Pole data passed by value to kernels.
+template <typename T> struct PoleSet {
+    int N;
+    T re[SLRF_MAX_POLES];
+    T im[SLRF_MAX_POLES];
+};
+
+// Device pencil.
+struct DevPencil {
+    int n = 0;
+    int64_t nnz = 0;
+    int32_t *rowptr = nullptr, *col = nullptr;
+    double *a = nullptr, *b = nullptr;      // FP64 values
+    float2 *ab32 = nullptr;                 // interleaved (a, b), FP32
+    double2 *ab64 = nullptr;                // interleaved (a, b), FP64
+    double *diag_a = nullptr, *diag_b = nullptr;
+};
+
+// ---------------------------------------------------------------- krylov.cu
+// Column-block layout of the Krylov state: complex n x W, W = N * Lp, row
+// stride W, pole j in columns [j*Lp, j*Lp + Lp), Lp even.
+struct KrylovDims {
+    int n, N, Lp, m;       // m <= Lp live columns per pole
+    int W() const { return N * Lp; }
+};
+
+// Per-column scalars of the Krylov solve (device arrays of length W).
+template <typename T> struct KrylovScalars {
+    cplx<T> *alpha, *rho, *beta, *ua;   // ua = 2 * coef_jc * alpha_jc
+    double *bnorm2, *rnorm2;
+    int32_t *flag;                       // 1 active, 0 converged, 2 breakdown, 3 maxit, 4 skipped
+    int32_t *iters;
+    cplx<double> *coef;                  // coef_jc = w_j * d_jc (d = 1 in the plain filter)
+    T *part;                             // [gy][W][4] partial sums
+    int32_t *active_count;               // 1 int
+};
+
+template <typename T>
+struct KrylovBuffers {
+    cplx<T> *P, *Q, *R;                  // n x W each
+    cplx<T> *dinv;                       // n x N Jacobi inverse diagonal
+    T *Uacc;                             // n x Lp accumulation of the filter output
+    KrylovScalars<T> s;
+    int gy;                              // row groups of the kernels
+};
+
+int krylov_row_groups(const Ctx &ctx, const KrylovDims &d, int prec_fp32);
+
+template <typename T>
+void krylov_dinv(Ctx &ctx, const DevPencil &A, const PoleSet<T> &ps, int precond, cplx<T> *dinv);
+
+// r = p = z = M^{-1} b from a real block shared by all poles (rhs: n x m, ld)
+// or, if rhs_c != nullptr, a complex block per pole (layout of the state).
+template <typename T>
+void krylov_init(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, const double *rhs, int64_t ldr,
+                 const cplx<double> *rhs_c);
+template <typename T>
+void krylov_reduce_init(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb);
+template <typename T>
+void krylov_spmm(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const cplx<T> *sig_dev,
+                 const cplx<T> *P, cplx<T> *Q, const int32_t *flag, T *part, int gy);
+template <typename T>
+void krylov_reduce_alpha(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb);
+template <typename T>
+void krylov_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb);
+template <typename T>
+void krylov_reduce_beta(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, double tol2, int maxit);
+template <typename T>
+void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb);
+void krylov_count_active(Ctx &ctx, int W, const int32_t *flag, int32_t *count);
+// mu[c] = sum over row groups of part slot 0/1 -> complex (for the SpMM step API)
+template <typename T>
+void krylov_reduce_mu(Ctx &ctx, const KrylovDims &d, const T *part, int gy, cplx<T> *mu);
+
+// ---------------------------------------------------------------- dense.cu
+// Y = A X and/or Z = B X, FP64, row-major n x m.
+void spmm_real(Ctx &ctx, const DevPencil &A, int m, const double *X, int64_t ldx, double *Y,
+               int64_t ldy, double *Z, int64_t ldz);
+// C = op(A) op(B) (+ beta C), row-major; opA/opB: 0 = N, 1 = T.
+// Dimensions: op(A) is M x K, op(B) is K x N.  split > 1 splits K into
+// `split` slices whose partial products go to work[split][M][N] and are then
+// summed in a fixed order.
+void dgemm(Ctx &ctx, int opA, int opB, int M, int N, int K, const double *A, int64_t lda,
+           const double *B, int64_t ldb, double beta, double *C, int64_t ldc, int split = 1,
+           double *work = nullptr, int kc = KC_TALL_GEMM);
+// Choose a split for a Gram of n rows.
+int gram_split(const Ctx &ctx, int m, int64_t n);
+// Residual of the Ritz pairs: Rout = BX diag(theta) - AX (if Rout != nullptr),
+// rho[c] = ||R_c|| / (|theta_c| ||BX_c||), rho_ax[c] = ||R_c|| / ||AX_c||.
+void residual(Ctx &ctx, int n, int m, const double *AX, const double *BX, int64_t ld,
+              const double *theta, double *Rout, int64_t ldr, double *rho, double *rho_ax,
+              double *work);
+// U = X diag(phi) + Ucorr(T, ld Lp)  (FP64 out)
+template <typename T>
+void filter_combine(Ctx &ctx, int n, int m, const double *X, int64_t ldx, const double *phi,
+                    const T *Ucorr, int ldc, double *U, int64_t ldu);
+void fill_zero(Ctx &ctx, void *p, size_t bytes);
+// Copy a strided row-major block (device).
+void copy_block(Ctx &ctx, int n, int m, const double *src, int64_t lds, double *dst, int64_t ldd);
+
+// ---------------------------------------------------------------- small.cu
+// All m x m matrices row-major, device.  status: device int, set nonzero on
+// failure (Cholesky pivot <= 0 or non-finite).
+void small_colscale(Ctx &ctx, int m, double *G, double *s);        // s = 1/sqrt(diag G); G = S G S
+void small_chol_upper(Ctx &ctx, int m, double *G, int32_t *status); // G = R^T R, R upper, in place
+void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv);
+void small_scale_rows(Ctx &ctx, int m, const double *s, double *T);  // T = diag(s) T
+// Symmetric eigensolver: lam ascending, Q eigenvectors (columns).  mode 1:
+// FP32 Jacobi followed by FP64 refinement; 0: FP64 Jacobi.
+void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode);
+size_t small_syev_work_bytes(int m);
+
+}  // namespace slrf

@@ -1,0 +1,625 @@
+// Block COCG over all (pole, column) shifted systems (A - sigma_j B) y = f.
+//
+// Section 1, Eq. (2): each outer step of Algorithm 1 needs N shifted solves
+// per column.  The paper solves them by preconditioned BiCGStab (Section
+// 4.2.1); A - sigma B is complex symmetric, so this library uses the
+// conjugate-orthogonal CG (unconjugated bilinear form x^T y) with a Jacobi
+// preconditioner M_j = diag(A - sigma_j B), which keeps the iteration a short
+// recurrence of SpMM + vector updates + per-column dot products.
+//
+// State layout ("column block"): complex n x W, W = N * Lp, row-major with row
+// stride W; pole j owns columns [j*Lp, j*Lp + Lp).  One row of the block is
+// W complex numbers, so a warp reading a row is fully coalesced, and every
+// matrix entry (col, a, b) is loaded once per row for all poles and columns.
+//
+// One iteration = 5 launches:
+//   spmm      Q = (A - sigma_j B) P        + partial mu = P^T Q per column
+//   alpha     alpha = rho / mu, ua = 2 coef alpha
+//   update    R -= alpha Q, U += Re(ua P)  + partial rho' = R^T M^{-1} R, |R|^2
+//   beta      beta = rho'/rho, convergence mask
+//   direction P = M^{-1} R + beta P
+// The filter output sum_j 2 Re(coef_jc Y_jc) is accumulated directly in U
+// (coef_jc = w_j in the plain filter, w_j/(theta_c - sigma_j) in the
+// residual-corrected one), so the per-pole solutions are never stored.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace slrf {
+
+template <typename T> struct VecN;
+template <> struct VecN<float> { static constexpr int VC = 2; };   // one float4 = 2 complex
+template <> struct VecN<double> { static constexpr int VC = 1; };  // one double2 = 1 complex
+
+template <typename T> struct ABT;
+template <> struct ABT<float> { using type = float2; };
+template <> struct ABT<double> { using type = double2; };
+
+template <typename T, int VC> struct CV { cplx<T> v[VC]; };
+
+__device__ __forceinline__ CV<float, 2> ldcv(const float2 *p) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    CV<float, 2> r;
+    r.v[0] = make_float2(t.x, t.y);
+    r.v[1] = make_float2(t.z, t.w);
+    return r;
+}
+__device__ __forceinline__ void stcv(float2 *p, const CV<float, 2> &a) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a.v[0].x, a.v[0].y, a.v[1].x, a.v[1].y);
+}
+__device__ __forceinline__ CV<double, 1> ldcv(const double2 *p) {
+    CV<double, 1> r;
+    r.v[0] = *p;
+    return r;
+}
+__device__ __forceinline__ void stcv(double2 *p, const CV<double, 1> &a) { *p = a.v[0]; }
+
+constexpr int TY = 8;   // rows processed concurrently by a block (warps)
+
+// ---------------------------------------------------------------------------
+// Jacobi inverse diagonal dinv[i][j] = 1 / (a_ii - sigma_j b_ii)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_dinv(int n, int N, const double *__restrict__ da, const double *__restrict__ db,
+                       PoleSet<T> ps, int precond, cplx<T> *__restrict__ dinv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * N) return;
+    const int row = (int)(i / N), j = (int)(i % N);
+    cplx<T> r;
+    if (precond == SLRF_PRECOND_JACOBI) {
+        // 1/(x + i y) = (x - i y)/(x^2 + y^2), evaluated in FP64
+        const double x = da[row] - (double)ps.re[j] * db[row];
+        const double y = -(double)ps.im[j] * db[row];
+        const double den = x * x + y * y;
+        r.x = (T)(x / den);
+        r.y = (T)(-y / den);
+    } else {
+        r.x = (T)1;
+        r.y = (T)0;
+    }
+    dinv[i] = r;
+}
+
+// ---------------------------------------------------------------------------
+// init: r = b, p = z = M^{-1} r, partial rho = r^T z, |b|^2
+// ---------------------------------------------------------------------------
+template <typename T, int VC>
+__global__ void __launch_bounds__(32 * TY)
+k_init(int n, int W, int Lp, int N, int m, const double *__restrict__ rhs, int64_t ldr,
+       const double2 *__restrict__ rhs_c, const cplx<T> *__restrict__ dinv, cplx<T> *__restrict__ R,
+       cplx<T> *__restrict__ P, const int32_t *__restrict__ flag, T *__restrict__ part) {
+    using C = cplx<T>;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    const int c0 = cg * VC;
+    int j = 0, cl = 0;
+    bool act[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) act[v] = false;
+    if (cg < ng) {
+        j = c0 / Lp;
+        cl = c0 - j * Lp;
+#pragma unroll
+        for (int v = 0; v < VC; ++v) act[v] = flag[c0 + v] == 1;
+    }
+    T acc[VC][3];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) acc[v][0] = acc[v][1] = acc[v][2] = (T)0;
+    if (cg < ng) {
+        for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
+            const C dv = dinv[(int64_t)row * N + j];
+            CV<T, VC> r, p;
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                C b = mk((T)0, (T)0);
+                if (act[v]) {
+                    if (rhs_c) {
+                        const double2 t = rhs_c[(int64_t)row * W + c0 + v];
+                        b = mk((T)t.x, (T)t.y);
+                    } else if (cl + v < m) {
+                        b = mk((T)rhs[(int64_t)row * ldr + cl + v], (T)0);
+                    }
+                }
+                r.v[v] = b;
+                const C z = cmul(dv, b);
+                p.v[v] = z;
+                const C rz = cmul(b, z);
+                acc[v][0] += rz.x;
+                acc[v][1] += rz.y;
+                acc[v][2] += cabs2(b);
+            }
+            stcv(R + (int64_t)row * W + c0, r);
+            stcv(P + (int64_t)row * W + c0, p);
+        }
+    }
+    __shared__ T red[TY][32][VC * 3];
+#pragma unroll
+    for (int v = 0; v < VC; ++v)
+#pragma unroll
+        for (int s = 0; s < 3; ++s) red[ty][tx][v * 3 + s] = acc[v][s];
+    __syncthreads();
+    if (ty == 0 && cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            T s0 = 0, s1 = 0, s2 = 0;
+            for (int y = 0; y < TY; ++y) {
+                s0 += red[y][tx][v * 3 + 0];
+                s1 += red[y][tx][v * 3 + 1];
+                s2 += red[y][tx][v * 3 + 2];
+            }
+            T *o = part + ((int64_t)blockIdx.y * W + c0 + v) * 4;
+            o[0] = s0;
+            o[1] = s1;
+            o[2] = s2;
+            o[3] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1: shifted block SpMM Q = (A - sigma_j B) P, fused mu = P^T Q partials
+// ---------------------------------------------------------------------------
+template <typename T, int VC>
+__global__ void __launch_bounds__(32 * TY)
+k_spmm_shifted(int n, int W, int Lp, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+               const typename ABT<T>::type *__restrict__ ab, const cplx<T> *__restrict__ sig,
+               const cplx<T> *__restrict__ P, cplx<T> *__restrict__ Q, const int32_t *__restrict__ flag,
+               T *__restrict__ part) {
+    using C = cplx<T>;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    const int c0 = cg * VC;
+    bool act = false;
+    C s = mk((T)0, (T)0);
+    if (cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) act |= flag[c0 + v] == 1;
+        s = sig[c0 / Lp];
+    }
+    C mu[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) mu[v] = mk((T)0, (T)0);
+    if (act) {
+        for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
+            const int k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
+            C sa[VC], sb[VC];
+#pragma unroll
+            for (int v = 0; v < VC; ++v) sa[v] = sb[v] = mk((T)0, (T)0);
+            for (int k = k0; k < k1; ++k) {
+                const int c = __ldg(col + k);
+                const auto w = __ldg(ab + k);
+                const CV<T, VC> p = ldcv(P + (int64_t)c * W + c0);
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    sa[v].x = fma(w.x, p.v[v].x, sa[v].x);
+                    sa[v].y = fma(w.x, p.v[v].y, sa[v].y);
+                    sb[v].x = fma(w.y, p.v[v].x, sb[v].x);
+                    sb[v].y = fma(w.y, p.v[v].y, sb[v].y);
+                }
+            }
+            CV<T, VC> q;
+#pragma unroll
+            for (int v = 0; v < VC; ++v) q.v[v] = csub(sa[v], cmul(s, sb[v]));
+            stcv(Q + (int64_t)row * W + c0, q);
+            const CV<T, VC> pr = ldcv(P + (int64_t)row * W + c0);
+#pragma unroll
+            for (int v = 0; v < VC; ++v) mu[v] = cfma(pr.v[v], q.v[v], mu[v]);
+        }
+    }
+    __shared__ T red[TY][32][VC * 2];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        red[ty][tx][2 * v] = mu[v].x;
+        red[ty][tx][2 * v + 1] = mu[v].y;
+    }
+    __syncthreads();
+    if (ty == 0 && cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            T s0 = 0, s1 = 0;
+            for (int y = 0; y < TY; ++y) {
+                s0 += red[y][tx][2 * v];
+                s1 += red[y][tx][2 * v + 1];
+            }
+            T *o = part + ((int64_t)blockIdx.y * W + c0 + v) * 4;
+            o[0] = s0;
+            o[1] = s1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// update: r -= alpha q ; U += Re(ua p) ; z = M^{-1} r ; partial r^T z, |r|^2
+// One thread owns VC columns of one pole-slot c and walks all N poles, so the
+// pole sum of the filter is formed in registers.
+// ---------------------------------------------------------------------------
+template <typename T, int VC, int NP>
+__global__ void __launch_bounds__(32 * TY)
+k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__restrict__ P,
+         const cplx<T> *__restrict__ Q, const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ alpha,
+         const cplx<T> *__restrict__ ua, const int32_t *__restrict__ flag, T *__restrict__ U,
+         T *__restrict__ part) {
+    using C = cplx<T>;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ngl = Lp / VC;
+    const int cgl = blockIdx.x * 32 + tx;
+    const int c0 = cgl * VC;
+    const bool live = cgl < ngl;
+    unsigned actmask = 0;   // bit j*VC + v
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            if (j < N)
+#pragma unroll
+                for (int v = 0; v < VC; ++v)
+                    if (flag[j * Lp + c0 + v] == 1) actmask |= 1u << (j * VC + v);
+    }
+    T acc[NP][VC][3];
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+#pragma unroll
+        for (int v = 0; v < VC; ++v) acc[j][v][0] = acc[j][v][1] = acc[j][v][2] = (T)0;
+
+    if (actmask) {
+        for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
+            T u[VC];
+#pragma unroll
+            for (int v = 0; v < VC; ++v) u[v] = (T)0;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                if (j >= N) break;
+                const unsigned mj = (actmask >> (j * VC)) & ((1u << VC) - 1);
+                if (!mj) continue;
+                const int64_t base = (int64_t)row * W + j * Lp + c0;
+                CV<T, VC> r = ldcv(R + base);
+                const CV<T, VC> p = ldcv(P + base);
+                const CV<T, VC> q = ldcv(Q + base);
+                const C dv = dinv[(int64_t)row * N + j];
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    if (!(mj & (1u << v))) continue;
+                    const C a = alpha[j * Lp + c0 + v];
+                    const C w = ua[j * Lp + c0 + v];
+                    r.v[v] = csub(r.v[v], cmul(a, q.v[v]));
+                    u[v] += w.x * p.v[v].x - w.y * p.v[v].y;
+                    const C z = cmul(dv, r.v[v]);
+                    const C rz = cmul(r.v[v], z);
+                    acc[j][v][0] += rz.x;
+                    acc[j][v][1] += rz.y;
+                    acc[j][v][2] += cabs2(r.v[v]);
+                }
+                stcv(R + base, r);
+            }
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < NP; ++j)
+                    if (j < N) any |= (actmask >> (j * VC + v)) & 1u;
+                if (any) U[(int64_t)row * Lp + c0 + v] += u[v];
+            }
+        }
+    }
+    __shared__ T red[TY][32][VC * 3];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        if (j >= N) break;
+#pragma unroll
+        for (int v = 0; v < VC; ++v)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) red[ty][tx][v * 3 + s] = acc[j][v][s];
+        __syncthreads();
+        if (ty == 0 && live) {
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                T s0 = 0, s1 = 0, s2 = 0;
+                for (int y = 0; y < TY; ++y) {
+                    s0 += red[y][tx][v * 3 + 0];
+                    s1 += red[y][tx][v * 3 + 1];
+                    s2 += red[y][tx][v * 3 + 2];
+                }
+                T *o = part + ((int64_t)blockIdx.y * W + j * Lp + c0 + v) * 4;
+                o[0] = s0;
+                o[1] = s1;
+                o[2] = s2;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// direction: p = M^{-1} r + beta p
+// ---------------------------------------------------------------------------
+template <typename T, int VC>
+__global__ void __launch_bounds__(32 * TY)
+k_direction(int n, int W, int Lp, int N, const cplx<T> *__restrict__ R, cplx<T> *__restrict__ P,
+            const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ beta,
+            const int32_t *__restrict__ flag) {
+    using C = cplx<T>;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    if (cg >= ng) return;
+    const int c0 = cg * VC;
+    const int j = c0 / Lp;
+    bool act[VC];
+    bool any = false;
+    C b[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        act[v] = flag[c0 + v] == 1;
+        any |= act[v];
+        b[v] = beta[c0 + v];
+    }
+    if (!any) return;
+    for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
+        const int64_t base = (int64_t)row * W + c0;
+        const C dv = dinv[(int64_t)row * N + j];
+        const CV<T, VC> r = ldcv(R + base);
+        CV<T, VC> p = ldcv(P + base);
+#pragma unroll
+        for (int v = 0; v < VC; ++v)
+            if (act[v]) p.v[v] = cfma(b[v], p.v[v], cmul(dv, r.v[v]));
+        stcv(P + base, p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-column reductions (one warp per column, lanes over row groups, FP64)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void warp_sum3(const T *part, int gy, int W, int col, double &s0, double &s1,
+                                          double &s2) {
+    const int lane = threadIdx.x & 31;
+    s0 = s1 = s2 = 0.0;
+    for (int g = lane; g < gy; g += 32) {
+        const T *o = part + ((int64_t)g * W + col) * 4;
+        s0 += (double)o[0];
+        s1 += (double)o[1];
+        s2 += (double)o[2];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+    }
+}
+
+template <typename T>
+__global__ void k_reduce_init(int W, int gy, const T *__restrict__ part, KrylovScalars<T> s) {
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= W) return;
+    double s0, s1, s2;
+    warp_sum3(part, gy, W, col, s0, s1, s2);
+    if ((threadIdx.x & 31) == 0) {
+        s.rho[col] = mk((T)s0, (T)s1);
+        s.bnorm2[col] = s2;
+        s.rnorm2[col] = s2;
+        s.iters[col] = 0;
+        if (s.flag[col] == 1 && !(s2 > 0.0)) s.flag[col] = 0;   // zero right-hand side: y = 0
+    }
+}
+
+template <typename T>
+__global__ void k_reduce_alpha(int W, int gy, const T *__restrict__ part, KrylovScalars<T> s) {
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= W) return;
+    double s0, s1, s2;
+    warp_sum3(part, gy, W, col, s0, s1, s2);
+    if ((threadIdx.x & 31) == 0 && s.flag[col] == 1) {
+        const double den = s0 * s0 + s1 * s1;
+        const double rr = (double)s.rho[col].x, ri = (double)s.rho[col].y;
+        if (!(den > 0.0) || !isfinite(den)) {
+            s.flag[col] = 2;
+            return;
+        }
+        // alpha = rho / mu
+        const double ar = (rr * s0 + ri * s1) / den;
+        const double ai = (ri * s0 - rr * s1) / den;
+        s.alpha[col] = mk((T)ar, (T)ai);
+        const double2 c = s.coef[col];
+        s.ua[col] = mk((T)(2.0 * (c.x * ar - c.y * ai)), (T)(2.0 * (c.x * ai + c.y * ar)));
+    }
+}
+
+template <typename T>
+__global__ void k_reduce_beta(int W, int gy, const T *__restrict__ part, KrylovScalars<T> s, double tol2,
+                              int maxit) {
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= W) return;
+    double s0, s1, s2;
+    warp_sum3(part, gy, W, col, s0, s1, s2);
+    if ((threadIdx.x & 31) == 0 && s.flag[col] == 1) {
+        const int it = s.iters[col] + 1;
+        s.iters[col] = it;
+        s.rnorm2[col] = s2;
+        if (s2 <= tol2 * s.bnorm2[col]) {
+            s.flag[col] = 0;
+            return;
+        }
+        if (it >= maxit) {
+            s.flag[col] = 3;
+            return;
+        }
+        const double rr = (double)s.rho[col].x, ri = (double)s.rho[col].y;
+        const double den = rr * rr + ri * ri;
+        if (!(den > 0.0) || !isfinite(s2)) {
+            s.flag[col] = 2;
+            return;
+        }
+        // beta = rho' / rho
+        const double br = (s0 * rr + s1 * ri) / den;
+        const double bi = (s1 * rr - s0 * ri) / den;
+        s.beta[col] = mk((T)br, (T)bi);
+        s.rho[col] = mk((T)s0, (T)s1);
+    }
+}
+
+__global__ void k_count_active(int W, const int32_t *__restrict__ flag, int32_t *__restrict__ count) {
+    __shared__ int tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    int c = 0;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) c += flag[i] == 1;
+    atomicAdd(&tot, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *count = tot;
+}
+
+template <typename T>
+__global__ void k_reduce_mu(int W, int gy, const T *__restrict__ part, cplx<T> *__restrict__ mu, int Lp, int m) {
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= W) return;
+    double s0, s1, s2;
+    warp_sum3(part, gy, W, col, s0, s1, s2);
+    const int j = col / Lp, c = col - j * Lp;
+    if ((threadIdx.x & 31) == 0 && c < m) mu[j * m + c] = mk((T)s0, (T)s1);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+int krylov_row_groups(const Ctx &ctx, const KrylovDims &d, int prec_fp32) {
+    const int VC = prec_fp32 ? 2 : 1;
+    const int gx = (d.W() / VC + 31) / 32;
+    const int target = ctx.sm_count * 8;
+    int gy = target / (gx > 0 ? gx : 1);
+    const int maxgy = (d.n + TY - 1) / TY;
+    if (gy > maxgy) gy = maxgy;
+    if (gy < 1) gy = 1;
+    return gy;
+}
+
+template <typename T>
+void krylov_dinv(Ctx &ctx, const DevPencil &A, const PoleSet<T> &ps, int precond, cplx<T> *dinv) {
+    const int64_t tot = (int64_t)A.n * ps.N;
+    ctx.before(KC_KRYLOV_INIT, (double)tot * sizeof(cplx<T>) + 16.0 * A.n, 0);
+    k_dinv<T><<<(unsigned)((tot + 255) / 256), 256, 0, ctx.stream>>>(A.n, ps.N, A.diag_a, A.diag_b, ps, precond, dinv);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_init(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, const double *rhs, int64_t ldr,
+                 const cplx<double> *rhs_c) {
+    constexpr int VC = VecN<T>::VC;
+    const int W = d.W();
+    dim3 grid((W / VC + 31) / 32, kb.gy), block(32, TY);
+    const double vb = (double)d.n * W * sizeof(cplx<T>);
+    ctx.before(KC_KRYLOV_INIT, 2 * vb + (double)d.n * d.m * 8, 0);
+    k_init<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, d.m, rhs, ldr, rhs_c, kb.dinv, kb.R, kb.P,
+                                                  kb.s.flag, kb.s.part);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_reduce_init(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
+    const int W = d.W();
+    ctx.before(KC_KRYLOV_REDUCE, (double)kb.gy * W * 4 * sizeof(T), 0);
+    k_reduce_init<T><<<(W * 32 + 255) / 256, 256, 0, ctx.stream>>>(W, kb.gy, kb.s.part, kb.s);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_spmm(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const cplx<T> *sig, const cplx<T> *P,
+                 cplx<T> *Q, const int32_t *flag, T *part, int gy) {
+    constexpr int VC = VecN<T>::VC;
+    const int W = d.W();
+    dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
+    // algorithmic bytes: pattern + (a,b) pairs once, P read once, Q written once
+    const double bytes = 4.0 * (d.n + 1) + (double)A.nnz * (4 + 2 * sizeof(T)) + 2.0 * d.n * W * sizeof(cplx<T>);
+    const double flops = 8.0 * (double)A.nnz * W;
+    ctx.before(KC_SHIFTED_SPMM, bytes, flops);
+    k_spmm_shifted<T, VC><<<grid, block, 0, ctx.stream>>>(
+        d.n, W, d.Lp, A.rowptr, A.col,
+        reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.ab32 : (const void *)A.ab64),
+        sig, P, Q, flag, part);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_reduce_alpha(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
+    const int W = d.W();
+    ctx.before(KC_KRYLOV_REDUCE, (double)kb.gy * W * 4 * sizeof(T), 0);
+    k_reduce_alpha<T><<<(W * 32 + 255) / 256, 256, 0, ctx.stream>>>(W, kb.gy, kb.s.part, kb.s);
+    ctx.after();
+}
+
+template <typename T, int NP>
+static void launch_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
+    constexpr int VC = VecN<T>::VC;
+    const int W = d.W();
+    dim3 grid((d.Lp / VC + 31) / 32, kb.gy), block(32, TY);
+    const double vb = (double)d.n * W * sizeof(cplx<T>);
+    ctx.before(KC_KRYLOV_UPDATE, 4 * vb + 2.0 * d.n * d.Lp * sizeof(T) + (double)d.n * d.N * sizeof(cplx<T>),
+               16.0 * d.n * W);
+    k_update<T, VC, NP><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv, kb.s.alpha,
+                                                         kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
+    if (d.N <= 2)
+        launch_update<T, 2>(ctx, d, kb);
+    else if (d.N <= 4)
+        launch_update<T, 4>(ctx, d, kb);
+    else if (d.N <= 8)
+        launch_update<T, 8>(ctx, d, kb);
+    else
+        launch_update<T, 16>(ctx, d, kb);
+}
+
+template <typename T>
+void krylov_reduce_beta(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, double tol2, int maxit) {
+    const int W = d.W();
+    ctx.before(KC_KRYLOV_REDUCE, (double)kb.gy * W * 4 * sizeof(T), 0);
+    k_reduce_beta<T><<<(W * 32 + 255) / 256, 256, 0, ctx.stream>>>(W, kb.gy, kb.s.part, kb.s, tol2, maxit);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
+    constexpr int VC = VecN<T>::VC;
+    const int W = d.W();
+    dim3 grid((W / VC + 31) / 32, kb.gy), block(32, TY);
+    const double vb = (double)d.n * W * sizeof(cplx<T>);
+    ctx.before(KC_KRYLOV_DIR, 3 * vb + (double)d.n * d.N * sizeof(cplx<T>), 10.0 * d.n * W);
+    k_direction<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.dinv, kb.s.beta, kb.s.flag);
+    ctx.after();
+}
+
+void krylov_count_active(Ctx &ctx, int W, const int32_t *flag, int32_t *count) {
+    ctx.before(KC_KRYLOV_REDUCE, 4.0 * W, 0);
+    k_count_active<<<1, 256, 0, ctx.stream>>>(W, flag, count);
+    ctx.after();
+}
+
+template <typename T>
+void krylov_reduce_mu(Ctx &ctx, const KrylovDims &d, const T *part, int gy, cplx<T> *mu) {
+    const int W = d.W();
+    ctx.before(KC_KRYLOV_REDUCE, (double)gy * W * 4 * sizeof(T), 0);
+    k_reduce_mu<T><<<(W * 32 + 255) / 256, 256, 0, ctx.stream>>>(W, gy, part, mu, d.Lp, d.m);
+    ctx.after();
+}
+
+#define INST(T)                                                                                                \
+    template void krylov_dinv<T>(Ctx &, const DevPencil &, const PoleSet<T> &, int, cplx<T> *);                \
+    template void krylov_init<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &, const double *, int64_t,       \
+                                 const cplx<double> *);                                                       \
+    template void krylov_reduce_init<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                       \
+    template void krylov_spmm<T>(Ctx &, const KrylovDims &, const DevPencil &, const cplx<T> *,               \
+                                 const cplx<T> *, cplx<T> *, const int32_t *, T *, int);                       \
+    template void krylov_reduce_alpha<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                      \
+    template void krylov_update<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                            \
+    template void krylov_reduce_beta<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &, double, int);          \
+    template void krylov_direction<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                         \
+    template void krylov_reduce_mu<T>(Ctx &, const KrylovDims &, const T *, int, cplx<T> *);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace slrf

@@ -1,0 +1,485 @@
+// Small dense m x m kernels of the projection step (m = subspace size L):
+// Cholesky factor and triangular inverse for Cholesky-QR2 B-orthonormalisation,
+// and the symmetric eigensolver of the projected problem (Algorithm 1, "solve
+// the eigenvalue problem A_hat s_i = theta_i B_hat s_i" once B_hat = I).
+//
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so
+// the eigensolver has two modes:
+//  0. cyclic parallel Jacobi in FP64 (round-robin pair ordering, all m/2
+//     rotations of a round applied at once) as ONE cooperative multi-block
+//     kernel: each round is "rotations -> row phase -> grid barrier -> column
+//     phase -> grid barrier", so the O(m^3) rotation work of a sweep is spread
+//     over many SMs;
+//  1. the same Jacobi in FP32 in one block's shared memory first (fast, gives
+//     eigenvectors S0 good to ~1e-6), then S0 is re-orthonormalised in FP64
+//     (Cholesky of S0^T S0 ~ I), T = S0^T A S0 is formed by FP64 GEMMs, and the
+//     cooperative FP64 Jacobi polishes the nearly diagonal T in 2-3 sweeps
+//     (Jacobi converges quadratically; unlike first-order refinement it is
+//     robust to clustered and graded spectra).
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+#include <float.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace slrf {
+
+// ---------------------------------------------------------------------------
+// column scaling of a Gram matrix: s_i = 1/sqrt(g_ii), G <- S G S
+// ---------------------------------------------------------------------------
+__global__ void k_colscale(int m, double *__restrict__ G, double *__restrict__ s) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int i = (int)(e / m), j = (int)(e % m);
+    const double gi = G[(int64_t)i * m + i], gj = G[(int64_t)j * m + j];
+    const double si = gi > 0.0 ? 1.0 / sqrt(gi) : 0.0;
+    const double sj = gj > 0.0 ? 1.0 / sqrt(gj) : 0.0;
+    // every thread reads the diagonal before any writes it: write to a copy
+    // is avoided by updating the diagonal last (see k_colscale_diag).
+    if (i != j) G[e] *= si * sj;
+    if (i == j) s[i] = si;
+}
+__global__ void k_colscale_diag(int m, double *__restrict__ G, const double *__restrict__ s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) G[(int64_t)i * m + i] *= s[i] * s[i];
+}
+
+void small_colscale(Ctx &ctx, int m, double *G, double *s) {
+    const int64_t tot = (int64_t)m * m;
+    ctx.before(KC_SMALL_DENSE, 16.0 * tot, tot);
+    k_colscale<<<(unsigned)((tot + 255) / 256), 256, 0, ctx.stream>>>(m, G, s);
+    ctx.after();
+    ctx.before(KC_SMALL_DENSE, 16.0 * m, m);
+    k_colscale_diag<<<(m + 255) / 256, 256, 0, ctx.stream>>>(m, G, s);
+    ctx.after();
+}
+
+__global__ void k_scale_rows(int m, const double *__restrict__ s, double *__restrict__ T) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    T[e] *= s[e / m];
+}
+void small_scale_rows(Ctx &ctx, int m, const double *s, double *T) {
+    const int64_t tot = (int64_t)m * m;
+    ctx.before(KC_SMALL_DENSE, 16.0 * tot, tot);
+    k_scale_rows<<<(unsigned)((tot + 255) / 256), 256, 0, ctx.stream>>>(m, s, T);
+    ctx.after();
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky G = R^T R (R upper), one block, right-looking
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_chol_upper(int m, double *__restrict__ G, int32_t *__restrict__ status,
+                                                      int use_smem) {
+    extern __shared__ double sm[];
+    double *A = use_smem ? sm : G;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    if (use_smem)
+        for (int e = tid; e < m * m; e += bs) A[e] = G[e];
+    __shared__ int bad;
+    __shared__ double dinv;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (tid == 0) {
+            const double d = A[k * m + k];
+            if (!(d > 0.0) || !isfinite(d)) {
+                bad = k + 1;
+            } else {
+                const double r = sqrt(d);
+                A[k * m + k] = r;
+                dinv = 1.0 / r;
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        for (int j = k + 1 + tid; j < m; j += bs) A[k * m + j] *= dinv;
+        __syncthreads();
+        const int r = m - k - 1;
+        for (int e = tid; e < r * r; e += bs) {
+            const int i = k + 1 + e / r, j = k + 1 + e % r;
+            if (j >= i) A[i * m + j] -= A[k * m + i] * A[k * m + j];
+        }
+        __syncthreads();
+    }
+    if (!bad)
+        for (int e = tid; e < m * m; e += bs) {
+            const int i = e / m, j = e % m;
+            if (j < i) A[e] = 0.0;
+        }
+    __syncthreads();
+    if (use_smem)
+        for (int e = tid; e < m * m; e += bs) G[e] = A[e];
+    if (tid == 0) *status = bad;
+}
+
+void small_chol_upper(Ctx &ctx, int m, double *G, int32_t *status) {
+    const size_t smem = (size_t)m * m * sizeof(double);
+    const int use_smem = smem <= 200 * 1024;
+    if (use_smem) cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
+    k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, status, use_smem);
+    ctx.after();
+}
+
+// ---------------------------------------------------------------------------
+// X = R^{-1}, R upper triangular; thread per column, back substitution
+// ---------------------------------------------------------------------------
+__global__ void k_triinv_upper(int m, const double *__restrict__ R, double *__restrict__ X) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        for (int i = m - 1; i > j; --i) X[(int64_t)i * m + j] = 0.0;
+        for (int i = j; i >= 0; --i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= j; ++k) s -= R[(int64_t)i * m + k] * X[(int64_t)k * m + j];
+            X[(int64_t)i * m + j] = s / R[(int64_t)i * m + i];
+        }
+    }
+}
+
+void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv) {
+    ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
+    k_triinv_upper<<<(m + 63) / 64, 64, 0, ctx.stream>>>(m, R, Rinv);
+    ctx.after();
+}
+
+// ---------------------------------------------------------------------------
+// cyclic parallel Jacobi (one block).  A, V in shared memory when they fit.
+// Output: lam ascending (FP64), Q (FP64, columns = eigenvectors).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rr_pair(int k, int r, int mp, int &a, int &b) {
+    // circle method: position 0 fixed, positions 1..mp-1 rotate by r
+    a = (k == 0) ? 0 : ((k - 1 + r) % (mp - 1)) + 1;
+    b = ((mp - 2 - k + r) % (mp - 1)) + 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict__ Vg, double *__restrict__ lam,
+         double *__restrict__ Q, int max_sweeps, int use_smem, int32_t *__restrict__ info) {
+    extern __shared__ unsigned char smraw[];
+    T *A = use_smem ? reinterpret_cast<T *>(smraw) : Ag;
+    T *V = use_smem ? A + (size_t)m * m : Vg;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int mp = m + (m & 1);
+    const int npair = mp / 2;
+    __shared__ T cs[512], sn[512];
+    __shared__ int pp[512], qq[512];
+    __shared__ int nrot;
+    __shared__ double red[32];
+    __shared__ T absmin;
+
+    double fro = 0.0;
+    for (int e = tid; e < m * m; e += bs) {
+        const double v = S[e];
+        A[e] = (T)v;
+        V[e] = (T)((e / m) == (e % m) ? 1 : 0);
+        fro += v * v;
+    }
+    // block reduce of ||S||_F^2
+    for (int off = 16; off > 0; off >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, off);
+    if ((tid & 31) == 0) red[tid >> 5] = fro;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0;
+        for (int w = 0; w < (bs + 31) / 32; ++w) t += red[w];
+        const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
+        // FP32 only needs eigenvectors good enough for the FP64 refinement
+        absmin = (T)(sqrt(t) * (double)eps * (sizeof(T) == 4 ? 1.0 / sqrt((double)m) : 0.5 / (double)m));
+    }
+    __syncthreads();
+    const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
+
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) nrot = 0;
+        __syncthreads();
+        for (int r = 0; r < mp - 1; ++r) {
+            for (int k = tid; k < npair; k += bs) {
+                int a, b;
+                rr_pair(k, r, mp, a, b);
+                const int p = min(a, b), q = max(a, b);
+                T c = 1, s = 0;
+                if (q < m) {
+                    const T apq = A[p * m + q];
+                    const T app = A[p * m + p], aqq = A[q * m + q];
+                    const T thr = eps * sqrt(fabs(app * aqq));
+                    if (fabs(apq) > thr && fabs(apq) > absmin) {
+                        const T th = (aqq - app) / (2 * apq);
+                        const T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt((T)1 + th * th));
+                        c = (T)1 / sqrt((T)1 + t * t);
+                        s = t * c;
+                        atomicAdd(&nrot, 1);
+                    }
+                }
+                cs[k] = c;
+                sn[k] = s;
+                pp[k] = p;
+                qq[k] = (q < m && s != (T)0) ? q : -1;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int e = tid; e < npair * m; e += bs) {
+                const int k = e / m, col = e % m;
+                const int q = qq[k];
+                if (q < 0) continue;
+                const int p = pp[k];
+                const T c = cs[k], s = sn[k];
+                const T apk = A[p * m + col], aqk = A[q * m + col];
+                A[p * m + col] = c * apk - s * aqk;
+                A[q * m + col] = s * apk + c * aqk;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int e = tid; e < npair * m; e += bs) {
+                const int k = e / m, row = e % m;
+                const int q = qq[k];
+                if (q < 0) continue;
+                const int p = pp[k];
+                const T c = cs[k], s = sn[k];
+                const T akp = A[row * m + p], akq = A[row * m + q];
+                A[row * m + p] = c * akp - s * akq;
+                A[row * m + q] = s * akp + c * akq;
+                const T vkp = V[row * m + p], vkq = V[row * m + q];
+                V[row * m + p] = c * vkp - s * vkq;
+                V[row * m + q] = s * vkp + c * vkq;
+            }
+            __syncthreads();
+            for (int k = tid; k < npair; k += bs) {
+                const int q = qq[k];
+                if (q < 0) continue;
+                const int p = pp[k];
+                A[p * m + q] = 0;
+                A[q * m + p] = 0;
+            }
+            __syncthreads();
+        }
+        if (nrot == 0) break;
+        __syncthreads();
+    }
+    // sort eigenvalues ascending (rank sort), permute columns into Q (FP64)
+    for (int i = tid; i < m; i += bs) {
+        const T di = A[i * m + i];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+            const T dj = A[j * m + j];
+            rank += (dj < di) || (dj == di && j < i);
+        }
+        lam[rank] = (double)di;
+        for (int row = 0; row < m; ++row) Q[(int64_t)row * m + rank] = (double)V[row * m + i];
+    }
+    if (tid == 0 && info) *info = sweep;
+}
+
+// ---------------------------------------------------------------------------
+// cooperative FP64 Jacobi on a global m x m matrix A (overwritten; diag = lam)
+// accumulating V <- V J.  cnt[2]: rotation counters (device).  All blocks
+// compute the same rotations from the same data, so no broadcast is needed.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_jacobi_coop(int m, double *__restrict__ A, double *__restrict__ V, double *__restrict__ lam, int max_sweeps,
+              const double *__restrict__ normA, int *__restrict__ cnt, int32_t *__restrict__ info) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    const int mp = m + (m & 1);
+    const int npair = mp / 2;
+    __shared__ double cs[512], sn[512], dp[512], dq[512];
+    __shared__ int pp[512], qq[512];
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    const double eps = DBL_EPSILON;
+    const double absmin = (*normA) * eps * 0.5 / (double)m;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt[sweep & 1] = 0;
+        __syncthreads();
+        for (int r = 0; r < mp - 1; ++r) {
+            // Every block derives all rotations of the round from the pair
+            // blocks (p,p), (q,q), (p,q).  Those entries are not written by the
+            // row phase (below), so a block still reading them here cannot race
+            // with a block that has moved on to the row phase.
+            for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+                int a, b;
+                rr_pair(k, r, mp, a, b);
+                const int p = min(a, b), q = max(a, b);
+                double c = 1, s = 0, t = 0, app = 0, aqq = 0, apq = 0;
+                if (q < m) {
+                    apq = A[(int64_t)p * m + q];
+                    app = A[(int64_t)p * m + p];
+                    aqq = A[(int64_t)q * m + q];
+                    if (fabs(apq) > eps * sqrt(fabs(app * aqq)) && fabs(apq) > absmin) {
+                        const double th = (aqq - app) / (2 * apq);
+                        t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                        if (blockIdx.x == 0) atomicAdd(&cnt[sweep & 1], 1);
+                    }
+                }
+                cs[k] = c;
+                sn[k] = s;
+                dp[k] = app - t * apq;   // rotated diagonal of the pair block
+                dq[k] = aqq + t * apq;
+                pp[k] = p;
+                qq[k] = (q < m && s != 0.0) ? q : -1;
+            }
+            __syncthreads();
+            // rows p, q <- J^T (rows p, q), except the pair block itself
+            for (int64_t e = gtid; e < (int64_t)npair * m; e += gsz) {
+                const int k = (int)(e / m), col = (int)(e % m);
+                const int q = qq[k];
+                if (q < 0) continue;
+                const int p = pp[k];
+                if (col == p || col == q) continue;
+                const double c = cs[k], s = sn[k];
+                const double apk = A[(int64_t)p * m + col], aqk = A[(int64_t)q * m + col];
+                A[(int64_t)p * m + col] = c * apk - s * aqk;
+                A[(int64_t)q * m + col] = s * apk + c * aqk;
+            }
+            grid.sync();
+            // columns p, q <- (columns p, q) J; the pair block in closed form
+            for (int64_t e = gtid; e < (int64_t)npair * m; e += gsz) {
+                const int k = (int)(e / m), row = (int)(e % m);
+                const int q = qq[k];
+                if (q < 0) continue;
+                const int p = pp[k];
+                const double c = cs[k], s = sn[k];
+                if (row == p) {
+                    A[(int64_t)p * m + p] = dp[k];
+                    A[(int64_t)p * m + q] = 0.0;
+                } else if (row == q) {
+                    A[(int64_t)q * m + q] = dq[k];
+                    A[(int64_t)q * m + p] = 0.0;
+                } else {
+                    const double akp = A[(int64_t)row * m + p], akq = A[(int64_t)row * m + q];
+                    A[(int64_t)row * m + p] = c * akp - s * akq;
+                    A[(int64_t)row * m + q] = s * akp + c * akq;
+                }
+                const double vkp = V[(int64_t)row * m + p], vkq = V[(int64_t)row * m + q];
+                V[(int64_t)row * m + p] = c * vkp - s * vkq;
+                V[(int64_t)row * m + q] = s * vkp + c * vkq;
+            }
+            grid.sync();
+        }
+        const int n_rot = *(volatile int *)&cnt[sweep & 1];
+        grid.sync();
+        if (n_rot == 0) break;
+    }
+    for (int64_t i = gtid; i < m; i += gsz) lam[i] = A[i * m + i];
+    if (gtid == 0 && info) *info = sweep;
+}
+
+__global__ void k_identity(int m, double *__restrict__ V) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < (int64_t)m * m) V[e] = (e / m == e % m) ? 1.0 : 0.0;
+}
+
+// final ordering: lam ascending, Q columns permuted
+__global__ void k_sort_eig(int m, const double *__restrict__ lam_in, const double *__restrict__ S,
+                           double *__restrict__ lam, double *__restrict__ Q) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const double di = lam_in[i];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+            const double dj = lam_in[j];
+            rank += (dj < di) || (dj == di && j < i);
+        }
+        lam[rank] = di;
+        for (int row = 0; row < m; ++row) Q[(int64_t)row * m + rank] = S[(int64_t)row * m + i];
+    }
+}
+
+__global__ void k_fro(int m, const double *__restrict__ S, double *__restrict__ out) {
+    __shared__ double red[32];
+    double s = 0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) s += S[e] * S[e];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int w = 0; w < (blockDim.x + 31) / 32; ++w) t += red[w];
+        *out = sqrt(t);
+    }
+}
+
+size_t small_syev_work_bytes(int m) {
+    const size_t mp = (size_t)(m + (m & 1));
+    const size_t m2 = (size_t)m * m;
+    // A32/V32 global fallback (2 mp^2 doubles) + S0, S1, G, Y, T, V (6 m^2) + lam0, normA, counters
+    return 2 * mp * mp * sizeof(double) + 6 * m2 * sizeof(double) + 2 * (size_t)m * sizeof(double) + 4096;
+}
+
+static void coop_jacobi(Ctx &ctx, int m, double *A, double *V, double *lam, int max_sweeps, const double *normA,
+                        int *cnt) {
+    static int max_blocks = -1;
+    if (max_blocks < 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 256, 0);
+        max_blocks = per_sm * ctx.sm_count;
+    }
+    const int64_t work = (int64_t)((m + 1) / 2) * m;
+    int blocks = (int)std::min<int64_t>((work + 255) / 256, std::min(max_blocks, ctx.sm_count));
+    if (blocks < 1) blocks = 1;
+    int32_t *info = nullptr;
+    void *args[] = {&m, &A, &V, &lam, &max_sweeps, (void *)&normA, &cnt, &info};
+    ctx.before(KC_SMALL_DENSE, 24.0 * m * m, 9.0 * (double)m * m * m * 3);
+    cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(blocks), dim3(256), args, 0, ctx.stream);
+    ctx.after();
+}
+
+void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode) {
+    const size_t m2 = (size_t)m * m;
+    const size_t mp = (size_t)(m + (m & 1));
+    char *w = reinterpret_cast<char *>(work);
+    void *Ag = w;
+    void *Vg = w + mp * mp * sizeof(double);
+    double *S0 = reinterpret_cast<double *>(w + 2 * mp * mp * sizeof(double));
+    double *S1 = S0 + m2;
+    double *G = S1 + m2;
+    double *Ym = G + m2;
+    double *Tm = Ym + m2;
+    double *Vm = Tm + m2;
+    double *lam0 = Vm + m2;
+    double *normA = lam0 + m;
+    int *cnt = reinterpret_cast<int *>(normA + m);
+    int32_t *cst = cnt + 4;
+
+    ctx.before(KC_SMALL_DENSE, 8.0 * m2, 2.0 * m2);
+    k_fro<<<1, 1024, 0, ctx.stream>>>(m, S, normA);
+    ctx.after();
+    ctx.before(KC_SMALL_DENSE, 8.0 * m2, 0);
+    k_identity<<<(unsigned)((m2 + 255) / 256), 256, 0, ctx.stream>>>(m, Vm);
+    ctx.after();
+    if (mode == 0) {
+        cudaMemcpyAsync(Tm, S, m2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream);
+        coop_jacobi(ctx, m, Tm, Vm, lam0, 60, normA, cnt);
+        ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
+        k_sort_eig<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, lam0, Vm, lam, Q);
+        ctx.after();
+        return;
+    }
+    // stage 1: FP32 Jacobi in shared memory (global fallback for large m)
+    const size_t smem = 2 * m2 * sizeof(float);
+    const int use_smem = smem <= 200 * 1024;
+    if (use_smem) cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ctx.before(KC_SMALL_DENSE, 24.0 * m2, 9.0 * (double)m * m2 * 8);
+    k_jacobi<float><<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, S, (float *)Ag, (float *)Vg, lam0, S0, 40,
+                                                                    use_smem, nullptr);
+    ctx.after();
+    // stage 2: FP64 re-orthonormalisation S1 = S0 R^{-1}, G = S0^T S0 = R^T R
+    dgemm(ctx, 1, 0, m, m, m, S0, m, S0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
+    small_chol_upper(ctx, m, G, cst);
+    small_triinv_upper(ctx, m, G, Ym);
+    dgemm(ctx, 0, 0, m, m, m, S0, m, Ym, m, 0.0, S1, m, 1, nullptr, KC_SMALL_DENSE);
+    // T = S1^T A S1, then polish T by FP64 Jacobi, S = S1 V
+    dgemm(ctx, 0, 0, m, m, m, S, m, S1, m, 0.0, Ym, m, 1, nullptr, KC_SMALL_DENSE);
+    dgemm(ctx, 1, 0, m, m, m, S1, m, Ym, m, 0.0, Tm, m, 1, nullptr, KC_SMALL_DENSE);
+    coop_jacobi(ctx, m, Tm, Vm, lam0, 20, normA, cnt);
+    dgemm(ctx, 0, 0, m, m, m, S1, m, Vm, m, 0.0, S0, m, 1, nullptr, KC_SMALL_DENSE);
+    ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
+    k_sort_eig<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, lam0, S0, lam, Q);
+    ctx.after();
+}
+
+}  // namespace slrf

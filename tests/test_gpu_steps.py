@@ -1,0 +1,140 @@
+"""GPU parity of the individual hot-path steps against the FP64 oracle,
+through the C ABI.  Sizes span several tiles and a ragged tail."""
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+from oracle import filter as ofilt
+from oracle import poles, rr
+from workloads import pencil_1d, pencil_2d_q1, pencil_3d_elasticity, start_block
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api(lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_21618_gb300 import api as a
+    return a
+
+
+def _cplx_block(n, N, m, ldp, seed):
+    rng = np.random.default_rng(seed)
+    P = np.zeros((n, N, ldp), dtype=complex)
+    P[:, :, :m] = rng.standard_normal((n, N, m)) + 1j * rng.standard_normal((n, N, m))
+    return P
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("pencil,N,m", [("2d", 3, 37), ("3d", 2, 10), ("1d", 1, 1), ("2d", 9, 5)])
+def test_shifted_spmm_matches_oracle(api, prec, pencil, N, m):
+    p = {"2d": lambda: pencil_2d_q1(23, seed=4), "3d": lambda: pencil_3d_elasticity(5, seed=2),
+         "1d": lambda: pencil_1d(77)}[pencil]()
+    s, w = poles.quadrature_poles("gauss_legendre", N, 300.0)
+    ldp = m + (m & 1)
+    P = _cplx_block(p.n, N, m, ldp, 1)
+    h = api.Handle(p)
+    f = api.Filter(s, w)
+    cdt = np.complex64 if prec == "fp32" else np.complex128
+    Pd = torch.from_numpy(P.astype(cdt).view(np.float32 if prec == "fp32" else np.float64).copy()).cuda()
+    Q = torch.zeros_like(Pd)
+    mu = torch.zeros(2 * N * m, dtype=Pd.dtype, device="cuda")
+    h.shifted_spmm(f, Pd, m, ldp, prec=api.PREC_MIXED if prec == "fp32" else api.PREC_FP64, Q=Q, mu=mu)
+    torch.cuda.synchronize()
+    Qh = Q.cpu().numpy().view(cdt).reshape(p.n, N, ldp).astype(complex)
+    muh = mu.cpu().numpy().view(cdt).reshape(N, m).astype(complex)
+    tol = 2e-6 if prec == "fp32" else 1e-13
+    A, B = p.A(), p.B()
+    Pq = P.astype(cdt).astype(complex)   # the rounded input the kernel saw
+    for j in range(N):
+        ref = ofilt.shifted_product(A, B, s[j], Pq[:, j, :m])
+        scale = np.abs(A).sum(axis=1).max() * np.abs(Pq).max() * (1 + abs(s[j]))
+        assert np.abs(Qh[:, j, :m] - ref).max() <= tol * scale
+        muref = np.sum(Pq[:, j, :m] * ref, axis=0)
+        assert np.abs(muh[j] - muref).max() <= tol * scale * np.abs(Pq).max() * p.n
+
+
+@pytest.mark.parametrize("m", [1, 30, 65])
+def test_spmm_ab_matches_scipy(api, m):
+    p = pencil_2d_q1(31, seed=8)
+    X = start_block(p.n, m, 3)
+    h = api.Handle(p)
+    Xd = torch.from_numpy(X).cuda()
+    Y, Z = h.spmm_ab(Xd)
+    np.testing.assert_allclose(Y.cpu().numpy(), p.A() @ X, rtol=1e-13, atol=1e-13 * np.abs(p.A() @ X).max())
+    np.testing.assert_allclose(Z.cpu().numpy(), p.B() @ X, rtol=1e-13, atol=1e-13 * np.abs(p.B() @ X).max())
+
+
+@pytest.mark.parametrize("n,m", [(1000, 1), (5000, 64), (20011, 150), (3001, 77)])
+def test_gram_matches_numpy(api, n, m):
+    p = pencil_1d(n)
+    X = start_block(n, m, 1)
+    Y = start_block(n, m, 2)
+    h = api.Handle(p)
+    G = h.gram(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()).cpu().numpy()
+    ref = X.T @ Y
+    assert np.abs(G - ref).max() <= 1e-13 * np.abs(X).max() * np.abs(Y).max() * n
+
+
+def _sym_with_spectrum(m, lam, seed):
+    Qr, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((m, m)))
+    return (Qr * lam[None, :]) @ Qr.T
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("case", ["random", "graded", "clusters", "tiny", "odd"])
+def test_syev_matches_lapack(api, mode, case):
+    rng = np.random.default_rng(5)
+    if case == "random":
+        m = 150
+        S = rng.standard_normal((m, m))
+        S = S + S.T
+    elif case == "graded":
+        m = 120
+        S = _sym_with_spectrum(m, np.geomspace(1.0, 3e3, m), 1)
+    elif case == "clusters":
+        m = 64
+        lam = np.repeat(np.linspace(1, 50, 16), 4)          # exact multiplicity 4
+        lam[::7] += 1e-9 * lam[::7]                           # and near-multiplicities
+        S = _sym_with_spectrum(m, lam, 2)
+    elif case == "tiny":
+        m = 1
+        S = np.array([[3.5]])
+    else:
+        m = 33
+        S = rng.standard_normal((m, m))
+        S = S @ S.T
+    p = pencil_1d(max(m, 8))
+    h = api.Handle(p)
+    h.set_opts(eig_refine=mode)
+    lam, Q = h.syev(torch.from_numpy(np.ascontiguousarray(S)).cuda())
+    lam = lam.cpu().numpy()
+    Q = Q.cpu().numpy()
+    ref = la.eigvalsh(S)
+    nrm = np.linalg.norm(S, 2)
+    assert np.abs(lam - ref).max() <= 1e-13 * nrm * max(1, m / 10)
+    assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-13 * m
+    assert np.abs(S @ Q - Q * lam[None, :]).max() <= 1e-12 * nrm
+
+
+@pytest.mark.parametrize("m", [5, 24])
+def test_rayleigh_ritz_matches_oracle(api, m):
+    p = pencil_2d_q1(26, seed=12)
+    A, B = p.A(), p.B()
+    # a filtered-looking block: exact low eigenvectors mixed with noise
+    lam, Xe = la.eigh(A.toarray(), B.toarray())
+    U = Xe[:, :m] @ start_block(m, m, 1) + 1e-3 * start_block(p.n, m, 2)
+    h = api.Handle(p)
+    theta, X, resid = h.rayleigh_ritz(torch.from_numpy(U).cuda())
+    theta_o, X_o = rr.rayleigh_ritz(A, B, U)
+    rho_o, _ = rr.residuals(A, B, X_o, theta_o)
+    np.testing.assert_allclose(theta.cpu().numpy(), theta_o, rtol=1e-11)
+    np.testing.assert_allclose(resid.cpu().numpy(), rho_o, rtol=1e-6, atol=1e-13)
+    Xh = X.cpu().numpy()
+    np.testing.assert_allclose(Xh.T @ (B @ Xh), np.eye(m), atol=1e-11)
+    # Ritz vectors agree up to sign (simple Ritz values)
+    sgn = np.sign(np.sum(Xh * X_o, axis=0))
+    np.testing.assert_allclose(Xh * sgn[None, :], X_o, atol=1e-8 * np.abs(X_o).max())
