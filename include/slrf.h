@@ -220,6 +220,27 @@ slrf_status slrf_syev(slrf_handle *h, int32_t m, const double *S, double *lam, d
 slrf_status slrf_rayleigh_ritz(slrf_handle *h, int32_t m, const double *U, int64_t ldu,
                                double *theta, double *X, int64_t ldx, double *resid);
 
+/* ---- allocation-free variant ---------------------------------------------- */
+
+/* G = X^T Y (m x m row-major, device) for X, Y device n x m row-major FP64,
+ * like slrf_gram but with no handle and no device allocation.  The paper has
+ * no counterpart: this exists for callers that may not allocate device memory
+ * themselves (code whose device memory is owned by another allocator or a
+ * fixed pool, or that cannot afford cudaMalloc's implicit synchronisation).
+ * Its split-K scratch is a static device array of SLRF_NOALLOC_SCRATCH_BYTES
+ * held by every GPU that loads the library; m*m*8 must fit in it (m <= 724),
+ * larger m returns SLRF_EINVAL (message in slrf_noalloc_last_error()).
+ * The first call on a device looks up that array's device address (with that
+ * device current), so make the first call before any stream capture.  All
+ * calls share the scratch: calls that overlap on the GPU (concurrent streams)
+ * race.  Work is enqueued on cuda_stream (a cudaStream_t); returns after
+ * enqueuing. */
+#define SLRF_NOALLOC_SCRATCH_BYTES (4u << 20)
+slrf_status slrf_gram_noalloc(int64_t n, int32_t m, const double *X, int64_t ldx, const double *Y,
+                              int64_t ldy, double *G, void *cuda_stream);
+/* Text of the last error of slrf_gram_noalloc on this thread ("" if none). */
+const char *slrf_noalloc_last_error(void);
+
 /* ---- pole/weight sets (host) -------------------------------------------- */
 
 /* Fill N upper-half poles/weights (host arrays of length N) for a rule:

@@ -89,6 +89,8 @@ _SIGNATURES = {
                                     C.POINTER(C.c_double)]),
     "slrf_filter_eval": (C.c_int, [C.POINTER(slrf_filter), C.POINTER(C.c_double), C.c_int64,
                                    C.POINTER(C.c_double)]),
+    "slrf_gram_noalloc": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, _P]),
+    "slrf_noalloc_last_error": (C.c_char_p, []),
 }
 
 _lib = None
