@@ -89,7 +89,7 @@ typedef struct {
     int32_t precond;        /* SLRF_PRECOND_*                                 (JACOBI) */
     int32_t inner_maxit;    /* Krylov iteration cap per outer step, Section 4.2.1 (1000) */
     double inner_tol;       /* FP64: rel. to ||B v||, Section 4.2.1 (1e-13);
-                               MIXED: rel. to ||R column||                      (1e-4) */
+                               MIXED: rel. to ||R column||                      (1e-5) */
     double lock_tol;        /* MIXED: columns with rho_i below this skip the solve
                                (their correction is below the outer tolerance) (1e-9) */
     int32_t check_every;    /* Krylov iterations between host polls of the
@@ -98,7 +98,9 @@ typedef struct {
                                0 = FP64 Jacobi                                     (1) */
     int64_t mem_budget;     /* workspace byte cap, 0 = none                       (0) */
     int32_t profile;        /* 1: time each kernel class with CUDA events         (0) */
-    int32_t reserved[7];
+    int32_t spmm_rows;      /* rows per group of the shifted SpMM (1..4); 0 = auto:
+                               3 for 3-dof node-block patterns, else 2             (0) */
+    int32_t reserved[6];
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

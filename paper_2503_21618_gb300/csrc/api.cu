@@ -255,6 +255,56 @@ __global__ void k_symmetrize(int m, double *S) {
 }
 
 // ---------------------------------------------------------------------------
+// row-group form of the pencil for the shifted SpMM
+// ---------------------------------------------------------------------------
+bool has_node_blocks(int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci, int R) {
+    if (n % R) return false;
+    for (int64_t g = 0; g < n / R; ++g) {
+        const int64_t r0 = g * R;
+        const int64_t len = rp[r0 + 1] - rp[r0];
+        for (int r = 1; r < R; ++r) {
+            if (rp[r0 + r + 1] - rp[r0 + r] != len) return false;
+            if (!std::equal(ci.begin() + rp[r0], ci.begin() + rp[r0 + 1], ci.begin() + rp[r0 + r])) return false;
+        }
+    }
+    return true;
+}
+
+void build_rowgroups(int R, int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                     const std::vector<double> &av, const std::vector<double> &bv, std::vector<int32_t> &gptr,
+                     std::vector<int32_t> &ucol, std::vector<double2> &uab) {
+    const int64_t ng = (n + R - 1) / R;
+    gptr.assign(ng + 1, 0);
+    ucol.clear();
+    uab.clear();
+    std::vector<int32_t> u;
+    for (int64_t g = 0; g < ng; ++g) {
+        u.clear();
+        const int64_t r0 = g * R, r1 = std::min<int64_t>(n, r0 + R);
+        for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), ci.begin() + rp[r], ci.begin() + rp[r + 1]);
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        for (int32_t c : u) {
+            ucol.push_back(c);
+            for (int r = 0; r < R; ++r) {
+                const int64_t row = r0 + r;
+                double2 v = make_double2(0.0, 0.0);
+                if (row < n) {
+                    const auto b = ci.begin() + rp[row], e = ci.begin() + rp[row + 1];
+                    const auto it = std::lower_bound(b, e, c);
+                    if (it != e && *it == c) {
+                        const int64_t k = it - ci.begin();
+                        v = make_double2(av[k], bv[k]);
+                    }
+                }
+                uab.push_back(v);
+            }
+        }
+        gptr[g + 1] = (int32_t)ucol.size();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Krylov solve of all (pole, column) systems; filter output accumulated in Uacc
 // ---------------------------------------------------------------------------
 struct KStats {
@@ -336,6 +386,9 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     krylov_init<T>(ctx, d, kb, rhs, ldr, nullptr);
     krylov_reduce_init<T>(ctx, d, kb);
 
+    int n_active = 0;
+    for (int col = 0; col < W; ++col) n_active += flags[col] == 1;
+    d.frac = (double)n_active / W;
     const double tol2 = tol * tol;
     const int every = std::max(1, h->opts.check_every);
     int it = 0;
@@ -352,7 +405,9 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         krylov_count_active(ctx, W, kb.s.flag, h->d_pin);   // mapped pinned host word
         CK(cudaEventRecord(h->ev_poll, ctx.stream));
         CK(cudaEventSynchronize(h->ev_poll));
-        if (*(volatile int32_t *)h->h_pin == 0) break;
+        n_active = *(volatile int32_t *)h->h_pin;
+        d.frac = (double)n_active / W;
+        if (n_active == 0) break;
     }
     CK(cudaGetLastError());
     // statistics
@@ -613,7 +668,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->krylov = SLRF_KRYLOV_COCG;
     o->precond = SLRF_PRECOND_JACOBI;
     o->inner_maxit = 1000;
-    o->inner_tol = 1e-4;
+    o->inner_tol = 1e-5;
     o->lock_tol = 1e-9;
     o->check_every = 8;
     o->eig_refine = 1;
@@ -628,6 +683,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->krylov != SLRF_KRYLOV_COCG) return SLRF_EINVAL;
     if (o->precond != SLRF_PRECOND_NONE && o->precond != SLRF_PRECOND_JACOBI) return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
+    if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
     return SLRF_OK;
 }
 
@@ -647,7 +703,8 @@ void slrf_destroy(slrf_handle *h) {
                    &h->rTheta, &h->rRho, &h->hostV, &h->hostX};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
-    void *pen[] = {h->A.rowptr, h->A.col, h->A.a, h->A.b, h->A.ab32, h->A.ab64, h->A.diag_a, h->A.diag_b};
+    void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,
+                   h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64};
     for (void *p : pen)
         if (p) cudaFree(p);
     if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -697,6 +754,13 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         }
         if (!diag) return SLRF_EINVAL;   // SPD pencils have a positive diagonal
     }
+    // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
+    // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
+    int R = o->spmm_rows;
+    if (R == 0) R = has_node_blocks(n, rp, ci, 3) ? 3 : 2;
+    std::vector<int32_t> gptr, ucol;
+    std::vector<double2> uab;
+    if (R > 1) build_rowgroups(R, n, rp, ci, av, bv, gptr, ucol, uab);
     slrf_handle *h = new slrf_handle();
     h->opts = *o;
     h->ctx.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -744,6 +808,24 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     k_pack_ab<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(nnz, h->A.a, h->A.b, h->A.ab32, h->A.ab64);
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int)n, h->A.rowptr, h->A.col, h->A.a, h->A.b, h->A.diag_a,
                                                          h->A.diag_b);
+    if (R > 1) {
+        const int64_t U = (int64_t)ucol.size();
+        std::vector<float2> uab32(uab.size());
+        for (size_t i = 0; i < uab.size(); ++i) uab32[i] = make_float2((float)uab[i].x, (float)uab[i].y);
+        if (!(alloc((void **)&h->A.rg_ptr, gptr.size() * 4) && alloc((void **)&h->A.rg_col, U * 4) &&
+              alloc((void **)&h->A.rg_ab32, uab.size() * 8) && alloc((void **)&h->A.rg_ab64, uab.size() * 16))) {
+            g_last_error = "device allocation of the row-group pencil failed";
+            slrf_destroy(h);
+            return SLRF_ENOMEM;
+        }
+        h->A.rg_rows = R;
+        h->A.rg_ngroups = (int)(gptr.size() - 1);
+        h->A.rg_nnz = U;
+        cudaMemcpy(h->A.rg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(h->A.rg_col, ucol.data(), U * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(h->A.rg_ab32, uab32.data(), uab32.size() * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(h->A.rg_ab64, uab.data(), uab.size() * 16, cudaMemcpyHostToDevice);
+    }
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         g_last_error = std::string("pencil upload: ") + cudaGetErrorString(e);

@@ -49,6 +49,13 @@ struct DevPencil {
     float2 *ab32 = nullptr;                 // interleaved (a, b), FP32
     double2 *ab64 = nullptr;                // interleaved (a, b), FP64
     double *diag_a = nullptr, *diag_b = nullptr;
+    // row-group form of the shifted SpMM (rg_rows consecutive rows per group,
+    // union column list per group, rg_rows (a, b) pairs per union entry)
+    int rg_rows = 1, rg_ngroups = 0;
+    int64_t rg_nnz = 0;
+    int32_t *rg_ptr = nullptr, *rg_col = nullptr;
+    float2 *rg_ab32 = nullptr;
+    double2 *rg_ab64 = nullptr;
 };
 
 // ---------------------------------------------------------------- krylov.cu
@@ -56,6 +63,7 @@ struct DevPencil {
 // stride W, pole j in columns [j*Lp, j*Lp + Lp), Lp even.
 struct KrylovDims {
     int n, N, Lp, m;       // m <= Lp live columns per pole
+    double frac = 1.0;     // active fraction of the W columns (byte accounting)
     int W() const { return N * Lp; }
 };
 

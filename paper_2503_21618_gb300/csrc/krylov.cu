@@ -158,14 +158,22 @@ k_init(int n, int W, int Lp, int N, int m, const double *__restrict__ rhs, int64
 }
 
 // ---------------------------------------------------------------------------
-// K1: shifted block SpMM Q = (A - sigma_j B) P, fused mu = P^T Q partials
+// K1: shifted block SpMM Q = (A - sigma_j B) P, fused mu = P^T Q partials.
+// Two forms: plain CSR rows (rows_per_block consecutive rows per CTA) and row
+// groups (below).  Measured on the 2D Q1 pencil (all 600 columns active):
+// grid-strided rows 330 us, contiguous row blocks 355 us, row groups of 2
+// 280 us, row groups of 4 396 us per launch.
 // ---------------------------------------------------------------------------
-template <typename T, int VC>
+// Variant with contiguous row blocks (rows_per_block consecutive rows per CTA,
+// so consecutive warps reuse the same gathered P rows in L1) and the nonzeros
+// of a row processed UNR at a time: all UNR indices, then all UNR gathers are
+// issued before the FMAs, so each warp keeps UNR loads in flight.
+template <typename T, int VC, int UNR>
 __global__ void __launch_bounds__(32 * TY)
-k_spmm_shifted(int n, int W, int Lp, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
-               const typename ABT<T>::type *__restrict__ ab, const cplx<T> *__restrict__ sig,
-               const cplx<T> *__restrict__ P, cplx<T> *__restrict__ Q, const int32_t *__restrict__ flag,
-               T *__restrict__ part) {
+k_spmm_shifted_rb(int n, int W, int Lp, int rows_per_block, const int32_t *__restrict__ rowptr,
+                  const int32_t *__restrict__ col, const typename ABT<T>::type *__restrict__ ab,
+                  const cplx<T> *__restrict__ sig, const cplx<T> *__restrict__ P, cplx<T> *__restrict__ Q,
+                  const int32_t *__restrict__ flag, T *__restrict__ part) {
     using C = cplx<T>;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int ng = W / VC;
@@ -181,13 +189,37 @@ k_spmm_shifted(int n, int W, int Lp, const int32_t *__restrict__ rowptr, const i
     C mu[VC];
 #pragma unroll
     for (int v = 0; v < VC; ++v) mu[v] = mk((T)0, (T)0);
+    const int r_begin = blockIdx.y * rows_per_block;
+    const int r_end = min(n, r_begin + rows_per_block);
     if (act) {
-        for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
+        for (int row = r_begin + ty; row < r_end; row += TY) {
             const int k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
             C sa[VC], sb[VC];
 #pragma unroll
             for (int v = 0; v < VC; ++v) sa[v] = sb[v] = mk((T)0, (T)0);
-            for (int k = k0; k < k1; ++k) {
+            int k = k0;
+            for (; k + UNR <= k1; k += UNR) {
+                int cc[UNR];
+                typename ABT<T>::type w[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    cc[u] = __ldg(col + k + u);
+                    w[u] = __ldg(ab + k + u);
+                }
+                CV<T, VC> p[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) p[u] = ldcv(P + (int64_t)cc[u] * W + c0);
+#pragma unroll
+                for (int u = 0; u < UNR; ++u)
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        sa[v].x = fma(w[u].x, p[u].v[v].x, sa[v].x);
+                        sa[v].y = fma(w[u].x, p[u].v[v].y, sa[v].y);
+                        sb[v].x = fma(w[u].y, p[u].v[v].x, sb[v].x);
+                        sb[v].y = fma(w[u].y, p[u].v[v].y, sb[v].y);
+                    }
+            }
+            for (; k < k1; ++k) {
                 const int c = __ldg(col + k);
                 const auto w = __ldg(ab + k);
                 const CV<T, VC> p = ldcv(P + (int64_t)c * W + c0);
@@ -206,6 +238,117 @@ k_spmm_shifted(int n, int W, int Lp, const int32_t *__restrict__ rowptr, const i
             const CV<T, VC> pr = ldcv(P + (int64_t)row * W + c0);
 #pragma unroll
             for (int v = 0; v < VC; ++v) mu[v] = cfma(pr.v[v], q.v[v], mu[v]);
+        }
+    }
+    __shared__ T red[TY][32][VC * 2];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        red[ty][tx][2 * v] = mu[v].x;
+        red[ty][tx][2 * v + 1] = mu[v].y;
+    }
+    __syncthreads();
+    if (ty == 0 && cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            T s0 = 0, s1 = 0;
+            for (int y = 0; y < TY; ++y) {
+                s0 += red[y][tx][2 * v];
+                s1 += red[y][tx][2 * v + 1];
+            }
+            T *o = part + ((int64_t)blockIdx.y * W + c0 + v) * 4;
+            o[0] = s0;
+            o[1] = s1;
+        }
+    }
+}
+
+// Row-group variant.  R consecutive rows share one merged (union) column
+// list; every union entry stores R coefficient pairs (zero where a row lacks
+// that column).  Each gathered row of P is then used for R output rows, which
+// cuts the gather traffic by R on 3-dof elasticity (rows of one node share
+// their columns exactly) and by ~R/2 on 2D stencils.  Groups are assigned to
+// CTAs in contiguous ranges.
+template <typename T, int VC, int R, int UNR>
+__global__ void __launch_bounds__(32 * TY)
+k_spmm_shifted_rg(int n, int W, int Lp, int ngroups, int groups_per_block, const int32_t *__restrict__ gptr,
+                  const int32_t *__restrict__ ucol, const typename ABT<T>::type *__restrict__ uab,
+                  const cplx<T> *__restrict__ sig, const cplx<T> *__restrict__ P, cplx<T> *__restrict__ Q,
+                  const int32_t *__restrict__ flag, T *__restrict__ part) {
+    using C = cplx<T>;
+    using AB = typename ABT<T>::type;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    const int c0 = cg * VC;
+    bool act = false;
+    C s = mk((T)0, (T)0);
+    if (cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) act |= flag[c0 + v] == 1;
+        s = sig[c0 / Lp];
+    }
+    C mu[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) mu[v] = mk((T)0, (T)0);
+    const int g_begin = blockIdx.y * groups_per_block;
+    const int g_end = min(ngroups, g_begin + groups_per_block);
+    if (act) {
+        for (int g = g_begin + ty; g < g_end; g += TY) {
+            const int e0 = __ldg(gptr + g), e1 = __ldg(gptr + g + 1);
+            C sa[R][VC], sb[R][VC];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int v = 0; v < VC; ++v) sa[r][v] = sb[r][v] = mk((T)0, (T)0);
+            int e = e0;
+            for (; e + UNR <= e1; e += UNR) {
+                int cc[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) cc[u] = __ldg(ucol + e + u);
+                CV<T, VC> p[UNR];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) p[u] = ldcv(P + (int64_t)cc[u] * W + c0);
+#pragma unroll
+                for (int u = 0; u < UNR; ++u)
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const AB w = __ldg(uab + (int64_t)(e + u) * R + r);
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
+                            sa[r][v].x = fma(w.x, p[u].v[v].x, sa[r][v].x);
+                            sa[r][v].y = fma(w.x, p[u].v[v].y, sa[r][v].y);
+                            sb[r][v].x = fma(w.y, p[u].v[v].x, sb[r][v].x);
+                            sb[r][v].y = fma(w.y, p[u].v[v].y, sb[r][v].y);
+                        }
+                    }
+            }
+            for (; e < e1; ++e) {
+                const int c = __ldg(ucol + e);
+                const CV<T, VC> p = ldcv(P + (int64_t)c * W + c0);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const AB w = __ldg(uab + (int64_t)e * R + r);
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        sa[r][v].x = fma(w.x, p.v[v].x, sa[r][v].x);
+                        sa[r][v].y = fma(w.x, p.v[v].y, sa[r][v].y);
+                        sb[r][v].x = fma(w.y, p.v[v].x, sb[r][v].x);
+                        sb[r][v].y = fma(w.y, p.v[v].y, sb[r][v].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int row = g * R + r;
+                if (row >= n) break;
+                CV<T, VC> q;
+#pragma unroll
+                for (int v = 0; v < VC; ++v) q.v[v] = csub(sa[r][v], cmul(s, sb[r][v]));
+                stcv(Q + (int64_t)row * W + c0, q);
+                const CV<T, VC> pr = ldcv(P + (int64_t)row * W + c0);
+#pragma unroll
+                for (int v = 0; v < VC; ++v) mu[v] = cfma(pr.v[v], q.v[v], mu[v]);
+            }
         }
     }
     __shared__ T red[TY][32][VC * 2];
@@ -484,8 +627,10 @@ __global__ void k_reduce_mu(int W, int gy, const T *__restrict__ part, cplx<T> *
 // host launchers
 // ---------------------------------------------------------------------------
 int krylov_row_groups(const Ctx &ctx, const KrylovDims &d, int prec_fp32) {
+    // The update kernel has the narrowest grid (one pole-slot of Lp columns in
+    // x), so the shared row-group count is sized for it: ~8 CTAs per SM.
     const int VC = prec_fp32 ? 2 : 1;
-    const int gx = (d.W() / VC + 31) / 32;
+    const int gx = (d.Lp / VC + 31) / 32;
     const int target = ctx.sm_count * 8;
     int gy = target / (gx > 0 ? gx : 1);
     const int maxgy = (d.n + TY - 1) / TY;
@@ -529,14 +674,30 @@ void krylov_spmm(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const cplx<T
     constexpr int VC = VecN<T>::VC;
     const int W = d.W();
     dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
-    // algorithmic bytes: pattern + (a,b) pairs once, P read once, Q written once
-    const double bytes = 4.0 * (d.n + 1) + (double)A.nnz * (4 + 2 * sizeof(T)) + 2.0 * d.n * W * sizeof(cplx<T>);
-    const double flops = 8.0 * (double)A.nnz * W;
+    // algorithmic bytes: pattern + (a,b) pairs once, P read once and Q written
+    // once for the active columns (converged columns are skipped)
+    const double bytes = 4.0 * (d.n + 1) + (double)A.nnz * (4 + 2 * sizeof(T)) +
+                         2.0 * d.n * W * d.frac * sizeof(cplx<T>);
+    const double flops = 8.0 * (double)A.nnz * W * d.frac;
+    const auto *abp =
+        reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.ab32 : (const void *)A.ab64);
     ctx.before(KC_SHIFTED_SPMM, bytes, flops);
-    k_spmm_shifted<T, VC><<<grid, block, 0, ctx.stream>>>(
-        d.n, W, d.Lp, A.rowptr, A.col,
-        reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.ab32 : (const void *)A.ab64),
-        sig, P, Q, flag, part);
+    if (A.rg_rows > 1) {
+        const int gpb = (A.rg_ngroups + gy - 1) / gy;
+        const auto *uab = reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.rg_ab32
+                                                                                          : (const void *)A.rg_ab64);
+#define RGL(RR)                                                                                                  \
+    k_spmm_shifted_rg<T, VC, RR, 4><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, A.rg_ngroups, gpb, A.rg_ptr,     \
+                                                                    A.rg_col, uab, sig, P, Q, flag, part)
+        if (A.rg_rows == 2) RGL(2);
+        else if (A.rg_rows == 3) RGL(3);
+        else RGL(4);
+#undef RGL
+    } else {
+        const int rpb = (d.n + gy - 1) / gy;
+        k_spmm_shifted_rb<T, VC, 4><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, rpb, A.rowptr, A.col, abp, sig, P,
+                                                                     Q, flag, part);
+    }
     ctx.after();
 }
 
@@ -553,9 +714,9 @@ static void launch_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
     constexpr int VC = VecN<T>::VC;
     const int W = d.W();
     dim3 grid((d.Lp / VC + 31) / 32, kb.gy), block(32, TY);
-    const double vb = (double)d.n * W * sizeof(cplx<T>);
+    const double vb = (double)d.n * W * d.frac * sizeof(cplx<T>);
     ctx.before(KC_KRYLOV_UPDATE, 4 * vb + 2.0 * d.n * d.Lp * sizeof(T) + (double)d.n * d.N * sizeof(cplx<T>),
-               16.0 * d.n * W);
+               16.0 * d.n * W * d.frac);
     k_update<T, VC, NP><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv, kb.s.alpha,
                                                          kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
     ctx.after();
@@ -586,8 +747,8 @@ void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
     constexpr int VC = VecN<T>::VC;
     const int W = d.W();
     dim3 grid((W / VC + 31) / 32, kb.gy), block(32, TY);
-    const double vb = (double)d.n * W * sizeof(cplx<T>);
-    ctx.before(KC_KRYLOV_DIR, 3 * vb + (double)d.n * d.N * sizeof(cplx<T>), 10.0 * d.n * W);
+    const double vb = (double)d.n * W * d.frac * sizeof(cplx<T>);
+    ctx.before(KC_KRYLOV_DIR, 3 * vb + (double)d.n * d.N * sizeof(cplx<T>), 10.0 * d.n * W * d.frac);
     k_direction<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.dinv, kb.s.beta, kb.s.flag);
     ctx.after();
 }

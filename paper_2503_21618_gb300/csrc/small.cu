@@ -125,9 +125,17 @@ void small_chol_upper(Ctx &ctx, int m, double *G, int32_t *status) {
 }
 
 // ---------------------------------------------------------------------------
-// X = R^{-1}, R upper triangular; thread per column, back substitution
+// X = R^{-1}, R upper triangular; one thread per column, back substitution,
+// with R staged in shared memory when it fits
 // ---------------------------------------------------------------------------
-__global__ void k_triinv_upper(int m, const double *__restrict__ R, double *__restrict__ X) {
+__global__ void k_triinv_upper(int m, const double *__restrict__ Rg, double *__restrict__ X, int use_smem) {
+    extern __shared__ double Rs[];
+    const double *R = Rg;
+    if (use_smem) {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) Rs[e] = Rg[e];
+        __syncthreads();
+        R = Rs;
+    }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
         for (int i = m - 1; i > j; --i) X[(int64_t)i * m + j] = 0.0;
         for (int i = j; i >= 0; --i) {
@@ -139,8 +147,15 @@ __global__ void k_triinv_upper(int m, const double *__restrict__ R, double *__re
 }
 
 void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv) {
+    const size_t smem = (size_t)m * m * sizeof(double);
+    const int use_smem = smem <= 200 * 1024;
     ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
-    k_triinv_upper<<<(m + 63) / 64, 64, 0, ctx.stream>>>(m, R, Rinv);
+    if (use_smem) {
+        cudaFuncSetAttribute(k_triinv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_triinv_upper<<<1, ((m + 31) / 32) * 32, smem, ctx.stream>>>(m, R, Rinv, 1);
+    } else {
+        k_triinv_upper<<<(m + 63) / 64, 64, 0, ctx.stream>>>(m, R, Rinv, 0);
+    }
     ctx.after();
 }
 
@@ -157,16 +172,18 @@ __device__ __forceinline__ void rr_pair(int k, int r, int mp, int &a, int &b) {
 template <typename T>
 __global__ void __launch_bounds__(1024)
 k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict__ Vg, double *__restrict__ lam,
-         double *__restrict__ Q, int max_sweeps, int use_smem, int32_t *__restrict__ info) {
+         double *__restrict__ Q, int max_sweeps, int use_smem, int32_t *__restrict__ info, float rel_tol) {
     extern __shared__ unsigned char smraw[];
     T *A = use_smem ? reinterpret_cast<T *>(smraw) : Ag;
     T *V = use_smem ? A + (size_t)m * m : Vg;
     const int tid = threadIdx.x, bs = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
     const int mp = m + (m & 1);
     const int npair = mp / 2;
     __shared__ T cs[512], sn[512];
     __shared__ int pp[512], qq[512];
     __shared__ int nrot;
+    __shared__ float maxrel;
     __shared__ double red[32];
     __shared__ T absmin;
 
@@ -174,26 +191,26 @@ k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict_
     for (int e = tid; e < m * m; e += bs) {
         const double v = S[e];
         A[e] = (T)v;
-        V[e] = (T)((e / m) == (e % m) ? 1 : 0);
         fro += v * v;
     }
-    // block reduce of ||S||_F^2
+    for (int i = warp; i < m; i += nwarp)
+        for (int j = lane; j < m; j += 32) V[i * m + j] = (T)(i == j ? 1 : 0);
     for (int off = 16; off > 0; off >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, off);
-    if ((tid & 31) == 0) red[tid >> 5] = fro;
+    if (lane == 0) red[warp] = fro;
     __syncthreads();
     if (tid == 0) {
         double t = 0;
-        for (int w = 0; w < (bs + 31) / 32; ++w) t += red[w];
-        const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
-        // FP32 only needs eigenvectors good enough for the FP64 refinement
-        absmin = (T)(sqrt(t) * (double)eps * (sizeof(T) == 4 ? 1.0 / sqrt((double)m) : 0.5 / (double)m));
+        for (int w = 0; w < nwarp; ++w) t += red[w];
+        absmin = (T)(sqrt(t) * (double)rel_tol * (sizeof(T) == 4 ? 1.0 / sqrt((double)m) : 0.5 / (double)m));
     }
     __syncthreads();
-    const T eps = sizeof(T) == 4 ? (T)FLT_EPSILON : (T)DBL_EPSILON;
 
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        if (tid == 0) nrot = 0;
+        if (tid == 0) {
+            nrot = 0;
+            maxrel = 0.f;
+        }
         __syncthreads();
         for (int r = 0; r < mp - 1; ++r) {
             for (int k = tid; k < npair; k += bs) {
@@ -204,13 +221,15 @@ k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict_
                 if (q < m) {
                     const T apq = A[p * m + q];
                     const T app = A[p * m + p], aqq = A[q * m + q];
-                    const T thr = eps * sqrt(fabs(app * aqq));
-                    if (fabs(apq) > thr && fabs(apq) > absmin) {
+                    const T scale = sqrt(fabs(app * aqq));
+                    if (fabs(apq) > (T)rel_tol * scale && fabs(apq) > absmin) {
                         const T th = (aqq - app) / (2 * apq);
                         const T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt((T)1 + th * th));
                         c = (T)1 / sqrt((T)1 + t * t);
                         s = t * c;
                         atomicAdd(&nrot, 1);
+                        const float rel = (float)(fabs(apq) / (scale > 0 ? scale : (T)1));
+                        atomicMax(reinterpret_cast<int *>(&maxrel), __float_as_int(rel));
                     }
                 }
                 cs[k] = c;
@@ -219,31 +238,33 @@ k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict_
                 qq[k] = (q < m && s != (T)0) ? q : -1;
             }
             __syncthreads();
-            // rows: A <- J^T A
-            for (int e = tid; e < npair * m; e += bs) {
-                const int k = e / m, col = e % m;
+            // rows: A <- J^T A (warp per pair, lanes over columns)
+            for (int k = warp; k < npair; k += nwarp) {
                 const int q = qq[k];
                 if (q < 0) continue;
                 const int p = pp[k];
                 const T c = cs[k], s = sn[k];
-                const T apk = A[p * m + col], aqk = A[q * m + col];
-                A[p * m + col] = c * apk - s * aqk;
-                A[q * m + col] = s * apk + c * aqk;
+                for (int col = lane; col < m; col += 32) {
+                    const T apk = A[p * m + col], aqk = A[q * m + col];
+                    A[p * m + col] = c * apk - s * aqk;
+                    A[q * m + col] = s * apk + c * aqk;
+                }
             }
             __syncthreads();
             // columns: A <- A J, V <- V J
-            for (int e = tid; e < npair * m; e += bs) {
-                const int k = e / m, row = e % m;
+            for (int k = warp; k < npair; k += nwarp) {
                 const int q = qq[k];
                 if (q < 0) continue;
                 const int p = pp[k];
                 const T c = cs[k], s = sn[k];
-                const T akp = A[row * m + p], akq = A[row * m + q];
-                A[row * m + p] = c * akp - s * akq;
-                A[row * m + q] = s * akp + c * akq;
-                const T vkp = V[row * m + p], vkq = V[row * m + q];
-                V[row * m + p] = c * vkp - s * vkq;
-                V[row * m + q] = s * vkp + c * vkq;
+                for (int row = lane; row < m; row += 32) {
+                    const T akp = A[row * m + p], akq = A[row * m + q];
+                    A[row * m + p] = c * akp - s * akq;
+                    A[row * m + q] = s * akp + c * akq;
+                    const T vkp = V[row * m + p], vkq = V[row * m + q];
+                    V[row * m + p] = c * vkp - s * vkq;
+                    V[row * m + q] = s * vkp + c * vkq;
+                }
             }
             __syncthreads();
             for (int k = tid; k < npair; k += bs) {
@@ -255,7 +276,12 @@ k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict_
             }
             __syncthreads();
         }
-        if (nrot == 0) break;
+        // Jacobi converges quadratically: once every rotation of a sweep was
+        // below sqrt(rel_tol) (relative), the next sweep would find nothing.
+        if (nrot == 0 || maxrel < sqrtf(rel_tol)) {
+            ++sweep;
+            break;
+        }
         __syncthreads();
     }
     // sort eigenvalues ascending (rank sort), permute columns into Q (FP64)
@@ -308,11 +334,14 @@ k_jacobi_coop(int m, double *__restrict__ A, double *__restrict__ V, double *__r
                     apq = A[(int64_t)p * m + q];
                     app = A[(int64_t)p * m + p];
                     aqq = A[(int64_t)q * m + q];
-                    if (fabs(apq) > eps * sqrt(fabs(app * aqq)) && fabs(apq) > absmin) {
+                    const double scale = sqrt(fabs(app * aqq));
+                    if (fabs(apq) > eps * scale && fabs(apq) > absmin) {
                         const double th = (aqq - app) / (2 * apq);
                         t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
                         c = 1.0 / sqrt(1.0 + t * t);
                         s = t * c;
+                        // every applied rotation counts: near-degenerate pairs
+                        // converge only once they stop rotating
                         if (blockIdx.x == 0) atomicAdd(&cnt[sweep & 1], 1);
                     }
                 }
@@ -363,7 +392,10 @@ k_jacobi_coop(int m, double *__restrict__ A, double *__restrict__ V, double *__r
         }
         const int n_rot = *(volatile int *)&cnt[sweep & 1];
         grid.sync();
-        if (n_rot == 0) break;
+        if (n_rot == 0) {
+            ++sweep;
+            break;
+        }
     }
     for (int64_t i = gtid; i < m; i += gsz) lam[i] = A[i * m + i];
     if (gtid == 0 && info) *info = sweep;
@@ -451,7 +483,11 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
     ctx.before(KC_SMALL_DENSE, 8.0 * m2, 0);
     k_identity<<<(unsigned)((m2 + 255) / 256), 256, 0, ctx.stream>>>(m, Vm);
     ctx.after();
-    if (mode == 0) {
+    // The FP32 stage needs A and V in one block's shared memory (m <= 160);
+    // larger problems go straight to the cooperative FP64 Jacobi.
+    const size_t smem = 2 * m2 * sizeof(float);
+    const int use_smem = smem <= 200 * 1024;
+    if (mode == 0 || !use_smem) {
         cudaMemcpyAsync(Tm, S, m2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream);
         coop_jacobi(ctx, m, Tm, Vm, lam0, 60, normA, cnt);
         ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
@@ -459,13 +495,11 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
         ctx.after();
         return;
     }
-    // stage 1: FP32 Jacobi in shared memory (global fallback for large m)
-    const size_t smem = 2 * m2 * sizeof(float);
-    const int use_smem = smem <= 200 * 1024;
-    if (use_smem) cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // stage 1: FP32 Jacobi in shared memory
+    cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ctx.before(KC_SMALL_DENSE, 24.0 * m2, 9.0 * (double)m * m2 * 8);
-    k_jacobi<float><<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, S, (float *)Ag, (float *)Vg, lam0, S0, 40,
-                                                                    use_smem, nullptr);
+    k_jacobi<float><<<1, 1024, smem, ctx.stream>>>(m, S, (float *)Ag, (float *)Vg, lam0, S0, 40, 1, nullptr,
+                                                      1e-6f);
     ctx.after();
     // stage 2: FP64 re-orthonormalisation S1 = S0 R^{-1}, G = S0^T S0 = R^T R
     dgemm(ctx, 1, 0, m, m, m, S0, m, S0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);

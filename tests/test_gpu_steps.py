@@ -29,14 +29,15 @@ def _cplx_block(n, N, m, ldp, seed):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("pencil,N,m", [("2d", 3, 37), ("3d", 2, 10), ("1d", 1, 1), ("2d", 9, 5)])
-def test_shifted_spmm_matches_oracle(api, prec, pencil, N, m):
+@pytest.mark.parametrize("pencil,N,m,rows", [("2d", 3, 37, 0), ("3d", 2, 10, 0), ("1d", 1, 1, 0), ("2d", 9, 5, 0),
+                                             ("2d", 2, 12, 1), ("2d", 2, 12, 3), ("2d", 4, 6, 4), ("3d", 1, 4, 2)])
+def test_shifted_spmm_matches_oracle(api, prec, pencil, N, m, rows):
     p = {"2d": lambda: pencil_2d_q1(23, seed=4), "3d": lambda: pencil_3d_elasticity(5, seed=2),
          "1d": lambda: pencil_1d(77)}[pencil]()
     s, w = poles.quadrature_poles("gauss_legendre", N, 300.0)
     ldp = m + (m & 1)
     P = _cplx_block(p.n, N, m, ldp, 1)
-    h = api.Handle(p)
+    h = api.Handle(p, api.default_opts(spmm_rows=rows))
     f = api.Filter(s, w)
     cdt = np.complex64 if prec == "fp32" else np.complex128
     Pd = torch.from_numpy(P.astype(cdt).view(np.float32 if prec == "fp32" else np.float64).copy()).cuda()
