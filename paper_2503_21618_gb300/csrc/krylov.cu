@@ -160,9 +160,13 @@ k_init(int n, int W, int Lp, int N, int m, const double *__restrict__ rhs, int64
 // ---------------------------------------------------------------------------
 // K1: shifted block SpMM Q = (A - sigma_j B) P, fused mu = P^T Q partials.
 // Two forms: plain CSR rows (rows_per_block consecutive rows per CTA) and row
-// groups (below).  Measured on the 2D Q1 pencil (all 600 columns active):
+// groups (below).  Measured on the 2D Q1 pencil (mean launch over a solve):
 // grid-strided rows 330 us, contiguous row blocks 355 us, row groups of 2
-// 280 us, row groups of 4 396 us per launch.
+// 280 us, row groups of 4 396 us.  Alternatives measured and dropped
+// (standalone launch, all 600 columns, L2 flushed, row groups of 2: 371 us):
+// warp-cooperative index loads broadcast by shuffles (same), cp.async
+// staging of the gathers in shared memory (500-570 us), unroll depth 6 / 12
+// (433 / 363 us).
 // ---------------------------------------------------------------------------
 // Variant with contiguous row blocks (rows_per_block consecutive rows per CTA,
 // so consecutive warps reuse the same gathered P rows in L1) and the nonzeros
