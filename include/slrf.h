@@ -46,7 +46,8 @@ typedef enum {
     SLRF_STAGNATION = 7,          /* residuals stopped decreasing; outputs written   */
     SLRF_BREAKDOWN = 8,           /* Krylov breakdown in every remaining column      */
     SLRF_SUBSPACE_TOO_SMALL = 9,  /* all L Ritz values lie in (0, gamma]             */
-    SLRF_CHOLQR_FAIL = 10         /* B-Gram matrix not numerically positive definite */
+    SLRF_CHOLQR_FAIL = 10,        /* B-Gram matrix not numerically positive definite */
+    SLRF_PENDING = 11             /* server request not finished yet                 */
 } slrf_status;
 
 typedef struct slrf_handle slrf_handle;
@@ -221,6 +222,64 @@ slrf_status slrf_syev(slrf_handle *h, int32_t m, const double *S, double *lam, d
  * projection, small eigenproblem and residual steps. */
 slrf_status slrf_rayleigh_ritz(slrf_handle *h, int32_t m, const double *U, int64_t ldu,
                                double *theta, double *X, int64_t ldx, double *resid);
+
+/* ---- many problems ---------------------------------------------------------- */
+
+/* Algorithm 1 for nprob independent problems at once.  Problem i uses handle
+ * h[i] (all distinct; create each on its own CUDA stream so that the problems'
+ * kernels overlap), filter f[i], interval (0, gamma[i]], subspace size L[i] and
+ * the device buffers V0[i] (ld ldv[i]), theta[i], X[i] (ld ldx[i]), resid[i],
+ * with the layouts of slrf_subspace_iterate.  n_threads host threads drive
+ * the problems (<= 0: one per problem).  status[i] and n_conv[i] (and rep[i]
+ * if rep != NULL) receive each problem's outcome.  Returns SLRF_OK if every
+ * problem returned SLRF_OK, else the first other status.  All reductions run
+ * in a fixed order, so each problem's outputs are bit-identical to solving it
+ * alone.  (Batched pencils of the spec workload; the paper solves one
+ * pencil at a time, Section 4.) */
+slrf_status slrf_batch_iterate(int32_t nprob, slrf_handle *const *h, const slrf_filter *f,
+                               const double *gamma, const int32_t *L, const double *const *V0,
+                               const int64_t *ldv, double tol, int32_t max_outer,
+                               double *const *theta, double *const *X, const int64_t *ldx,
+                               double *const *resid, int32_t *n_conv, slrf_status *status,
+                               slrf_report *rep, int32_t n_threads);
+
+/* A request server: eigen-solve requests of any size and interval are queued,
+ * admitted in arrival order as soon as their device-memory estimate
+ * (slrf_request_bytes) fits in the free part of the server's budget, and run
+ * by n_workers worker threads, each on its own stream and handle, so that
+ * requests arriving while others run overlap with them on the GPU. */
+typedef struct slrf_server slrf_server;
+typedef struct {
+    slrf_pencil pencil;   /* host CSR (on_device must be 0); copied at submit   */
+    slrf_filter filter;   /* host arrays; copied at submit                      */
+    double gamma;         /* interval (0, gamma]                                */
+    int32_t L;            /* subspace size                                      */
+    const double *V0;     /* host n x L row-major start block; copied at submit */
+    double tol;           /* outer tolerance on rho_i                           */
+    int32_t max_outer;
+    slrf_opts opts;       /* per-request options (slrf_opts_default)            */
+} slrf_request;
+
+/* Device bytes a request is admitted with (pencil + workspace + staging). */
+int64_t slrf_request_bytes(const slrf_request *r);
+/* Create a server on the current device with n_workers (1..64) workers and a
+ * device-memory budget in bytes (0: 90 % of the currently free memory). */
+slrf_status slrf_server_create(slrf_server **s, int32_t n_workers, int64_t mem_budget);
+/* Queue a request; *ticket identifies it.  SLRF_EBUDGET if it can never fit. */
+slrf_status slrf_server_submit(slrf_server *s, const slrf_request *r, int64_t *ticket);
+/* Fetch a finished request: with wait = 0 returns SLRF_PENDING if it is still
+ * queued or running; otherwise (or once done) copies theta[L], X (n x L, ld L),
+ * resid[L] (any may be NULL), n_conv, rep, latency_ms (submit to completion)
+ * and the request's own status into *result, forgets the ticket and returns
+ * SLRF_OK. */
+slrf_status slrf_server_poll(slrf_server *s, int64_t ticket, int32_t wait, double *theta, double *X,
+                             double *resid, int32_t *n_conv, slrf_report *rep, double *latency_ms,
+                             slrf_status *result);
+/* Queue length, running requests, finished requests, admitted bytes. */
+slrf_status slrf_server_stats(slrf_server *s, int64_t *queued, int64_t *running, int64_t *finished,
+                              int64_t *bytes_in_use);
+/* Finish queued and running requests, then stop the workers and free the server. */
+void slrf_server_destroy(slrf_server *s);
 
 /* ---- allocation-free variant ---------------------------------------------- */
 

@@ -16,7 +16,7 @@ from . import _build
 
 # ---------------------------------------------------------------- constants
 OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
-NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL = 6, 7, 8, 9, 10
+NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PENDING = 6, 7, 8, 9, 10, 11
 PREC_FP64, PREC_MIXED = 0, 1
 KRYLOV_COCG = 0
 PRECOND_NONE, PRECOND_JACOBI = 0, 1
@@ -62,6 +62,11 @@ class slrf_report(C.Structure):
         return d
 
 
+class slrf_request(C.Structure):
+    _fields_ = [("pencil", slrf_pencil), ("filter", slrf_filter), ("gamma", C.c_double), ("L", C.c_int32),
+                ("V0", C.c_void_p), ("tol", C.c_double), ("max_outer", C.c_int32), ("opts", slrf_opts)]
+
+
 _P = C.c_void_p
 _SIGNATURES = {
     "slrf_status_str": (C.c_char_p, [C.c_int]),
@@ -89,6 +94,18 @@ _SIGNATURES = {
                                     C.POINTER(C.c_double)]),
     "slrf_filter_eval": (C.c_int, [C.POINTER(slrf_filter), C.POINTER(C.c_double), C.c_int64,
                                    C.POINTER(C.c_double)]),
+    "slrf_batch_iterate": (C.c_int, [C.c_int32, C.POINTER(_P), C.POINTER(slrf_filter), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int32), C.POINTER(_P), C.POINTER(C.c_int64), C.c_double,
+                                     C.c_int32, C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(_P),
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int), C.POINTER(slrf_report), C.c_int32]),
+    "slrf_request_bytes": (C.c_int64, [C.POINTER(slrf_request)]),
+    "slrf_server_create": (C.c_int, [C.POINTER(_P), C.c_int32, C.c_int64]),
+    "slrf_server_submit": (C.c_int, [_P, C.POINTER(slrf_request), C.POINTER(C.c_int64)]),
+    "slrf_server_poll": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.POINTER(C.c_int32),
+                                   C.POINTER(slrf_report), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+    "slrf_server_stats": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)]),
+    "slrf_server_destroy": (None, [_P]),
     "slrf_gram_noalloc": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, _P]),
     "slrf_noalloc_last_error": (C.c_char_p, []),
 }
@@ -315,3 +332,95 @@ class Handle:
                                          _dptr(resid))
         _check(st, "slrf_rayleigh_ritz", allowed)
         return theta, X, resid
+
+
+# ---------------------------------------------------------------- many problems
+def batch_iterate(handles, filters, gammas, V0s, tol=1e-8, max_outer=50, n_threads=0):
+    """Solve independent problems concurrently (one handle, i.e. one stream, each).
+
+    handles: list of Handle; filters: list of Filter; gammas: floats; V0s: list
+    of torch CUDA tensors (n_i x L_i).  Returns a list of
+    (theta, X, resid, n_conv, status, report) per problem.
+    """
+    import torch
+    k = len(handles)
+    lib = load()
+    torch.cuda.synchronize()   # inputs written on torch's stream must be complete
+    hs = (C.c_void_p * k)(*[h.h for h in handles])
+    fs = (slrf_filter * k)(*[f.c for f in filters])
+    gam = (C.c_double * k)(*gammas)
+    Ls = (C.c_int32 * k)(*[v.shape[1] for v in V0s])
+    outs = [(torch.empty(v.shape[1], dtype=torch.float64, device=v.device), torch.empty_like(v),
+             torch.empty(v.shape[1], dtype=torch.float64, device=v.device)) for v in V0s]
+    v0p = (C.c_void_p * k)(*[v.data_ptr() for v in V0s])
+    ldv = (C.c_int64 * k)(*[v.stride(0) for v in V0s])
+    thp = (C.c_void_p * k)(*[o[0].data_ptr() for o in outs])
+    xp = (C.c_void_p * k)(*[o[1].data_ptr() for o in outs])
+    ldx = (C.c_int64 * k)(*[o[1].stride(0) for o in outs])
+    rp = (C.c_void_p * k)(*[o[2].data_ptr() for o in outs])
+    nconv = (C.c_int32 * k)()
+    st = (C.c_int * k)()
+    reps = (slrf_report * k)()
+    lib.slrf_batch_iterate(k, hs, fs, gam, Ls, v0p, ldv, tol, max_outer, thp, xp, ldx, rp, nconv, st, reps,
+                           n_threads)
+    torch.cuda.synchronize()
+    return [(outs[i][0], outs[i][1], outs[i][2], nconv[i], st[i], reps[i]) for i in range(k)]
+
+
+class Server:
+    """Request server (include/slrf.h slrf_server_*): host inputs, host outputs."""
+
+    def __init__(self, n_workers=2, mem_budget=0):
+        self.lib = load()
+        s = C.c_void_p()
+        _check(self.lib.slrf_server_create(C.byref(s), n_workers, int(mem_budget)), "slrf_server_create")
+        self.s = s
+        self._keep = {}
+
+    def request(self, pencil, f: Filter, gamma, V0, tol=1e-8, max_outer=50, opts=None):
+        arrs = [np.ascontiguousarray(pencil.row_ptr, dtype=np.int32), np.ascontiguousarray(pencil.col_idx, dtype=np.int32),
+                np.ascontiguousarray(pencil.a_val, dtype=np.float64), np.ascontiguousarray(pencil.b_val, dtype=np.float64),
+                np.ascontiguousarray(V0, dtype=np.float64)]
+        r = slrf_request(slrf_pencil(int(pencil.n), int(arrs[1].size), *[x.ctypes.data for x in arrs[:4]], 0), f.c,
+                         float(gamma), int(V0.shape[1]), arrs[4].ctypes.data, float(tol), int(max_outer),
+                         opts or default_opts())
+        return r, arrs
+
+    def bytes(self, req):
+        return self.lib.slrf_request_bytes(C.byref(req[0]))
+
+    def submit(self, pencil, f: Filter, gamma, V0, tol=1e-8, max_outer=50, opts=None):
+        req = self.request(pencil, f, gamma, V0, tol, max_outer, opts)
+        t = C.c_int64()
+        _check(self.lib.slrf_server_submit(self.s, C.byref(req[0]), C.byref(t)), "slrf_server_submit")
+        self._keep[t.value] = (int(pencil.n), int(V0.shape[1]))
+        return t.value
+
+    def poll(self, ticket, wait=True):
+        n, L = self._keep[ticket]
+        theta, X, resid = np.zeros(L), np.zeros((n, L)), np.zeros(L)
+        nconv, lat, res = C.c_int32(), C.c_double(), C.c_int()
+        rep = slrf_report()
+        st = self.lib.slrf_server_poll(self.s, ticket, 1 if wait else 0, theta.ctypes.data, X.ctypes.data,
+                                       resid.ctypes.data, C.byref(nconv), C.byref(rep), C.byref(lat), C.byref(res))
+        if st == PENDING:
+            return None
+        _check(st, "slrf_server_poll")
+        del self._keep[ticket]
+        return theta, X, resid, nconv.value, res.value, rep, lat.value
+
+    def stats(self):
+        q, r, f, b = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        self.lib.slrf_server_stats(self.s, C.byref(q), C.byref(r), C.byref(f), C.byref(b))
+        return {"queued": q.value, "running": r.value, "finished": f.value, "bytes_in_use": b.value}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.slrf_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <complex>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -32,6 +33,40 @@ thread_local std::string g_last_error;
         slrf_status s_ = (expr);                    \
         if (s_ != SLRF_OK) return s_;               \
     } while (0)
+
+// Pinned, device-mapped host words through which the Krylov loop polls its
+// active-column count: one process-wide page handed out in 64-byte slots, so
+// creating or destroying a handle never calls cudaHostAlloc/cudaFreeHost
+// (which can synchronise the device).
+std::mutex g_pin_mu;
+int32_t *g_pin_host = nullptr, *g_pin_dev = nullptr;
+std::vector<int> g_pin_free;
+constexpr int kPinSlots = 1024, kPinStride = 16;
+
+bool pin_acquire(int32_t **hp, int32_t **dp) {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    if (!g_pin_host) {
+        if (cudaHostAlloc((void **)&g_pin_host, (size_t)kPinSlots * kPinStride * 4,
+                          cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&g_pin_dev, g_pin_host, 0) != cudaSuccess) {
+            cudaGetLastError();
+            g_pin_host = g_pin_dev = nullptr;
+            return false;
+        }
+        for (int i = kPinSlots - 1; i >= 0; --i) g_pin_free.push_back(i);
+    }
+    if (g_pin_free.empty()) return false;
+    const int i = g_pin_free.back();
+    g_pin_free.pop_back();
+    *hp = g_pin_host + (size_t)i * kPinStride;
+    *dp = g_pin_dev + (size_t)i * kPinStride;
+    return true;
+}
+
+void pin_release(int32_t *hp) {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_pin_free.push_back((int)((hp - g_pin_host) / kPinStride));
+}
 
 const char *kKernelClassNames[SLRF_NKERNEL_CLASSES] = {
     "shifted_spmm", "krylov_update", "krylov_direction", "krylov_reduce", "krylov_init", "spmm_real",
@@ -126,16 +161,18 @@ slrf_status ensure(slrf_handle *h, Buf &b, size_t bytes) {
     if (h->opts.mem_budget > 0 &&
         h->pencil_bytes + h->ws_bytes - b.bytes + bytes > (size_t)h->opts.mem_budget)
         return SLRF_EBUDGET;
+    // stream-ordered allocation: growing one handle's workspace never waits
+    // for work of other handles on other streams
     if (b.p) {
-        cudaStreamSynchronize(h->ctx.stream);
-        cudaFree(b.p);
+        cudaFreeAsync(b.p, h->ctx.stream);
         h->ws_bytes -= b.bytes;
         b.p = nullptr;
         b.bytes = 0;
     }
-    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&b.p, bytes, h->ctx.stream) != cudaSuccess) {
         cudaGetLastError();
-        g_last_error = "cudaMalloc of " + std::to_string(bytes) + " bytes failed";
+        b.p = nullptr;
+        g_last_error = "device allocation of " + std::to_string(bytes) + " bytes failed";
         return SLRF_ENOMEM;
     }
     b.bytes = bytes;
@@ -633,6 +670,24 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
 
 }  // namespace
 
+namespace slrf {
+size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count) {
+    const size_t Lp = (size_t)(L + 1) / 2 * 2, W = (size_t)N * Lp;
+    const size_t ts = precision == SLRF_PREC_MIXED ? 4 : 8;   // Krylov real type
+    const size_t gy = std::max<size_t>(1, std::min<size_t>((size_t)(n + 7) / 8, (size_t)sm_count * 8));
+    const size_t pencil = (size_t)(n + 1) * 4 + (size_t)nnz * (4 + 8 + 8 + 8 + 16) + (size_t)n * 16 +
+                          (size_t)nnz * (4 + 3 * 24) + (size_t)n * 4;
+    const size_t krylov = 3 * (size_t)n * W * 2 * ts + (size_t)n * N * 2 * ts + (size_t)n * Lp * ts +
+                          gy * W * 4 * ts + W * (8 * ts + 40) + 4096;
+    const size_t split = (size_t)sm_count * 4;
+    const size_t rr = 8 * (size_t)n * L * 8 + split * L * L * 8 + (40 * (size_t)L * L + 64 * (size_t)L) * 8 +
+                      (size_t)sm_count * 12 * L * 8 + 8192;
+    return pencil + krylov + rr;
+}
+}  // namespace slrf
+
+int slrf::handle_device(const slrf_handle *h) { return h->device; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -651,6 +706,7 @@ const char *slrf_status_str(slrf_status s) {
         case SLRF_BREAKDOWN: return "SLRF_BREAKDOWN";
         case SLRF_SUBSPACE_TOO_SMALL: return "SLRF_SUBSPACE_TOO_SMALL";
         case SLRF_CHOLQR_FAIL: return "SLRF_CHOLQR_FAIL";
+        case SLRF_PENDING: return "SLRF_PENDING";
     }
     return "SLRF_UNKNOWN";
 }
@@ -697,17 +753,17 @@ slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
 
 void slrf_destroy(slrf_handle *h) {
     if (!h) return;
-    cudaStreamSynchronize(h->ctx.stream);
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rW1, &h->rQ1, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
                    &h->rTheta, &h->rRho, &h->hostV, &h->hostX};
     for (Buf *b : bufs)
-        if (b->p) cudaFree(b->p);
+        if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,
                    h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64};
     for (void *p : pen)
-        if (p) cudaFree(p);
-    if (h->h_pin) cudaFreeHost(h->h_pin);
+        if (p) cudaFreeAsync(p, h->ctx.stream);
+    cudaStreamSynchronize(h->ctx.stream);
+    if (h->h_pin) pin_release(h->h_pin);
     if (h->ev_poll) cudaEventDestroy(h->ev_poll);
     if (h->ev_t0) cudaEventDestroy(h->ev_t0);
     if (h->ev_t1) cudaEventDestroy(h->ev_t1);
@@ -775,7 +831,8 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         return SLRF_EBUDGET;
     }
     auto alloc = [&](void **ptr, size_t bytes) -> bool {
-        if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+        if (cudaMallocAsync(ptr, bytes, h->ctx.stream) != cudaSuccess) {
+            *ptr = nullptr;
             cudaGetLastError();
             return false;
         }
@@ -786,16 +843,11 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
               alloc((void **)&h->A.a, nnz * 8) && alloc((void **)&h->A.b, nnz * 8) &&
               alloc((void **)&h->A.ab32, nnz * 8) && alloc((void **)&h->A.ab64, nnz * 16) &&
               alloc((void **)&h->A.diag_a, n * 8) && alloc((void **)&h->A.diag_b, n * 8) &&
-              cudaHostAlloc((void **)&h->h_pin, 64, cudaHostAllocMapped) == cudaSuccess;
+              pin_acquire(&h->h_pin, &h->d_pin);
     if (!ok) {
         g_last_error = "device allocation of the pencil failed";
         slrf_destroy(h);
         return SLRF_ENOMEM;
-    }
-    if (cudaHostGetDevicePointer((void **)&h->d_pin, h->h_pin, 0) != cudaSuccess) {
-        g_last_error = "mapped host memory is not available";
-        slrf_destroy(h);
-        return SLRF_ECUDA;
     }
     cudaEventCreate(&h->ev_poll);
     cudaEventCreate(&h->ev_t0);
@@ -821,10 +873,12 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         h->A.rg_rows = R;
         h->A.rg_ngroups = (int)(gptr.size() - 1);
         h->A.rg_nnz = U;
-        cudaMemcpy(h->A.rg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(h->A.rg_col, ucol.data(), U * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(h->A.rg_ab32, uab32.data(), uab32.size() * 8, cudaMemcpyHostToDevice);
-        cudaMemcpy(h->A.rg_ab64, uab.data(), uab.size() * 16, cudaMemcpyHostToDevice);
+        // stream-ordered after the allocations; pageable sources are staged
+        // before each call returns
+        cudaMemcpyAsync(h->A.rg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(h->A.rg_col, ucol.data(), U * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(h->A.rg_ab32, uab32.data(), uab32.size() * 8, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(h->A.rg_ab64, uab.data(), uab.size() * 16, cudaMemcpyHostToDevice, s);
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -153,4 +153,11 @@ void small_scale_rows(Ctx &ctx, int m, const double *s, double *T);  // T = diag
 void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode);
 size_t small_syev_work_bytes(int m);
 
+// ---------------------------------------------------------------- api.cu
+// Upper bound of the device bytes a handle needs for a solve of subspace size
+// L with N poles (pencil copies + Krylov state + projection workspace + the
+// staging of the host-buffer entry point).
+size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count);
+int handle_device(const slrf_handle *h);
+
 }  // namespace slrf

@@ -21,6 +21,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.h"
 
@@ -442,22 +443,31 @@ size_t small_syev_work_bytes(int m) {
     return 2 * mp * mp * sizeof(double) + 6 * m2 * sizeof(double) + 2 * (size_t)m * sizeof(double) + 4096;
 }
 
+// At most one cooperative (grid-barrier) kernel of this process is in flight
+// on the device at any time: concurrent handles on other streams take turns,
+// so two partially resident cooperative grids can never wait on each other.
+static std::mutex g_coop_mutex;
+
 static void coop_jacobi(Ctx &ctx, int m, double *A, double *V, double *lam, int max_sweeps, const double *normA,
                         int *cnt) {
-    static int max_blocks = -1;
-    if (max_blocks < 0) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 256, 0);
-        max_blocks = per_sm * ctx.sm_count;
-    }
+    static const int per_sm = [] {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_jacobi_coop, 256, 0);
+        return b;
+    }();
     const int64_t work = (int64_t)((m + 1) / 2) * m;
-    int blocks = (int)std::min<int64_t>((work + 255) / 256, std::min(max_blocks, ctx.sm_count));
+    int blocks = (int)std::min<int64_t>((work + 255) / 256, std::min(per_sm * ctx.sm_count, ctx.sm_count));
     if (blocks < 1) blocks = 1;
     int32_t *info = nullptr;
     void *args[] = {&m, &A, &V, &lam, &max_sweeps, (void *)&normA, &cnt, &info};
+    thread_local cudaEvent_t done = nullptr;
+    if (!done) cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    std::lock_guard<std::mutex> lock(g_coop_mutex);
     ctx.before(KC_SMALL_DENSE, 24.0 * m * m, 9.0 * (double)m * m * m * 3);
     cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(blocks), dim3(256), args, 0, ctx.stream);
     ctx.after();
+    cudaEventRecord(done, ctx.stream);
+    cudaEventSynchronize(done);
 }
 
 void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode) {
