@@ -188,6 +188,83 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# many problems: batched pencils and a served request stream
+# ---------------------------------------------------------------------------
+def serve_stream(pkg, count, n_lo=10000, n_hi=500000, nev_lo=20, nev_hi=200, rate=1.0, workers=2):
+    """Submit a seeded Poisson-arrival stream of 2D/3D eigen-solve requests to
+    the library's server; return latency percentiles and throughput."""
+    import numpy as np
+    from workloads import serving_stream
+    stream = serving_stream(count, n_lo=n_lo, n_hi=n_hi, nev_lo=nev_lo, nev_hi=nev_hi, rate_per_s=rate)
+    filters = [pkg.design_poles("slrf", 4, pr["gamma"], 1.0, 0.01) for _, pr in stream]
+    srv = pkg.api.Server(n_workers=workers)
+    t0 = time.perf_counter()
+    tickets = []
+    for (t_arr, pr), f in zip(stream, filters):
+        delay = t_arr - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(pr["pencil"], f, pr["gamma"], pr["V0"], tol=TOL, max_outer=MAX_OUTER))
+    lat, conv, statuses, sizes = [], 0, [], []
+    for t, (_, pr) in zip(tickets, stream):
+        th, X, r, nc, st, rep, lt = srv.poll(t, wait=True)
+        lat.append(lt)
+        conv += nc if st == pkg.OK else 0
+        statuses.append(int(st))
+        sizes.append(int(pr["pencil"].n))
+    wall = time.perf_counter() - t0
+    srv.close()
+    return {"requests": count, "workers": workers, "arrival_rate_per_s": rate,
+            "n_range": [min(sizes), max(sizes)], "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "eigenpairs_per_s": conv / wall, "wall_s": wall,
+            "converged_eigenpairs": conv, "ok": sum(1 for x in statuses if x == 0)}
+
+
+def run_serve(args, pkg, rank, world):
+    if rank != 0:
+        return
+    res = serve_stream(pkg, args.requests, rate=0.5, workers=4)
+    print(json.dumps({"metric": "served eigenpairs/s and latency (2D/3D FE requests, Poisson arrivals)",
+                      "value": res["eigenpairs_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                      "data": "synthetic", "dtype": "f32/f64", "config": {"workload": "serve"}, "serving": res}),
+          flush=True)
+
+
+def run_batch(args, pkg, rank, world):
+    import torch
+    from workloads import batch_workload
+    probs = batch_workload(args.problems)
+    filters = [pkg.design_poles("slrf", 4, pr["gamma"], 1.0, 0.01) for pr in probs]
+    V0s = [torch.from_numpy(pr["V0"]).cuda() for pr in probs]
+    streams = [torch.cuda.Stream() for _ in probs]
+    handles = [pkg.Handle(pr["pencil"], stream=st) for pr, st in zip(probs, streams)]
+    gam = [pr["gamma"] for pr in probs]
+    pkg.api.batch_iterate(handles, filters, gam, V0s, tol=TOL, max_outer=MAX_OUTER)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = pkg.api.batch_iterate(handles, filters, gam, V0s, tol=TOL, max_outer=MAX_OUTER)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    conv = sum(r[3] for r in res if r[4] == pkg.OK)
+    t0 = time.perf_counter()
+    for h, f, g, v in zip(handles, filters, gam, V0s):
+        h.subspace_iterate(f, g, v, tol=TOL, max_outer=MAX_OUTER)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    if rank == 0:
+        print(json.dumps({"metric": "batched eigenpairs/s (64 FE pencils, n log-uniform in [1k, 50k])",
+                          "value": conv / t_batch, "unit": UNIT, "n_gpus": world, "higher_is_better": True,
+                          "data": "synthetic", "dtype": "f32/f64",
+                          "config": {"workload": "batch", "problems": len(probs),
+                                     "kinds": {k: sum(1 for p in probs if p["kind"] == k) for k in ("1d", "2d", "3d")}},
+                          "seconds_batched": t_batch, "seconds_one_by_one": t_seq,
+                          "eigenpairs_per_s_one_by_one": conv / t_seq, "converged_eigenpairs": conv,
+                          "ok": sum(1 for r in res if r[4] == pkg.OK)}), flush=True)
+    for h in handles:
+        h.close()
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -198,6 +275,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="also time one plain FP64 solve")
+    ap.add_argument("--workload", default="fem2d_q1_300", choices=["fem2d_q1_300", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
+    ap.add_argument("--problems", type=int, default=64, help="batch: number of pencils")
     args = ap.parse_args()
     rank, world, local = dist_env()
 
@@ -220,6 +300,13 @@ def main():
         dist.barrier()
     import paper_2503_21618_gb300 as pkg
     from workloads import config_pencil, interval_for, start_block
+
+    if args.workload == "batch":
+        run_batch(args, pkg, rank, world)
+        return
+    if args.workload == "serve":
+        run_serve(args, pkg, rank, world)
+        return
 
     p = config_pencil(WORKLOAD)
     iv = interval_for(WORKLOAD)
@@ -333,6 +420,7 @@ def main():
         }
         if plain is not None:
             line["plain_fp64"] = plain
+        line["serving"] = serve_stream(pkg, count=8, n_hi=40000, nev_hi=60, rate=4.0, workers=2)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(p, iv, max(outer) if outer else 1)
         print(json.dumps(line), flush=True)

@@ -290,3 +290,82 @@ def interval_for(name: str) -> dict:
     with open(path) as f:
         table = json.load(f)
     return table[name]
+
+
+# --------------------------------------------------------------------------
+# problem streams for the batched and serving workloads
+# --------------------------------------------------------------------------
+def weyl_gamma(kind: str, nev: int) -> float:
+    """An interval end expected to hold about ``nev`` eigenvalues.
+
+    Weyl-law estimates of the counting function N(lambda) of the continuous
+    problems (geometric-mean coefficient 1): 1D Dirichlet N = sqrt(lambda)/pi;
+    2D Dirichlet unit square N = lambda/(4 pi) - sqrt(lambda)/pi; 3D elasticity
+    by an empirical fit (below).  The exact count of a discrete pencil differs
+    by a few per cent; callers size the subspace with slack.
+    """
+    k = nev + 0.5
+    if kind == "1d":
+        return (math.pi * k) ** 2
+    if kind == "2d":
+        s = 2.0 + math.sqrt(4.0 + 4.0 * math.pi * k)
+        return s * s
+    if kind == "3d":
+        # Weyl's leading term undercounts the clamped cube with free faces (its
+        # surface modes); N(lambda) = 0.092 lambda^{3/2} + 0.99 lambda, fitted to
+        # dense spectra of these pencils, is solved for lambda by bisection.
+        lo, hi = 0.0, 1e6
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if 0.092 * mid ** 1.5 + 0.99 * mid < k:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+    raise KeyError(kind)
+
+
+def random_problem(rng, kind: str, n_lo: int, n_hi: int, nev_lo: int, nev_hi: int, seed: int):
+    """One random pencil of the given kind with n log-uniform in [n_lo, n_hi].
+
+    Returns dict(pencil, kind, nev_target, L, gamma, V0).  L = 1.5 NEV
+    (rounded up to even).  The grid size is rounded to the nearest valid one.
+    """
+    n_target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+    nev = int(rng.integers(nev_lo, nev_hi + 1))
+    if kind == "1d":
+        pencil = pencil_1d(max(50, int(round(n_target))))
+    elif kind == "2d":
+        m = max(8, int(round(math.sqrt(n_target)) + 1))
+        pencil = pencil_2d_q1(m, seed=seed)
+    else:
+        p = max(4, int(round((n_target / 3.0) ** (1.0 / 3.0))))
+        pencil = pencil_3d_elasticity(p, seed=seed)
+    L = int(math.ceil(1.5 * nev / 2.0) * 2)
+    L = min(L, pencil.n // 2)
+    return dict(pencil=pencil, kind=kind, nev_target=nev, L=L, gamma=weyl_gamma(kind, nev),
+                V0=start_block(pencil.n, L, seed + 7))
+
+
+def batch_workload(count: int = 64, seed: int = BASE_SEED + 4, n_lo: int = 1000, n_hi: int = 50000):
+    """Independent pencils: kind uniform in {1d, 2d, 3d}, n log-uniform, NEV in [10, 60]."""
+    rng = np.random.default_rng(seed)
+    kinds = ("1d", "2d", "3d")
+    return [random_problem(rng, kinds[int(rng.integers(0, 3))], n_lo, n_hi, 10, 60, seed * 1000 + i)
+            for i in range(count)]
+
+
+def serving_stream(count: int, seed: int = BASE_SEED + 5, n_lo: int = 10000, n_hi: int = 500000,
+                   nev_lo: int = 20, nev_hi: int = 200, rate_per_s: float = 1.0):
+    """A Poisson-arrival request stream of 2D/3D pencils (50/50).
+
+    Returns a list of (arrival_time_s, problem dict) sorted by arrival time.
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        kind = "2d" if rng.uniform() < 0.5 else "3d"
+        out.append((t, random_problem(rng, kind, n_lo, n_hi, nev_lo, nev_hi, seed * 1000 + i)))
+    return out
