@@ -144,7 +144,8 @@ struct slrf_handle {
     size_t ws_bytes = 0;
     // named workspace buffers (grow only)
     Buf kP, kQ, kR, kDinv, kU, kPart, kSig, kScal, kFlags;
-    Buf rW1, rQ1, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
+    Buf rW1, rQ1, rQ2, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
+    int64_t shifted_cholqr = 0;   // Rayleigh-Ritz steps that needed the shifted fallback
     Buf hostV, hostX;   // device staging for the host-buffer entry points
     int32_t *h_pin = nullptr;   // pinned host words for polls
     int32_t *d_pin = nullptr;   // device alias of h_pin
@@ -491,18 +492,48 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     int32_t *st = reinterpret_cast<int32_t *>(s + 2 * m);
     double *syw = reinterpret_cast<double *>(reinterpret_cast<char *>(s + 4 * m));
 
-    // pass 1: G = U^T B U, column scaling, R1 = chol, T1 = S R1^{-1}, Q1 = U T1
+    // pass 1: G = U^T B U, column scaling, R1 = chol, T1 = S R1^{-1}, Q1 = U T1.
+    // If the scaled Gram is not numerically positive definite, R1 comes from
+    // G + s I with the shifted Cholesky-QR shift s = 11 (n m + m (m + 1)) u
+    // ||U S||^2 (Fukaya et al., SIAM J. Sci. Comput. 2020; ||U S||^2 <= m after
+    // the column scaling) and a third pass follows (shifted Cholesky-QR3).
+    const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * m;
+    int32_t *pin_status = h->d_pin + 1;   // mapped: the host reads it after pass 1
     spmm_real(ctx, h->A, m, U, ldu, nullptr, 0, W1, m);
     dgemm(ctx, 1, 0, m, m, (int)n, U, ldu, W1, m, 0.0, G, m, split, spw, KC_GRAM);
     small_colscale(ctx, m, G, s);
-    small_chol_upper(ctx, m, G, st);
-    small_triinv_upper(ctx, m, G, T1);
+    small_chol_upper(ctx, m, G, R1, pin_status, shift);
+    small_triinv_upper(ctx, m, R1, T1);
     small_scale_rows(ctx, m, s, T1);
     dgemm(ctx, 0, 0, (int)n, m, m, U, ldu, T1, m, 0.0, Q1, m, 1, nullptr, KC_TALL_GEMM);
+    CK(cudaEventRecord(h->ev_poll, ctx.stream));
+    CK(cudaEventSynchronize(h->ev_poll));
+    const int32_t st1 = *(volatile int32_t *)(h->h_pin + 1);
+    if (st1 > 0) {
+        if (chol_status) {
+            chol_status[0] = st1;
+            chol_status[1] = 0;
+        }
+        return SLRF_OK;   // reported as SLRF_CHOLQR_FAIL by the caller
+    }
+    if (st1 < 0) {
+        // extra pass on the shifted factor: Q1 <- Q1 R^{-1} with R = chol(Q1^T B Q1)
+        CKS(ensure(h, h->rQ2, (size_t)n * m * sizeof(double)));
+        double *Q2 = as<double>(h->rQ2);
+        spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
+        dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, G, m, split, spw, KC_GRAM);
+        small_chol_upper(ctx, m, G, G, st + 2, 0.0);
+        small_triinv_upper(ctx, m, G, T1);
+        dgemm(ctx, 0, 0, (int)n, m, m, Q1, m, T1, m, 0.0, Q2, m, 1, nullptr, KC_TALL_GEMM);
+        CK(cudaMemcpyAsync(Q1, Q2, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream));
+        h->shifted_cholqr += 1;
+    } else {
+        CK(cudaMemsetAsync(st + 2, 0, sizeof(int32_t), ctx.stream));
+    }
     // pass 2: G2 = Q1^T B Q1, R2 = chol, T2 = R2^{-1}
     spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
     dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, G, m, split, spw, KC_GRAM);
-    small_chol_upper(ctx, m, G, st + 1);
+    small_chol_upper(ctx, m, G, G, st + 1, 0.0);
     small_triinv_upper(ctx, m, G, T2);
     // projected A: A_hat = T2^T (Q1^T A Q1) T2
     spmm_real(ctx, h->A, m, Q1, m, W1, m, nullptr, 0);
@@ -517,7 +548,13 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     dgemm(ctx, 0, 0, m, m, m, T2, m, Sm, m, 0.0, Mm, m, 1, nullptr, KC_SMALL_DENSE);
     dgemm(ctx, 0, 0, (int)n, m, m, Q1, m, Mm, m, 0.0, X, ldx, 1, nullptr, KC_TALL_GEMM);
     spmm_real(ctx, h->A, m, X, ldx, AX, m, BX, m);
-    if (chol_status) CK(cudaMemcpyAsync(chol_status, st, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+    if (chol_status) {
+        // pass 2 (and the extra pass) must succeed; pass 1's status was read above
+        CK(cudaMemcpyAsync(chol_status, st + 1, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        chol_status[0] = chol_status[0] > 0 ? chol_status[0] : (chol_status[1] > 0 ? chol_status[1] : 0);
+        chol_status[1] = 0;
+    }
     return SLRF_OK;
 }
 
@@ -754,7 +791,7 @@ slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
 void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
-                   &h->rW1, &h->rQ1, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
+                   &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
                    &h->rTheta, &h->rRho, &h->hostV, &h->hostX};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);

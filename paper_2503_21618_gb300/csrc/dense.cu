@@ -54,7 +54,10 @@ void spmm_real(Ctx &ctx, const DevPencil &A, int m, const double *X, int64_t ldx
 }
 
 // ---------------------------------------------------------------------------
-// DGEMM, row-major, C = op(A) op(B) (+ beta C), 64x64x16 tiles, 4x4 per thread
+// DGEMM, row-major, C = op(A) op(B) (+ beta C), 64x64x16 tiles, 4x4 per thread.
+// On GB300 the FP64 tensor-core path (mma.sync m8n8k4 f64) measured slower
+// than this CUDA-core kernel on the Gram shapes (0.62 vs 0.70 TFLOP/s at
+// 89 401 x 150, 0.79 vs 0.90 at 187 200 x 300), so FP64 products stay here.
 // ---------------------------------------------------------------------------
 constexpr int BM = 64, BN = 64, BK = 16;
 

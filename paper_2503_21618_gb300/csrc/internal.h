@@ -145,7 +145,9 @@ void copy_block(Ctx &ctx, int n, int m, const double *src, int64_t lds, double *
 // All m x m matrices row-major, device.  status: device int, set nonzero on
 // failure (Cholesky pivot <= 0 or non-finite).
 void small_colscale(Ctx &ctx, int m, double *G, double *s);        // s = 1/sqrt(diag G); G = S G S
-void small_chol_upper(Ctx &ctx, int m, double *G, int32_t *status); // G = R^T R, R upper, in place
+// G + s I = R^T R (R upper) into R (may alias G); s = 0, or shift_on_fail if
+// the unshifted factorisation breaks down (*status = -1 then).
+void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *status, double shift_on_fail);
 void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv);
 void small_scale_rows(Ctx &ctx, int m, const double *s, double *T);  // T = diag(s) T
 // Symmetric eigensolver: lam ascending, Q eigenvectors (columns).  mode 1:

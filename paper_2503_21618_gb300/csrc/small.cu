@@ -70,39 +70,49 @@ void small_scale_rows(Ctx &ctx, int m, const double *s, double *T) {
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky G = R^T R (R upper), one block, right-looking
+// Cholesky G + shift I = R^T R (R upper), one block, right-looking.  G is read
+// and left untouched; R is written to Rg.  If the factorisation of G breaks
+// down (pivot <= 0 or non-finite) and shift_on_fail > 0, it is redone on
+// G + shift_on_fail I (shifted Cholesky-QR) and *status = -1; an
+// unrecoverable breakdown sets *status = k + 1 (k = failing pivot).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_chol_upper(int m, double *__restrict__ G, int32_t *__restrict__ status,
-                                                      int use_smem) {
+__global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *__restrict__ G, double *__restrict__ Rg,
+                                                      int32_t *__restrict__ status, int use_smem,
+                                                      double shift_on_fail) {
     extern __shared__ double sm[];
-    double *A = use_smem ? sm : G;
+    double *A = use_smem ? sm : Rg;
     const int tid = threadIdx.x, bs = blockDim.x;
-    if (use_smem)
-        for (int e = tid; e < m * m; e += bs) A[e] = G[e];
     __shared__ int bad;
     __shared__ double dinv;
-    if (tid == 0) bad = 0;
-    __syncthreads();
-    for (int k = 0; k < m; ++k) {
-        if (tid == 0) {
-            const double d = A[k * m + k];
-            if (!(d > 0.0) || !isfinite(d)) {
-                bad = k + 1;
-            } else {
-                const double r = sqrt(d);
-                A[k * m + k] = r;
-                dinv = 1.0 / r;
+    double shift = 0.0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int e = tid; e < m * m; e += bs) A[e] = G[e] + ((e / m == e % m) ? shift : 0.0);
+        if (tid == 0) bad = 0;
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            if (tid == 0) {
+                const double d = A[k * m + k];
+                if (!(d > 0.0) || !isfinite(d)) {
+                    bad = k + 1;
+                } else {
+                    const double r = sqrt(d);
+                    A[k * m + k] = r;
+                    dinv = 1.0 / r;
+                }
             }
+            __syncthreads();
+            if (bad) break;
+            for (int j = k + 1 + tid; j < m; j += bs) A[k * m + j] *= dinv;
+            __syncthreads();
+            const int r = m - k - 1;
+            for (int e = tid; e < r * r; e += bs) {
+                const int i = k + 1 + e / r, j = k + 1 + e % r;
+                if (j >= i) A[i * m + j] -= A[k * m + i] * A[k * m + j];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (bad) break;
-        for (int j = k + 1 + tid; j < m; j += bs) A[k * m + j] *= dinv;
-        __syncthreads();
-        const int r = m - k - 1;
-        for (int e = tid; e < r * r; e += bs) {
-            const int i = k + 1 + e / r, j = k + 1 + e % r;
-            if (j >= i) A[i * m + j] -= A[k * m + i] * A[k * m + j];
-        }
+        if (!bad || !(shift_on_fail > 0.0) || attempt == 1) break;
+        shift = shift_on_fail;
         __syncthreads();
     }
     if (!bad)
@@ -112,16 +122,16 @@ __global__ void __launch_bounds__(1024) k_chol_upper(int m, double *__restrict__
         }
     __syncthreads();
     if (use_smem)
-        for (int e = tid; e < m * m; e += bs) G[e] = A[e];
-    if (tid == 0) *status = bad;
+        for (int e = tid; e < m * m; e += bs) Rg[e] = A[e];
+    if (tid == 0) *status = bad ? bad : (shift > 0.0 ? -1 : 0);
 }
 
-void small_chol_upper(Ctx &ctx, int m, double *G, int32_t *status) {
+void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *status, double shift_on_fail) {
     const size_t smem = (size_t)m * m * sizeof(double);
     const int use_smem = smem <= 200 * 1024;
     if (use_smem) cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
-    k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, status, use_smem);
+    k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, R, status, use_smem, shift_on_fail);
     ctx.after();
 }
 
@@ -513,7 +523,7 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
     ctx.after();
     // stage 2: FP64 re-orthonormalisation S1 = S0 R^{-1}, G = S0^T S0 = R^T R
     dgemm(ctx, 1, 0, m, m, m, S0, m, S0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
-    small_chol_upper(ctx, m, G, cst);
+    small_chol_upper(ctx, m, G, G, cst, 0.0);
     small_triinv_upper(ctx, m, G, Ym);
     dgemm(ctx, 0, 0, m, m, m, S0, m, Ym, m, 0.0, S1, m, 1, nullptr, KC_SMALL_DENSE);
     // T = S1^T A S1, then polish T by FP64 Jacobi, S = S1 V

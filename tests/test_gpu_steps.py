@@ -139,3 +139,20 @@ def test_rayleigh_ritz_matches_oracle(api, m):
     # Ritz vectors agree up to sign (simple Ritz values)
     sgn = np.sign(np.sum(Xh * X_o, axis=0))
     np.testing.assert_allclose(Xh * sgn[None, :], X_o, atol=1e-8 * np.abs(X_o).max())
+
+
+def test_rayleigh_ritz_survives_dependent_columns(api):
+    # A repeated column (up to 1e-13) makes the B-Gram singular in FP64: the
+    # unshifted Cholesky breaks down and the shifted Cholesky-QR3 fallback
+    # must still return the exact Ritz values of the well-determined part.
+    p = pencil_2d_q1(20, seed=3)
+    A, B = p.A(), p.B()
+    lam, Xe = la.eigh(A.toarray(), B.toarray())
+    U = Xe[:, :6] @ start_block(6, 6, 4)
+    U = np.concatenate([U, U[:, :1] + 1e-13 * start_block(p.n, 1, 5)], axis=1)
+    h = api.Handle(p)
+    theta, X, resid = h.rayleigh_ritz(torch.from_numpy(np.ascontiguousarray(U)).cuda())
+    th = np.sort(theta.cpu().numpy())
+    # six Ritz values reproduce lambda_1..6; the seventh comes from the noise direction
+    hits = [np.min(np.abs(th - l)) / l for l in lam[:6]]
+    assert max(hits) < 1e-9
