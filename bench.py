@@ -230,6 +230,45 @@ def run_serve(args, pkg, rank, world):
           flush=True)
 
 
+def run_filters(args, pkg, rank, world):
+    """The paper's filter comparison (Section 3.2, Tables 4 and 5) on the 2D
+    workload: the same solve with SLRF and circle-quadrature pole sets."""
+    if rank != 0:
+        return
+    import torch
+    from workloads import config_pencil, interval_for, start_block
+    p = config_pencil(WORKLOAD)
+    iv = interval_for(WORKLOAD)
+    g = iv["gamma"]
+    V0 = torch.from_numpy(start_block(p.n, iv["L"], 2505)).cuda()
+    cases = [("SLRF a=1 b=0.01", pkg.design_poles("slrf", 4, g, 1.0, 0.01)),
+             ("SLRF a=0.5 b=0.01", pkg.design_poles("slrf", 4, g, 0.5, 0.01)),
+             ("SLRF a=2 b=0.01", pkg.design_poles("slrf", 4, g, 2.0, 0.01)),
+             ("SLRF a=1 b=1", pkg.design_poles("slrf", 4, g, 1.0, 1.0)),
+             ("midpoint", pkg.design_poles("midpoint", 4, g)),
+             ("Gauss-Legendre", pkg.design_poles("gauss_legendre", 4, g)),
+             ("Gauss-Chebyshev", pkg.design_poles("gauss_chebyshev", 4, g))]
+    h = pkg.Handle(p)
+    rows = []
+    for name, f in cases:
+        h.subspace_iterate(f, g, V0, tol=TOL, max_outer=MAX_OUTER)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        th, X, r, nc, st, rep = h.subspace_iterate(f, g, V0, tol=TOL, max_outer=MAX_OUTER)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        sep = abs(sum((-2.0 * (w / (g - s) ** 2)).real for s, w in zip(f.sigma, f.w)))
+        rows.append({"filter": name, "status": int(st), "converged": int(nc), "seconds": round(t, 3),
+                     "eigenpairs_per_s": round((nc if st == pkg.OK else 0) / t, 2), "outer_iters": rep.outer_iters,
+                     "spmv_total": int(rep.spmv), "spmv_per_outer": round(rep.spmv / max(1, rep.outer_iters), 1),
+                     "iters_per_pole": [round(x, 1) for x in list(rep.iters_per_pole)[:4]],
+                     "min_imag_pole_over_gamma": round(float(min(f.sigma.imag)) / g, 4),
+                     "separation_factor_gamma": round(sep * g, 3)})
+    h.close()
+    print(json.dumps({"metric": "filter comparison (2D Q1 n=89401, 100 eigenpairs, N=4 poles)",
+                      "unit": UNIT, "data": "synthetic", "config": {"workload": WORKLOAD}, "rows": rows}), flush=True)
+
+
 def run_batch(args, pkg, rank, world):
     import torch
     from workloads import batch_workload
@@ -275,7 +314,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain", action="store_true", help="also time one plain FP64 solve")
-    ap.add_argument("--workload", default="fem2d_q1_300", choices=["fem2d_q1_300", "batch", "serve"])
+    ap.add_argument("--workload", default="fem2d_q1_300", choices=["fem2d_q1_300", "batch", "serve", "filters"])
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
     ap.add_argument("--problems", type=int, default=64, help="batch: number of pencils")
     args = ap.parse_args()
@@ -306,6 +345,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, pkg, rank, world)
+        return
+    if args.workload == "filters":
+        run_filters(args, pkg, rank, world)
         return
 
     p = config_pencil(WORKLOAD)
