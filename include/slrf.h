@@ -101,7 +101,10 @@ typedef struct {
     int32_t profile;        /* 1: time each kernel class with CUDA events         (0) */
     int32_t spmm_rows;      /* rows per group of the shifted SpMM (1..4); 0 = auto:
                                3 for 3-dof node-block patterns, else 2             (0) */
-    int32_t reserved[6];
+    int32_t gram_ozaki;     /* Grams of the projection step: 1 = FP64-accurate
+                               int8 tensor-core products (Ozaki splitting),
+                               0 = FP64 CUDA cores                                 (1) */
+    int32_t reserved[5];
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

@@ -40,7 +40,8 @@ class slrf_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("krylov", C.c_int32), ("precond", C.c_int32),
                 ("inner_maxit", C.c_int32), ("inner_tol", C.c_double), ("lock_tol", C.c_double),
                 ("check_every", C.c_int32), ("eig_refine", C.c_int32), ("mem_budget", C.c_int64),
-                ("profile", C.c_int32), ("spmm_rows", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("profile", C.c_int32), ("spmm_rows", C.c_int32), ("gram_ozaki", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class slrf_report(C.Structure):

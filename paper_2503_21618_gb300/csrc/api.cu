@@ -144,6 +144,7 @@ struct slrf_handle {
     size_t ws_bytes = 0;
     // named workspace buffers (grow only)
     Buf kP, kQ, kR, kDinv, kU, kPart, kSig, kScal, kFlags;
+    Buf rOz;   // Ozaki Gram digits and partials
     Buf rW1, rQ1, rQ2, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
     int64_t shifted_cholqr = 0;   // Rayleigh-Ritz steps that needed the shifted fallback
     Buf hostV, hostX;   // device staging for the host-buffer entry points
@@ -471,6 +472,21 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     return SLRF_OK;
 }
 
+// G = X^T Y with the handle's Gram method (int8 tensor-core Ozaki or FP64)
+slrf_status gram(slrf_handle *h, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                 double *G) {
+    Ctx &ctx = h->ctx;
+    if (h->opts.gram_ozaki) {
+        CKS(ensure(h, h->rOz, ozaki_gram_work_bytes(n, m, ctx.sm_count)));
+        ozaki_gram(ctx, n, m, X, ldx, Y, ldy, G, h->rOz.p);
+        return SLRF_OK;
+    }
+    const int split = gram_split(ctx, m, n);
+    CKS(ensure(h, h->rSplit, (size_t)split * m * m * sizeof(double)));
+    dgemm(ctx, 1, 0, m, m, (int)n, X, ldx, Y, ldy, 0.0, G, m, split, as<double>(h->rSplit), KC_GRAM);
+    return SLRF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky-QR2 + Rayleigh-Ritz of span(U): theta (ascending), X = U M, AX, BX
 // (all n x m with leading dimension m except U/X which take ldu/ldx)
@@ -500,7 +516,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * m;
     int32_t *pin_status = h->d_pin + 1;   // mapped: the host reads it after pass 1
     spmm_real(ctx, h->A, m, U, ldu, nullptr, 0, W1, m);
-    dgemm(ctx, 1, 0, m, m, (int)n, U, ldu, W1, m, 0.0, G, m, split, spw, KC_GRAM);
+    CKS(gram(h, n, m, U, ldu, W1, m, G));
     small_colscale(ctx, m, G, s);
     small_chol_upper(ctx, m, G, R1, pin_status, shift);
     small_triinv_upper(ctx, m, R1, T1);
@@ -521,7 +537,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
         CKS(ensure(h, h->rQ2, (size_t)n * m * sizeof(double)));
         double *Q2 = as<double>(h->rQ2);
         spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
-        dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, G, m, split, spw, KC_GRAM);
+        CKS(gram(h, n, m, Q1, m, W1, m, G));
         small_chol_upper(ctx, m, G, G, st + 2, 0.0);
         small_triinv_upper(ctx, m, G, T1);
         dgemm(ctx, 0, 0, (int)n, m, m, Q1, m, T1, m, 0.0, Q2, m, 1, nullptr, KC_TALL_GEMM);
@@ -532,12 +548,12 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     }
     // pass 2: G2 = Q1^T B Q1, R2 = chol, T2 = R2^{-1}
     spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
-    dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, G, m, split, spw, KC_GRAM);
+    CKS(gram(h, n, m, Q1, m, W1, m, G));
     small_chol_upper(ctx, m, G, G, st + 1, 0.0);
     small_triinv_upper(ctx, m, G, T2);
     // projected A: A_hat = T2^T (Q1^T A Q1) T2
     spmm_real(ctx, h->A, m, Q1, m, W1, m, nullptr, 0);
-    dgemm(ctx, 1, 0, m, m, (int)n, Q1, m, W1, m, 0.0, Ah1, m, split, spw, KC_GRAM);
+    CKS(gram(h, n, m, Q1, m, W1, m, Ah1));
     dgemm(ctx, 0, 0, m, m, m, Ah1, m, T2, m, 0.0, R1, m, 1, nullptr, KC_SMALL_DENSE);
     dgemm(ctx, 1, 0, m, m, m, T2, m, R1, m, 0.0, Ah, m, 1, nullptr, KC_SMALL_DENSE);
     ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
@@ -719,7 +735,8 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
     const size_t split = (size_t)sm_count * 4;
     const size_t rr = 8 * (size_t)n * L * 8 + split * L * L * 8 + (40 * (size_t)L * L + 64 * (size_t)L) * 8 +
                       (size_t)sm_count * 12 * L * 8 + 8192;
-    return pencil + krylov + rr;
+    const size_t ozaki = 2 * 7 * (size_t)((L + 63) / 64 * 64) * (size_t)((n + 63) / 64 * 64) + (size_t)sm_count * 4 * L * L * 8;
+    return pencil + krylov + rr + ozaki;
 }
 }  // namespace slrf
 
@@ -767,6 +784,8 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->eig_refine = 1;
     o->mem_budget = 0;
     o->profile = 0;
+    o->spmm_rows = 0;
+    o->gram_ozaki = 1;
     return SLRF_OK;
 }
 
@@ -791,7 +810,7 @@ slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
 void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
-                   &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
+                   &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
                    &h->rTheta, &h->rRho, &h->hostV, &h->hostX};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
@@ -1064,10 +1083,7 @@ slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx
 slrf_status slrf_gram(slrf_handle *h, int32_t m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
                       double *G) {
     if (!h || !X || !Y || !G || m < 1 || ldx < m || ldy < m) return SLRF_EINVAL;
-    const int64_t n = h->A.n;
-    const int split = gram_split(h->ctx, m, n);
-    CKS(ensure(h, h->rSplit, (size_t)split * m * m * sizeof(double)));
-    dgemm(h->ctx, 1, 0, m, m, (int)n, X, ldx, Y, ldy, 0.0, G, m, split, as<double>(h->rSplit), KC_GRAM);
+    CKS(gram(h, h->A.n, m, X, ldx, Y, ldy, G));
     CK(cudaGetLastError());
     return SLRF_OK;
 }

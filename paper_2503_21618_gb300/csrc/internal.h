@@ -141,6 +141,12 @@ void fill_zero(Ctx &ctx, void *p, size_t bytes);
 // Copy a strided row-major block (device).
 void copy_block(Ctx &ctx, int n, int m, const double *src, int64_t lds, double *dst, int64_t ldd);
 
+// ---------------------------------------------------------------- ozaki.cu
+// G = X^T Y (m x m, row-major, ld m) from int8 tensor-core digit products.
+size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count);
+void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
+                void *work);
+
 // ---------------------------------------------------------------- small.cu
 // All m x m matrices row-major, device.  status: device int, set nonzero on
 // failure (Cholesky pivot <= 0 or non-finite).

@@ -1,0 +1,267 @@
+// FP64-accurate Gram G = X^T Y on the integer tensor cores (Ozaki scheme).
+//
+// FP64 arithmetic on this GPU runs at ~1 TFLOP/s (CUDA cores and the FP64
+// tensor path alike, measured), while int8 mma.sync runs at ~150 TOP/s.  The
+// Gram of two tall n x m blocks is therefore computed from exact integer
+// pieces (error-free splitting, Ozaki et al., Numer. Algorithms 59, 2012):
+//
+//  * every column a of X is scaled by 2^-e_a, e_a = exponent of max_i |X_ia|
+//    plus one, so |X_ia 2^-e_a| < 1/2;
+//  * the scaled value is rounded to a fixed-point integer F with 7S fraction
+//    bits and cut into S balanced base-128 digits D_s in [-64, 64] (int8):
+//    X_ia = 2^e_a sum_s D_s,ia 2^(-7(s+1)) + (rounding below 2^(e_a - 7S - 1));
+//  * products of digits are exact in int32 (|D E| <= 2^12; a K-slice of at
+//    most 2^19/(d+1) rows keeps every partial sum below 2^31), and all digit
+//    pairs with the same s + t = d share one scale, so
+//        G_ab = 2^(e_a + f_b) sum_{d < S} 2^(-7(d+2)) sum_{s+t=d} D_s^T E_t;
+//  * the int32 sums are converted to FP64 once per (CTA, d) and the K-slices
+//    are reduced in a fixed order.
+// With S = 7 the truncation error is ~2^-50 relative to max|X_a| max|Y_b| n.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace slrf {
+
+constexpr int OZ_S = 7;          // digits per value
+constexpr int OZ_TM = 64;        // CTA output tile (rows a) = (cols b)
+
+// ---------------------------------------------------------------------------
+// column exponents: e[a] = ilogb(max_i |X_ia|) + 2 (so |X 2^-e| < 1/2)
+// ---------------------------------------------------------------------------
+__global__ void k_oz_colmax(int64_t n, int m, const double *__restrict__ X, int64_t ldx,
+                            unsigned long long *__restrict__ maxbits) {
+    const int a = blockIdx.x * 32 + threadIdx.x;
+    if (a >= m) return;
+    double mx = 0.0;
+    for (int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y; i < n; i += (int64_t)gridDim.y * blockDim.y)
+        mx = fmax(mx, fabs(X[i * ldx + a]));
+    // for non-negative doubles the bit pattern orders like the value
+    atomicMax(maxbits + a, (unsigned long long)__double_as_longlong(mx));
+}
+
+__global__ void k_oz_exponent(int m, const unsigned long long *__restrict__ maxbits, int *__restrict__ e) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    const double mx = __longlong_as_double((long long)maxbits[a]);
+    e[a] = mx > 0.0 ? ilogb(mx) + 2 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// digits: slices[s][a][i] (transposed, row pitch npad bytes), integer-exact
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void oz_digits(double x, int e, int8_t d[OZ_S]) {
+    // F = round(x 2^(7S - e)) exactly, from the integer significand
+    long long F = 0;
+    if (x != 0.0) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+        const int ex = (int)((bits >> 52) & 0x7ff);
+        unsigned long long mant = bits & ((1ull << 52) - 1);
+        int E;
+        if (ex == 0) {
+            E = -1074;                 // subnormal
+        } else {
+            mant |= 1ull << 52;
+            E = ex - 1075;
+        }
+        const int sh = E - e + 7 * OZ_S;   // x 2^(7S-e) = mant 2^sh
+        unsigned long long mag;
+        if (sh >= 0)
+            mag = mant << sh;              // |x 2^-e| < 1/2 keeps this below 2^(7S-1)
+        else if (sh > -64)
+            mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+        else
+            mag = 0;
+        F = (bits >> 63) ? -(long long)mag : (long long)mag;
+    }
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+        const int k = 7 * (OZ_S - 1 - s);
+        long long D;
+        if (k > 0)
+            D = (F + (1ll << (k - 1))) >> k;   // balanced digit (round half up)
+        else
+            D = F;
+        F -= D << k;
+        d[s] = (int8_t)D;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_oz_split(int64_t n, int m, int64_t npad, const double *__restrict__ X, int64_t ldx, const int *__restrict__ e,
+           int8_t *__restrict__ slices, int mpad) {
+    // 32 x 32 tile: read along a (coalesced), write along i (coalesced)
+    __shared__ int8_t tile[OZ_S][32][33];
+    const int a0 = blockIdx.x * 32, i0base = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int64_t i0 = i0base; i0 < npad; i0 += (int64_t)gridDim.y * 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t i = i0 + r;
+            const int a = a0 + tx;
+            int8_t d[OZ_S];
+            const double x = (i < n && a < m) ? X[i * ldx + a] : 0.0;
+            oz_digits(x, a < m ? e[a] : 0, d);
+#pragma unroll
+            for (int s = 0; s < OZ_S; ++s) tile[s][r][tx] = d[s];
+        }
+        __syncthreads();
+        for (int c = ty; c < 32; c += 8) {
+            const int a = a0 + c;
+            if (a < mpad) {
+                const int64_t i = i0 + tx;
+#pragma unroll
+                for (int s = 0; s < OZ_S; ++s) slices[((int64_t)s * mpad + a) * npad + i] = tile[s][tx][c];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IMMA Gram of digit slices: work[z][a][b] = sum_d 2^(-7(d+2)) sum_{s+t=d} D_s^T E_t
+// over the K-slice z.  CTA = 4 warps, 64 x 64 tile, warp 32 x 32 (2 x 4 mma).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void imma16832(int c[4], const unsigned a[4], const unsigned b[2]) {
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128)
+k_oz_gram(int m, int mpad, int64_t npad, int64_t kslice, const int8_t *__restrict__ SX,
+          const int8_t *__restrict__ SY, double *__restrict__ work) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int a_base = blockIdx.y * OZ_TM + (warp >> 1) * 32;
+    const int b_base = blockIdx.x * OZ_TM + (warp & 1) * 32;
+    const int64_t k_begin = blockIdx.z * kslice;
+    const int64_t k_end = min(npad, k_begin + kslice);
+    const int64_t plane = (int64_t)mpad * npad;
+    double acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) acc[i][j][h] = 0.0;
+
+    for (int d = 0; d < OZ_S; ++d) {
+        int c[2][4][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) c[i][j][h] = 0;
+        for (int s = 0; s <= d; ++s) {
+            const int8_t *Xs = SX + s * plane;
+            const int8_t *Yt = SY + (d - s) * plane;
+            for (int64_t k = k_begin; k < k_end; k += 32) {
+                unsigned af[2][4], bf[4][2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int8_t *r0 = Xs + (int64_t)(a_base + i * 16 + g) * npad + k + 4 * q;
+                    const int8_t *r1 = r0 + 8 * npad;
+                    af[i][0] = __ldg(reinterpret_cast<const unsigned *>(r0));
+                    af[i][1] = __ldg(reinterpret_cast<const unsigned *>(r1));
+                    af[i][2] = __ldg(reinterpret_cast<const unsigned *>(r0 + 16));
+                    af[i][3] = __ldg(reinterpret_cast<const unsigned *>(r1 + 16));
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int8_t *r = Yt + (int64_t)(b_base + j * 8 + g) * npad + k + 4 * q;
+                    bf[j][0] = __ldg(reinterpret_cast<const unsigned *>(r));
+                    bf[j][1] = __ldg(reinterpret_cast<const unsigned *>(r + 16));
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) imma16832(c[i][j], af[i], bf[j]);
+            }
+        }
+        const double scale = ldexp(1.0, -7 * (d + 2));
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) acc[i][j][h] = fma((double)c[i][j][h], scale, acc[i][j][h]);
+    }
+    // C fragment: c0, c1 at (row g, cols 2q, 2q+1); c2, c3 at (row g+8, ...)
+    double *W = work + (int64_t)blockIdx.z * m * m;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int a = a_base + i * 16 + g + (h >= 2 ? 8 : 0);
+                const int b = b_base + j * 8 + 2 * q + (h & 1);
+                if (a < m && b < m) W[(int64_t)a * m + b] = acc[i][j][h];
+            }
+}
+
+__global__ void k_oz_reduce(int m, int split, const double *__restrict__ work, const int *__restrict__ ex,
+                            const int *__restrict__ ey, double *__restrict__ G, int64_t ldg) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    const int a = (int)(idx / m), b = (int)(idx % m);
+    double s = 0.0;
+    for (int z = 0; z < split; ++z) s += work[(int64_t)z * m * m + idx];
+    G[(int64_t)a * ldg + b] = ldexp(s, ex[a] + ey[b]);
+}
+
+// ---------------------------------------------------------------------------
+size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count) {
+    const int64_t npad = (n + 63) / 64 * 64;
+    const int mpad = (m + OZ_TM - 1) / OZ_TM * OZ_TM;
+    const size_t slices = 2 * (size_t)OZ_S * mpad * npad;
+    const size_t split = (size_t)sm_count * 4;
+    return slices + split * m * m * sizeof(double) + 2 * (size_t)m * (sizeof(int) + 8) + 1024;
+}
+
+void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
+                void *work) {
+    const int64_t npad = (n + 63) / 64 * 64;
+    const int mpad = (m + OZ_TM - 1) / OZ_TM * OZ_TM;
+    char *w = reinterpret_cast<char *>(work);
+    int8_t *SX = reinterpret_cast<int8_t *>(w);
+    int8_t *SY = SX + (size_t)OZ_S * mpad * npad;
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(SY + (size_t)OZ_S * mpad * npad);
+    int *ex = reinterpret_cast<int *>(mb + 2 * m);
+    int *ey = ex + m;
+    double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(ey + m) + 16 - ((uintptr_t)(ey + m) & 15));
+    const int tiles = mpad / OZ_TM;
+    // K-slices: enough CTAs to fill the GPU, each at most 2^16 rows (int32 bound)
+    int split = (ctx.sm_count * 4 + tiles * tiles - 1) / (tiles * tiles);
+    int64_t kslice = (npad + split - 1) / split;
+    kslice = (kslice + 31) / 32 * 32;
+    if (kslice > 65536) kslice = 65536;
+    split = (int)((npad + kslice - 1) / kslice);
+
+    cudaMemsetAsync(mb, 0, 2 * (size_t)m * sizeof(unsigned long long), ctx.stream);
+    const dim3 cgrid((m + 31) / 32, 64), cblock(32, 8);
+    ctx.before(KC_GRAM, 8.0 * (double)n * m * 2, 0);
+    k_oz_colmax<<<cgrid, cblock, 0, ctx.stream>>>(n, m, X, ldx, mb);
+    k_oz_colmax<<<cgrid, cblock, 0, ctx.stream>>>(n, m, Y, ldy, mb + m);
+    k_oz_exponent<<<(2 * m + 127) / 128, 128, 0, ctx.stream>>>(2 * m, mb, ex);
+    ctx.after();
+    // digits (rows beyond n and columns beyond m become zeros)
+    const dim3 sgrid(mpad / 32, (unsigned)std::min<int64_t>(npad / 32, 4096)), sblock(32, 8);
+    ctx.before(KC_GRAM, 8.0 * (double)n * m * 2 + 2.0 * OZ_S * mpad * npad, 0);
+    k_oz_split<<<sgrid, sblock, 0, ctx.stream>>>(n, m, npad, X, ldx, ex, SX, mpad);
+    k_oz_split<<<sgrid, sblock, 0, ctx.stream>>>(n, m, npad, Y, ldy, ey, SY, mpad);
+    ctx.after();
+    const dim3 ggrid(tiles, tiles, split);
+    const double pairs = OZ_S * (OZ_S + 1) / 2.0;
+    ctx.before(KC_GRAM, 2.0 * OZ_S * mpad * npad, 2.0 * pairs * (double)mpad * mpad * npad);
+    k_oz_gram<<<ggrid, 128, 0, ctx.stream>>>(m, mpad, npad, kslice, SX, SY, part);
+    ctx.after();
+    ctx.before(KC_GRAM, 8.0 * (double)split * m * m, 0);
+    k_oz_reduce<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, ctx.stream>>>(m, split, part, ex, ey, G, m);
+    ctx.after();
+}
+
+}  // namespace slrf

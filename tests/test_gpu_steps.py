@@ -69,15 +69,31 @@ def test_spmm_ab_matches_scipy(api, m):
     np.testing.assert_allclose(Z.cpu().numpy(), p.B() @ X, rtol=1e-13, atol=1e-13 * np.abs(p.B() @ X).max())
 
 
-@pytest.mark.parametrize("n,m", [(1000, 1), (5000, 64), (20011, 150), (3001, 77)])
-def test_gram_matches_numpy(api, n, m):
+@pytest.mark.parametrize("ozaki", [1, 0])
+@pytest.mark.parametrize("n,m", [(1000, 1), (5000, 64), (20011, 150), (3001, 77), (70000, 65)])
+def test_gram_matches_numpy(api, n, m, ozaki):
     p = pencil_1d(n)
     X = start_block(n, m, 1)
     Y = start_block(n, m, 2)
-    h = api.Handle(p)
+    h = api.Handle(p, api.default_opts(gram_ozaki=ozaki))
     G = h.gram(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()).cpu().numpy()
     ref = X.T @ Y
     assert np.abs(G - ref).max() <= 1e-13 * np.abs(X).max() * np.abs(Y).max() * n
+
+
+def test_ozaki_gram_graded_columns(api):
+    # columns spanning 16 orders of magnitude, zero and subnormal-free tiny columns
+    n, m = 9000, 40
+    rng = np.random.default_rng(3)
+    X = start_block(n, m, 4) * 10.0 ** rng.uniform(-8, 8, m)[None, :]
+    Y = start_block(n, m, 5) * 10.0 ** rng.uniform(-8, 8, m)[None, :]
+    X[:, 3] = 0.0
+    h = api.Handle(pencil_1d(n), api.default_opts(gram_ozaki=1))
+    G = h.gram(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()).cpu().numpy()
+    ref = X.T @ Y
+    bound = 1e-13 * np.abs(X).max(axis=0)[:, None] * np.abs(Y).max(axis=0)[None, :] * n
+    assert np.all(np.abs(G - ref) <= bound)
+    assert np.all(G[3] == 0.0)
 
 
 def _sym_with_spectrum(m, lam, seed):
