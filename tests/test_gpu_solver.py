@@ -189,3 +189,29 @@ def test_full_2d_config_matches_stored_oracle_spectrum(api):
     r = p.A() @ xs - (p.B() @ xs) * theta[idx][None, :]
     rho = np.linalg.norm(r, axis=0) / (np.abs(theta[idx]) * np.linalg.norm(p.B() @ xs, axis=0))
     assert rho.max() <= 1e-8
+
+
+# --------------------------------------------------------------------------
+# full 3D elasticity workload (40^3 nodes x 3 dof, one face clamped, L = 300)
+# --------------------------------------------------------------------------
+def test_full_3d_config_matches_stored_oracle_spectrum(api):
+    name = "fem3d_elastic_40"
+    p = config_pencil(name)
+    iv = interval_for(name)
+    lam = np.array(iv["lambda"])
+    f = api.Filter(*poles.slrf_poles(4, 1.0, 0.01, iv["gamma"]))
+    V0 = start_block(p.n, iv["L"], 2506)
+    h = api.Handle(p)
+    theta, X, resid, nconv, st, rep = h.subspace_iterate(f, iv["gamma"], torch.from_numpy(V0).cuda(),
+                                                         tol=1e-8, max_outer=40)
+    theta = theta.cpu().numpy()
+    assert st == api.OK
+    assert nconv == rep.n_wanted == iv["nev"] == iv["inertia_count"]
+    _check_eigs(theta, resid.cpu().numpy(), lam, iv["nev"])
+    Xh = X.cpu().numpy()
+    idx = np.array([0, 1, 77, 150, 199])
+    xs = Xh[:, idx]
+    r = p.A() @ xs - (p.B() @ xs) * theta[idx][None, :]
+    rho = np.linalg.norm(r, axis=0) / (np.abs(theta[idx]) * np.linalg.norm(p.B() @ xs, axis=0))
+    assert rho.max() <= 1e-8
+    np.testing.assert_allclose(xs.T @ (p.B() @ xs), np.eye(len(idx)), atol=1e-10)
