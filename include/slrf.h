@@ -80,7 +80,14 @@ typedef struct {
 enum { SLRF_PREC_FP64 = 0,  /* plain: FP64 Krylov to inner_tol relative to ||B v||        */
        SLRF_PREC_MIXED = 1  /* FP32 Krylov on the FP64 residual R = B X Theta - A X      */ };
 enum { SLRF_KRYLOV_COCG = 0 };
-enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1 };
+/* Preconditioner of the shifted solves.  JACOBI: diag(A - sigma_j B).  MG:
+ * smoothed-aggregation multigrid cycle (one hierarchy for all poles, built
+ * from A; Galerkin pencils (P^T A P, P^T B P) on every level; damped Jacobi
+ * smoothing; exact coarsest solve by the eigendecomposition of the coarsest
+ * pencil).  The paper's own solver is ILU-preconditioned BiCGStab
+ * (Section 4.2.1); both options keep the preconditioner complex symmetric,
+ * as COCG requires. */
+enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1, SLRF_PRECOND_MG = 2 };
 enum { SLRF_RULE_MIDPOINT = 0, SLRF_RULE_GAUSS_LEGENDRE = 1, SLRF_RULE_GAUSS_CHEBYSHEV = 2,
        SLRF_RULE_SLRF = 3 };
 
@@ -104,12 +111,24 @@ typedef struct {
     int32_t gram_ozaki;     /* Grams of the projection step: 1 = FP64-accurate
                                int8 tensor-core products (Ozaki splitting),
                                0 = FP64 CUDA cores                                 (1) */
-    int32_t reserved[5];
+    int32_t mg_nu;          /* MG: Jacobi sweeps per side on the levels below the
+                               finest (the finest always takes one)                (2) */
+    int32_t mg_cycle;       /* MG: coarse visits per level, 1 = V-, 2 = W-cycle    (1) */
+    int32_t mg_coarse;      /* MG: coarsening stops at or below this size         (256) */
+    int32_t mg_block;       /* MG: dofs per node for aggregation, 0 = auto (3 for
+                               3-dof node-block patterns, else 1)                   (0) */
+    double mg_omega;        /* MG: Jacobi damping relative to the spectral radius:
+                               level l smooths with mg_omega / rho(D_l^-1 A_l),
+                               0 < mg_omega < 2                                  (4/3) */
+    double mg_theta;        /* MG: strength-of-connection threshold of the
+                               aggregation, 0 = auto (0.08 for scalar problems,
+                               0.15 for node blocks)                                (0) */
+    int32_t reserved[4];
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the
  * paper: spmv counts one shifted product per (pole, column). */
-#define SLRF_NKERNEL_CLASSES 12
+#define SLRF_NKERNEL_CLASSES 15
 typedef struct {
     int32_t outer_iters;          /* filter applications                         */
     int32_t n_wanted;             /* Ritz values in (0, gamma]                   */
@@ -148,10 +167,13 @@ slrf_status slrf_opts_default(slrf_opts *o);
 /* Create a handle: validate the pencil (n >= 1, CSR monotone, indices in
  * range, finite values), copy it to the current CUDA device in the layouts the
  * kernels use, and bind `cuda_stream` (a cudaStream_t, NULL = legacy default
- * stream).  Problem statement: Section 1, Eq. (1). */
+ * stream).  With opts.precond == SLRF_PRECOND_MG the multigrid hierarchy is
+ * built here (host) and uploaded.  Problem statement: Section 1, Eq. (1). */
 slrf_status slrf_create(slrf_handle **h, const slrf_pencil *p, const slrf_opts *o,
                         void *cuda_stream);
-/* Replace the handle's options (workspace is resized lazily). */
+/* Replace the handle's options (workspace is resized lazily; switching to
+ * SLRF_PRECOND_MG or changing mg_coarse / mg_block / mg_theta rebuilds the
+ * multigrid hierarchy on the next solve). */
 slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o);
 /* Release the handle and all its device memory.  NULL is ignored. */
 void slrf_destroy(slrf_handle *h);
@@ -160,8 +182,8 @@ void slrf_destroy(slrf_handle *h);
 
 /* U = sum_j 2 Re(w_j (A - sigma_j B)^{-1} B V)  (Section 3; Algorithm 1, the
  * solve loop and the accumulation).  V, U: device, n x m row-major.  The N*m
- * shifted systems are solved by Jacobi-preconditioned COCG in the handle's
- * precision to opts.inner_tol relative residual (FP64: Section 4.2.1 uses
+ * shifted systems are solved by preconditioned COCG (opts.precond) in the
+ * handle's precision to opts.inner_tol relative residual (FP64: Section 4.2.1 uses
  * 1e-13).  In MIXED precision the solves run in FP32, so U is accurate to
  * about kappa(A - sigma B) * max(inner_tol, 1e-7); slrf_subspace_iterate
  * recovers FP64 accuracy by filtering the FP64 residual instead.  Returns
@@ -304,6 +326,23 @@ slrf_status slrf_gram_noalloc(int64_t n, int32_t m, const double *X, int64_t ldx
                               int64_t ldy, double *G, void *cuda_stream);
 /* Text of the last error of slrf_gram_noalloc on this thread ("" if none). */
 const char *slrf_noalloc_last_error(void);
+
+/* ---- multigrid hierarchy (inspection) -------------------------------------- */
+
+#define SLRF_MG_MAX_LEVELS 16
+/* Build the SLRF_PRECOND_MG hierarchy of a HOST pencil (p->on_device must be
+ * 0) with the mg_* fields of *o (NULL = defaults), on the host only, and
+ * report it: *n_levels, level_n[l] and level_nnz[l] (arrays of
+ * SLRF_MG_MAX_LEVELS) the size and stored entries of each level pencil,
+ * *setup_ms the host time.  Optional outputs of the coarsest level (size
+ * n_c = level_n[*n_levels - 1]), NULL to skip: coarse_lam[n_c], the
+ * eigenvalues of the coarsest pencil ascending, and coarse_a / coarse_b
+ * (n_c x n_c row-major, dense) the coarsest pencil itself.  No device work.
+ * Returns SLRF_EINVAL for invalid input, SLRF_BREAKDOWN if the setup fails
+ * (message in slrf_last_error()). */
+slrf_status slrf_mg_describe(const slrf_pencil *p, const slrf_opts *o, int32_t *n_levels, int64_t *level_n,
+                             int64_t *level_nnz, double *setup_ms, double *coarse_lam, double *coarse_a,
+                             double *coarse_b);
 
 /* ---- pole/weight sets (host) -------------------------------------------- */
 

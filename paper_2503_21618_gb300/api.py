@@ -19,11 +19,12 @@ OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PENDING = 6, 7, 8, 9, 10, 11
 PREC_FP64, PREC_MIXED = 0, 1
 KRYLOV_COCG = 0
-PRECOND_NONE, PRECOND_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG = 0, 1, 2
 RULE_MIDPOINT, RULE_GAUSS_LEGENDRE, RULE_GAUSS_CHEBYSHEV, RULE_SLRF = 0, 1, 2, 3
 RULES = {"midpoint": 0, "gauss_legendre": 1, "gauss_chebyshev": 2, "slrf": 3}
 MAX_POLES = 16
-NKERNEL_CLASSES = 12
+NKERNEL_CLASSES = 15
+MG_MAX_LEVELS = 16
 
 
 class slrf_pencil(C.Structure):
@@ -41,7 +42,8 @@ class slrf_opts(C.Structure):
                 ("inner_maxit", C.c_int32), ("inner_tol", C.c_double), ("lock_tol", C.c_double),
                 ("check_every", C.c_int32), ("eig_refine", C.c_int32), ("mem_budget", C.c_int64),
                 ("profile", C.c_int32), ("spmm_rows", C.c_int32), ("gram_ozaki", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("mg_nu", C.c_int32), ("mg_cycle", C.c_int32), ("mg_coarse", C.c_int32), ("mg_block", C.c_int32),
+                ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("reserved", C.c_int32 * 4)]
 
 
 class slrf_report(C.Structure):
@@ -109,6 +111,8 @@ _SIGNATURES = {
     "slrf_server_destroy": (None, [_P]),
     "slrf_gram_noalloc": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, _P]),
     "slrf_noalloc_last_error": (C.c_char_p, []),
+    "slrf_mg_describe": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P, _P]),
 }
 
 _lib = None
@@ -195,6 +199,38 @@ def filter_eval(f: Filter, x) -> np.ndarray:
     out = np.zeros_like(x)
     _check(load().slrf_filter_eval(C.byref(f.c), x.ctypes.data_as(C.POINTER(C.c_double)), x.size,
                                    out.ctypes.data_as(C.POINTER(C.c_double))), "slrf_filter_eval")
+    return out
+
+
+def mg_describe(pencil, opts: slrf_opts | None = None, coarse: bool = False) -> dict:
+    """Multigrid hierarchy of a host pencil (built on the host by the library).
+
+    Returns level sizes and stored entries, the setup time and, with
+    ``coarse=True``, the coarsest pencil (dense) and its eigenvalues."""
+    lib = load()
+    keep = [np.ascontiguousarray(pencil.row_ptr, dtype=np.int32),
+            np.ascontiguousarray(pencil.col_idx, dtype=np.int32),
+            np.ascontiguousarray(pencil.a_val, dtype=np.float64),
+            np.ascontiguousarray(pencil.b_val, dtype=np.float64)]
+    p = slrf_pencil(int(pencil.n), int(keep[1].size), *[a.ctypes.data for a in keep], 0)
+    o = opts or default_opts()
+    nl = C.c_int32()
+    ln = (C.c_int64 * MG_MAX_LEVELS)()
+    lz = (C.c_int64 * MG_MAX_LEVELS)()
+    ms = C.c_double()
+    _check(lib.slrf_mg_describe(C.byref(p), C.byref(o), C.byref(nl), ln, lz, C.byref(ms), None, None, None),
+           "slrf_mg_describe")
+    out = {"levels": [int(ln[i]) for i in range(nl.value)], "nnz": [int(lz[i]) for i in range(nl.value)],
+           "setup_ms": ms.value}
+    if coarse:
+        nc = out["levels"][-1]
+        lam = np.zeros(nc)
+        Ac = np.zeros((nc, nc))
+        Bc = np.zeros((nc, nc))
+        _check(lib.slrf_mg_describe(C.byref(p), C.byref(o), C.byref(nl), ln, lz, C.byref(ms),
+                                    lam.ctypes.data_as(C.c_void_p), Ac.ctypes.data_as(C.c_void_p),
+                                    Bc.ctypes.data_as(C.c_void_p)), "slrf_mg_describe")
+        out.update(coarse_lambda=lam, coarse_A=Ac, coarse_B=Bc)
     return out
 
 

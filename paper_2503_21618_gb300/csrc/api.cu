@@ -8,10 +8,12 @@
 #include <algorithm>
 #include <complex>
 #include <mutex>
+#include <type_traits>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+#include "mg.h"
 #include "slrf.h"
 
 using namespace slrf;
@@ -70,7 +72,8 @@ void pin_release(int32_t *hp) {
 
 const char *kKernelClassNames[SLRF_NKERNEL_CLASSES] = {
     "shifted_spmm", "krylov_update", "krylov_direction", "krylov_reduce", "krylov_init", "spmm_real",
-    "gram", "tall_gemm", "small_dense", "residual", "filter_combine", "other"};
+    "gram", "tall_gemm", "small_dense", "residual", "filter_combine", "other", "mg_smooth", "mg_transfer",
+    "mg_coarse"};
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -148,6 +151,17 @@ struct slrf_handle {
     Buf rW1, rQ1, rQ2, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
     int64_t shifted_cholqr = 0;   // Rayleigh-Ritz steps that needed the shifted fallback
     Buf hostV, hostX;   // device staging for the host-buffer entry points
+    // multigrid preconditioner: hierarchy (static), per-solve level blocks, Z
+    Buf mgStatic, mgState, kZ;
+    bool mg_ready = false;
+    int mg_block = 0, mg_coarse = 0;      // parameters the hierarchy was built with
+    double mg_theta = 0.0;
+    std::vector<double> mg_lam;           // coarsest eigenvalues
+    std::vector<int64_t> mg_level_n, mg_level_nnz;
+    double mg_setup_ms = 0.0;
+    std::vector<char> mg_cinv_host;       // staging of 1/(lambda_k - sigma_j)
+    slrf::MgSolve<float> mg32;
+    slrf::MgSolve<double> mg64;
     int32_t *h_pin = nullptr;   // pinned host words for polls
     int32_t *d_pin = nullptr;   // device alias of h_pin
     cudaEvent_t ev_poll = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
@@ -343,6 +357,275 @@ void build_rowgroups(int R, int64_t n, const std::vector<int32_t> &rp, const std
     }
 }
 
+// CSR monotone with sorted, in-range columns, finite values and a positive
+// diagonal in every row (SPD pencils have one).
+bool pencil_valid(int64_t n, int64_t nnz, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                  const std::vector<double> &av, const std::vector<double> &bv) {
+    if (rp[0] != 0 || rp[n] != nnz) return false;
+    for (int64_t i = 0; i < n; ++i) {
+        if (rp[i + 1] < rp[i]) return false;
+        bool diag = false;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            if (ci[k] < 0 || ci[k] >= n) return false;
+            if (k > rp[i] && ci[k] <= ci[k - 1]) return false;
+            if (!isfinite(av[k]) || !isfinite(bv[k])) return false;
+            if (ci[k] == i) diag = av[k] > 0 && bv[k] > 0;
+        }
+        if (!diag) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// multigrid hierarchy: host build, upload, per-solve preparation
+// ---------------------------------------------------------------------------
+int mg_block_for(const slrf_opts &o, int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci) {
+    if (o.mg_block > 0) return o.mg_block;
+    return has_node_blocks(n, rp, ci, 3) ? 3 : 1;
+}
+
+MgParams mg_params(const slrf_opts &o, int block) {
+    MgParams prm;
+    prm.block = block;
+    prm.coarse_target = o.mg_coarse;
+    prm.max_levels = MG_MAX_LEVELS;
+    // node blocks of 3-dof elasticity couple to all 26 neighbours; 0.15 keeps
+    // about the 6 face neighbours, so aggregates stay near 7 nodes
+    prm.theta = o.mg_theta > 0 ? o.mg_theta : (block > 1 ? 0.15 : 0.08);
+    return prm;
+}
+
+// Pack the hierarchy into one device buffer: level pencils (levels
+// 1 .. nlev-2; the coarsest is solved exactly), transfers P and P^T (FP32 and
+// FP64 values), coarsest eigenvectors (FP32 and FP64).
+slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
+    const int nlev = (int)H.lv.size();
+    if (nlev > MG_MAX_LEVELS) {
+        g_last_error = "multigrid setup: too many levels";
+        return SLRF_BREAKDOWN;
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    struct LvOff {
+        size_t ptr = 0, col = 0, ab32 = 0, ab64 = 0, da = 0, db = 0;
+        size_t pptr = 0, pcol = 0, pv32 = 0, pv64 = 0, rptr = 0, rcol = 0, rv32 = 0, rv64 = 0;
+    };
+    std::vector<LvOff> lo(nlev);
+    for (int l = 0; l < nlev; ++l) {
+        const HostLevel &L = H.lv[l];
+        if (l >= 1 && l < nlev - 1) {
+            const size_t nz = L.col.size();
+            lo[l].ptr = take((L.n + 1) * 4);
+            lo[l].col = take(nz * 4);
+            lo[l].ab32 = take(nz * 8);
+            lo[l].ab64 = take(nz * 16);
+            lo[l].da = take(L.n * 8);
+            lo[l].db = take(L.n * 8);
+        }
+        if (l < nlev - 1) {
+            const size_t pz = L.P.col.size();
+            lo[l].pptr = take((L.P.n_rows + 1) * 4);
+            lo[l].pcol = take(pz * 4);
+            lo[l].pv32 = take(pz * 4);
+            lo[l].pv64 = take(pz * 8);
+            lo[l].rptr = take((L.Rt.n_rows + 1) * 4);
+            lo[l].rcol = take(pz * 4);
+            lo[l].rv32 = take(pz * 4);
+            lo[l].rv64 = take(pz * 8);
+        }
+    }
+    const int nc = H.lv.back().n;
+    const size_t v32 = take((size_t)nc * nc * 4), v64 = take((size_t)nc * nc * 8);
+    std::vector<char> stage(off);
+    auto put = [&](size_t o, const void *src, size_t bytes) { memcpy(stage.data() + o, src, bytes); };
+    for (int l = 0; l < nlev; ++l) {
+        const HostLevel &L = H.lv[l];
+        if (l >= 1 && l < nlev - 1) {
+            const size_t nz = L.col.size();
+            put(lo[l].ptr, L.ptr.data(), (L.n + 1) * 4);
+            put(lo[l].col, L.col.data(), nz * 4);
+            float2 *a32 = reinterpret_cast<float2 *>(stage.data() + lo[l].ab32);
+            double2 *a64 = reinterpret_cast<double2 *>(stage.data() + lo[l].ab64);
+            for (size_t k = 0; k < nz; ++k) {
+                a32[k] = make_float2((float)L.a[k], (float)L.b[k]);
+                a64[k] = make_double2(L.a[k], L.b[k]);
+            }
+            put(lo[l].da, L.diag_a.data(), L.n * 8);
+            put(lo[l].db, L.diag_b.data(), L.n * 8);
+        }
+        if (l < nlev - 1) {
+            const size_t pz = L.P.col.size();
+            put(lo[l].pptr, L.P.ptr.data(), (L.P.n_rows + 1) * 4);
+            put(lo[l].pcol, L.P.col.data(), pz * 4);
+            put(lo[l].pv64, L.P.val.data(), pz * 8);
+            put(lo[l].rptr, L.Rt.ptr.data(), (L.Rt.n_rows + 1) * 4);
+            put(lo[l].rcol, L.Rt.col.data(), pz * 4);
+            put(lo[l].rv64, L.Rt.val.data(), pz * 8);
+            float *p32 = reinterpret_cast<float *>(stage.data() + lo[l].pv32);
+            float *r32 = reinterpret_cast<float *>(stage.data() + lo[l].rv32);
+            for (size_t k = 0; k < pz; ++k) {
+                p32[k] = (float)L.P.val[k];
+                r32[k] = (float)L.Rt.val[k];
+            }
+        }
+    }
+    {
+        float *V32 = reinterpret_cast<float *>(stage.data() + v32);
+        for (size_t k = 0; k < (size_t)nc * nc; ++k) V32[k] = (float)H.V[k];
+        put(v64, H.V.data(), (size_t)nc * nc * 8);
+    }
+    CKS(ensure(h, h->mgStatic, off));
+    char *base = reinterpret_cast<char *>(h->mgStatic.p);
+    CK(cudaMemcpyAsync(base, stage.data(), off, cudaMemcpyHostToDevice, h->ctx.stream));
+    CK(cudaStreamSynchronize(h->ctx.stream));   // the staging vector is pageable and local
+    auto fill = [&](auto &mg, auto tag) {
+        using T = decltype(tag);
+        mg = std::remove_reference_t<decltype(mg)>();
+        mg.nlev = nlev;
+        mg.nc = nc;
+        const DevPencil &A = h->A;
+        MgLevel<T> &L0 = mg.lv[0];
+        L0.R = A.rg_rows > 1 ? A.rg_rows : 1;
+        L0.ngroups = A.rg_rows > 1 ? A.rg_ngroups : A.n;
+        L0.nnz_union = A.rg_rows > 1 ? A.rg_nnz : A.nnz;
+        L0.gptr = A.rg_rows > 1 ? A.rg_ptr : A.rowptr;
+        L0.gcol = A.rg_rows > 1 ? A.rg_col : A.col;
+        if (sizeof(T) == 4)
+            L0.ab = reinterpret_cast<const cplx<T> *>(A.rg_rows > 1 ? (const void *)A.rg_ab32 : (const void *)A.ab32);
+        else
+            L0.ab = reinterpret_cast<const cplx<T> *>(A.rg_rows > 1 ? (const void *)A.rg_ab64 : (const void *)A.ab64);
+        L0.diag_a = A.diag_a;
+        L0.diag_b = A.diag_b;
+        for (int l = 0; l < nlev; ++l) {
+            const HostLevel &HL = H.lv[l];
+            MgLevel<T> &L = mg.lv[l];
+            L.n = HL.n;
+            L.rho = HL.rho;
+            if (l >= 1 && l < nlev - 1) {
+                L.R = 1;
+                L.ngroups = HL.n;
+                L.nnz_union = (int64_t)HL.col.size();
+                L.gptr = reinterpret_cast<const int32_t *>(base + lo[l].ptr);
+                L.gcol = reinterpret_cast<const int32_t *>(base + lo[l].col);
+                L.ab = reinterpret_cast<const cplx<T> *>(base + (sizeof(T) == 4 ? lo[l].ab32 : lo[l].ab64));
+                L.diag_a = reinterpret_cast<const double *>(base + lo[l].da);
+                L.diag_b = reinterpret_cast<const double *>(base + lo[l].db);
+            }
+            if (l < nlev - 1) {
+                L.p_nnz = L.r_nnz = (int64_t)HL.P.col.size();
+                L.pptr = reinterpret_cast<const int32_t *>(base + lo[l].pptr);
+                L.pcol = reinterpret_cast<const int32_t *>(base + lo[l].pcol);
+                L.pval = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? lo[l].pv32 : lo[l].pv64));
+                L.rptr = reinterpret_cast<const int32_t *>(base + lo[l].rptr);
+                L.rcol = reinterpret_cast<const int32_t *>(base + lo[l].rcol);
+                L.rval = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? lo[l].rv32 : lo[l].rv64));
+            }
+        }
+        mg.V = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? v32 : v64));
+    };
+    fill(h->mg32, 0.0f);
+    fill(h->mg64, 0.0);
+    h->mg_lam = H.lam;
+    h->mg_level_n.clear();
+    h->mg_level_nnz.clear();
+    for (int l = 0; l < nlev; ++l) {
+        h->mg_level_n.push_back(H.lv[l].n);
+        h->mg_level_nnz.push_back(l == 0 ? h->A.nnz : (int64_t)H.lv[l].col.size());
+    }
+    h->mg_setup_ms = H.ms_setup;
+    h->mg_block = block;
+    h->mg_coarse = h->opts.mg_coarse;
+    h->mg_theta = h->opts.mg_theta;
+    h->mg_ready = true;
+    return SLRF_OK;
+}
+
+slrf_status mg_build_upload(slrf_handle *h, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                            const std::vector<double> &av, const std::vector<double> &bv) {
+    const int block = mg_block_for(h->opts, h->A.n, rp, ci);
+    HostHierarchy H;
+    const std::string err = mg_build(h->A.n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(h->opts, block), H);
+    if (!err.empty()) {
+        g_last_error = err;
+        return SLRF_BREAKDOWN;
+    }
+    return mg_upload(h, H, block);
+}
+
+// Build the hierarchy if the options ask for one it does not have yet (from
+// the device copy of the pencil).
+slrf_status mg_ensure(slrf_handle *h) {
+    if (h->mg_ready && h->mg_coarse == h->opts.mg_coarse && h->mg_theta == h->opts.mg_theta &&
+        (h->opts.mg_block == 0 || h->opts.mg_block == h->mg_block))
+        return SLRF_OK;
+    const int64_t n = h->A.n, nnz = h->A.nnz;
+    std::vector<int32_t> rp(n + 1), ci(nnz);
+    std::vector<double> av(nnz), bv(nnz);
+    CK(cudaMemcpyAsync(rp.data(), h->A.rowptr, (n + 1) * 4, cudaMemcpyDeviceToHost, h->ctx.stream));
+    CK(cudaMemcpyAsync(ci.data(), h->A.col, nnz * 4, cudaMemcpyDeviceToHost, h->ctx.stream));
+    CK(cudaMemcpyAsync(av.data(), h->A.a, nnz * 8, cudaMemcpyDeviceToHost, h->ctx.stream));
+    CK(cudaMemcpyAsync(bv.data(), h->A.b, nnz * 8, cudaMemcpyDeviceToHost, h->ctx.stream));
+    CK(cudaStreamSynchronize(h->ctx.stream));
+    return mg_build_upload(h, rp, ci, av, bv);
+}
+
+template <typename T> MgSolve<T> &mg_of(slrf_handle *h);
+template <> MgSolve<float> &mg_of<float>(slrf_handle *h) { return h->mg32; }
+template <> MgSolve<double> &mg_of<double>(slrf_handle *h) { return h->mg64; }
+
+// Per-solve level blocks, 1/(lambda_k - sigma_j) and the damped Jacobi
+// diagonals of every smoothed level.
+template <typename T>
+slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d, KrylovBuffers<T> &kb) {
+    CKS(mg_ensure(h));
+    MgSolve<T> &mg = mg_of<T>(h);
+    mg.nu = std::max(1, h->opts.mg_nu);
+    mg.gamma = std::max(1, h->opts.mg_cycle);
+    mg.omega = h->opts.mg_omega;
+    const int W = d.W(), N = d.N, nc = mg.nc;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    std::vector<size_t> o_r(mg.nlev), o_z(mg.nlev), o_t(mg.nlev), o_d(mg.nlev);
+    for (int l = 1; l < mg.nlev; ++l) {
+        const size_t blk = (size_t)mg.lv[l].n * W * sizeof(cplx<T>);
+        o_r[l] = take(blk);
+        o_z[l] = take(blk);
+        o_t[l] = take(blk);
+        if (l < mg.nlev - 1) o_d[l] = take((size_t)mg.lv[l].n * N * sizeof(cplx<T>));
+    }
+    const size_t o_c = take((size_t)nc * N * sizeof(cplx<T>));
+    CKS(ensure(h, h->mgState, off));
+    char *base = reinterpret_cast<char *>(h->mgState.p);
+    mg.lv[0].dinv = kb.dinv;
+    for (int l = 1; l < mg.nlev; ++l) {
+        mg.lv[l].r = reinterpret_cast<cplx<T> *>(base + o_r[l]);
+        mg.lv[l].z = reinterpret_cast<cplx<T> *>(base + o_z[l]);
+        mg.lv[l].t = reinterpret_cast<cplx<T> *>(base + o_t[l]);
+        mg.lv[l].dinv = l < mg.nlev - 1 ? reinterpret_cast<cplx<T> *>(base + o_d[l]) : nullptr;
+    }
+    mg.cinv = reinterpret_cast<cplx<T> *>(base + o_c);
+    // the previous solve of this handle synchronised before returning, so the
+    // staging vector is free to be rewritten
+    h->mg_cinv_host.resize((size_t)nc * N * sizeof(cplx<T>));
+    cplx<T> *ci = reinterpret_cast<cplx<T> *>(h->mg_cinv_host.data());
+    for (int k = 0; k < nc; ++k)
+        for (int j = 0; j < N; ++j) {
+            const cd v = 1.0 / (cd(h->mg_lam[k], 0.0) - cd(f->sigma_re[j], f->sigma_im[j]));
+            ci[(size_t)k * N + j] = mk((T)v.real(), (T)v.imag());
+        }
+    CK(cudaMemcpyAsync(mg.cinv, ci, h->mg_cinv_host.size(), cudaMemcpyHostToDevice, h->ctx.stream));
+    mg_dinv<T>(h->ctx, mg, make_poleset<T>(f));
+    return SLRF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Krylov solve of all (pole, column) systems; filter output accumulated in Uacc
 // ---------------------------------------------------------------------------
@@ -419,10 +702,23 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     for (int j = 0; j < N; ++j) sg[j] = mk((T)f->sigma_re[j], (T)f->sigma_im[j]);
     CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
     // the host vectors above are pageable; make the copies complete before they go out of scope
-    const PoleSet<T> ps = make_poleset<T>(f);
-    krylov_dinv<T>(ctx, h->A, ps, h->opts.precond, kb.dinv);
+    const bool use_mg = h->opts.precond == SLRF_PRECOND_MG;
+    kb.Z = nullptr;
+    if (use_mg) {
+        CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
+        kb.Z = as<cplx<T>>(h->kZ);
+        CKS(mg_prepare<T>(h, f, d, kb));
+    } else {
+        const PoleSet<T> ps = make_poleset<T>(f);
+        krylov_dinv<T>(ctx, h->A, ps, h->opts.precond, kb.dinv);
+    }
+    const cplx<T> *sig = as<cplx<T>>(h->kSig);
     fill_zero(ctx, kb.Uacc, (size_t)n * d.Lp * sizeof(T));
     krylov_init<T>(ctx, d, kb, rhs, ldr, nullptr);
+    if (use_mg) {
+        mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q);
+        krylov_direction<T>(ctx, d, kb, 1);
+    }
     krylov_reduce_init<T>(ctx, d, kb);
 
     int n_active = 0;
@@ -434,9 +730,10 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     for (; it < maxit;) {
         const int chunk = std::min(every, maxit - it);
         for (int k = 0; k < chunk; ++k) {
-            krylov_spmm<T>(ctx, d, h->A, as<cplx<T>>(h->kSig), kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
+            krylov_spmm<T>(ctx, d, h->A, sig, kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
             krylov_reduce_alpha<T>(ctx, d, kb);
             krylov_update<T>(ctx, d, kb);
+            if (use_mg) mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q);
             krylov_reduce_beta<T>(ctx, d, kb, tol2, maxit);
             krylov_direction<T>(ctx, d, kb);
         }
@@ -786,6 +1083,12 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->profile = 0;
     o->spmm_rows = 0;
     o->gram_ozaki = 1;
+    o->mg_nu = 2;
+    o->mg_cycle = 1;
+    o->mg_coarse = 256;
+    o->mg_block = 0;
+    o->mg_omega = 4.0 / 3.0;
+    o->mg_theta = 0.0;
     return SLRF_OK;
 }
 
@@ -793,9 +1096,63 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (!o) return SLRF_EINVAL;
     if (o->precision != SLRF_PREC_FP64 && o->precision != SLRF_PREC_MIXED) return SLRF_EINVAL;
     if (o->krylov != SLRF_KRYLOV_COCG) return SLRF_EINVAL;
-    if (o->precond != SLRF_PRECOND_NONE && o->precond != SLRF_PRECOND_JACOBI) return SLRF_EINVAL;
+    if (o->precond != SLRF_PRECOND_NONE && o->precond != SLRF_PRECOND_JACOBI && o->precond != SLRF_PRECOND_MG)
+        return SLRF_EINVAL;
+    if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
+        o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
+        !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0))
+        return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
+    return SLRF_OK;
+}
+
+slrf_status slrf_mg_describe(const slrf_pencil *p, const slrf_opts *o, int32_t *n_levels, int64_t *level_n,
+                             int64_t *level_nnz, double *setup_ms, double *coarse_lam, double *coarse_a,
+                             double *coarse_b) {
+    if (!p || p->on_device || !n_levels || !level_n || !level_nnz) return SLRF_EINVAL;
+    if (p->n < 1 || p->n > (1LL << 31) - 2 || p->nnz < p->n || p->nnz > (1LL << 31) - 1 || !p->row_ptr ||
+        !p->col_idx || !p->a_val || !p->b_val)
+        return SLRF_EINVAL;
+    slrf_opts def;
+    slrf_opts_default(&def);
+    if (!o) o = &def;
+    CKS(check_opts(o));
+    const int64_t n = p->n, nnz = p->nnz;
+    std::vector<int32_t> rp(p->row_ptr, p->row_ptr + n + 1), ci(p->col_idx, p->col_idx + nnz);
+    std::vector<double> av(p->a_val, p->a_val + nnz), bv(p->b_val, p->b_val + nnz);
+    if (!pencil_valid(n, nnz, rp, ci, av, bv)) return SLRF_EINVAL;
+    const int block = mg_block_for(*o, n, rp, ci);
+    HostHierarchy H;
+    const std::string err = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(*o, block), H);
+    if (!err.empty()) {
+        g_last_error = err;
+        return SLRF_BREAKDOWN;
+    }
+    const int nlev = (int)H.lv.size();
+    if (nlev > SLRF_MG_MAX_LEVELS) return SLRF_BREAKDOWN;
+    *n_levels = nlev;
+    for (int l = 0; l < nlev; ++l) {
+        level_n[l] = H.lv[l].n;
+        level_nnz[l] = l == 0 ? nnz : (int64_t)H.lv[l].col.size();
+    }
+    if (setup_ms) *setup_ms = H.ms_setup;
+    const HostLevel &Lc = H.lv.back();
+    const int nc = Lc.n;
+    if (coarse_lam) std::copy(H.lam.begin(), H.lam.end(), coarse_lam);
+    if (coarse_a || coarse_b) {
+        const int32_t *cp = nlev == 1 ? rp.data() : Lc.ptr.data();
+        const int32_t *cc = nlev == 1 ? ci.data() : Lc.col.data();
+        const double *ca = nlev == 1 ? av.data() : Lc.a.data();
+        const double *cb = nlev == 1 ? bv.data() : Lc.b.data();
+        if (coarse_a) std::fill(coarse_a, coarse_a + (size_t)nc * nc, 0.0);
+        if (coarse_b) std::fill(coarse_b, coarse_b + (size_t)nc * nc, 0.0);
+        for (int i = 0; i < nc; ++i)
+            for (int32_t k = cp[i]; k < cp[i + 1]; ++k) {
+                if (coarse_a) coarse_a[(size_t)i * nc + cc[k]] = ca[k];
+                if (coarse_b) coarse_b[(size_t)i * nc + cc[k]] = cb[k];
+            }
+    }
     return SLRF_OK;
 }
 
@@ -811,7 +1168,7 @@ void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
-                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX};
+                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,
@@ -854,18 +1211,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     CK(cudaMemcpy(ci.data(), p->col_idx, nnz * sizeof(int32_t), kind));
     CK(cudaMemcpy(av.data(), p->a_val, nnz * sizeof(double), kind));
     CK(cudaMemcpy(bv.data(), p->b_val, nnz * sizeof(double), kind));
-    if (rp[0] != 0 || rp[n] != nnz) return SLRF_EINVAL;
-    for (int64_t i = 0; i < n; ++i) {
-        if (rp[i + 1] < rp[i]) return SLRF_EINVAL;
-        bool diag = false;
-        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-            if (ci[k] < 0 || ci[k] >= n) return SLRF_EINVAL;
-            if (k > rp[i] && ci[k] <= ci[k - 1]) return SLRF_EINVAL;
-            if (!isfinite(av[k]) || !isfinite(bv[k])) return SLRF_EINVAL;
-            if (ci[k] == i) diag = av[k] > 0 && bv[k] > 0;
-        }
-        if (!diag) return SLRF_EINVAL;   // SPD pencils have a positive diagonal
-    }
+    if (!pencil_valid(n, nnz, rp, ci, av, bv)) return SLRF_EINVAL;
     // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
     // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
     int R = o->spmm_rows;
@@ -941,6 +1287,13 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         g_last_error = std::string("pencil upload: ") + cudaGetErrorString(e);
         slrf_destroy(h);
         return SLRF_ECUDA;
+    }
+    if (o->precond == SLRF_PRECOND_MG) {
+        const slrf_status st = mg_build_upload(h, rp, ci, av, bv);
+        if (st != SLRF_OK) {
+            slrf_destroy(h);
+            return st;
+        }
     }
     *out = h;
     return SLRF_OK;

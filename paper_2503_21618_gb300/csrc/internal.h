@@ -83,6 +83,7 @@ struct KrylovBuffers {
     cplx<T> *P, *Q, *R;                  // n x W each
     cplx<T> *dinv;                       // n x N Jacobi inverse diagonal
     T *Uacc;                             // n x Lp accumulation of the filter output
+    cplx<T> *Z = nullptr;                // n x W preconditioned residual (multigrid); nullptr: Jacobi
     KrylovScalars<T> s;
     int gy;                              // row groups of the kernels
 };
@@ -108,12 +109,48 @@ template <typename T>
 void krylov_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb);
 template <typename T>
 void krylov_reduce_beta(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, double tol2, int maxit);
+// p = z + beta p (z = Z, or M^{-1} r with the Jacobi diagonal); init: p = z
 template <typename T>
-void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb);
+void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, int init = 0);
 void krylov_count_active(Ctx &ctx, int W, const int32_t *flag, int32_t *count);
 // mu[c] = sum over row groups of part slot 0/1 -> complex (for the SpMM step API)
 template <typename T>
 void krylov_reduce_mu(Ctx &ctx, const KrylovDims &d, const T *part, int gy, cplx<T> *mu);
+
+// ---------------------------------------------------------------- mg.cu
+// Device view of the multigrid hierarchy for one Krylov precision T.  Level 0
+// is the caller's pencil (row-group form); levels 1.. are Galerkin pencils in
+// CSR (R = 1).  Transfers P_l (n_l x n_{l+1}) and R_l = P_l^T are stored as
+// CSR with real values.  r/z/t are the per-solve level blocks (levels >= 1),
+// dinv the damped Jacobi inverse n_l x N.
+constexpr int MG_MAX_LEVELS = 16;
+template <typename T> struct MgLevel {
+    int n = 0, R = 1, ngroups = 0;
+    int64_t nnz_union = 0;
+    const int32_t *gptr = nullptr, *gcol = nullptr;
+    const cplx<T> *ab = nullptr;              // R (a, b) pairs per union entry
+    const double *diag_a = nullptr, *diag_b = nullptr;
+    int64_t p_nnz = 0, r_nnz = 0;
+    const int32_t *pptr = nullptr, *pcol = nullptr, *rptr = nullptr, *rcol = nullptr;
+    const T *pval = nullptr, *rval = nullptr;
+    cplx<T> *r = nullptr, *z = nullptr, *t = nullptr, *dinv = nullptr;
+    double rho = 1.0;                         // spectral radius of D^{-1} A on this level
+};
+template <typename T> struct MgSolve {
+    int nlev = 0, nc = 0;
+    int nu = 1, gamma = 1;        // coarse-level sweeps per side, coarse visits per level
+    double omega = 4.0 / 3.0;     // Jacobi damping on level l: omega / rho_l
+    MgLevel<T> lv[MG_MAX_LEVELS];
+    const T *V = nullptr;         // coarsest eigenvectors, nc x nc row-major
+    cplx<T> *cinv = nullptr;      // nc x N: 1 / (lambda_k - sigma_j)
+};
+template <typename T>
+void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps);
+// Z0 = cycle(R0) for all active columns of the state; T0 is an n x W
+// scratch block; part receives the partial sums r^T z (slots 0, 1).
+template <typename T>
+void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig, const int32_t *flag, T *part,
+              int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0);
 
 // ---------------------------------------------------------------- dense.cu
 // Y = A X and/or Z = B X, FP64, row-major n x m.

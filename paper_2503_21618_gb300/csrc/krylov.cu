@@ -378,11 +378,13 @@ k_spmm_shifted_rg(int n, int W, int Lp, int ngroups, int groups_per_block, const
 }
 
 // ---------------------------------------------------------------------------
-// update: r -= alpha q ; U += Re(ua p) ; z = M^{-1} r ; partial r^T z, |r|^2
+// update: r -= alpha q ; U += Re(ua p) ; partial |r|^2 and, with the Jacobi
+// preconditioner (JAC), z = M^{-1} r and partial r^T z (with multigrid the
+// cycle that follows forms z and r^T z).
 // One thread owns VC columns of one pole-slot c and walks all N poles, so the
 // pole sum of the filter is formed in registers.
 // ---------------------------------------------------------------------------
-template <typename T, int VC, int NP>
+template <typename T, int VC, int NP, bool JAC>
 __global__ void __launch_bounds__(32 * TY)
 k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__restrict__ P,
          const cplx<T> *__restrict__ Q, const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ alpha,
@@ -423,7 +425,8 @@ k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__
                 CV<T, VC> r = ldcv(R + base);
                 const CV<T, VC> p = ldcv(P + base);
                 const CV<T, VC> q = ldcv(Q + base);
-                const C dv = dinv[(int64_t)row * N + j];
+                C dv = mk((T)0, (T)0);
+                if (JAC) dv = dinv[(int64_t)row * N + j];
 #pragma unroll
                 for (int v = 0; v < VC; ++v) {
                     if (!(mj & (1u << v))) continue;
@@ -431,10 +434,12 @@ k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__
                     const C w = ua[j * Lp + c0 + v];
                     r.v[v] = csub(r.v[v], cmul(a, q.v[v]));
                     u[v] += w.x * p.v[v].x - w.y * p.v[v].y;
-                    const C z = cmul(dv, r.v[v]);
-                    const C rz = cmul(r.v[v], z);
-                    acc[j][v][0] += rz.x;
-                    acc[j][v][1] += rz.y;
+                    if (JAC) {
+                        const C z = cmul(dv, r.v[v]);
+                        const C rz = cmul(r.v[v], z);
+                        acc[j][v][0] += rz.x;
+                        acc[j][v][1] += rz.y;
+                    }
                     acc[j][v][2] += cabs2(r.v[v]);
                 }
                 stcv(R + base, r);
@@ -468,8 +473,10 @@ k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__
                     s2 += red[y][tx][v * 3 + 2];
                 }
                 T *o = part + ((int64_t)blockIdx.y * W + j * Lp + c0 + v) * 4;
-                o[0] = s0;
-                o[1] = s1;
+                if (JAC) {
+                    o[0] = s0;
+                    o[1] = s1;
+                }
                 o[2] = s2;
             }
         }
@@ -478,13 +485,13 @@ k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__
 }
 
 // ---------------------------------------------------------------------------
-// direction: p = M^{-1} r + beta p
+// direction: p = z + beta p, z = Z (multigrid) or M^{-1} r (Jacobi); init: p = z
 // ---------------------------------------------------------------------------
-template <typename T, int VC>
+template <typename T, int VC, bool MGZ>
 __global__ void __launch_bounds__(32 * TY)
-k_direction(int n, int W, int Lp, int N, const cplx<T> *__restrict__ R, cplx<T> *__restrict__ P,
-            const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ beta,
-            const int32_t *__restrict__ flag) {
+k_direction(int n, int W, int Lp, int N, const cplx<T> *__restrict__ R, const cplx<T> *__restrict__ Z,
+            cplx<T> *__restrict__ P, const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ beta,
+            const int32_t *__restrict__ flag, int init) {
     using C = cplx<T>;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int ng = W / VC;
@@ -499,17 +506,29 @@ k_direction(int n, int W, int Lp, int N, const cplx<T> *__restrict__ R, cplx<T> 
     for (int v = 0; v < VC; ++v) {
         act[v] = flag[c0 + v] == 1;
         any |= act[v];
-        b[v] = beta[c0 + v];
+        b[v] = init ? mk((T)0, (T)0) : beta[c0 + v];
     }
     if (!any) return;
     for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
         const int64_t base = (int64_t)row * W + c0;
-        const C dv = dinv[(int64_t)row * N + j];
-        const CV<T, VC> r = ldcv(R + base);
-        CV<T, VC> p = ldcv(P + base);
+        CV<T, VC> z;
+        if (MGZ) {
+            z = ldcv(Z + base);
+        } else {
+            const C dv = dinv[(int64_t)row * N + j];
+            z = ldcv(R + base);
 #pragma unroll
-        for (int v = 0; v < VC; ++v)
-            if (act[v]) p.v[v] = cfma(b[v], p.v[v], cmul(dv, r.v[v]));
+            for (int v = 0; v < VC; ++v) z.v[v] = cmul(dv, z.v[v]);
+        }
+        CV<T, VC> p;
+        if (init) {
+            p = z;
+        } else {
+            p = ldcv(P + base);
+#pragma unroll
+            for (int v = 0; v < VC; ++v)
+                if (act[v]) p.v[v] = cfma(b[v], p.v[v], z.v[v]);
+        }
         stcv(P + base, p);
     }
 }
@@ -721,8 +740,12 @@ static void launch_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
     const double vb = (double)d.n * W * d.frac * sizeof(cplx<T>);
     ctx.before(KC_KRYLOV_UPDATE, 4 * vb + 2.0 * d.n * d.Lp * sizeof(T) + (double)d.n * d.N * sizeof(cplx<T>),
                16.0 * d.n * W * d.frac);
-    k_update<T, VC, NP><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv, kb.s.alpha,
-                                                         kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
+    if (kb.Z)
+        k_update<T, VC, NP, false><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv,
+                                                                    kb.s.alpha, kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
+    else
+        k_update<T, VC, NP, true><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv,
+                                                                   kb.s.alpha, kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
     ctx.after();
 }
 
@@ -747,13 +770,19 @@ void krylov_reduce_beta(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, dou
 }
 
 template <typename T>
-void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
+void krylov_direction(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb, int init) {
     constexpr int VC = VecN<T>::VC;
     const int W = d.W();
     dim3 grid((W / VC + 31) / 32, kb.gy), block(32, TY);
     const double vb = (double)d.n * W * d.frac * sizeof(cplx<T>);
-    ctx.before(KC_KRYLOV_DIR, 3 * vb + (double)d.n * d.N * sizeof(cplx<T>), 10.0 * d.n * W * d.frac);
-    k_direction<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.dinv, kb.s.beta, kb.s.flag);
+    ctx.before(KC_KRYLOV_DIR, (init ? 2 : 3) * vb + (kb.Z ? 0.0 : (double)d.n * d.N * sizeof(cplx<T>)),
+               10.0 * d.n * W * d.frac);
+    if (kb.Z)
+        k_direction<T, VC, true><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.Z, kb.P, kb.dinv,
+                                                                 kb.s.beta, kb.s.flag, init);
+    else
+        k_direction<T, VC, false><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.Z, kb.P, kb.dinv,
+                                                                  kb.s.beta, kb.s.flag, init);
     ctx.after();
 }
 
@@ -781,7 +810,7 @@ void krylov_reduce_mu(Ctx &ctx, const KrylovDims &d, const T *part, int gy, cplx
     template void krylov_reduce_alpha<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                      \
     template void krylov_update<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                            \
     template void krylov_reduce_beta<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &, double, int);          \
-    template void krylov_direction<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &);                         \
+    template void krylov_direction<T>(Ctx &, const KrylovDims &, KrylovBuffers<T> &, int);                    \
     template void krylov_reduce_mu<T>(Ctx &, const KrylovDims &, const T *, int, cplx<T> *);
 INST(float)
 INST(double)

@@ -1,0 +1,65 @@
+// Smoothed-aggregation multigrid hierarchy of a pencil (A, B) (host side).
+//
+// The shifted systems (A - sigma_j B) y = f of Section 1, Eq. (2) have poles
+// with a large imaginary part (Section 3.1: sigma = gamma x (1 + i alpha)),
+// the setting in which a multigrid cycle with Jacobi smoothing is an
+// effective preconditioner for a shifted Laplace-type operator.  One
+// hierarchy serves every pole: the prolongators P_l are built from A alone
+// and the Galerkin coarse pencils (P^T A P, P^T B P) keep the pair form, so
+// the coarse operator of pole j is A_c - sigma_j B_c on every level.  The
+// coarsest pencil is diagonalised once, V^T A_c V = diag(lambda),
+// V^T B_c V = I, which gives its exact shifted inverse for any pole:
+// (A_c - sigma B_c)^{-1} = V (diag(lambda) - sigma)^{-1} V^T.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace slrf {
+
+struct HostCsr {
+    int n_rows = 0, n_cols = 0;
+    std::vector<int32_t> ptr, col;
+    std::vector<double> val;
+};
+
+struct HostLevel {
+    int n = 0;                          // rows of this level
+    // pencil of this level (union pattern, pair values); empty for level 0,
+    // which is the caller's pencil
+    std::vector<int32_t> ptr, col;
+    std::vector<double> a, b;
+    std::vector<double> diag_a, diag_b;
+    double rho = 1.0;                   // spectral radius of D^{-1} A (levels that are smoothed)
+    // transfer to the next level (empty on the coarsest level)
+    HostCsr P;    // n x n_next
+    HostCsr Rt;   // n_next x n, the transpose of P
+};
+
+struct MgParams {
+    int block = 1;           // dofs per node (1, or 3 for 3-dof elasticity)
+    int coarse_target = 256; // stop coarsening at or below this size
+    int max_levels = 10;
+    double theta = 0.08;     // strength-of-connection threshold
+};
+
+struct HostHierarchy {
+    std::vector<HostLevel> lv;   // lv[0] .. lv[nlev-1]; the last is the coarsest
+    std::vector<double> V;       // coarsest: n_c x n_c row-major, B_c-orthonormal eigenvectors
+    std::vector<double> lam;     // coarsest: eigenvalues, ascending
+    double ms_setup = 0.0;
+};
+
+// Build the hierarchy of the n x n pencil given in CSR with shared pattern
+// (a = A values, b = B values).  Returns an empty string on success, else a
+// description of the failure (non-positive diagonal, coarse mass matrix not
+// positive definite, coarsening stalled).
+std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double *a, const double *b,
+                     const MgParams &prm, HostHierarchy &H);
+
+// Dense symmetric eigensolver (FP64, host): S = Q diag(w) Q^T, w ascending,
+// Q row-major n x n with the eigenvectors in its columns.  S is overwritten.
+void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vector<double> &Q);
+
+}  // namespace slrf

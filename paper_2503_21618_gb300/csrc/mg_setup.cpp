@@ -1,0 +1,516 @@
+// Host construction of the smoothed-aggregation hierarchy (see mg.h).
+//
+// Per level: strength graph on nodes (blocks of `block` dofs), greedy
+// aggregation, tentative prolongator T (piecewise constant per dof
+// component), one damped-Jacobi smoothing step P = (I - w D^{-1} A) T with
+// w = 4 / (3 rho(D^{-1} A)), Galerkin pencil (P^T A P, P^T B P).  The
+// coarsest pencil is reduced to a standard eigenproblem through the Cholesky
+// factor of B_c and diagonalised by Householder tridiagonalisation and the
+// implicit symmetric QR iteration with Wilkinson shifts (Golub & Van Loan,
+// Matrix Computations, Sections 8.3.1 and 8.3.3).  Everything is FP64 and
+// deterministic: the row products are computed in parallel, but every row
+// is formed by one thread in a fixed order and sorted by column.
+#include "mg.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+#include <thread>
+
+namespace slrf {
+namespace {
+
+int n_threads(int64_t work) {
+    unsigned hc = std::thread::hardware_concurrency();
+    int t = (int)std::min<unsigned>(hc ? hc : 1, 16u);
+    if (work < 200000) t = 1;
+    return std::max(1, t);
+}
+
+// Run fn(r0, r1, tid) over contiguous row ranges in parallel.
+template <class Fn>
+void parallel_for_rows(int nrows, int nt, Fn fn) {
+    if (nt <= 1) {
+        fn(0, nrows, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) {
+        const int r0 = (int)((int64_t)nrows * t / nt), r1 = (int)((int64_t)nrows * (t + 1) / nt);
+        th.emplace_back(fn, r0, r1, t);
+    }
+    for (auto &x : th) x.join();
+}
+
+// Sparse rows produced by a per-row accumulator (sparse accumulator with a
+// marker array), one or two value arrays.  `row_fn(i, add)` calls
+// add(col, va, vb) for every contribution to row i.
+struct RowsOut {
+    std::vector<int32_t> ptr, col;
+    std::vector<double> a, b;
+};
+
+template <class RowFn>
+void build_rows(int nrows, int ncols, bool pair, int64_t work, RowFn row_fn, RowsOut &out) {
+    const int nt = n_threads(work);
+    struct Part {
+        std::vector<int32_t> len, col;
+        std::vector<double> a, b;
+    };
+    std::vector<Part> parts(nt);
+    parallel_for_rows(nrows, nt, [&](int r0, int r1, int t) {
+        Part &p = parts[t];
+        p.len.reserve(r1 - r0);
+        std::vector<int32_t> mark(ncols, -1), cols;
+        std::vector<double> acc_a(ncols, 0.0), acc_b(pair ? ncols : 0, 0.0);
+        for (int i = r0; i < r1; ++i) {
+            cols.clear();
+            auto add = [&](int c, double va, double vb) {
+                if (mark[c] != i) {
+                    mark[c] = i;
+                    acc_a[c] = 0.0;
+                    if (pair) acc_b[c] = 0.0;
+                    cols.push_back(c);
+                }
+                acc_a[c] += va;
+                if (pair) acc_b[c] += vb;
+            };
+            row_fn(i, add);
+            std::sort(cols.begin(), cols.end());
+            p.len.push_back((int32_t)cols.size());
+            for (int c : cols) {
+                p.col.push_back(c);
+                p.a.push_back(acc_a[c]);
+                if (pair) p.b.push_back(acc_b[c]);
+            }
+        }
+    });
+    out.ptr.assign(nrows + 1, 0);
+    {
+        int row = 0;
+        for (auto &p : parts)
+            for (int32_t l : p.len) {
+                out.ptr[row + 1] = out.ptr[row] + l;
+                ++row;
+            }
+    }
+    const int64_t tot = out.ptr[nrows];
+    out.col.resize(tot);
+    out.a.resize(tot);
+    if (pair) out.b.resize(tot);
+    int64_t off = 0;
+    for (auto &p : parts) {
+        std::copy(p.col.begin(), p.col.end(), out.col.begin() + off);
+        std::copy(p.a.begin(), p.a.end(), out.a.begin() + off);
+        if (pair) std::copy(p.b.begin(), p.b.end(), out.b.begin() + off);
+        off += (int64_t)p.col.size();
+    }
+}
+
+HostCsr transpose(const HostCsr &M) {
+    HostCsr T;
+    T.n_rows = M.n_cols;
+    T.n_cols = M.n_rows;
+    T.ptr.assign(T.n_rows + 1, 0);
+    for (int32_t c : M.col) T.ptr[c + 1]++;
+    for (int i = 0; i < T.n_rows; ++i) T.ptr[i + 1] += T.ptr[i];
+    T.col.resize(M.col.size());
+    T.val.resize(M.col.size());
+    std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
+    for (int i = 0; i < M.n_rows; ++i)   // ascending i keeps each row of T sorted
+        for (int32_t k = M.ptr[i]; k < M.ptr[i + 1]; ++k) {
+            const int32_t d = fill[M.col[k]]++;
+            T.col[d] = i;
+            T.val[d] = M.val[k];
+        }
+    return T;
+}
+
+// Strong node neighbours: ||A_IJ||_F >= theta * sqrt(||A_II||_F ||A_JJ||_F).
+void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, int bs, double theta,
+              std::vector<int32_t> &sptr, std::vector<int32_t> &scol) {
+    const int nn = n / bs;
+    std::vector<double> dnorm(nn, 0.0);   // ||A_II||_F^2
+    for (int i = 0; i < n; ++i)
+        for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k)
+            if (col[k] / bs == i / bs) dnorm[i / bs] += a[k] * a[k];
+    sptr.assign(nn + 1, 0);
+    scol.clear();
+    std::vector<int32_t> mark(nn, -1), nb;
+    std::vector<double> acc(nn, 0.0);
+    const double th2 = theta * theta;
+    for (int I = 0; I < nn; ++I) {
+        nb.clear();
+        for (int i = I * bs; i < I * bs + bs; ++i)
+            for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+                const int J = col[k] / bs;
+                if (J == I) continue;
+                if (mark[J] != I) {
+                    mark[J] = I;
+                    acc[J] = 0.0;
+                    nb.push_back(J);
+                }
+                acc[J] += a[k] * a[k];
+            }
+        std::sort(nb.begin(), nb.end());
+        for (int J : nb)
+            if (acc[J] >= th2 * std::sqrt(dnorm[I] * dnorm[J])) scol.push_back(J);
+        sptr[I + 1] = (int32_t)scol.size();
+    }
+}
+
+// Greedy aggregation in node order: (1) a node whose strong neighbours are
+// all free starts an aggregate with them; (2) a free node joins the
+// aggregate of a strong neighbour assigned in (1); (3) what is left forms
+// aggregates with its free strong neighbours.
+int aggregate(int nn, const std::vector<int32_t> &sptr, const std::vector<int32_t> &scol, std::vector<int32_t> &agg) {
+    agg.assign(nn, -1);
+    int na = 0;
+    for (int i = 0; i < nn; ++i) {
+        if (agg[i] >= 0) continue;
+        bool free_all = true;
+        for (int32_t k = sptr[i]; k < sptr[i + 1] && free_all; ++k) free_all = agg[scol[k]] < 0;
+        if (!free_all) continue;
+        agg[i] = na;
+        for (int32_t k = sptr[i]; k < sptr[i + 1]; ++k) agg[scol[k]] = na;
+        ++na;
+    }
+    std::vector<int32_t> first(agg);
+    for (int i = 0; i < nn; ++i) {
+        if (agg[i] >= 0) continue;
+        for (int32_t k = sptr[i]; k < sptr[i + 1]; ++k)
+            if (first[scol[k]] >= 0) {
+                agg[i] = first[scol[k]];
+                break;
+            }
+    }
+    for (int i = 0; i < nn; ++i) {
+        if (agg[i] >= 0) continue;
+        agg[i] = na;
+        for (int32_t k = sptr[i]; k < sptr[i + 1]; ++k)
+            if (agg[scol[k]] < 0) agg[scol[k]] = na;
+        ++na;
+    }
+    return na;
+}
+
+// Largest |eigenvalue| of D^{-1} A by power iteration (deterministic start).
+double rho_dinv_a(int n, const int32_t *ptr, const int32_t *col, const double *a, const std::vector<double> &d) {
+    std::vector<double> x(n), y(n);
+    uint64_t s = 0x9E3779B97F4A7C15ull;
+    for (int i = 0; i < n; ++i) {
+        s = s * 6364136223846793005ull + 1442695040888963407ull;
+        x[i] = 0.5 + (double)(s >> 11) * (1.0 / 9007199254740992.0);
+    }
+    double lam = 0.0;
+    for (int it = 0; it < 30; ++it) {
+        double nx = 0.0, ny = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double t = 0.0;
+            for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) t += a[k] * x[col[k]];
+            y[i] = t / d[i];
+            nx += x[i] * x[i];
+            ny += y[i] * y[i];
+        }
+        lam = std::sqrt(ny / nx);
+        const double inv = 1.0 / std::sqrt(ny);
+        for (int i = 0; i < n; ++i) x[i] = y[i] * inv;
+    }
+    return lam;
+}
+
+// In-place dense Cholesky S = L L^T (lower, row-major); false if not SPD.
+bool cholesky_lower(int n, std::vector<double> &S) {
+    for (int j = 0; j < n; ++j) {
+        double djj = S[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) djj -= S[(size_t)j * n + k] * S[(size_t)j * n + k];
+        if (!(djj > 0.0) || !std::isfinite(djj)) return false;
+        const double ljj = std::sqrt(djj);
+        S[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = S[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= S[(size_t)i * n + k] * S[(size_t)j * n + k];
+            S[(size_t)i * n + j] = t / ljj;
+        }
+        for (int k = j + 1; k < n; ++k) S[(size_t)j * n + k] = 0.0;
+    }
+    return true;
+}
+
+// Coarsest level: V^T A_c V = diag(lam), V^T B_c V = I.
+std::string coarse_eig(const HostLevel &L, std::vector<double> &V, std::vector<double> &lam) {
+    const int n = L.n;
+    std::vector<double> Ad((size_t)n * n, 0.0), Bd((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int32_t k = L.ptr[i]; k < L.ptr[i + 1]; ++k) {
+            Ad[(size_t)i * n + L.col[k]] = L.a[k];
+            Bd[(size_t)i * n + L.col[k]] = L.b[k];
+        }
+    // symmetrise (Galerkin products are symmetric up to rounding)
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double sa = 0.5 * (Ad[(size_t)i * n + j] + Ad[(size_t)j * n + i]);
+            const double sb = 0.5 * (Bd[(size_t)i * n + j] + Bd[(size_t)j * n + i]);
+            Ad[(size_t)i * n + j] = Ad[(size_t)j * n + i] = sa;
+            Bd[(size_t)i * n + j] = Bd[(size_t)j * n + i] = sb;
+        }
+    if (!cholesky_lower(n, Bd)) return "multigrid setup: coarse mass matrix is not positive definite";
+    // X = L^{-1} A_c (forward substitution, column by column of A_c)
+    std::vector<double> X(Ad);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            double t = X[(size_t)i * n + c];
+            for (int k = 0; k < i; ++k) t -= Bd[(size_t)i * n + k] * X[(size_t)k * n + c];
+            X[(size_t)i * n + c] = t / Bd[(size_t)i * n + i];
+        }
+    // C = L^{-1} X^T  (= L^{-1} A_c L^{-T})
+    std::vector<double> C((size_t)n * n);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            double t = X[(size_t)c * n + i];
+            for (int k = 0; k < i; ++k) t -= Bd[(size_t)i * n + k] * C[(size_t)k * n + c];
+            C[(size_t)i * n + c] = t / Bd[(size_t)i * n + i];
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double s = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+            C[(size_t)i * n + j] = C[(size_t)j * n + i] = s;
+        }
+    std::vector<double> Q;
+    host_syev(n, C, lam, Q);
+    // V = L^{-T} Q (back substitution)
+    V.assign((size_t)n * n, 0.0);
+    for (int c = 0; c < n; ++c)
+        for (int i = n - 1; i >= 0; --i) {
+            double t = Q[(size_t)i * n + c];
+            for (int k = i + 1; k < n; ++k) t -= Bd[(size_t)k * n + i] * V[(size_t)k * n + c];
+            V[(size_t)i * n + c] = t / Bd[(size_t)i * n + i];
+        }
+    return "";
+}
+
+}  // namespace
+
+void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vector<double> &Q) {
+    Q.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    std::vector<double> v(n), p(n), q(n), qv(n);
+    // Householder reduction to tridiagonal form: S <- H S H on the trailing
+    // block, Q <- Q H, for each column k.
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;   // length of the sub-column
+        double xn = 0.0;
+        for (int i = 0; i < m; ++i) {
+            v[i] = S[(size_t)(k + 1 + i) * n + k];
+            xn += v[i] * v[i];
+        }
+        xn = std::sqrt(xn);
+        if (xn == 0.0) continue;
+        const double alpha = v[0] > 0 ? -xn : xn;
+        v[0] -= alpha;
+        double vv = 0.0;
+        for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+        if (!(vv > 0.0)) continue;
+        const double beta = 2.0 / vv;
+        // p = beta * S22 v
+        for (int i = 0; i < m; ++i) {
+            double t = 0.0;
+            const double *row = &S[(size_t)(k + 1 + i) * n + k + 1];
+            for (int j = 0; j < m; ++j) t += row[j] * v[j];
+            p[i] = beta * t;
+        }
+        double vp = 0.0;
+        for (int i = 0; i < m; ++i) vp += v[i] * p[i];
+        const double K = vp / vv;
+        for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
+        for (int i = 0; i < m; ++i) {
+            double *row = &S[(size_t)(k + 1 + i) * n + k + 1];
+            for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+        }
+        S[(size_t)(k + 1) * n + k] = S[(size_t)k * n + k + 1] = alpha;
+        for (int i = 1; i < m; ++i) S[(size_t)(k + 1 + i) * n + k] = S[(size_t)k * n + k + 1 + i] = 0.0;
+        // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T
+        for (int r = 0; r < n; ++r) {
+            double t = 0.0;
+            const double *row = &Q[(size_t)r * n + k + 1];
+            for (int j = 0; j < m; ++j) t += row[j] * v[j];
+            qv[r] = beta * t;
+        }
+        for (int r = 0; r < n; ++r) {
+            double *row = &Q[(size_t)r * n + k + 1];
+            for (int j = 0; j < m; ++j) row[j] -= qv[r] * v[j];
+        }
+    }
+    std::vector<double> d(n), e(n > 0 ? n : 1, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = S[(size_t)i * n + i];
+    for (int i = 0; i + 1 < n; ++i) e[i] = S[(size_t)(i + 1) * n + i];
+    // Implicit symmetric QR steps with Wilkinson shifts on the unreduced
+    // trailing block; each Givens rotation R on (k, k+1) maps T -> R T R^T
+    // and Q -> Q R^T.
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1;
+    int64_t guard = 0;
+    const int64_t guard_max = 60LL * n + 100;
+    while (hi > 0 && guard < guard_max) {
+        for (int i = 0; i < hi; ++i)
+            if (std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
+        while (hi > 0 && e[hi - 1] == 0.0) --hi;
+        if (hi == 0) break;
+        int lo = hi - 1;
+        while (lo > 0 && e[lo - 1] != 0.0) --lo;
+        ++guard;
+        const double dd = 0.5 * (d[hi - 1] - d[hi]);
+        const double eh = e[hi - 1];
+        const double mu = d[hi] - eh * eh / (dd + (dd >= 0 ? 1.0 : -1.0) * std::hypot(dd, eh));
+        double x = d[lo] - mu, z = e[lo], bulge = 0.0;
+        for (int k = lo; k < hi; ++k) {
+            if (k > lo) {
+                x = e[k - 1];
+                z = bulge;
+            }
+            const double r = std::hypot(x, z);
+            double c = 1.0, s = 0.0;
+            if (r > 0.0) {
+                c = x / r;
+                s = z / r;
+            }
+            if (k > lo) e[k - 1] = r;
+            const double a0 = d[k], b0 = e[k], a1 = d[k + 1];
+            d[k] = c * c * a0 + 2.0 * c * s * b0 + s * s * a1;
+            d[k + 1] = s * s * a0 - 2.0 * c * s * b0 + c * c * a1;
+            e[k] = c * s * (a1 - a0) + (c * c - s * s) * b0;
+            if (k + 1 < hi) {
+                bulge = s * e[k + 1];
+                e[k + 1] = c * e[k + 1];
+            }
+            for (int row = 0; row < n; ++row) {
+                double *qr = &Q[(size_t)row * n];
+                const double zk = qr[k], zk1 = qr[k + 1];
+                qr[k] = c * zk + s * zk1;
+                qr[k + 1] = -s * zk + c * zk1;
+            }
+        }
+    }
+    // ascending order
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int i, int j) { return d[i] < d[j]; });
+    w.resize(n);
+    std::vector<double> Qs((size_t)n * n);
+    for (int c = 0; c < n; ++c) {
+        w[c] = d[idx[c]];
+        for (int r = 0; r < n; ++r) Qs[(size_t)r * n + c] = Q[(size_t)r * n + idx[c]];
+    }
+    Q.swap(Qs);
+}
+
+std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double *a, const double *b,
+                     const MgParams &prm, HostHierarchy &H) {
+    const auto t0 = std::chrono::steady_clock::now();
+    H = HostHierarchy();
+    const int bs = (prm.block > 1 && n % prm.block == 0) ? prm.block : 1;
+    // current level as raw arrays (level 0 borrows the caller's pencil)
+    const int32_t *cp = ptr, *cc = col;
+    const double *ca = a, *cb = b;
+    int cn = n;
+    H.lv.emplace_back();
+    H.lv[0].n = n;
+    for (;;) {
+        HostLevel &L = H.lv.back();
+        L.diag_a.assign(cn, 0.0);
+        L.diag_b.assign(cn, 0.0);
+        for (int i = 0; i < cn; ++i)
+            for (int32_t k = cp[i]; k < cp[i + 1]; ++k)
+                if (cc[k] == i) {
+                    L.diag_a[i] += ca[k];
+                    L.diag_b[i] += cb[k];
+                }
+        for (int i = 0; i < cn; ++i)
+            if (!(L.diag_a[i] > 0.0) || !(L.diag_b[i] > 0.0))
+                return "multigrid setup: non-positive diagonal entry in row " + std::to_string(i);
+        if (cn <= prm.coarse_target || (int)H.lv.size() >= prm.max_levels) break;
+        // aggregation on the node graph
+        std::vector<int32_t> sptr, scol, agg;
+        strength(cn, cp, cc, ca, bs, prm.theta, sptr, scol);
+        const int nn = cn / bs;
+        const int na = aggregate(nn, sptr, scol, agg);
+        const int nc = na * bs;
+        if (nc >= cn || nc > 0.85 * cn) break;   // coarsening stalled
+        std::vector<int32_t> asz(na, 0);
+        for (int I = 0; I < nn; ++I) asz[agg[I]]++;
+        std::vector<int32_t> tcol(cn);
+        std::vector<double> tval(cn);
+        for (int i = 0; i < cn; ++i) {
+            const int I = i / bs, c = i % bs;
+            tcol[i] = agg[I] * bs + c;
+            tval[i] = 1.0 / std::sqrt((double)asz[agg[I]]);
+        }
+        // P = T - w D^{-1} A T
+        L.rho = rho_dinv_a(cn, cp, cc, ca, L.diag_a);
+        const double w = 4.0 / (3.0 * L.rho);
+        RowsOut Pr;
+        build_rows(cn, nc, false, (int64_t)cp[cn], [&](int i, auto &add) {
+            const double f = -w / L.diag_a[i];
+            for (int32_t k = cp[i]; k < cp[i + 1]; ++k) add(tcol[cc[k]], f * ca[k] * tval[cc[k]], 0.0);
+            add(tcol[i], tval[i], 0.0);
+        }, Pr);
+        L.P.n_rows = cn;
+        L.P.n_cols = nc;
+        L.P.ptr = std::move(Pr.ptr);
+        L.P.col = std::move(Pr.col);
+        L.P.val = std::move(Pr.a);
+        L.Rt = transpose(L.P);
+        // (A P, B P), then P^T (A P, B P)
+        RowsOut APr;
+        const HostCsr &P = L.P;
+        build_rows(cn, nc, true, (int64_t)cp[cn] * 8, [&](int i, auto &add) {
+            for (int32_t k = cp[i]; k < cp[i + 1]; ++k) {
+                const int j = cc[k];
+                for (int32_t t = P.ptr[j]; t < P.ptr[j + 1]; ++t) add(P.col[t], ca[k] * P.val[t], cb[k] * P.val[t]);
+            }
+        }, APr);
+        HostLevel next;
+        next.n = nc;
+        RowsOut Cr;
+        const HostCsr &Rt = L.Rt;
+        build_rows(nc, nc, true, (int64_t)APr.ptr[cn] * 4, [&](int I, auto &add) {
+            for (int32_t t = Rt.ptr[I]; t < Rt.ptr[I + 1]; ++t) {
+                const int i = Rt.col[t];
+                const double r = Rt.val[t];
+                for (int32_t k = APr.ptr[i]; k < APr.ptr[i + 1]; ++k) add(APr.col[k], r * APr.a[k], r * APr.b[k]);
+            }
+        }, Cr);
+        next.ptr = std::move(Cr.ptr);
+        next.col = std::move(Cr.col);
+        next.a = std::move(Cr.a);
+        next.b = std::move(Cr.b);
+        H.lv.push_back(std::move(next));
+        HostLevel &N2 = H.lv.back();
+        cp = N2.ptr.data();
+        cc = N2.col.data();
+        ca = N2.a.data();
+        cb = N2.b.data();
+        cn = nc;
+    }
+    HostLevel &Lc = H.lv.back();
+    if (H.lv.size() == 1) {   // no coarsening: the coarsest level is the pencil itself
+        Lc.ptr.assign(ptr, ptr + n + 1);
+        Lc.col.assign(col, col + ptr[n]);
+        Lc.a.assign(a, a + ptr[n]);
+        Lc.b.assign(b, b + ptr[n]);
+    }
+    if (Lc.n > 4096) return "multigrid setup: coarsening stalled at " + std::to_string(Lc.n) + " unknowns";
+    std::string err = coarse_eig(Lc, H.V, H.lam);
+    if (!err.empty()) return err;
+    if (H.lv.size() == 1) {   // level 0 keeps no pencil copy
+        Lc.ptr.clear();
+        Lc.col.clear();
+        Lc.a.clear();
+        Lc.b.clear();
+    }
+    H.ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return "";
+}
+
+}  // namespace slrf
