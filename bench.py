@@ -33,8 +33,9 @@ METRIC = "eigenpairs/s at resid 1e-8 (2D Q1 n=89401, 100 eigenpairs, mixed FP32/
 UNIT = "eigenpairs/s"
 TOL = 1e-8
 MAX_OUTER = 40
-ROOFLINE_CLASS = "shifted_spmm"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "shifted_spmm_fem2d_q1_300.md")
+# kernel classes that can carry the roofline: the source file their kernels
+# live in (digest checked against the ncu summary) and that summary
+ROOFLINE_SOURCES = {"shifted_spmm": "krylov.cu", "mg_fine": "mg.cu"}
 
 
 def dist_env():
@@ -99,23 +100,24 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def source_digest() -> str:
-    path = os.path.join(ROOT, "paper_2503_21618_gb300", "csrc", "krylov.cu")
+def source_digest(kclass: str) -> str:
+    path = os.path.join(ROOT, "paper_2503_21618_gb300", "csrc", ROOFLINE_SOURCES[kclass])
     with open(path, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes per launch of the roofline kernel from the committed ncu
-    summary, or None if absent or taken on a different kernel source."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def ncu_traffic_per_launch(kclass: str):
+    """DRAM bytes per launch of the roofline kernel class from the committed
+    ncu summary, or None if absent or taken on a different kernel source."""
+    summary = os.path.join(ROOT, "profiles", f"{kclass}_fem2d_q1_300.md")
+    if not os.path.exists(summary):
         return None, "no ncu summary"
-    text = open(PROFILE_SUMMARY).read()
+    text = open(summary).read()
     m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
     d = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     if not m:
         return None, "summary has no traffic line"
-    if not d or d.group(1) != source_digest():
+    if not d or d.group(1) != source_digest(kclass):
         return None, "kernel changed since the ncu capture"
     return float(m.group(1)), "ncu"
 
@@ -397,10 +399,12 @@ def main():
             a = tot.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
             for key in a:
                 a[key] += v[key]
-    k = tot.get(ROOFLINE_CLASS, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+    # the roofline kernel: the class with the largest device time
+    rclass = max((c for c in ROOFLINE_SOURCES if c in tot), key=lambda c: tot[c]["ms"])
+    k = tot[rclass]
     peaks, peak_src = measured_peaks()
     achieved = (k["bytes"] / k["launches"]) / (k["ms"] / k["launches"] / 1e3) / 1e9 if k["launches"] else None
-    traffic, traffic_src = ncu_traffic_per_launch()
+    traffic, traffic_src = ncu_traffic_per_launch(rclass)
     launches = sum(r["kernel_launches"] for r in reps)
     kshare = {kk: round(v["ms"] / max(1e-9, sum(x["ms"] for x in tot.values())), 4) for kk, v in tot.items()}
 
@@ -446,11 +450,12 @@ def main():
             "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "L": L, "nev": nev, "n_poles": N,
                        "filter": "SLRF alpha=1 beta=0.01 (library designer)", "precision": "mixed",
                        "inner_tol": opts.inner_tol, "tol": TOL, "parallelism": f"replicas x{world}",
+                       "precond": "multigrid (smoothed aggregation)" if "mg_fine" in tot else "jacobi",
                        "l2": "inputs larger than L2 (Krylov state 1.29 GB per solve)"},
             "converged_per_step": conv, "outer_iters": outer,
             "gpu_launches": int(launches),
             "clocks": clk,
-            "roofline": {"kernel": ROOFLINE_CLASS, "bound": "hbm", "achieved": achieved,
+            "roofline": {"kernel": rclass, "bound": "hbm", "achieved": achieved,
                          "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
                          "peak_source": f"{peak_src} hbm_gbs", "traffic": traffic,

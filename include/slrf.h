@@ -84,17 +84,19 @@ enum { SLRF_KRYLOV_COCG = 0 };
  * smoothed-aggregation multigrid cycle (one hierarchy for all poles, built
  * from A; Galerkin pencils (P^T A P, P^T B P) on every level; damped Jacobi
  * smoothing; exact coarsest solve by the eigendecomposition of the coarsest
- * pencil).  The paper's own solver is ILU-preconditioned BiCGStab
- * (Section 4.2.1); both options keep the preconditioner complex symmetric,
- * as COCG requires. */
-enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1, SLRF_PRECOND_MG = 2 };
+ * pencil).  AUTO: MG for scalar pencils, JACOBI for 3-dof node-block
+ * (elasticity) pencils, where the hierarchy's translation-only aggregates do
+ * not pay off for shifts deep inside the spectrum.  The paper's own solver
+ * is ILU-preconditioned BiCGStab (Section 4.2.1); every option keeps the
+ * preconditioner complex symmetric, as COCG requires. */
+enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1, SLRF_PRECOND_MG = 2, SLRF_PRECOND_AUTO = 3 };
 enum { SLRF_RULE_MIDPOINT = 0, SLRF_RULE_GAUSS_LEGENDRE = 1, SLRF_RULE_GAUSS_CHEBYSHEV = 2,
        SLRF_RULE_SLRF = 3 };
 
 typedef struct {
     int32_t precision;      /* SLRF_PREC_*                                     (MIXED) */
     int32_t krylov;         /* SLRF_KRYLOV_*                                    (COCG) */
-    int32_t precond;        /* SLRF_PRECOND_*                                 (JACOBI) */
+    int32_t precond;        /* SLRF_PRECOND_*                                   (AUTO) */
     int32_t inner_maxit;    /* Krylov iteration cap per outer step, Section 4.2.1 (1000) */
     double inner_tol;       /* FP64: rel. to ||B v||, Section 4.2.1 (1e-13);
                                MIXED: rel. to ||R column||                      (1e-5) */
@@ -121,8 +123,7 @@ typedef struct {
                                level l smooths with mg_omega / rho(D_l^-1 A_l),
                                0 < mg_omega < 2                                  (4/3) */
     double mg_theta;        /* MG: strength-of-connection threshold of the
-                               aggregation, 0 = auto (0.08 for scalar problems,
-                               0.15 for node blocks)                                (0) */
+                               aggregation, 0 = 0.08                                (0) */
     int32_t reserved[4];
 } slrf_opts;
 
@@ -167,8 +168,8 @@ slrf_status slrf_opts_default(slrf_opts *o);
 /* Create a handle: validate the pencil (n >= 1, CSR monotone, indices in
  * range, finite values), copy it to the current CUDA device in the layouts the
  * kernels use, and bind `cuda_stream` (a cudaStream_t, NULL = legacy default
- * stream).  With opts.precond == SLRF_PRECOND_MG the multigrid hierarchy is
- * built here (host) and uploaded.  Problem statement: Section 1, Eq. (1). */
+ * stream).  When the preconditioner resolves to multigrid (MG, or AUTO on a
+ * scalar pencil) the hierarchy is built here (host) and uploaded.  Problem statement: Section 1, Eq. (1). */
 slrf_status slrf_create(slrf_handle **h, const slrf_pencil *p, const slrf_opts *o,
                         void *cuda_stream);
 /* Replace the handle's options (workspace is resized lazily; switching to

@@ -9,6 +9,6 @@ B-orthonormalisation and Rayleigh-Ritz.  The compute lives in the CUDA library
 """
 from .api import (Filter, Handle, SlrfError, default_opts, design_poles, filter_eval, load,  # noqa: F401
                   mg_describe, OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PREC_FP64, PREC_MIXED,
-                  PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG)
+                  PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG, PRECOND_AUTO)
 
 __all__ = ["Filter", "Handle", "SlrfError", "default_opts", "design_poles", "filter_eval", "load", "mg_describe"]

@@ -72,7 +72,7 @@ void pin_release(int32_t *hp) {
 
 const char *kKernelClassNames[SLRF_NKERNEL_CLASSES] = {
     "shifted_spmm", "krylov_update", "krylov_direction", "krylov_reduce", "krylov_init", "spmm_real",
-    "gram", "tall_gemm", "small_dense", "residual", "filter_combine", "other", "mg_smooth", "mg_transfer",
+    "gram", "tall_gemm", "small_dense", "residual", "filter_combine", "other", "mg_fine", "mg_transfer",
     "mg_coarse"};
 }  // namespace
 
@@ -153,6 +153,7 @@ struct slrf_handle {
     Buf hostV, hostX;   // device staging for the host-buffer entry points
     // multigrid preconditioner: hierarchy (static), per-solve level blocks, Z
     Buf mgStatic, mgState, kZ;
+    bool node_blocks = false;             // 3-dof node-block pattern (elasticity)
     bool mg_ready = false;
     int mg_block = 0, mg_coarse = 0;      // parameters the hierarchy was built with
     double mg_theta = 0.0;
@@ -389,9 +390,7 @@ MgParams mg_params(const slrf_opts &o, int block) {
     prm.block = block;
     prm.coarse_target = o.mg_coarse;
     prm.max_levels = MG_MAX_LEVELS;
-    // node blocks of 3-dof elasticity couple to all 26 neighbours; 0.15 keeps
-    // about the 6 face neighbours, so aggregates stay near 7 nodes
-    prm.theta = o.mg_theta > 0 ? o.mg_theta : (block > 1 ? 0.15 : 0.08);
+    prm.theta = o.mg_theta > 0 ? o.mg_theta : 0.08;
     return prm;
 }
 
@@ -573,6 +572,14 @@ slrf_status mg_ensure(slrf_handle *h) {
     return mg_build_upload(h, rp, ci, av, bv);
 }
 
+// SLRF_PRECOND_AUTO: multigrid for scalar pencils; Jacobi for 3-dof
+// node-block (elasticity) pencils, where the translation-only aggregation
+// of the hierarchy measured no faster than Jacobi on shifts deep inside
+// the spectrum.
+bool uses_mg(const slrf_handle *h) {
+    return h->opts.precond == SLRF_PRECOND_MG || (h->opts.precond == SLRF_PRECOND_AUTO && !h->node_blocks);
+}
+
 template <typename T> MgSolve<T> &mg_of(slrf_handle *h);
 template <> MgSolve<float> &mg_of<float>(slrf_handle *h) { return h->mg32; }
 template <> MgSolve<double> &mg_of<double>(slrf_handle *h) { return h->mg64; }
@@ -702,7 +709,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     for (int j = 0; j < N; ++j) sg[j] = mk((T)f->sigma_re[j], (T)f->sigma_im[j]);
     CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
     // the host vectors above are pageable; make the copies complete before they go out of scope
-    const bool use_mg = h->opts.precond == SLRF_PRECOND_MG;
+    const bool use_mg = uses_mg(h);
     kb.Z = nullptr;
     if (use_mg) {
         CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
@@ -710,7 +717,8 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         CKS(mg_prepare<T>(h, f, d, kb));
     } else {
         const PoleSet<T> ps = make_poleset<T>(f);
-        krylov_dinv<T>(ctx, h->A, ps, h->opts.precond, kb.dinv);
+        krylov_dinv<T>(ctx, h->A, ps, h->opts.precond == SLRF_PRECOND_NONE ? SLRF_PRECOND_NONE : SLRF_PRECOND_JACOBI,
+                       kb.dinv);
     }
     const cplx<T> *sig = as<cplx<T>>(h->kSig);
     fill_zero(ctx, kb.Uacc, (size_t)n * d.Lp * sizeof(T));
@@ -1021,7 +1029,7 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
 }  // namespace
 
 namespace slrf {
-size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count) {
+size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count, int mg_coarse) {
     const size_t Lp = (size_t)(L + 1) / 2 * 2, W = (size_t)N * Lp;
     const size_t ts = precision == SLRF_PREC_MIXED ? 4 : 8;   // Krylov real type
     const size_t gy = std::max<size_t>(1, std::min<size_t>((size_t)(n + 7) / 8, (size_t)sm_count * 8));
@@ -1033,7 +1041,17 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
     const size_t rr = 8 * (size_t)n * L * 8 + split * L * L * 8 + (40 * (size_t)L * L + 64 * (size_t)L) * 8 +
                       (size_t)sm_count * 12 * L * 8 + 8192;
     const size_t ozaki = 2 * 7 * (size_t)((L + 63) / 64 * 64) * (size_t)((n + 63) / 64 * 64) + (size_t)sm_count * 4 * L * L * 8;
-    return pencil + krylov + rr + ozaki;
+    // multigrid (mg_coarse > 0): Z block, level blocks r/z/t and Jacobi
+    // diagonals (the levels below the finest hold at most n/2 rows together),
+    // transfers and Galerkin pencils (bounded by the fine pattern), coarsest
+    // eigenvectors and shifted inverses
+    size_t mgb = 0;
+    if (mg_coarse > 0) {
+        const size_t nh = (size_t)n / 2 + 1, nc = (size_t)mg_coarse;
+        mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 96 * (size_t)nnz + nc * nc * 12 +
+              nc * N * 2 * ts + 16 * 4096;
+    }
+    return pencil + krylov + rr + ozaki + mgb;
 }
 }  // namespace slrf
 
@@ -1073,7 +1091,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     memset(o, 0, sizeof(*o));
     o->precision = SLRF_PREC_MIXED;
     o->krylov = SLRF_KRYLOV_COCG;
-    o->precond = SLRF_PRECOND_JACOBI;
+    o->precond = SLRF_PRECOND_AUTO;
     o->inner_maxit = 1000;
     o->inner_tol = 1e-5;
     o->lock_tol = 1e-9;
@@ -1096,8 +1114,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (!o) return SLRF_EINVAL;
     if (o->precision != SLRF_PREC_FP64 && o->precision != SLRF_PREC_MIXED) return SLRF_EINVAL;
     if (o->krylov != SLRF_KRYLOV_COCG) return SLRF_EINVAL;
-    if (o->precond != SLRF_PRECOND_NONE && o->precond != SLRF_PRECOND_JACOBI && o->precond != SLRF_PRECOND_MG)
-        return SLRF_EINVAL;
+    if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_AUTO) return SLRF_EINVAL;
     if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
         o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
         !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0))
@@ -1214,13 +1231,15 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     if (!pencil_valid(n, nnz, rp, ci, av, bv)) return SLRF_EINVAL;
     // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
     // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
+    const bool blocks = has_node_blocks(n, rp, ci, 3);
     int R = o->spmm_rows;
-    if (R == 0) R = has_node_blocks(n, rp, ci, 3) ? 3 : 2;
+    if (R == 0) R = blocks ? 3 : 2;
     std::vector<int32_t> gptr, ucol;
     std::vector<double2> uab;
     if (R > 1) build_rowgroups(R, n, rp, ci, av, bv, gptr, ucol, uab);
     slrf_handle *h = new slrf_handle();
     h->opts = *o;
+    h->node_blocks = blocks;
     h->ctx.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     h->ctx.profile = o->profile != 0;
     cudaGetDevice(&h->device);
@@ -1288,7 +1307,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         slrf_destroy(h);
         return SLRF_ECUDA;
     }
-    if (o->precond == SLRF_PRECOND_MG) {
+    if (uses_mg(h)) {
         const slrf_status st = mg_build_upload(h, rp, ci, av, bv);
         if (st != SLRF_OK) {
             slrf_destroy(h);

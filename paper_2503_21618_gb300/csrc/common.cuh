@@ -49,9 +49,9 @@ enum KernelClass {
     KC_RESIDUAL = 9,       // residual R = B X Theta - A X and norms
     KC_FILTER_COMBINE = 10,// U = X Phi(Theta) + correction, conversions
     KC_OTHER = 11,
-    KC_MG_SMOOTH = 12,     // multigrid: shifted level products (residual, Jacobi sweeps)
+    KC_MG_FINE = 12,       // multigrid: finest-level shifted products (residual, Jacobi sweep)
     KC_MG_TRANSFER = 13,   // multigrid: restriction, prolongation, first sweep
-    KC_MG_COARSE = 14,     // multigrid: coarsest-level solve
+    KC_MG_COARSE = 14,     // multigrid: coarser-level products and the coarsest solve
 };
 
 }  // namespace slrf

@@ -418,7 +418,7 @@ void launch_sspmm(Ctx &ctx, const KrylovDims &d, const MgLevel<T> &L, int gy, co
     const double vb = vec_bytes<T>(d, L.n);
     const double bytes = 4.0 * (L.ngroups + 1) + (double)L.nnz_union * (4 + L.R * sizeof(cplx<T>)) +
                          (MODE == MG_SMOOTH ? 4 : 3) * vb + (double)L.n * d.N * sizeof(cplx<T>);
-    ctx.before(KC_MG_SMOOTH, bytes, 8.0 * (double)L.nnz_union * L.R * W * d.frac);
+    ctx.before(L.n == d.n ? KC_MG_FINE : KC_MG_COARSE, bytes, 8.0 * (double)L.nnz_union * L.R * W * d.frac);
 #define SSP(RR)                                                                                                   \
     k_mg_sspmm<T, VC, RR, MODE><<<grid, block, 0, ctx.stream>>>(L.n, W, d.Lp, d.N, L.ngroups, gpb, L.gptr, L.gcol, \
                                                                L.ab, sig, L.dinv, X, Rv, Out, flag, part)

@@ -118,6 +118,12 @@ struct slrf_server {
 
 namespace {
 
+// Coarsest-size target to budget for when the request's preconditioner may
+// resolve to multigrid (AUTO is budgeted as multigrid: an upper bound), else 0.
+int request_mg_coarse(const slrf_opts &o) {
+    return (o.precond == SLRF_PRECOND_MG || o.precond == SLRF_PRECOND_AUTO) ? o.mg_coarse : 0;
+}
+
 void worker_main(slrf_server *s) {
     cudaSetDevice(s->device);
     cudaStream_t stream = nullptr;
@@ -179,7 +185,8 @@ extern "C" int64_t slrf_request_bytes(const slrf_request *r) {
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    return (int64_t)workspace_estimate(r->pencil.n, r->pencil.nnz, r->L, r->filter.n_poles, r->opts.precision, sms);
+    return (int64_t)workspace_estimate(r->pencil.n, r->pencil.nnz, r->L, r->filter.n_poles, r->opts.precision, sms,
+                                       request_mg_coarse(r->opts));
 }
 
 extern "C" slrf_status slrf_server_create(slrf_server **out, int32_t n_workers, int64_t mem_budget) {
@@ -231,7 +238,8 @@ extern "C" slrf_status slrf_server_submit(slrf_server *s, const slrf_request *r,
     q->tol = r->tol;
     q->max_outer = r->max_outer;
     q->opts = r->opts;
-    q->bytes = workspace_estimate(p.n, p.nnz, r->L, f.n_poles, r->opts.precision, s->sm_count);
+    q->bytes = workspace_estimate(p.n, p.nnz, r->L, f.n_poles, r->opts.precision, s->sm_count,
+                                  request_mg_coarse(r->opts));
     q->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);

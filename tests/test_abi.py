@@ -42,7 +42,7 @@ def test_status_strings(lib):
 def test_opts_defaults(lib):
     from paper_2503_21618_gb300 import api
     o = api.default_opts()
-    assert o.precision == api.PREC_MIXED and o.inner_maxit == 1000 and o.precond == api.PRECOND_JACOBI
+    assert o.precision == api.PREC_MIXED and o.inner_maxit == 1000 and o.precond == api.PRECOND_AUTO
 
 
 def test_create_rejects_bad_input_without_gpu(lib):

@@ -1,0 +1,117 @@
+"""GPU checks of the multigrid-preconditioned shifted solves (SLRF_PRECOND_MG)
+through the C ABI: the preconditioner changes the Krylov iterates, never the
+filter, so every variant must reproduce the oracle's filter (exact sparse LU
+per pole) to the FP64 inner tolerance, and the eigenpairs of Algorithm 1."""
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+from oracle import filter as ofilt
+from oracle import poles
+from workloads import pencil_1d, pencil_2d_q1, pencil_3d_elasticity, start_block
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api(lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_21618_gb300 import api as a
+    return a
+
+
+def rel_err(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _filter_case(p, nev, N=4):
+    lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
+    gamma = 0.5 * (lam[nev - 1] + lam[nev])
+    s, w = poles.slrf_poles(N, 1.0, 0.01, gamma)
+    return lam, gamma, s, w
+
+
+@pytest.mark.parametrize("variant", [
+    dict(precond=1),                                  # Jacobi
+    dict(precond=2),                                  # V-cycle, default levels
+    dict(precond=2, mg_coarse=16),                    # deeper hierarchy, exact solve on <= 16 unknowns
+    dict(precond=2, mg_coarse=16, mg_cycle=2),        # W-cycle
+    dict(precond=2, mg_coarse=16, mg_nu=1, mg_omega=1.0),
+])
+def test_filter_apply_fp64_each_cycle_matches_exact_lu(api, variant):
+    p = pencil_2d_q1(22, seed=9)                      # n = 441
+    _, _, s, w = _filter_case(p, 15)
+    V = start_block(p.n, 13, 4)                       # 13 columns: odd, ragged against the 2-column groups
+    h = api.Handle(p, api.default_opts(precision=api.PREC_FP64, inner_tol=1e-13, inner_maxit=3000, **variant))
+    U, st, rep = h.filter_apply(api.Filter(s, w), torch.from_numpy(V).cuda())
+    assert st == api.OK
+    assert rel_err(U.cpu().numpy(), ofilt.filter_apply(p.A(), p.B(), s, w, V)) < 1e-10
+    if variant["precond"] == 2:
+        assert rep.as_dict()["kernels"]["mg_fine"]["launches"] > 0
+
+
+def test_multigrid_cuts_the_iterations(api):
+    p = pencil_2d_q1(40, seed=3)                      # n = 1521, three levels
+    _, _, s, w = _filter_case(p, 20)
+    V = start_block(p.n, 16, 6)
+    its = {}
+    for pc in (api.PRECOND_JACOBI, api.PRECOND_MG):
+        h = api.Handle(p, api.default_opts(precision=api.PREC_FP64, inner_tol=1e-10, precond=pc))
+        U, st, rep = h.filter_apply(api.Filter(s, w), torch.from_numpy(V).cuda())
+        assert st == api.OK
+        its[pc] = max(rep.iters_per_pole[:4])
+    assert its[api.PRECOND_MG] * 3 < its[api.PRECOND_JACOBI]
+
+
+def test_single_level_hierarchy_is_an_exact_solve(api):
+    p = pencil_1d(200)                                # n <= 256: the coarsest level is the pencil
+    assert api.mg_describe(p)["levels"] == [200]
+    _, _, s, w = _filter_case(p, 8)
+    V = start_block(p.n, 6, 7)
+    h = api.Handle(p, api.default_opts(precision=api.PREC_FP64, inner_tol=1e-12, precond=api.PRECOND_MG))
+    U, st, rep = h.filter_apply(api.Filter(s, w), torch.from_numpy(V).cuda())
+    assert st == api.OK
+    assert rel_err(U.cpu().numpy(), ofilt.filter_apply(p.A(), p.B(), s, w, V)) < 1e-10
+    assert max(rep.iters_per_pole[:4]) <= 3
+
+
+def test_node_block_hierarchy(api):
+    p = pencil_3d_elasticity(5)                       # n = 300, 3-dof nodes: row groups of 3 on the finest level
+    _, _, s, w = _filter_case(p, 10)
+    V = start_block(p.n, 8, 8)
+    o = api.default_opts(precision=api.PREC_FP64, inner_tol=1e-12, inner_maxit=3000, precond=api.PRECOND_MG,
+                         mg_coarse=30)
+    assert len(api.mg_describe(p, o)["levels"]) >= 2
+    h = api.Handle(p, o)
+    U, st, _ = h.filter_apply(api.Filter(s, w), torch.from_numpy(V).cuda())
+    assert st == api.OK
+    assert rel_err(U.cpu().numpy(), ofilt.filter_apply(p.A(), p.B(), s, w, V)) < 1e-10
+
+
+def test_switching_to_multigrid_builds_the_hierarchy_lazily(api):
+    p = pencil_2d_q1(22, seed=9)
+    _, _, s, w = _filter_case(p, 15)
+    V = torch.from_numpy(start_block(p.n, 10, 4)).cuda()
+    h = api.Handle(p, api.default_opts(precision=api.PREC_FP64, inner_tol=1e-13, precond=api.PRECOND_JACOBI))
+    U1, st1, _ = h.filter_apply(api.Filter(s, w), V)
+    h.set_opts(precond=api.PRECOND_MG)
+    U2, st2, rep = h.filter_apply(api.Filter(s, w), V)
+    assert st1 == st2 == api.OK
+    assert "mg_fine" in rep.as_dict()["kernels"]
+    assert rel_err(U2.cpu().numpy(), U1.cpu().numpy()) < 1e-10
+
+
+@pytest.mark.parametrize("precond", ["JACOBI", "MG"])
+def test_subspace_2d_each_preconditioner_matches_dense(api, precond):
+    p = pencil_2d_q1(40, seed=5)
+    lam, gamma, s, w = _filter_case(p, 25)
+    h = api.Handle(p, api.default_opts(precond=getattr(api, "PRECOND_" + precond)))
+    theta, X, resid, nconv, st, rep = h.subspace_iterate(api.Filter(s, w), gamma,
+                                                         torch.from_numpy(start_block(p.n, 38, 11)).cuda(),
+                                                         tol=1e-8, max_outer=30)
+    assert st == api.OK and nconv == rep.n_wanted == 25
+    th = theta.cpu().numpy()[:25]
+    assert np.max(np.abs(th - lam[:25]) / lam[:25]) < 1e-10
