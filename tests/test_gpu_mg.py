@@ -82,7 +82,9 @@ def test_node_block_hierarchy(api):
     p = pencil_3d_elasticity(5)                       # n = 300, 3-dof nodes: row groups of 3 on the finest level
     _, _, s, w = _filter_case(p, 10)
     V = start_block(p.n, 8, 8)
-    o = api.default_opts(precision=api.PREC_FP64, inner_tol=1e-12, inner_maxit=3000, precond=api.PRECOND_MG,
+    # 1e-13 like the other FP64 filter checks: this pencil's shifted systems are
+    # worse conditioned, so 1e-12 leaves ~1.2e-10 in the solution (Jacobi too)
+    o = api.default_opts(precision=api.PREC_FP64, inner_tol=1e-13, inner_maxit=3000, precond=api.PRECOND_MG,
                          mg_coarse=30)
     assert len(api.mg_describe(p, o)["levels"]) >= 2
     h = api.Handle(p, o)
