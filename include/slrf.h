@@ -110,9 +110,9 @@ typedef struct {
     int32_t profile;        /* 1: time each kernel class with CUDA events         (0) */
     int32_t spmm_rows;      /* rows per group of the shifted SpMM (1..4); 0 = auto:
                                3 for 3-dof node-block patterns, else 2             (0) */
-    int32_t gram_ozaki;     /* Grams of the projection step: 1 = FP64-accurate
-                               int8 tensor-core products (Ozaki splitting),
-                               0 = FP64 CUDA cores                                 (1) */
+    int32_t gram_ozaki;     /* Grams and tall products (Q1 = U T1, X = Q1 M) of the
+                               projection step: 1 = FP64-accurate int8 tensor-core
+                               products (Ozaki splitting), 0 = FP64 CUDA cores     (1) */
     int32_t mg_nu;          /* MG: Jacobi sweeps per side on the levels below the
                                finest (the finest always takes one)                (2) */
     int32_t mg_cycle;       /* MG: coarse visits per level, 1 = V-, 2 = W-cycle    (1) */

@@ -148,6 +148,7 @@ struct slrf_handle {
     // named workspace buffers (grow only)
     Buf kP, kQ, kR, kDinv, kU, kPart, kSig, kScal, kFlags;
     Buf rOz;   // Ozaki Gram digits and partials
+    Buf rOzT;  // Ozaki tall-product digits
     Buf rW1, rQ1, rQ2, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
     int64_t shifted_cholqr = 0;   // Rayleigh-Ritz steps that needed the shifted fallback
     Buf hostV, hostX;   // device staging for the host-buffer entry points
@@ -792,6 +793,22 @@ slrf_status gram(slrf_handle *h, int64_t n, int m, const double *X, int64_t ldx,
     return SLRF_OK;
 }
 
+// C = (A diag(cs)) B for a tall A (n x k) and a small B (k x m): FP64-accurate
+// int8 tensor-core digits with the handle's Ozaki option, else the FP64 tile
+// GEMM (cs applied to the rows of B in place; B is scratch of the caller).
+slrf_status tall_product(slrf_handle *h, int64_t n, int k, int m, const double *A, int64_t lda, const double *cs,
+                         double *B, int64_t ldb, double *C, int64_t ldc) {
+    Ctx &ctx = h->ctx;
+    if (h->opts.gram_ozaki && ozaki_tall_fits(k)) {
+        CKS(ensure(h, h->rOzT, ozaki_tall_work_bytes(n, k, m)));
+        ozaki_tall(ctx, n, k, m, A, lda, cs, B, ldb, C, ldc, h->rOzT.p, KC_TALL_GEMM);
+        return SLRF_OK;
+    }
+    if (cs) small_scale_rows(ctx, k, cs, B);
+    dgemm(ctx, 0, 0, (int)n, m, k, A, lda, B, ldb, 0.0, C, ldc, 1, nullptr, KC_TALL_GEMM);
+    return SLRF_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky-QR2 + Rayleigh-Ritz of span(U): theta (ascending), X = U M, AX, BX
 // (all n x m with leading dimension m except U/X which take ldu/ldx)
@@ -825,8 +842,8 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     small_colscale(ctx, m, G, s);
     small_chol_upper(ctx, m, G, R1, pin_status, shift);
     small_triinv_upper(ctx, m, R1, T1);
-    small_scale_rows(ctx, m, s, T1);
-    dgemm(ctx, 0, 0, (int)n, m, m, U, ldu, T1, m, 0.0, Q1, m, 1, nullptr, KC_TALL_GEMM);
+    // Q1 = (U S) R1^{-1}: the column scaling S makes the split operand well scaled
+    CKS(tall_product(h, n, m, m, U, ldu, s, T1, m, Q1, m));
     CK(cudaEventRecord(h->ev_poll, ctx.stream));
     CK(cudaEventSynchronize(h->ev_poll));
     const int32_t st1 = *(volatile int32_t *)(h->h_pin + 1);
@@ -845,7 +862,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
         CKS(gram(h, n, m, Q1, m, W1, m, G));
         small_chol_upper(ctx, m, G, G, st + 2, 0.0);
         small_triinv_upper(ctx, m, G, T1);
-        dgemm(ctx, 0, 0, (int)n, m, m, Q1, m, T1, m, 0.0, Q2, m, 1, nullptr, KC_TALL_GEMM);
+        CKS(tall_product(h, n, m, m, Q1, m, nullptr, T1, m, Q2, m));
         CK(cudaMemcpyAsync(Q1, Q2, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream));
         h->shifted_cholqr += 1;
     } else {
@@ -867,7 +884,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     small_syev(ctx, m, Ah, theta, Sm, syw, h->opts.eig_refine);
     // X = Q1 (T2 S); AX, BX by SpMM
     dgemm(ctx, 0, 0, m, m, m, T2, m, Sm, m, 0.0, Mm, m, 1, nullptr, KC_SMALL_DENSE);
-    dgemm(ctx, 0, 0, (int)n, m, m, Q1, m, Mm, m, 0.0, X, ldx, 1, nullptr, KC_TALL_GEMM);
+    CKS(tall_product(h, n, m, m, Q1, m, nullptr, Mm, m, X, ldx));
     spmm_real(ctx, h->A, m, X, ldx, AX, m, BX, m);
     if (chol_status) {
         // pass 2 (and the extra pass) must succeed; pass 1's status was read above
@@ -1040,7 +1057,8 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
     const size_t split = (size_t)sm_count * 4;
     const size_t rr = 8 * (size_t)n * L * 8 + split * L * L * 8 + (40 * (size_t)L * L + 64 * (size_t)L) * 8 +
                       (size_t)sm_count * 12 * L * 8 + 8192;
-    const size_t ozaki = 2 * 7 * (size_t)((L + 63) / 64 * 64) * (size_t)((n + 63) / 64 * 64) + (size_t)sm_count * 4 * L * L * 8;
+    const size_t ozaki = 2 * 7 * (size_t)((L + 63) / 64 * 64) * (size_t)((n + 63) / 64 * 64) + (size_t)sm_count * 4 * L * L * 8 +
+                         ozaki_tall_work_bytes(n, L, L);
     // multigrid (mg_coarse > 0): Z block, level blocks r/z/t and Jacobi
     // diagonals (the levels below the finest hold at most n/2 rows together),
     // transfers and Galerkin pencils (bounded by the fine pattern), coarsest
@@ -1185,7 +1203,7 @@ void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
-                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ};
+                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,

@@ -183,6 +183,12 @@ void copy_block(Ctx &ctx, int n, int m, const double *src, int64_t lds, double *
 size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count);
 void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
                 void *work);
+// C = (A diag(cs)) B, A n x k, B k x m, C n x m (row-major, leading dims),
+// cs = nullptr for no column scaling; FP64-accurate from int8 digit products.
+size_t ozaki_tall_work_bytes(int64_t n, int k, int m);
+bool ozaki_tall_fits(int k);
+void ozaki_tall(Ctx &ctx, int64_t n, int k, int m, const double *A, int64_t lda, const double *cs, const double *B,
+                int64_t ldb, double *C, int64_t ldc, void *work, int kc);
 
 // ---------------------------------------------------------------- small.cu
 // All m x m matrices row-major, device.  status: device int, set nonzero on

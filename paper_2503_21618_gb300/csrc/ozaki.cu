@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace slrf {
@@ -261,6 +263,156 @@ void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const 
     ctx.after();
     ctx.before(KC_GRAM, 8.0 * (double)split * m * m, 0);
     k_oz_reduce<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, ctx.stream>>>(m, split, part, ex, ey, G, m);
+    ctx.after();
+}
+
+// ---------------------------------------------------------------------------
+// Tall product C = (A diag(cs)) B on the same digits: A is n x k (row-major,
+// n large, k small), B is k x m, C is n x m.  Rows of A take their own
+// exponent (max over the row of |A_ai cs_i|), columns of B theirs, so the
+// error is ~2^-50 of max_i |A_ai cs_i| * sum_i |B_ib|; the optional column
+// scaling cs (nullptr = 1) lets a caller whose columns differ widely in size
+// split the well-scaled A diag(cs) instead of A.
+// ---------------------------------------------------------------------------
+constexpr int OZ_TA = 128;       // tall product: CTA tile rows (4 warps x 32)
+constexpr int OZ_TB = 32;        // tall product: CTA tile columns
+
+// One warp per row: exponent e[a] and the digits of A_a diag(cs), written to
+// slices[s][a][i] (row pitch kpad, zero beyond k and beyond n).
+__global__ void __launch_bounds__(256)
+k_oz_rowsplit(int64_t n, int k, int kpad, int64_t npad, const double *__restrict__ A, int64_t lda,
+              const double *__restrict__ cs, int *__restrict__ e, int8_t *__restrict__ slices) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (a >= npad) return;
+    const bool live = a < n;
+    double mx = 0.0;
+    if (live)
+        for (int i = lane; i < k; i += 32) mx = fmax(mx, fabs(A[a * lda + i] * (cs ? cs[i] : 1.0)));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    const int ea = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (lane == 0 && live) e[a] = ea;
+    for (int i = lane; i < kpad; i += 32) {
+        const double x = (live && i < k) ? A[a * lda + i] * (cs ? cs[i] : 1.0) : 0.0;
+        int8_t d[OZ_S];
+        oz_digits(x, ea, d);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) slices[((int64_t)s * npad + a) * kpad + i] = d[s];
+    }
+}
+
+// C tile 128 x 32 per CTA, warp 32 x 32 (2 x 4 mma), all of K per CTA (k is
+// small: kpad <= 2^16 keeps each diagonal's int32 sum exact).
+__global__ void __launch_bounds__(128)
+k_oz_tall(int64_t n, int m, int kpad, int64_t npad, int mpad, const int8_t *__restrict__ SA,
+          const int8_t *__restrict__ SB, const int *__restrict__ ea, const int *__restrict__ eb, double *__restrict__ C,
+          int64_t ldc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int64_t a_base = blockIdx.y * (int64_t)OZ_TA + warp * 32;
+    const int b_base = blockIdx.x * OZ_TB;
+    const int64_t planeA = npad * kpad, planeB = (int64_t)mpad * kpad;
+    double acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) acc[i][j][h] = 0.0;
+    for (int d = 0; d < OZ_S; ++d) {
+        int c[2][4][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) c[i][j][h] = 0;
+        for (int s = 0; s <= d; ++s) {
+            const int8_t *As = SA + s * planeA;
+            const int8_t *Bt = SB + (d - s) * planeB;
+            for (int kk = 0; kk < kpad; kk += 32) {
+                unsigned af[2][4], bf[4][2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int8_t *r0 = As + (a_base + i * 16 + g) * kpad + kk + 4 * q;
+                    const int8_t *r1 = r0 + 8 * (int64_t)kpad;
+                    af[i][0] = __ldg(reinterpret_cast<const unsigned *>(r0));
+                    af[i][1] = __ldg(reinterpret_cast<const unsigned *>(r1));
+                    af[i][2] = __ldg(reinterpret_cast<const unsigned *>(r0 + 16));
+                    af[i][3] = __ldg(reinterpret_cast<const unsigned *>(r1 + 16));
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int8_t *r = Bt + (int64_t)(b_base + j * 8 + g) * kpad + kk + 4 * q;
+                    bf[j][0] = __ldg(reinterpret_cast<const unsigned *>(r));
+                    bf[j][1] = __ldg(reinterpret_cast<const unsigned *>(r + 16));
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) imma16832(c[i][j], af[i], bf[j]);
+            }
+        }
+        const double scale = ldexp(1.0, -7 * (d + 2));
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int h = 0; h < 4; ++h) acc[i][j][h] = fma((double)c[i][j][h], scale, acc[i][j][h]);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int64_t a = a_base + i * 16 + g + (h >= 2 ? 8 : 0);
+                const int b = b_base + j * 8 + 2 * q + (h & 1);
+                if (a < n && b < m) C[a * ldc + b] = ldexp(acc[i][j][h], ea[a] + eb[b]);
+            }
+}
+
+size_t ozaki_tall_work_bytes(int64_t n, int k, int m) {
+    const int64_t npad = (n + OZ_TA - 1) / OZ_TA * OZ_TA;
+    const int kpad = (k + 31) / 32 * 32, mpad = (m + OZ_TB - 1) / OZ_TB * OZ_TB;
+    return (size_t)OZ_S * npad * kpad + (size_t)OZ_S * mpad * kpad + 256 + (size_t)npad * sizeof(int) +
+           (size_t)m * (sizeof(int) + 8) + 1024;
+}
+
+bool ozaki_tall_fits(int k) { return (k + 31) / 32 * 32 <= 65536; }
+
+void ozaki_tall(Ctx &ctx, int64_t n, int k, int m, const double *A, int64_t lda, const double *cs, const double *B,
+                int64_t ldb, double *C, int64_t ldc, void *work, int kc) {
+    const int64_t npad = (n + OZ_TA - 1) / OZ_TA * OZ_TA;
+    const int kpad = (k + 31) / 32 * 32, mpad = (m + OZ_TB - 1) / OZ_TB * OZ_TB;
+    char *w = reinterpret_cast<char *>(work);
+    int8_t *SA = reinterpret_cast<int8_t *>(w);
+    int8_t *SB = SA + (size_t)OZ_S * npad * kpad;
+    char *tail = reinterpret_cast<char *>(SB + (size_t)OZ_S * mpad * kpad);
+    tail += (256 - ((uintptr_t)tail & 255)) & 255;
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(tail);
+    int *eb = reinterpret_cast<int *>(mb + m);
+    int *ea = eb + m;
+    // B: column exponents and transposed digits (rows = K, columns = m)
+    cudaMemsetAsync(mb, 0, (size_t)m * sizeof(unsigned long long), ctx.stream);
+    const dim3 cgrid((m + 31) / 32, (unsigned)std::min<int64_t>((k + 7) / 8, 64)), cblock(32, 8);
+    ctx.before(kc, 8.0 * (double)k * m * 2 + 1.0 * OZ_S * mpad * kpad, 0);
+    k_oz_colmax<<<cgrid, cblock, 0, ctx.stream>>>(k, m, B, ldb, mb);
+    k_oz_exponent<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, mb, eb);
+    const dim3 sgrid(mpad / 32, (unsigned)std::min<int64_t>(kpad / 32, 4096)), sblock(32, 8);
+    k_oz_split<<<sgrid, sblock, 0, ctx.stream>>>(k, m, kpad, B, ldb, eb, SB, mpad);
+    ctx.after();
+    // A: row exponents and digits
+    ctx.before(kc, 8.0 * (double)n * k + 1.0 * OZ_S * npad * kpad, 0);
+    k_oz_rowsplit<<<(unsigned)(npad / 8), 256, 0, ctx.stream>>>(n, k, kpad, npad, A, lda, cs, ea, SA);
+    ctx.after();
+    const dim3 grid(mpad / OZ_TB, (unsigned)(npad / OZ_TA));
+    const double pairs = OZ_S * (OZ_S + 1) / 2.0;
+    ctx.before(kc, (double)OZ_S * (npad * kpad * (double)(mpad / OZ_TB) + (double)mpad * kpad) + 8.0 * (double)n * m,
+               2.0 * pairs * (double)npad * mpad * kpad);
+    k_oz_tall<<<grid, 128, 0, ctx.stream>>>(n, m, kpad, npad, mpad, SA, SB, ea, eb, C, ldc);
     ctx.after();
 }
 

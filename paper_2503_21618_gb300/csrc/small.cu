@@ -136,37 +136,35 @@ void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *stat
 }
 
 // ---------------------------------------------------------------------------
-// X = R^{-1}, R upper triangular; one thread per column, back substitution,
-// with R staged in shared memory when it fits
+// X = R^{-1} for upper triangular R (m x m, row-major): one warp per column j,
+// back substitution x_i = (delta_ij - sum_{k=i+1..j} R_ik x_k) / R_ii with the
+// column in shared memory and each sum split over the lanes (R rows are read
+// coalesced; R stays in L1/L2).  Entries below the diagonal are set to zero.
 // ---------------------------------------------------------------------------
-__global__ void k_triinv_upper(int m, const double *__restrict__ Rg, double *__restrict__ X, int use_smem) {
-    extern __shared__ double Rs[];
-    const double *R = Rg;
-    if (use_smem) {
-        for (int e = threadIdx.x; e < m * m; e += blockDim.x) Rs[e] = Rg[e];
-        __syncthreads();
-        R = Rs;
-    }
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        for (int i = m - 1; i > j; --i) X[(int64_t)i * m + j] = 0.0;
-        for (int i = j; i >= 0; --i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= j; ++k) s -= R[(int64_t)i * m + k] * X[(int64_t)k * m + j];
-            X[(int64_t)i * m + j] = s / R[(int64_t)i * m + i];
+__global__ void __launch_bounds__(32) k_triinv_upper(int m, const double *__restrict__ R, double *__restrict__ X) {
+    extern __shared__ double xcol[];
+    const int j = blockIdx.x, lane = threadIdx.x;
+    for (int i = j + 1 + lane; i < m; i += 32) X[(int64_t)i * m + j] = 0.0;
+    for (int i = j; i >= 0; --i) {
+        const double *Ri = R + (int64_t)i * m;
+        double s = 0.0;
+        for (int k = i + 1 + lane; k <= j; k += 32) s = fma(Ri[k], xcol[k], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            const double x = ((i == j ? 1.0 : 0.0) - s) / Ri[i];
+            xcol[i] = x;
+            X[(int64_t)i * m + j] = x;
         }
+        __syncwarp();
     }
 }
 
 void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv) {
-    const size_t smem = (size_t)m * m * sizeof(double);
-    const int use_smem = smem <= 200 * 1024;
+    const size_t smem = (size_t)m * sizeof(double);
     ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
-    if (use_smem) {
-        cudaFuncSetAttribute(k_triinv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_triinv_upper<<<1, ((m + 31) / 32) * 32, smem, ctx.stream>>>(m, R, Rinv, 1);
-    } else {
-        k_triinv_upper<<<(m + 63) / 64, 64, 0, ctx.stream>>>(m, R, Rinv, 0);
-    }
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_triinv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_triinv_upper<<<m, 32, smem, ctx.stream>>>(m, R, Rinv);
     ctx.after();
 }
 
