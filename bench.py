@@ -315,7 +315,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plain", action="store_true", help="also time one plain FP64 solve")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU baseline solve")
     ap.add_argument("--workload", default="fem2d_q1_300", choices=["fem2d_q1_300", "batch", "serve", "filters"])
     ap.add_argument("--requests", type=int, default=40, help="serve: number of requests")
     ap.add_argument("--problems", type=int, default=64, help="batch: number of pencils")
@@ -357,7 +357,11 @@ def main():
     L, nev, N = iv["L"], iv["nev"], iv["n_poles"]
     f = pkg.design_poles("slrf", N, iv["gamma"], 1.0, 0.01)
     opts = pkg.default_opts(profile=1)
-    h = pkg.Handle(p, opts)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    h = pkg.Handle(p, opts)     # pencil upload, row groups, multigrid hierarchy (host)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
     V0 = torch.from_numpy(start_block(p.n, L, 2505)).cuda()
     theta = torch.empty(L, dtype=torch.float64, device="cuda")
     X = torch.empty_like(V0)
@@ -431,7 +435,7 @@ def main():
                "includes": "handle creation from host CSR, V0 upload, solve, X/theta/resid download"}
 
     plain = None
-    if args.plain and rank == 0:
+    if not args.no_plain and rank == 0:
         hp64 = pkg.Handle(p, pkg.default_opts(precision=pkg.PREC_FP64, inner_tol=1e-13, inner_maxit=1000))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -463,6 +467,10 @@ def main():
                          "launches": k["launches"], "avg_launch_us": (k["ms"] / k["launches"] * 1e3)
                          if k["launches"] else None},
             "kernel_time_share": kshare,
+            "time_split": {"setup_ms": t_setup * 1e3,
+                           "krylov_ms_per_step": sum(r["ms_krylov"] for r in reps) / len(reps),
+                           "rr_ms_per_step": sum(r["ms_rr"] for r in reps) / len(reps),
+                           "setup": "handle creation: pencil upload, row groups, multigrid hierarchy (host)"},
             "e2e": e2e,
         }
         if plain is not None:

@@ -124,7 +124,10 @@ typedef struct {
                                0 < mg_omega < 2                                  (4/3) */
     double mg_theta;        /* MG: strength-of-connection threshold of the
                                aggregation, 0 = 0.08                                (0) */
-    int32_t reserved[4];
+    int32_t stagnation_window; /* outer steps without a 10% drop of the largest
+                               wanted residual after which slrf_subspace_iterate
+                               stops with SLRF_STAGNATION; 0 = never           (8) */
+    int32_t reserved[3];
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the
@@ -201,8 +204,9 @@ slrf_status slrf_filter_apply(slrf_handle *h, const slrf_filter *f, const double
  * residuals.  MIXED runs the filter on R = B X Theta - A X (FP64) with FP32
  * Krylov, using U = X Phi(Theta) + sum_j 2 Re(w_j (A - sigma_j B)^{-1} R D_j),
  * D_j = (Theta - sigma_j)^{-1}, an identity of the filter operator.
- * Returns SLRF_OK, or NOT_CONVERGED / SUBSPACE_TOO_SMALL / CHOLQR_FAIL with
- * the outputs of the last completed step written. */
+ * Returns SLRF_OK, or NOT_CONVERGED / SUBSPACE_TOO_SMALL / CHOLQR_FAIL /
+ * STAGNATION (opts.stagnation_window) with the outputs of the last completed
+ * step written. */
 slrf_status slrf_subspace_iterate(slrf_handle *h, const slrf_filter *f, double gamma, int32_t L,
                                   const double *V0, int64_t ldv, double tol, int32_t max_outer,
                                   double *theta, double *X, int64_t ldx, double *resid,

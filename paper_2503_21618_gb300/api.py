@@ -43,7 +43,8 @@ class slrf_opts(C.Structure):
                 ("check_every", C.c_int32), ("eig_refine", C.c_int32), ("mem_budget", C.c_int64),
                 ("profile", C.c_int32), ("spmm_rows", C.c_int32), ("gram_ozaki", C.c_int32),
                 ("mg_nu", C.c_int32), ("mg_cycle", C.c_int32), ("mg_coarse", C.c_int32), ("mg_block", C.c_int32),
-                ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("reserved", C.c_int32 * 4)]
+                ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("stagnation_window", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class slrf_report(C.Structure):
@@ -297,7 +298,7 @@ class Handle:
         return U, st, rep
 
     def subspace_iterate(self, f: Filter, gamma: float, V0, tol=1e-8, max_outer=50, theta=None, X=None,
-                         resid=None, allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL)):
+                         resid=None, allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, STAGNATION)):
         import torch
         L = V0.shape[1]
         dev = V0.device
@@ -313,7 +314,7 @@ class Handle:
         return theta, X, resid, nconv.value, st, rep
 
     def subspace_iterate_host(self, f: Filter, gamma: float, V0: np.ndarray, tol=1e-8, max_outer=50,
-                              allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL)):
+                              allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, STAGNATION)):
         V0 = np.ascontiguousarray(V0, dtype=np.float64)
         n, L = V0.shape
         theta = np.zeros(L)

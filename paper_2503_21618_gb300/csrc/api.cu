@@ -927,6 +927,19 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
     slrf_status status = SLRF_NOT_CONVERGED;
     int nw = 0, nc = 0;
     double worst = 0, worst_ax = 0;
+    // stagnation: outer steps since the largest wanted residual last fell below
+    // 0.9 of its best value
+    double best_worst = HUGE_VAL;
+    int since_best = 0;
+    auto stagnated = [&]() {
+        if (nw == 0 || h->opts.stagnation_window <= 0) return false;
+        if (worst < 0.9 * best_worst) {
+            best_worst = worst;
+            since_best = 0;
+            return false;
+        }
+        return ++since_best >= h->opts.stagnation_window;
+    };
 
     auto evaluate = [&]() -> slrf_status {
         residual(ctx, (int)n, L, AX, BX, L, theta, mixed ? Rm : nullptr, L, resid, rho_ax, rwork);
@@ -1014,6 +1027,10 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
         CKS(evaluate());
         if (chol[0] || chol[1]) {
             status = SLRF_CHOLQR_FAIL;
+            break;
+        }
+        if (!(nw > 0 && nc == nw) && stagnated()) {
+            status = SLRF_STAGNATION;
             break;
         }
         if (!mixed) {
@@ -1125,6 +1142,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->mg_block = 0;
     o->mg_omega = 4.0 / 3.0;
     o->mg_theta = 0.0;
+    o->stagnation_window = 8;
     return SLRF_OK;
 }
 
@@ -1135,7 +1153,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_AUTO) return SLRF_EINVAL;
     if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
         o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
-        !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0))
+        !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0) || o->stagnation_window < 0)
         return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;

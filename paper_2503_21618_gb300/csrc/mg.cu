@@ -75,13 +75,15 @@ __device__ __forceinline__ bool col_active(const int32_t *flag, int c0) {
 //   SMOOTH: out = x + D (r - M x), optional partial r^T out per column
 // ---------------------------------------------------------------------------
 template <typename T, int VC, int R, int MODE>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, 6)
 k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, int groups_per_block, const int32_t *__restrict__ gptr,
            const int32_t *__restrict__ ucol, const cplx<T> *__restrict__ uab, const cplx<T> *__restrict__ sig,
            const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ X, const cplx<T> *__restrict__ Rv,
            cplx<T> *__restrict__ Out, const int32_t *__restrict__ flag, T *__restrict__ part) {
     using C = cplx<T>;
-    constexpr int UNR = 4;
+    // measured on the 2D bench: 2-deep gathers at 6 CTAs per SM beat 4-deep at 4
+    // (125 vs 134 ms per solve) and 8-deep (155 ms)
+    constexpr int UNR = 2;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int ng = W / VC;
     const int cg = blockIdx.x * 32 + tx;

@@ -147,6 +147,25 @@ def test_subspace_too_small_is_reported(api):
     assert st == api.SUBSPACE_TOO_SMALL
 
 
+def test_stagnation_is_reported(api):
+    # a single pole far outside the spectrum gives an almost constant filter:
+    # the subspace stops improving, and the iteration says so instead of
+    # running to max_outer
+    n = 400
+    p = pencil_1d(n)
+    lam = inertia.lambda_1d(n)
+    gamma = 0.5 * (lam[7] + lam[8])
+    far = api.Filter([1e6 * gamma * (1 + 1j)], [1.0])
+    V0 = torch.from_numpy(start_block(n, 12, 3)).cuda()
+    h = api.Handle(p, api.default_opts(stagnation_window=4))
+    *_, nconv, st, rep = h.subspace_iterate(far, gamma, V0, tol=1e-8, max_outer=40)
+    assert st == api.STAGNATION
+    assert rep.outer_iters <= 6 and nconv < rep.n_wanted
+    h.set_opts(stagnation_window=0)
+    *_, nconv, st, rep = h.subspace_iterate(far, gamma, V0, tol=1e-8, max_outer=7)
+    assert st == api.NOT_CONVERGED and rep.outer_iters == 7
+
+
 def test_invalid_arguments_are_rejected(api):
     p = pencil_1d(50)
     h = api.Handle(p)
