@@ -79,7 +79,12 @@ typedef struct {
 
 enum { SLRF_PREC_FP64 = 0,  /* plain: FP64 Krylov to inner_tol relative to ||B v||        */
        SLRF_PREC_MIXED = 1  /* FP32 Krylov on the FP64 residual R = B X Theta - A X      */ };
-enum { SLRF_KRYLOV_COCG = 0 };
+/* COCG: conjugate-orthogonal CG (unconjugated bilinear form; needs a complex
+ * symmetric preconditioner), one shifted product and one preconditioner
+ * application per iteration.  BICGSTAB: right-preconditioned BiCGStab with
+ * Hermitian products (the paper's solver, Section 4.2.1), two of each per
+ * iteration; slrf_report.spmv counts both products. */
+enum { SLRF_KRYLOV_COCG = 0, SLRF_KRYLOV_BICGSTAB = 1 };
 /* Preconditioner of the shifted solves.  JACOBI: diag(A - sigma_j B).  MG:
  * smoothed-aggregation multigrid cycle (one hierarchy for all poles, built
  * from A; Galerkin pencils (P^T A P, P^T B P) on every level; damped Jacobi
@@ -125,8 +130,9 @@ typedef struct {
     double mg_theta;        /* MG: strength-of-connection threshold of the
                                aggregation, 0 = 0.08                                (0) */
     int32_t stagnation_window; /* outer steps without a 10% drop of the largest
-                               wanted residual after which slrf_subspace_iterate
-                               stops with SLRF_STAGNATION; 0 = never           (8) */
+                               wanted residual (of all Ritz pairs while none is
+                               wanted) after which slrf_subspace_iterate stops
+                               with SLRF_STAGNATION; 0 = never                  (8) */
     int32_t reserved[3];
 } slrf_opts;
 

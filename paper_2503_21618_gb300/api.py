@@ -18,7 +18,7 @@ from . import _build
 OK, EINVAL, ENOMEM, EBUDGET, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PENDING = 6, 7, 8, 9, 10, 11
 PREC_FP64, PREC_MIXED = 0, 1
-KRYLOV_COCG = 0
+KRYLOV_COCG, KRYLOV_BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG, PRECOND_AUTO = 0, 1, 2, 3
 RULE_MIDPOINT, RULE_GAUSS_LEGENDRE, RULE_GAUSS_CHEBYSHEV, RULE_SLRF = 0, 1, 2, 3
 RULES = {"midpoint": 0, "gauss_legendre": 1, "gauss_chebyshev": 2, "slrf": 3}

@@ -154,6 +154,7 @@ struct slrf_handle {
     Buf hostV, hostX;   // device staging for the host-buffer entry points
     // multigrid preconditioner: hierarchy (static), per-solve level blocks, Z
     Buf mgStatic, mgState, kZ;
+    Buf kBcg;   // BiCGStab: r^, v, y, z, t blocks and omega scalars
     bool node_blocks = false;             // 3-dof node-block pattern (elasticity)
     bool mg_ready = false;
     int mg_block = 0, mg_coarse = 0;      // parameters the hierarchy was built with
@@ -711,10 +712,26 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
     // the host vectors above are pageable; make the copies complete before they go out of scope
     const bool use_mg = uses_mg(h);
+    const bool bcg = h->opts.krylov == SLRF_KRYLOV_BICGSTAB;
     kb.Z = nullptr;
+    BcgBuffers<T> bb{};
+    if (bcg) {
+        const size_t blk = (size_t)n * W * sizeof(cplx<T>);
+        CKS(ensure(h, h->kBcg, 5 * blk + 2 * (size_t)W * sizeof(cplx<T>)));
+        char *q = reinterpret_cast<char *>(h->kBcg.p);
+        bb.Rh = reinterpret_cast<cplx<T> *>(q);
+        bb.V = reinterpret_cast<cplx<T> *>(q + blk);
+        bb.Y = reinterpret_cast<cplx<T> *>(q + 2 * blk);
+        bb.Z = reinterpret_cast<cplx<T> *>(q + 3 * blk);
+        bb.Tt = reinterpret_cast<cplx<T> *>(q + 4 * blk);
+        bb.omega = reinterpret_cast<cplx<T> *>(q + 5 * blk);
+        bb.ua2 = bb.omega + W;
+    }
     if (use_mg) {
-        CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
-        kb.Z = as<cplx<T>>(h->kZ);
+        if (!bcg) {
+            CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
+            kb.Z = as<cplx<T>>(h->kZ);
+        }
         CKS(mg_prepare<T>(h, f, d, kb));
     } else {
         const PoleSet<T> ps = make_poleset<T>(f);
@@ -724,7 +741,9 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     const cplx<T> *sig = as<cplx<T>>(h->kSig);
     fill_zero(ctx, kb.Uacc, (size_t)n * d.Lp * sizeof(T));
     krylov_init<T>(ctx, d, kb, rhs, ldr, nullptr);
-    if (use_mg) {
+    if (bcg) {
+        bicgstab_init<T>(ctx, d, kb, bb);
+    } else if (use_mg) {
         mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q);
         krylov_direction<T>(ctx, d, kb, 1);
     }
@@ -738,7 +757,24 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     int it = 0;
     for (; it < maxit;) {
         const int chunk = std::min(every, maxit - it);
-        for (int k = 0; k < chunk; ++k) {
+        for (int k = 0; k < chunk && bcg; ++k) {
+            // y = M^{-1} p ; v = A y ; alpha ; s = r - alpha v ; z = M^{-1} s ; t = A z ; omega ;
+            // x, r ; rho', beta ; p
+            if (use_mg)
+                mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.P, bb.Y, bb.Tt);
+            else
+                bicgstab_precond_jacobi<T>(ctx, d, kb, kb.P, bb.Y);
+            krylov_spmm<T>(ctx, d, h->A, sig, bb.Y, bb.V, kb.s.flag, kb.s.part, kb.gy);
+            bicgstab_alpha<T>(ctx, d, kb, bb);
+            bicgstab_s<T>(ctx, d, kb, bb, !use_mg);
+            if (use_mg) mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, bb.Z, bb.Tt);
+            krylov_spmm<T>(ctx, d, h->A, sig, bb.Z, bb.Tt, kb.s.flag, kb.s.part, kb.gy);
+            bicgstab_omega<T>(ctx, d, kb, bb);
+            bicgstab_update<T>(ctx, d, kb, bb);
+            krylov_reduce_beta<T>(ctx, d, kb, tol2, maxit);
+            bicgstab_direction<T>(ctx, d, kb, bb);
+        }
+        for (int k = 0; k < chunk && !bcg; ++k) {
             krylov_spmm<T>(ctx, d, h->A, sig, kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
             krylov_reduce_alpha<T>(ctx, d, kb);
             krylov_update<T>(ctx, d, kb);
@@ -772,7 +808,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
             if (fl[col] == 1 || fl[col] == 3) ++st.n_fail;
             if (fl[col] == 2) ++st.n_breakdown;
         }
-        st.spmv += s;
+        st.spmv += bcg ? 2 * s : s;
         st.iters_per_pole[j] = cnt ? (double)s / cnt : 0.0;
     }
     return SLRF_OK;
@@ -926,15 +962,16 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
     int outer = 0;
     slrf_status status = SLRF_NOT_CONVERGED;
     int nw = 0, nc = 0;
-    double worst = 0, worst_ax = 0;
-    // stagnation: outer steps since the largest wanted residual last fell below
-    // 0.9 of its best value
+    double worst = 0, worst_ax = 0, worst_all = 0;
+    // stagnation: outer steps since the largest wanted residual (all Ritz pairs
+    // while none is wanted yet) last fell below 0.9 of its best value
     double best_worst = HUGE_VAL;
     int since_best = 0;
     auto stagnated = [&]() {
-        if (nw == 0 || h->opts.stagnation_window <= 0) return false;
-        if (worst < 0.9 * best_worst) {
-            best_worst = worst;
+        if (h->opts.stagnation_window <= 0) return false;
+        const double w = nw > 0 ? worst : worst_all;
+        if (w < 0.9 * best_worst) {
+            best_worst = w;
             since_best = 0;
             return false;
         }
@@ -949,8 +986,9 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
         CK(cudaStreamSynchronize(ctx.stream));
         CK(cudaGetLastError());
         nw = nc = 0;
-        worst = worst_ax = 0;
+        worst = worst_ax = worst_all = 0;
         for (int i = 0; i < L; ++i) {
+            worst_all = std::max(worst_all, rh[i]);
             if (th[i] > 0 && th[i] <= gamma) {
                 ++nw;
                 if (rh[i] <= tol && rha[i] <= tol) ++nc;
@@ -1149,7 +1187,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
 static slrf_status check_opts(const slrf_opts *o) {
     if (!o) return SLRF_EINVAL;
     if (o->precision != SLRF_PREC_FP64 && o->precision != SLRF_PREC_MIXED) return SLRF_EINVAL;
-    if (o->krylov != SLRF_KRYLOV_COCG) return SLRF_EINVAL;
+    if (o->krylov != SLRF_KRYLOV_COCG && o->krylov != SLRF_KRYLOV_BICGSTAB) return SLRF_EINVAL;
     if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_AUTO) return SLRF_EINVAL;
     if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
         o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
@@ -1221,7 +1259,7 @@ void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
-                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT};
+                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT, &h->kBcg};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,

@@ -117,6 +117,27 @@ void krylov_count_active(Ctx &ctx, int W, const int32_t *flag, int32_t *count);
 template <typename T>
 void krylov_reduce_mu(Ctx &ctx, const KrylovDims &d, const T *part, int gy, cplx<T> *mu);
 
+// ---------------------------------------------------------------- bicgstab.cu
+// Extra state of block BiCGStab (n x W each) and its per-column omega.
+template <typename T> struct BcgBuffers {
+    cplx<T> *Rh, *V, *Y, *Z, *Tt;        // shadow residual, A y, M^{-1} p, M^{-1} s, A z
+    cplx<T> *omega, *ua2;                // omega and 2 coef omega (W each)
+};
+// r^ = r, p = r, partials for rho = (r^, r) and |b|^2 (then krylov_reduce_init)
+template <typename T> void bicgstab_init(Ctx &, const KrylovDims &, KrylovBuffers<T> &, BcgBuffers<T> &);
+template <typename T>
+void bicgstab_precond_jacobi(Ctx &, const KrylovDims &, KrylovBuffers<T> &, const cplx<T> *In, cplx<T> *Out);
+// alpha = rho / (r^, v)
+template <typename T> void bicgstab_alpha(Ctx &, const KrylovDims &, KrylovBuffers<T> &, BcgBuffers<T> &);
+// s = r - alpha v (in R); jacobi: also Z = D s
+template <typename T> void bicgstab_s(Ctx &, const KrylovDims &, KrylovBuffers<T> &, BcgBuffers<T> &, bool jacobi);
+// omega = (t, s) / (t, t)
+template <typename T> void bicgstab_omega(Ctx &, const KrylovDims &, KrylovBuffers<T> &, BcgBuffers<T> &);
+// U += filter terms of alpha y + omega z; r = s - omega t; partials of (r^, r), |r|^2
+template <typename T> void bicgstab_update(Ctx &, const KrylovDims &, KrylovBuffers<T> &, BcgBuffers<T> &);
+// p = r + (beta alpha / omega)(p - omega v) (after krylov_reduce_beta)
+template <typename T> void bicgstab_direction(Ctx &, const KrylovDims &, KrylovBuffers<T> &, BcgBuffers<T> &);
+
 // ---------------------------------------------------------------- mg.cu
 // Device view of the multigrid hierarchy for one Krylov precision T.  Level 0
 // is the caller's pencil (row-group form); levels 1.. are Galerkin pencils in
