@@ -207,19 +207,23 @@ def serve_stream(pkg, count, n_lo=10000, n_hi=500000, nev_lo=20, nev_hi=200, rat
         if delay > 0:
             time.sleep(delay)
         tickets.append(srv.submit(pr["pencil"], f, pr["gamma"], pr["V0"], tol=TOL, max_outer=MAX_OUTER))
-    lat, conv, statuses, sizes = [], 0, [], []
-    for t, (_, pr) in zip(tickets, stream):
+    lat, conv, statuses, sizes, detail = [], 0, [], [], []
+    for t, (t_arr, pr) in zip(tickets, stream):
         th, X, r, nc, st, rep, lt = srv.poll(t, wait=True)
         lat.append(lt)
         conv += nc if st == pkg.OK else 0
         statuses.append(int(st))
         sizes.append(int(pr["pencil"].n))
+        if len(detail) < 64:
+            detail.append({"kind": pr["kind"], "n": int(pr["pencil"].n), "nev": int(pr["nev_target"]),
+                           "arrival_s": round(float(t_arr), 3), "status": int(st), "latency_ms": round(float(lt), 1),
+                           "solve_ms": round(float(rep.ms_total), 1), "outer": int(rep.outer_iters)})
     wall = time.perf_counter() - t0
     srv.close()
     return {"requests": count, "workers": workers, "arrival_rate_per_s": rate,
             "n_range": [min(sizes), max(sizes)], "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "eigenpairs_per_s": conv / wall, "wall_s": wall,
-            "converged_eigenpairs": conv, "ok": sum(1 for x in statuses if x == 0)}
+            "converged_eigenpairs": conv, "ok": sum(1 for x in statuses if x == 0), "detail": detail}
 
 
 def run_serve(args, pkg, rank, world):
@@ -286,7 +290,9 @@ def run_batch(args, pkg, rank, world):
     res = pkg.api.batch_iterate(handles, filters, gam, V0s, tol=TOL, max_outer=MAX_OUTER)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    conv = sum(r[3] for r in res if r[4] == pkg.OK)
+    # every eigenpair that passed both gates counts, also from problems that
+    # stopped short of all wanted pairs (stagnation, iteration cap)
+    conv = sum(r[3] for r in res)
     t0 = time.perf_counter()
     for h, f, g, v in zip(handles, filters, gam, V0s):
         h.subspace_iterate(f, g, v, tol=TOL, max_outer=MAX_OUTER)
@@ -300,7 +306,12 @@ def run_batch(args, pkg, rank, world):
                                      "kinds": {k: sum(1 for p in probs if p["kind"] == k) for k in ("1d", "2d", "3d")}},
                           "seconds_batched": t_batch, "seconds_one_by_one": t_seq,
                           "eigenpairs_per_s_one_by_one": conv / t_seq, "converged_eigenpairs": conv,
-                          "ok": sum(1 for r in res if r[4] == pkg.OK)}), flush=True)
+                          "ok": sum(1 for r in res if r[4] == pkg.OK),
+                          "not_ok": [{"kind": pr["kind"], "n": int(pr["pencil"].n), "nev": int(pr["nev_target"]),
+                                      "status": int(r[4]), "n_conv": int(r[3]), "n_wanted": int(r[5].n_wanted),
+                                      "outer": int(r[5].outer_iters), "max_resid": float(r[5].max_resid),
+                                      "iters_per_pole": [round(x, 1) for x in r[5].iters_per_pole[:4]]}
+                                     for pr, r in zip(probs, res) if r[4] != pkg.OK]}), flush=True)
     for h in handles:
         h.close()
 

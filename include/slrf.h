@@ -129,6 +129,12 @@ typedef struct {
                                0 < mg_omega < 2                                  (4/3) */
     double mg_theta;        /* MG: strength-of-connection threshold of the
                                aggregation, 0 = 0.08                                (0) */
+    double mg_shift_limit;  /* MG: a level is smoothed only while
+                               max_j |sigma_j| max_i b_ii / a_ii <= this; the first
+                               level beyond it is solved exactly (its eigen-
+                               decomposition is computed on first use, up to 768
+                               unknowns; beyond that AUTO falls back to Jacobi
+                               for the solve)                                    (0.8) */
     int32_t stagnation_window; /* outer steps without a 10% drop of the largest
                                wanted residual (of all Ritz pairs while none is
                                wanted) after which slrf_subspace_iterate stops
@@ -159,6 +165,10 @@ typedef struct {
     double k_ms[SLRF_NKERNEL_CLASSES];
     double k_bytes[SLRF_NKERNEL_CLASSES];
     double k_flops[SLRF_NKERNEL_CLASSES];
+    int32_t mg_levels;            /* multigrid levels of the last Krylov solve
+                                     (0: Jacobi or no preconditioner)           */
+    int32_t krylov_fp64;          /* MIXED: 1 if the solve switched its Krylov
+                                     solves to FP64 after the FP32 ones stagnated */
 } slrf_report;
 
 /* ---- library -------------------------------------------------------- */

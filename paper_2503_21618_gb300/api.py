@@ -43,7 +43,8 @@ class slrf_opts(C.Structure):
                 ("check_every", C.c_int32), ("eig_refine", C.c_int32), ("mem_budget", C.c_int64),
                 ("profile", C.c_int32), ("spmm_rows", C.c_int32), ("gram_ozaki", C.c_int32),
                 ("mg_nu", C.c_int32), ("mg_cycle", C.c_int32), ("mg_coarse", C.c_int32), ("mg_block", C.c_int32),
-                ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("stagnation_window", C.c_int32),
+                ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("mg_shift_limit", C.c_double),
+                ("stagnation_window", C.c_int32),
                 ("reserved", C.c_int32 * 3)]
 
 
@@ -54,7 +55,7 @@ class slrf_report(C.Structure):
                 ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_krylov", C.c_double),
                 ("ms_rr", C.c_double), ("k_launches", C.c_int64 * NKERNEL_CLASSES),
                 ("k_ms", C.c_double * NKERNEL_CLASSES), ("k_bytes", C.c_double * NKERNEL_CLASSES),
-                ("k_flops", C.c_double * NKERNEL_CLASSES)]
+                ("k_flops", C.c_double * NKERNEL_CLASSES), ("mg_levels", C.c_int32), ("krylov_fp64", C.c_int32)]
 
     def as_dict(self, lib=None) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("k_") and k != "iters_per_pole"}

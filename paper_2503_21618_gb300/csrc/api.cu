@@ -163,6 +163,17 @@ struct slrf_handle {
     std::vector<int64_t> mg_level_n, mg_level_nnz;
     double mg_setup_ms = 0.0;
     std::vector<char> mg_cinv_host;       // staging of 1/(lambda_k - sigma_j)
+    // deep shifts truncate the cycle at the first level where the shift
+    // outweighs the diagonal; that level is then solved exactly
+    struct MgEig {
+        std::vector<double> lam;
+        Buf dev;                          // FP32 then FP64 eigenvectors
+    } mg_eig[slrf::MG_MAX_LEVELS];
+    std::vector<slrf::HostLevel> mg_host_lv;   // level pencils (no transfers)
+    std::vector<double> mg_maxba;              // per level max_i b_ii / a_ii
+    int mg_nlev_full = 0;
+    const float *mg_fullV32 = nullptr;
+    const double *mg_fullV64 = nullptr;
     slrf::MgSolve<float> mg32;
     slrf::MgSolve<double> mg64;
     int32_t *h_pin = nullptr;   // pinned host words for polls
@@ -531,6 +542,24 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
     fill(h->mg32, 0.0f);
     fill(h->mg64, 0.0);
     h->mg_lam = H.lam;
+    h->mg_nlev_full = nlev;
+    h->mg_fullV32 = h->mg32.V;
+    h->mg_fullV64 = h->mg64.V;
+    h->mg_maxba.clear();
+    h->mg_host_lv.clear();
+    for (int l = 0; l < nlev; ++l) {
+        h->mg_maxba.push_back(H.lv[l].maxba);
+        HostLevel c;
+        c.n = H.lv[l].n;
+        if (l >= 1) {
+            c.ptr = H.lv[l].ptr;
+            c.col = H.lv[l].col;
+            c.a = H.lv[l].a;
+            c.b = H.lv[l].b;
+        }
+        h->mg_host_lv.push_back(std::move(c));
+    }
+    for (auto &e : h->mg_eig) e.lam.clear();
     h->mg_level_n.clear();
     h->mg_level_nnz.clear();
     for (int l = 0; l < nlev; ++l) {
@@ -586,12 +615,67 @@ template <typename T> MgSolve<T> &mg_of(slrf_handle *h);
 template <> MgSolve<float> &mg_of<float>(slrf_handle *h) { return h->mg32; }
 template <> MgSolve<double> &mg_of<double>(slrf_handle *h) { return h->mg64; }
 
+constexpr int kMgExactMax = 768;   // largest level diagonalised on demand (host, O(n^3))
+
 // Per-solve level blocks, 1/(lambda_k - sigma_j) and the damped Jacobi
-// diagonals of every smoothed level.
+// diagonals of every smoothed level.  The cycle stops at the first level
+// whose shift weight max_j |sigma_j| max_i b_ii/a_ii exceeds mg_shift_limit
+// (there a Jacobi sweep no longer smooths the shifted operator); that level
+// is solved exactly.  *usable = false (AUTO only) when that level is too
+// large to diagonalise: the caller then uses Jacobi for this solve.
 template <typename T>
-slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d, KrylovBuffers<T> &kb) {
+slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d, KrylovBuffers<T> &kb,
+                       bool allow_fallback, bool *usable) {
+    *usable = true;
     CKS(mg_ensure(h));
     MgSolve<T> &mg = mg_of<T>(h);
+    const int nfull = h->mg_nlev_full;
+    double smax = 0.0;
+    for (int j = 0; j < f->n_poles; ++j) smax = std::max(smax, std::hypot(f->sigma_re[j], f->sigma_im[j]));
+    int c = nfull - 1;
+    for (int l = 1; l < nfull - 1; ++l)
+        if (smax * h->mg_maxba[l] > h->opts.mg_shift_limit) {
+            c = l;
+            break;
+        }
+    const std::vector<double> *lam = &h->mg_lam;
+    const T *V = reinterpret_cast<const T *>(sizeof(T) == 4 ? (const void *)h->mg_fullV32 : (const void *)h->mg_fullV64);
+    if (c < nfull - 1) {
+        auto &E = h->mg_eig[c];
+        const int ncl = h->mg_host_lv[c].n;
+        if (E.lam.empty() && ncl > kMgExactMax) {
+            if (allow_fallback) {
+                *usable = false;
+                return SLRF_OK;
+            }
+            c = nfull - 1;   // explicit MG: keep the full cycle
+        } else {
+            if (E.lam.empty()) {
+                std::vector<double> Vh;
+                const std::string err = mg_level_eig(h->mg_host_lv[c], Vh, E.lam);
+                if (!err.empty()) {
+                    E.lam.clear();
+                    g_last_error = err;
+                    return SLRF_BREAKDOWN;
+                }
+                const size_t nn = (size_t)ncl * ncl;
+                const size_t off64 = (nn * 4 + 255) / 256 * 256;
+                CKS(ensure(h, E.dev, off64 + nn * 8));
+                std::vector<char> stage(off64 + nn * 8);
+                float *v32 = reinterpret_cast<float *>(stage.data());
+                for (size_t k = 0; k < nn; ++k) v32[k] = (float)Vh[k];
+                memcpy(stage.data() + off64, Vh.data(), nn * 8);
+                CK(cudaMemcpyAsync(E.dev.p, stage.data(), stage.size(), cudaMemcpyHostToDevice, h->ctx.stream));
+                CK(cudaStreamSynchronize(h->ctx.stream));   // pageable staging
+            }
+            const size_t off64 = ((size_t)ncl * ncl * 4 + 255) / 256 * 256;
+            V = reinterpret_cast<const T *>(reinterpret_cast<char *>(E.dev.p) + (sizeof(T) == 4 ? 0 : off64));
+            lam = &E.lam;
+        }
+    }
+    mg.nlev = c + 1;
+    mg.nc = h->mg_host_lv[c].n;
+    mg.V = V;
     mg.nu = std::max(1, h->opts.mg_nu);
     mg.gamma = std::max(1, h->opts.mg_cycle);
     mg.omega = h->opts.mg_omega;
@@ -627,7 +711,7 @@ slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d
     cplx<T> *ci = reinterpret_cast<cplx<T> *>(h->mg_cinv_host.data());
     for (int k = 0; k < nc; ++k)
         for (int j = 0; j < N; ++j) {
-            const cd v = 1.0 / (cd(h->mg_lam[k], 0.0) - cd(f->sigma_re[j], f->sigma_im[j]));
+            const cd v = 1.0 / (cd((*lam)[k], 0.0) - cd(f->sigma_re[j], f->sigma_im[j]));
             ci[(size_t)k * N + j] = mk((T)v.real(), (T)v.imag());
         }
     CK(cudaMemcpyAsync(mg.cinv, ci, h->mg_cinv_host.size(), cudaMemcpyHostToDevice, h->ctx.stream));
@@ -644,6 +728,7 @@ struct KStats {
     double iters_per_pole[SLRF_MAX_POLES] = {};
     int n_fail = 0;               // columns that hit the cap or broke down
     int n_breakdown = 0;
+    int mg_levels = 0;            // multigrid levels used (0: none)
 };
 
 template <typename T>
@@ -711,7 +796,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     for (int j = 0; j < N; ++j) sg[j] = mk((T)f->sigma_re[j], (T)f->sigma_im[j]);
     CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
     // the host vectors above are pageable; make the copies complete before they go out of scope
-    const bool use_mg = uses_mg(h);
+    bool use_mg = uses_mg(h);
     const bool bcg = h->opts.krylov == SLRF_KRYLOV_BICGSTAB;
     kb.Z = nullptr;
     BcgBuffers<T> bb{};
@@ -728,11 +813,15 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         bb.ua2 = bb.omega + W;
     }
     if (use_mg) {
+        bool usable = true;
+        CKS(mg_prepare<T>(h, f, d, kb, h->opts.precond == SLRF_PRECOND_AUTO, &usable));
+        use_mg = usable;
+    }
+    if (use_mg) {
         if (!bcg) {
             CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
             kb.Z = as<cplx<T>>(h->kZ);
         }
-        CKS(mg_prepare<T>(h, f, d, kb));
     } else {
         const PoleSet<T> ps = make_poleset<T>(f);
         krylov_dinv<T>(ctx, h->A, ps, h->opts.precond == SLRF_PRECOND_NONE ? SLRF_PRECOND_NONE : SLRF_PRECOND_JACOBI,
@@ -797,6 +886,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     CK(cudaMemcpyAsync(its.data(), kb.s.iters, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
     CK(cudaStreamSynchronize(ctx.stream));
     st = KStats();
+    st.mg_levels = use_mg ? mg_of<T>(h).nlev : 0;
     for (int j = 0; j < N; ++j) {
         int64_t s = 0, cnt = 0;
         for (int c = 0; c < m; ++c) {
@@ -967,6 +1057,7 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
     // while none is wanted yet) last fell below 0.9 of its best value
     double best_worst = HUGE_VAL;
     int since_best = 0;
+    bool k64 = false;   // MIXED: Krylov solves escalated to FP64
     auto stagnated = [&]() {
         if (h->opts.stagnation_window <= 0) return false;
         const double w = nw > 0 ? worst : worst_all;
@@ -1039,11 +1130,19 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
                     phi[c] += 2.0 * (w * dj).real();
                 }
             }
-            KrylovBuffers<float> kb;
-            CKS(krylov_solve<float>(h, f, L, Rm, L, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d, st));
             CKS(ensure(h, h->rTheta, (size_t)L * sizeof(double)));
             CK(cudaMemcpyAsync(h->rTheta.p, phi.data(), L * sizeof(double), cudaMemcpyHostToDevice, ctx.stream));
-            filter_combine<float>(ctx, (int)n, L, X, ldx, as<double>(h->rTheta), kb.Uacc, d.Lp, U, L);
+            if (!k64) {
+                KrylovBuffers<float> kb;
+                CKS(krylov_solve<float>(h, f, L, Rm, L, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d,
+                                        st));
+                filter_combine<float>(ctx, (int)n, L, X, ldx, as<double>(h->rTheta), kb.Uacc, d.Lp, U, L);
+            } else {
+                KrylovBuffers<double> kb;
+                CKS(krylov_solve<double>(h, f, L, Rm, L, active, coef, h->opts.inner_tol, h->opts.inner_maxit, kb, d,
+                                         st));
+                filter_combine<double>(ctx, (int)n, L, X, ldx, as<double>(h->rTheta), kb.Uacc, d.Lp, U, L);
+            }
             CK(cudaStreamSynchronize(ctx.stream));   // phi is pageable host memory
         } else {
             // F = B V ; U = sum_j 2 Re(w_j (A - sigma_j B)^{-1} F)
@@ -1068,8 +1167,18 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
             break;
         }
         if (!(nw > 0 && nc == nw) && stagnated()) {
-            status = SLRF_STAGNATION;
-            break;
+            // The FP32 corrections of the mixed form contract only while
+            // kappa(A - sigma B) eps_32 < 1; past that the iteration stalls.
+            // Continue with FP64 Krylov solves of the same corrected form
+            // before giving up.
+            if (mixed && !k64) {
+                k64 = true;
+                best_worst = HUGE_VAL;
+                since_best = 0;
+            } else {
+                status = SLRF_STAGNATION;
+                break;
+            }
         }
         if (!mixed) {
             if (nw == L) {
@@ -1093,6 +1202,8 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
         rep->max_resid_ax = worst_ax;
         rep->krylov_iters = kit;
         rep->spmv = spmv;
+        rep->mg_levels = st.mg_levels;
+        rep->krylov_fp64 = k64 ? 1 : 0;
         for (int j = 0; j < N; ++j) rep->iters_per_pole[j] = outer ? ipp[j] / outer : 0.0;
     }
     return status;
@@ -1122,7 +1233,7 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
     if (mg_coarse > 0) {
         const size_t nh = (size_t)n / 2 + 1, nc = (size_t)mg_coarse;
         mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 96 * (size_t)nnz + nc * nc * 12 +
-              nc * N * 2 * ts + 16 * 4096;
+              nc * N * 2 * ts + 16 * 4096 + 768 * 768 * 12 + 768 * (size_t)N * 2 * ts;
     }
     return pencil + krylov + rr + ozaki + mgb;
 }
@@ -1180,6 +1291,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->mg_block = 0;
     o->mg_omega = 4.0 / 3.0;
     o->mg_theta = 0.0;
+    o->mg_shift_limit = 0.8;
     o->stagnation_window = 8;
     return SLRF_OK;
 }
@@ -1191,7 +1303,8 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_AUTO) return SLRF_EINVAL;
     if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
         o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
-        !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0) || o->stagnation_window < 0)
+        !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0) || o->stagnation_window < 0 ||
+        !(o->mg_shift_limit > 0.0))
         return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
@@ -1259,7 +1372,11 @@ void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
-                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT, &h->kBcg};
+                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT, &h->kBcg,
+                   &h->mg_eig[0].dev, &h->mg_eig[1].dev, &h->mg_eig[2].dev, &h->mg_eig[3].dev,
+                   &h->mg_eig[4].dev, &h->mg_eig[5].dev, &h->mg_eig[6].dev, &h->mg_eig[7].dev,
+                   &h->mg_eig[8].dev, &h->mg_eig[9].dev, &h->mg_eig[10].dev, &h->mg_eig[11].dev,
+                   &h->mg_eig[12].dev, &h->mg_eig[13].dev, &h->mg_eig[14].dev, &h->mg_eig[15].dev};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,
@@ -1430,6 +1547,7 @@ slrf_status slrf_filter_apply(slrf_handle *h, const slrf_filter *f, const double
         rep->spmv = st.spmv;
         for (int j = 0; j < N; ++j) rep->iters_per_pole[j] = st.iters_per_pole[j];
         rep->status_detail = st.n_fail + st.n_breakdown;
+        rep->mg_levels = st.mg_levels;
     }
     scope.finish();
     CK(cudaGetLastError());

@@ -32,6 +32,7 @@ struct HostLevel {
     std::vector<double> a, b;
     std::vector<double> diag_a, diag_b;
     double rho = 1.0;                   // spectral radius of D^{-1} A (levels that are smoothed)
+    double maxba = 0.0;                 // max_i b_ii / a_ii: |sigma| maxba is the shift's weight on the diagonal
     // transfer to the next level (empty on the coarsest level)
     HostCsr P;    // n x n_next
     HostCsr Rt;   // n_next x n, the transpose of P
@@ -57,6 +58,11 @@ struct HostHierarchy {
 // positive definite, coarsening stalled).
 std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double *a, const double *b,
                      const MgParams &prm, HostHierarchy &H);
+
+// V^T A_l V = diag(lam), V^T B_l V = I for a level with a pencil copy (n_l x n_l
+// row-major V, lam ascending); used for the coarsest level and, on demand, for
+// the level at which a deep shift truncates the cycle.
+std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector<double> &lam);
 
 // Dense symmetric eigensolver (FP64, host): S = Q diag(w) Q^T, w ascending,
 // Q row-major n x n with the eigenvectors in its columns.  S is overwritten.

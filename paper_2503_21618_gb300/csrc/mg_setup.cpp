@@ -238,8 +238,10 @@ bool cholesky_lower(int n, std::vector<double> &S) {
     return true;
 }
 
-// Coarsest level: V^T A_c V = diag(lam), V^T B_c V = I.
-std::string coarse_eig(const HostLevel &L, std::vector<double> &V, std::vector<double> &lam) {
+}  // namespace
+
+// V^T A_l V = diag(lam), V^T B_l V = I.
+std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector<double> &lam) {
     const int n = L.n;
     std::vector<double> Ad((size_t)n * n, 0.0), Bd((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i)
@@ -289,8 +291,6 @@ std::string coarse_eig(const HostLevel &L, std::vector<double> &V, std::vector<d
         }
     return "";
 }
-
-}  // namespace
 
 void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vector<double> &Q) {
     Q.assign((size_t)n * n, 0.0);
@@ -429,6 +429,7 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         for (int i = 0; i < cn; ++i)
             if (!(L.diag_a[i] > 0.0) || !(L.diag_b[i] > 0.0))
                 return "multigrid setup: non-positive diagonal entry in row " + std::to_string(i);
+        for (int i = 0; i < cn; ++i) L.maxba = std::max(L.maxba, L.diag_b[i] / L.diag_a[i]);
         if (cn <= prm.coarse_target || (int)H.lv.size() >= prm.max_levels) break;
         // aggregation on the node graph
         std::vector<int32_t> sptr, scol, agg;
@@ -501,7 +502,7 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         Lc.b.assign(b, b + ptr[n]);
     }
     if (Lc.n > 4096) return "multigrid setup: coarsening stalled at " + std::to_string(Lc.n) + " unknowns";
-    std::string err = coarse_eig(Lc, H.V, H.lam);
+    std::string err = mg_level_eig(Lc, H.V, H.lam);
     if (!err.empty()) return err;
     if (H.lv.size() == 1) {   // level 0 keeps no pencil copy
         Lc.ptr.clear();

@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -50,6 +52,8 @@ extern "C" slrf_status slrf_batch_iterate(int32_t nprob, slrf_handle *const *h, 
     }
     const int nt = n_threads <= 0 ? nprob : std::min<int>(n_threads, nprob);
     std::atomic<int> next{0};
+    const char *dbg = getenv("SLRF_DEBUG");
+    const bool debug = dbg && dbg[0] && dbg[0] != '0';
     auto work = [&]() {
         for (;;) {
             const int i = next.fetch_add(1);
@@ -57,6 +61,10 @@ extern "C" slrf_status slrf_batch_iterate(int32_t nprob, slrf_handle *const *h, 
             cudaSetDevice(handle_device(h[i]));
             status[i] = slrf_subspace_iterate(h[i], &f[i], gamma[i], L[i], V0[i], ldv[i], tol, max_outer, theta[i],
                                               X[i], ldx[i], resid[i], &n_conv[i], rep ? &rep[i] : nullptr);
+            // the error text is per thread: with SLRF_DEBUG set, report it here
+            if (status[i] != SLRF_OK && debug)
+                fprintf(stderr, "slrf_batch_iterate: problem %d: %s (%s)\n", i, slrf_status_str(status[i]),
+                        slrf_last_error());
         }
     };
     std::vector<std::thread> pool;

@@ -126,10 +126,12 @@ __global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *__rest
     if (tid == 0) *status = bad ? bad : (shift > 0.0 ? -1 : 0);
 }
 
+void raise_smem_limits();   // defined after the kernels it configures
+
 void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *status, double shift_on_fail) {
     const size_t smem = (size_t)m * m * sizeof(double);
     const int use_smem = smem <= 200 * 1024;
-    if (use_smem) cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limits();
     ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
     k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, R, status, use_smem, shift_on_fail);
     ctx.after();
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(32) k_triinv_upper(int m, const double *__rest
 void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv) {
     const size_t smem = (size_t)m * sizeof(double);
     ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_triinv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limits();
     k_triinv_upper<<<m, 32, smem, ctx.stream>>>(m, R, Rinv);
     ctx.after();
 }
@@ -514,7 +516,7 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
         return;
     }
     // stage 1: FP32 Jacobi in shared memory
-    cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limits();
     ctx.before(KC_SMALL_DENSE, 24.0 * m2, 9.0 * (double)m * m2 * 8);
     k_jacobi<float><<<1, 1024, smem, ctx.stream>>>(m, S, (float *)Ag, (float *)Vg, lam0, S0, 40, 1, nullptr,
                                                       1e-6f);
@@ -532,6 +534,23 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
     ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
     k_sort_eig<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, lam0, S0, lam, Q);
     ctx.after();
+}
+
+// Kernel attributes are process-wide: a handle lowering a kernel's dynamic
+// shared-memory limit to its own size while another thread is about to launch
+// with more would fail that launch ("invalid argument").  So the limits are
+// raised once, to the most any launch here uses (200 KB), and never changed.
+void raise_smem_limits() {
+    constexpr int kMaxDevices = 64;
+    static std::once_flag once[kMaxDevices];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::call_once(once[dev < 0 || dev >= kMaxDevices ? 0 : dev], [] {   // per device, with it current
+        const int lim = 200 * 1024;
+        cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_triinv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    });
 }
 
 }  // namespace slrf

@@ -117,3 +117,65 @@ def test_subspace_2d_each_preconditioner_matches_dense(api, precond):
     assert st == api.OK and nconv == rep.n_wanted == 25
     th = theta.cpu().numpy()[:25]
     assert np.max(np.abs(th - lam[:25]) / lam[:25]) < 1e-10
+
+
+def test_deep_shift_truncates_the_cycle(api):
+    # |sigma| max(b_ii/a_ii) passes 0.8 on level 1 (725 unknowns): the cycle
+    # stops there and solves that level exactly
+    p = pencil_2d_q1(80, seed=7)                      # levels 6241, 725, 107
+    s, w = poles.slrf_poles(4, 1.0, 0.01, 3500.0)
+    V = start_block(p.n, 6, 3)
+    ref = ofilt.filter_apply(p.A(), p.B(), s, w, V)
+    levels = {}
+    for limit in (0.8, 100.0):
+        h = api.Handle(p, api.default_opts(precision=api.PREC_FP64, inner_tol=1e-13, inner_maxit=3000,
+                                           precond=api.PRECOND_MG, mg_shift_limit=limit))
+        U, st, rep = h.filter_apply(api.Filter(s, w), torch.from_numpy(V).cuda())
+        assert st == api.OK
+        assert rel_err(U.cpu().numpy(), ref) < 1e-10
+        levels[limit] = rep.mg_levels
+    assert levels[0.8] == 2 and levels[100.0] == 3
+
+
+def test_auto_uses_jacobi_when_the_exact_level_is_too_large(api):
+    p = pencil_2d_q1(120, seed=7)                     # levels 14161, 1610, 226
+    s, w = poles.slrf_poles(4, 1.0, 0.01, 8000.0)     # level 1 (1610 > 768) would need the exact solve
+    V = torch.from_numpy(start_block(p.n, 4, 3)).cuda()
+    got = {}
+    for pc in (api.PRECOND_AUTO, api.PRECOND_MG):
+        h = api.Handle(p, api.default_opts(precond=pc, inner_maxit=3000))
+        U, st, rep = h.filter_apply(api.Filter(s, w), V, allowed=(api.OK, api.NOT_CONVERGED))
+        got[pc] = (st, rep.mg_levels)
+    # AUTO solves with Jacobi; forcing the full cycle smooths the shifted
+    # operator where it no longer can, and its deepest pole misses the cap
+    assert got[api.PRECOND_AUTO] == (api.OK, 0)
+    assert got[api.PRECOND_MG][1] == 3
+
+
+def test_unattainable_tolerance_ends_in_stagnation_after_fp64(api):
+    # 1D, n = 20 000: the eigenvector of lambda_1 cannot be stored in FP64 with
+    # a residual below ~eps lambda_max / lambda_1 = 5e-8, so rho <= 1e-8 is out
+    # of reach for it.  The mixed iteration retries with FP64 Krylov solves,
+    # then reports stagnation with the pairs it did converge.
+    from oracle import inertia
+    n = 20000
+    p = pencil_1d(n)
+    lam = inertia.lambda_1d(n, np.arange(1, 13))
+    gamma = 0.5 * (lam[9] + lam[10])
+    f = api.Filter(*poles.slrf_poles(4, 1.0, 0.01, gamma))
+    h = api.Handle(p)
+    theta, X, resid, nconv, st, rep = h.subspace_iterate(f, gamma, torch.from_numpy(start_block(n, 16, 4)).cuda(),
+                                                         tol=1e-8, max_outer=60)
+    assert st == api.STAGNATION and rep.krylov_fp64 == 1
+    r = resid.cpu().numpy()[:10]
+    assert nconv == int(np.sum(r <= 1e-8)) and 3 <= nconv < 10
+    floor = 2.2e-16 * lam_max_1d(n) / lam[0]
+    assert r[0] < 20 * floor
+    th = theta.cpu().numpy()[:10]
+    # Ritz values of pairs with residual rho are within ~rho of the eigenvalues
+    assert np.max(np.abs(th - lam[:10]) / lam[:10]) < 5e-7
+
+
+def lam_max_1d(n):
+    from oracle import inertia
+    return float(inertia.lambda_1d(n, np.array([n]))[0])
