@@ -108,7 +108,7 @@ typedef struct {
     double lock_tol;        /* MIXED: columns with rho_i below this skip the solve
                                (their correction is below the outer tolerance) (1e-9) */
     int32_t check_every;    /* Krylov iterations between host polls of the
-                               active-column count                               (8) */
+                               active-column count                               (4) */
     int32_t eig_refine;     /* small eigensolver: 1 = FP32 Jacobi + FP64 refinement,
                                0 = FP64 Jacobi                                     (1) */
     int64_t mem_budget;     /* workspace byte cap, 0 = none                       (0) */

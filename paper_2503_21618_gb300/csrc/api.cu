@@ -905,12 +905,13 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
 }
 
 // G = X^T Y with the handle's Gram method (int8 tensor-core Ozaki or FP64)
+// (symmetric: Y = B X with B symmetric, so only the upper tiles are computed)
 slrf_status gram(slrf_handle *h, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
-                 double *G) {
+                 double *G, bool symmetric = false) {
     Ctx &ctx = h->ctx;
     if (h->opts.gram_ozaki) {
         CKS(ensure(h, h->rOz, ozaki_gram_work_bytes(n, m, ctx.sm_count)));
-        ozaki_gram(ctx, n, m, X, ldx, Y, ldy, G, h->rOz.p);
+        ozaki_gram(ctx, n, m, X, ldx, Y, ldy, G, h->rOz.p, symmetric);
         return SLRF_OK;
     }
     const int split = gram_split(ctx, m, n);
@@ -964,7 +965,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * m;
     int32_t *pin_status = h->d_pin + 1;   // mapped: the host reads it after pass 1
     spmm_real(ctx, h->A, m, U, ldu, nullptr, 0, W1, m);
-    CKS(gram(h, n, m, U, ldu, W1, m, G));
+    CKS(gram(h, n, m, U, ldu, W1, m, G, true));
     small_colscale(ctx, m, G, s);
     small_chol_upper(ctx, m, G, R1, pin_status, shift);
     small_triinv_upper(ctx, m, R1, T1);
@@ -985,7 +986,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
         CKS(ensure(h, h->rQ2, (size_t)n * m * sizeof(double)));
         double *Q2 = as<double>(h->rQ2);
         spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
-        CKS(gram(h, n, m, Q1, m, W1, m, G));
+        CKS(gram(h, n, m, Q1, m, W1, m, G, true));
         small_chol_upper(ctx, m, G, G, st + 2, 0.0);
         small_triinv_upper(ctx, m, G, T1);
         CKS(tall_product(h, n, m, m, Q1, m, nullptr, T1, m, Q2, m));
@@ -996,12 +997,12 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     }
     // pass 2: G2 = Q1^T B Q1, R2 = chol, T2 = R2^{-1}
     spmm_real(ctx, h->A, m, Q1, m, nullptr, 0, W1, m);
-    CKS(gram(h, n, m, Q1, m, W1, m, G));
+    CKS(gram(h, n, m, Q1, m, W1, m, G, true));
     small_chol_upper(ctx, m, G, G, st + 1, 0.0);
     small_triinv_upper(ctx, m, G, T2);
     // projected A: A_hat = T2^T (Q1^T A Q1) T2
     spmm_real(ctx, h->A, m, Q1, m, W1, m, nullptr, 0);
-    CKS(gram(h, n, m, Q1, m, W1, m, Ah1));
+    CKS(gram(h, n, m, Q1, m, W1, m, Ah1, true));
     dgemm(ctx, 0, 0, m, m, m, Ah1, m, T2, m, 0.0, R1, m, 1, nullptr, KC_SMALL_DENSE);
     dgemm(ctx, 1, 0, m, m, m, T2, m, R1, m, 0.0, Ah, m, 1, nullptr, KC_SMALL_DENSE);
     ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
@@ -1279,7 +1280,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->inner_maxit = 1000;
     o->inner_tol = 1e-5;
     o->lock_tol = 1e-9;
-    o->check_every = 8;
+    o->check_every = 4;
     o->eig_refine = 1;
     o->mem_budget = 0;
     o->profile = 0;

@@ -147,6 +147,32 @@ __global__ void k_split_reduce(int M, int N, int split, const double *__restrict
     *o = (beta != 0.0 ? beta * *o : 0.0) + s;
 }
 
+// Small products (the m x m x m GEMMs of the projection): one output per
+// thread, 16 x 16 tiles staged in shared memory, so an m = 150 product runs on
+// 100 CTAs instead of the 9 that the 64 x 64 tiling of k_dgemm gives it.
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(256)
+k_dgemm_small(int M, int N, int K, const double *__restrict__ A, int64_t lda, const double *__restrict__ B,
+              int64_t ldb, double beta, double *__restrict__ C, int64_t ldc) {
+    __shared__ double As[16][17], Bs[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+    double s = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        const int ka = k0 + tx, kb = k0 + ty;
+        As[ty][tx] = (i < M && ka < K) ? (OPA ? A[(int64_t)ka * lda + i] : A[(int64_t)i * lda + ka]) : 0.0;
+        Bs[ty][tx] = (kb < K && j < N) ? (OPB ? B[(int64_t)j * ldb + kb] : B[(int64_t)kb * ldb + j]) : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) s = fma(As[ty][k], Bs[k][tx], s);
+        __syncthreads();
+    }
+    if (i < M && j < N) {
+        double *o = C + (int64_t)i * ldc + j;
+        *o = (beta != 0.0 ? beta * *o : 0.0) + s;
+    }
+}
+
 int gram_split(const Ctx &ctx, int m, int64_t n) {
     const int tiles = ((m + BM - 1) / BM) * ((m + BN - 1) / BN);
     int split = (ctx.sm_count * 4 + tiles - 1) / tiles;
@@ -160,6 +186,18 @@ void dgemm(Ctx &ctx, int opA, int opB, int M, int N, int K, const double *A, int
            int64_t ldb, double beta, double *C, int64_t ldc, int split, double *work, int kc) {
     if (M <= 0 || N <= 0) return;
     if (split < 1 || !work) split = 1;
+    if (split == 1 && M <= 1024 && N <= 1024 && K <= 4096) {
+        const dim3 grid((N + 15) / 16, (M + 15) / 16), block(16, 16);
+        ctx.before(kc, 8.0 * ((double)M * K + (double)K * N + (double)M * N), 2.0 * M * N * (double)K);
+#define LS(a, b) k_dgemm_small<a, b><<<grid, block, 0, ctx.stream>>>(M, N, K, A, lda, B, ldb, beta, C, ldc)
+        if (opA == 0 && opB == 0) LS(0, 0);
+        else if (opA == 1 && opB == 0) LS(1, 0);
+        else if (opA == 0 && opB == 1) LS(0, 1);
+        else LS(1, 1);
+#undef LS
+        ctx.after();
+        return;
+    }
     int Kc = (K + split - 1) / split;
     Kc = (Kc + BK - 1) / BK * BK;
     split = (K + Kc - 1) / Kc;

@@ -202,8 +202,10 @@ void copy_block(Ctx &ctx, int n, int m, const double *src, int64_t lds, double *
 // ---------------------------------------------------------------- ozaki.cu
 // G = X^T Y (m x m, row-major, ld m) from int8 tensor-core digit products.
 size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count);
+// symmetric: X^T Y is known to be symmetric (Y = B X with B symmetric): only
+// the tiles on and above the diagonal are computed and mirrored.
 void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
-                void *work);
+                void *work, bool symmetric = false);
 // C = (A diag(cs)) B, A n x k, B k x m, C n x m (row-major, leading dims),
 // cs = nullptr for no column scaling; FP64-accurate from int8 digit products.
 size_t ozaki_tall_work_bytes(int64_t n, int k, int m);

@@ -133,7 +133,9 @@ __device__ __forceinline__ void imma16832(int c[4], const unsigned a[4], const u
 
 __global__ void __launch_bounds__(128)
 k_oz_gram(int m, int mpad, int64_t npad, int64_t kslice, const int8_t *__restrict__ SX,
-          const int8_t *__restrict__ SY, double *__restrict__ work) {
+          const int8_t *__restrict__ SY, double *__restrict__ work, int symmetric) {
+    // a symmetric Gram needs the tiles on and above the diagonal only
+    if (symmetric && blockIdx.y > blockIdx.x) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, q = lane & 3;
     const int a_base = blockIdx.y * OZ_TM + (warp >> 1) * 32;
@@ -206,13 +208,19 @@ k_oz_gram(int m, int mpad, int64_t npad, int64_t kslice, const int8_t *__restric
 }
 
 __global__ void k_oz_reduce(int m, int split, const double *__restrict__ work, const int *__restrict__ ex,
-                            const int *__restrict__ ey, double *__restrict__ G, int64_t ldg) {
+                            const int *__restrict__ ey, double *__restrict__ G, int64_t ldg, int symmetric) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)m * m) return;
-    const int a = (int)(idx / m), b = (int)(idx % m);
+    int a = (int)(idx / m), b = (int)(idx % m);
+    const int ga = a, gb = b;
+    if (symmetric && a > b) {   // mirror the upper triangle (computed tiles only)
+        a = gb;
+        b = ga;
+    }
+    const int64_t src = (int64_t)a * m + b;
     double s = 0.0;
-    for (int z = 0; z < split; ++z) s += work[(int64_t)z * m * m + idx];
-    G[(int64_t)a * ldg + b] = ldexp(s, ex[a] + ey[b]);
+    for (int z = 0; z < split; ++z) s += work[(int64_t)z * m * m + src];
+    G[(int64_t)ga * ldg + gb] = ldexp(s, ex[a] + ey[b]);
 }
 
 // ---------------------------------------------------------------------------
@@ -225,7 +233,7 @@ size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count) {
 }
 
 void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
-                void *work) {
+                void *work, bool symmetric) {
     const int64_t npad = (n + 63) / 64 * 64;
     const int mpad = (m + OZ_TM - 1) / OZ_TM * OZ_TM;
     char *w = reinterpret_cast<char *>(work);
@@ -236,8 +244,9 @@ void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const 
     int *ey = ex + m;
     double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(ey + m) + 16 - ((uintptr_t)(ey + m) & 15));
     const int tiles = mpad / OZ_TM;
+    const int live = symmetric ? tiles * (tiles + 1) / 2 : tiles * tiles;   // tiles with work
     // K-slices: enough CTAs to fill the GPU, each at most 2^16 rows (int32 bound)
-    int split = (ctx.sm_count * 4 + tiles * tiles - 1) / (tiles * tiles);
+    int split = (ctx.sm_count * 4 + live - 1) / live;
     int64_t kslice = (npad + split - 1) / split;
     kslice = (kslice + 31) / 32 * 32;
     if (kslice > 65536) kslice = 65536;
@@ -258,11 +267,13 @@ void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const 
     ctx.after();
     const dim3 ggrid(tiles, tiles, split);
     const double pairs = OZ_S * (OZ_S + 1) / 2.0;
-    ctx.before(KC_GRAM, 2.0 * OZ_S * mpad * npad, 2.0 * pairs * (double)mpad * mpad * npad);
-    k_oz_gram<<<ggrid, 128, 0, ctx.stream>>>(m, mpad, npad, kslice, SX, SY, part);
+    ctx.before(KC_GRAM, 2.0 * OZ_S * mpad * npad,
+               2.0 * pairs * (double)live * OZ_TM * OZ_TM * npad);
+    k_oz_gram<<<ggrid, 128, 0, ctx.stream>>>(m, mpad, npad, kslice, SX, SY, part, symmetric ? 1 : 0);
     ctx.after();
     ctx.before(KC_GRAM, 8.0 * (double)split * m * m, 0);
-    k_oz_reduce<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, ctx.stream>>>(m, split, part, ex, ey, G, m);
+    k_oz_reduce<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, ctx.stream>>>(m, split, part, ex, ey, G, m,
+                                                                                    symmetric ? 1 : 0);
     ctx.after();
 }
 
