@@ -280,8 +280,11 @@ slrf_status slrf_rayleigh_ritz(slrf_handle *h, int32_t m, const double *U, int64
  * if rep != NULL) receive each problem's outcome.  Returns SLRF_OK if every
  * problem returned SLRF_OK, else the first other status.  All reductions run
  * in a fixed order, so each problem's outputs are bit-identical to solving it
- * alone.  (Batched pencils of the spec workload; the paper solves one
- * pencil at a time, Section 4.) */
+ * alone.  With the environment variable SLRF_DEBUG set, the error text of
+ * every problem that did not return SLRF_OK is printed to stderr (the text of
+ * slrf_last_error() belongs to the worker thread).  (Many independent
+ * pencils solved concurrently on one GPU; the paper solves one pencil at a
+ * time, Section 4.) */
 slrf_status slrf_batch_iterate(int32_t nprob, slrf_handle *const *h, const slrf_filter *f,
                                const double *gamma, const int32_t *L, const double *const *V0,
                                const int64_t *ldv, double tol, int32_t max_outer,

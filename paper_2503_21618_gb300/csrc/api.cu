@@ -1213,13 +1213,14 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
 }  // namespace
 
 namespace slrf {
-size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count, int mg_coarse) {
+size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count, int mg_coarse,
+                          int krylov) {
     const size_t Lp = (size_t)(L + 1) / 2 * 2, W = (size_t)N * Lp;
     const size_t ts = precision == SLRF_PREC_MIXED ? 4 : 8;   // Krylov real type
     const size_t gy = std::max<size_t>(1, std::min<size_t>((size_t)(n + 7) / 8, (size_t)sm_count * 8));
     const size_t pencil = (size_t)(n + 1) * 4 + (size_t)nnz * (4 + 8 + 8 + 8 + 16) + (size_t)n * 16 +
                           (size_t)nnz * (4 + 3 * 24) + (size_t)n * 4;
-    const size_t krylov = 3 * (size_t)n * W * 2 * ts + (size_t)n * N * 2 * ts + (size_t)n * Lp * ts +
+    const size_t kry = 3 * (size_t)n * W * 2 * ts + (size_t)n * N * 2 * ts + (size_t)n * Lp * ts +
                           gy * W * 4 * ts + W * (8 * ts + 40) + 4096;
     const size_t split = (size_t)sm_count * 4;
     const size_t rr = 8 * (size_t)n * L * 8 + split * L * L * 8 + (40 * (size_t)L * L + 64 * (size_t)L) * 8 +
@@ -1236,7 +1237,9 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
         mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 96 * (size_t)nnz + nc * nc * 12 +
               nc * N * 2 * ts + 16 * 4096 + 768 * 768 * 12 + 768 * (size_t)N * 2 * ts;
     }
-    return pencil + krylov + rr + ozaki + mgb;
+    // BiCGStab keeps five more n x W blocks (r^, v, y, z, t)
+    const size_t bcg = krylov == SLRF_KRYLOV_BICGSTAB ? 5 * (size_t)n * W * 2 * ts + 2 * W * 2 * ts : 0;
+    return pencil + kry + rr + ozaki + mgb + bcg;
 }
 }  // namespace slrf
 

@@ -231,8 +231,10 @@ size_t small_syev_work_bytes(int m);
 // Upper bound of the device bytes a handle needs for a solve of subspace size
 // L with N poles (pencil copies + Krylov state + projection workspace + the
 // staging of the host-buffer entry point; mg_coarse > 0: plus the multigrid
-// hierarchy and its level blocks, mg_coarse being the coarsest-size target).
-size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count, int mg_coarse);
+// hierarchy and its level blocks, mg_coarse being the coarsest-size target;
+// krylov = SLRF_KRYLOV_BICGSTAB: plus its extra blocks).
+size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, int sm_count, int mg_coarse,
+                          int krylov);
 int handle_device(const slrf_handle *h);
 
 }  // namespace slrf

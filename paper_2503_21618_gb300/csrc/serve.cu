@@ -194,7 +194,7 @@ extern "C" int64_t slrf_request_bytes(const slrf_request *r) {
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
     return (int64_t)workspace_estimate(r->pencil.n, r->pencil.nnz, r->L, r->filter.n_poles, r->opts.precision, sms,
-                                       request_mg_coarse(r->opts));
+                                       request_mg_coarse(r->opts), r->opts.krylov);
 }
 
 extern "C" slrf_status slrf_server_create(slrf_server **out, int32_t n_workers, int64_t mem_budget) {
@@ -247,7 +247,7 @@ extern "C" slrf_status slrf_server_submit(slrf_server *s, const slrf_request *r,
     q->max_outer = r->max_outer;
     q->opts = r->opts;
     q->bytes = workspace_estimate(p.n, p.nnz, r->L, f.n_poles, r->opts.precision, s->sm_count,
-                                  request_mg_coarse(r->opts));
+                                  request_mg_coarse(r->opts), r->opts.krylov);
     q->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);
