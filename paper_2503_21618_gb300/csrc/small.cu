@@ -311,7 +311,8 @@ k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict_
 
 // ---------------------------------------------------------------------------
 // cooperative FP64 Jacobi on a global m x m matrix A (overwritten; diag = lam)
-// accumulating V <- V J.  cnt[2]: rotation counters (device).  All blocks
+// accumulating V <- V J.  cnt[4] (device): rotation counters of the last two
+// sweeps (0, 1) and their pre-check flags (2, 3).  All blocks
 // compute the same rotations from the same data, so no broadcast is needed.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
@@ -327,9 +328,31 @@ k_jacobi_coop(int m, double *__restrict__ A, double *__restrict__ V, double *__r
     const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
     const double eps = DBL_EPSILON;
     const double absmin = (*normA) * eps * 0.5 / (double)m;
+    // cnt[2 + (sweep & 1)]: set when some pair still passes the rotation test
+    if (gtid == 0) cnt[2] = cnt[3] = 0;
+    grid.sync();
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (blockIdx.x == 0 && threadIdx.x == 0) cnt[sweep & 1] = 0;
+        // A sweep that would rotate nothing leaves A and V as they are: test
+        // every pair against the rotation criterion first (one pass over A)
+        // instead of running the sweep's 2 (mp - 1) grid barriers to find out.
+        {
+            int found = 0;
+            for (int64_t e = gtid; e < (int64_t)m * m && !found; e += gsz) {
+                const int p = (int)(e / m), q = (int)(e % m);
+                if (q <= p) continue;
+                const double apq = A[e];
+                const double scale = sqrt(fabs(A[(int64_t)p * m + p] * A[(int64_t)q * m + q]));
+                found = fabs(apq) > eps * scale && fabs(apq) > absmin;
+            }
+            if (found) atomicOr(&cnt[2 + (sweep & 1)], 1);
+            grid.sync();
+            const int any = *(volatile int *)&cnt[2 + (sweep & 1)];
+            // the other flag was last read before this sweep's barriers: reset it for the next sweep
+            if (gtid == 0) cnt[2 + ((sweep + 1) & 1)] = 0;
+            if (!any) break;
+        }
         __syncthreads();
         for (int r = 0; r < mp - 1; ++r) {
             // Every block derives all rotations of the round from the pair
