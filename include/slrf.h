@@ -246,6 +246,22 @@ slrf_status slrf_subspace_iterate_host(slrf_handle *h, const slrf_filter *f, dou
 slrf_status slrf_shifted_spmm(slrf_handle *h, const slrf_filter *f, int32_t prec, int32_t m,
                               int32_t ldp, const void *P, void *Q, void *mu);
 
+/* Z_j = C_j R_j for every pole j and column, where C_j is the preconditioner
+ * of the shifted system (A - sigma_j B) y = f (Section 4.2.1 preconditions
+ * the Krylov solves of Eq. (2)) that the handle's Krylov solves use with its
+ * options: one multigrid cycle (SLRF_PRECOND_MG, and AUTO where it picks
+ * multigrid; the deep-shift truncation applies), Jacobi
+ * diag(A - sigma_j B)^{-1} (JACOBI, and AUTO otherwise) or the identity
+ * (NONE).  R, Z: device complex blocks in the layout of slrf_shifted_spmm
+ * (prec, m, ldp as there); only the columns c < m of each pole are defined
+ * in Z on return.
+ * mu[j*m + c] = sum_i R_j[i,c] Z_j[i,c] (unconjugated, device) if mu != NULL.
+ * *mg_levels (if not NULL) receives the number of levels the cycle used
+ * (0: no multigrid).  Synchronous.  SLRF_EINVAL for bad sizes or filter,
+ * SLRF_BREAKDOWN if the hierarchy cannot be built. */
+slrf_status slrf_precond_apply(slrf_handle *h, const slrf_filter *f, int32_t prec, int32_t m,
+                               int32_t ldp, const void *R, void *Z, void *mu, int32_t *mg_levels);
+
 /* Y = A X and/or Z = B X (FP64, device, row-major n x m; either output may be
  * NULL).  Algorithm 1 products A U, B U, A X, B X. */
 slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx, double *Y,
@@ -367,6 +383,18 @@ const char *slrf_noalloc_last_error(void);
 slrf_status slrf_mg_describe(const slrf_pencil *p, const slrf_opts *o, int32_t *n_levels, int64_t *level_n,
                              int64_t *level_nnz, double *setup_ms, double *coarse_lam, double *coarse_a,
                              double *coarse_b);
+
+/* Prolongator P_l (level l to l + 1, n_l x n_{l+1}, CSR with sorted
+ * columns, FP64) of the hierarchy slrf_mg_describe builds, and rho_l, the
+ * spectral radius of diag(A_l)^{-1} A_l that scales level l's Jacobi
+ * damping (omega_l = mg_omega / rho_l).  First call with ptr = col = val =
+ * NULL for *n_rows, *n_cols, *nnz and *rho; then with host arrays
+ * ptr[n_rows + 1], col[nnz], val[nnz].  0 <= level <= n_levels - 2.  Host
+ * only.  SLRF_EINVAL for invalid input or a level out of range,
+ * SLRF_BREAKDOWN if the setup fails. */
+slrf_status slrf_mg_transfer(const slrf_pencil *p, const slrf_opts *o, int32_t level, int32_t *n_rows,
+                             int32_t *n_cols, int64_t *nnz, double *rho, int32_t *ptr, int32_t *col,
+                             double *val);
 
 /* ---- pole/weight sets (host) -------------------------------------------- */
 

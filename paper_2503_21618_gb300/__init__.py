@@ -8,7 +8,8 @@ B-orthonormalisation and Rayleigh-Ritz.  The compute lives in the CUDA library
 ``libslrf.so`` (C ABI in ``include/slrf.h``); this package is its binding.
 """
 from .api import (Filter, Handle, SlrfError, default_opts, design_poles, filter_eval, load,  # noqa: F401
-                  mg_describe, OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PREC_FP64, PREC_MIXED,
+                  mg_describe, mg_transfer, OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PREC_FP64, PREC_MIXED,
                   PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG, PRECOND_AUTO)
 
-__all__ = ["Filter", "Handle", "SlrfError", "default_opts", "design_poles", "filter_eval", "load", "mg_describe"]
+__all__ = ["Filter", "Handle", "SlrfError", "default_opts", "design_poles", "filter_eval", "load", "mg_describe",
+           "mg_transfer"]

@@ -90,6 +90,8 @@ _SIGNATURES = {
                                              C.c_double, C.c_int32, _P, _P, C.c_int64, _P, C.POINTER(C.c_int32),
                                              C.POINTER(slrf_report)]),
     "slrf_shifted_spmm": (C.c_int, [_P, C.POINTER(slrf_filter), C.c_int32, C.c_int32, C.c_int32, _P, _P, _P]),
+    "slrf_precond_apply": (C.c_int, [_P, C.POINTER(slrf_filter), C.c_int32, C.c_int32, C.c_int32, _P, _P, _P,
+                                     C.POINTER(C.c_int32)]),
     "slrf_spmm_ab": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64]),
     "slrf_gram": (C.c_int, [_P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P]),
     "slrf_syev": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
@@ -115,6 +117,8 @@ _SIGNATURES = {
     "slrf_noalloc_last_error": (C.c_char_p, []),
     "slrf_mg_describe": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P, _P]),
+    "slrf_mg_transfer": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.c_int32, C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P, _P]),
 }
 
 _lib = None
@@ -236,6 +240,29 @@ def mg_describe(pencil, opts: slrf_opts | None = None, coarse: bool = False) -> 
     return out
 
 
+def mg_transfer(pencil, level: int, opts: slrf_opts | None = None):
+    """Prolongator P_level of the host-built multigrid hierarchy as
+    (ptr, col, val, n_rows, n_cols) CSR arrays, and rho_level, the spectral
+    radius of diag(A_l)^{-1} A_l that scales the level's Jacobi damping."""
+    lib = load()
+    keep = [np.ascontiguousarray(pencil.row_ptr, dtype=np.int32),
+            np.ascontiguousarray(pencil.col_idx, dtype=np.int32),
+            np.ascontiguousarray(pencil.a_val, dtype=np.float64),
+            np.ascontiguousarray(pencil.b_val, dtype=np.float64)]
+    p = slrf_pencil(int(pencil.n), int(keep[1].size), *[a.ctypes.data for a in keep], 0)
+    o = opts or default_opts()
+    nr, nc, nz, rho = C.c_int32(), C.c_int32(), C.c_int64(), C.c_double()
+    _check(lib.slrf_mg_transfer(C.byref(p), C.byref(o), level, C.byref(nr), C.byref(nc), C.byref(nz), C.byref(rho),
+                                None, None, None), "slrf_mg_transfer")
+    ptr = np.zeros(nr.value + 1, np.int32)
+    col = np.zeros(nz.value, np.int32)
+    val = np.zeros(nz.value)
+    _check(lib.slrf_mg_transfer(C.byref(p), C.byref(o), level, C.byref(nr), C.byref(nc), C.byref(nz), C.byref(rho),
+                                ptr.ctypes.data_as(C.c_void_p), col.ctypes.data_as(C.c_void_p),
+                                val.ctypes.data_as(C.c_void_p)), "slrf_mg_transfer")
+    return (ptr, col, val, nr.value, nc.value), rho.value
+
+
 def _dptr(t, dtype_name="float64"):
     """Device pointer of a contiguous torch CUDA tensor (row-major)."""
     if not (hasattr(t, "is_cuda") and t.is_cuda):
@@ -336,6 +363,17 @@ class Handle:
         _check(self.lib.slrf_shifted_spmm(self.h, C.byref(f.c), prec, m, ldp, _dptr(P), _dptr(Q),
                                           _dptr(mu) if mu is not None else None), "slrf_shifted_spmm")
         return Q
+
+    def precond_apply(self, f: Filter, R, m, ldp, prec=PREC_MIXED, Z=None, mu=None):
+        """Z_j = C_j R_j (the Krylov preconditioner of every pole) in the block
+        layout of shifted_spmm; returns (Z, multigrid levels used)."""
+        import torch
+        Z = torch.zeros_like(R) if Z is None else Z
+        lv = C.c_int32()
+        _check(self.lib.slrf_precond_apply(self.h, C.byref(f.c), prec, m, ldp, _dptr(R), _dptr(Z),
+                                           _dptr(mu) if mu is not None else None, C.byref(lv)),
+               "slrf_precond_apply")
+        return Z, lv.value
 
     def spmm_ab(self, X, want_a=True, want_b=True):
         import torch

@@ -452,8 +452,68 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
     }
     const int nc = H.lv.back().n;
     const size_t v32 = take((size_t)nc * nc * 4), v64 = take((size_t)nc * nc * 8);
+    // fused finest-level transfers: F by fine row groups ("up") and by coarse rows ("down")
+    const HostLevel &H0 = H.lv[0];
+    const int R0 = h->A.rg_rows > 1 ? h->A.rg_rows : 1;
+    const int64_t n0 = H0.n, ng0 = (n0 + R0 - 1) / R0;
+    std::vector<int32_t> fu_ptr, fu_col, fd_ptr, fd_col;
+    std::vector<double2> fq;   // per stored pair: (A P, B P), (a_ii P, b_ii P)
+    if (nlev > 1) {
+        const int n1 = H.lv[1].n;
+        auto slot = [&](int64_t i, int32_t k, bool hit) {
+            if (!hit) {
+                fq.push_back(make_double2(0.0, 0.0));
+                fq.push_back(make_double2(0.0, 0.0));
+                return;
+            }
+            fq.push_back(make_double2(H0.fap[k], H0.fbp[k]));
+            fq.push_back(make_double2(H0.fp[k] * H0.diag_a[i], H0.fp[k] * H0.diag_b[i]));
+        };
+        fu_ptr.assign(ng0 + 1, 0);
+        std::vector<int32_t> u;
+        for (int64_t g = 0; g < ng0; ++g) {
+            const int64_t r0 = g * R0, r1 = std::min<int64_t>(n0, r0 + R0);
+            u.clear();
+            for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), H0.fcol.begin() + H0.fptr[r], H0.fcol.begin() + H0.fptr[r + 1]);
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            for (int32_t c : u) {
+                fu_col.push_back(c);
+                for (int r = 0; r < R0; ++r) {
+                    const int64_t row = r0 + r;
+                    if (row >= n0) {
+                        slot(0, 0, false);
+                        continue;
+                    }
+                    const auto b = H0.fcol.begin() + H0.fptr[row], e = H0.fcol.begin() + H0.fptr[row + 1];
+                    const auto it = std::lower_bound(b, e, c);
+                    slot(row, (int32_t)(it - H0.fcol.begin()), it != e && *it == c);
+                }
+            }
+            fu_ptr[g + 1] = (int32_t)fu_col.size();
+        }
+        // F^T: coarse row c lists the fine rows i with an entry (i, c), ascending
+        fd_ptr.assign(n1 + 1, 0);
+        for (int32_t c : H0.fcol) fd_ptr[c + 1]++;
+        for (int c = 0; c < n1; ++c) fd_ptr[c + 1] += fd_ptr[c];
+        fd_col.resize(H0.fcol.size());
+        std::vector<int32_t> fill(fd_ptr.begin(), fd_ptr.end() - 1), src(H0.fcol.size());
+        for (int64_t i = 0; i < n0; ++i)
+            for (int32_t k = H0.fptr[i]; k < H0.fptr[i + 1]; ++k) {
+                const int32_t dst = fill[H0.fcol[k]]++;
+                fd_col[dst] = (int32_t)i;
+                src[dst] = k;
+            }
+        for (size_t e = 0; e < fd_col.size(); ++e) slot(fd_col[e], src[e], true);
+    }
+    const size_t nslot = fq.size() / 2;
+    const size_t o_fup = take(fu_ptr.size() * 4), o_fuc = take(fu_col.size() * 4), o_fdp = take(fd_ptr.size() * 4),
+                 o_fdc = take(fd_col.size() * 4), o_fq = take(fq.size() * sizeof(double2)),
+                 o_fab32 = take(nslot * sizeof(float2)), o_fab64 = take(nslot * sizeof(double2));
     std::vector<char> stage(off);
-    auto put = [&](size_t o, const void *src, size_t bytes) { memcpy(stage.data() + o, src, bytes); };
+    auto put = [&](size_t o, const void *src, size_t bytes) {
+        if (bytes) memcpy(stage.data() + o, src, bytes);
+    };
     for (int l = 0; l < nlev; ++l) {
         const HostLevel &L = H.lv[l];
         if (l >= 1 && l < nlev - 1) {
@@ -490,6 +550,11 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
         for (size_t k = 0; k < (size_t)nc * nc; ++k) V32[k] = (float)H.V[k];
         put(v64, H.V.data(), (size_t)nc * nc * 8);
     }
+    put(o_fup, fu_ptr.data(), fu_ptr.size() * 4);
+    put(o_fuc, fu_col.data(), fu_col.size() * 4);
+    put(o_fdp, fd_ptr.data(), fd_ptr.size() * 4);
+    put(o_fdc, fd_col.data(), fd_col.size() * 4);
+    put(o_fq, fq.data(), fq.size() * sizeof(double2));
     CKS(ensure(h, h->mgStatic, off));
     char *base = reinterpret_cast<char *>(h->mgStatic.p);
     CK(cudaMemcpyAsync(base, stage.data(), off, cudaMemcpyHostToDevice, h->ctx.stream));
@@ -538,6 +603,16 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
             }
         }
         mg.V = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? v32 : v64));
+        if (nlev > 1) {
+            L0.fu_nnz = (int64_t)fu_col.size();
+            L0.fd_nnz = (int64_t)fd_col.size();
+            L0.fu_ptr = reinterpret_cast<const int32_t *>(base + o_fup);
+            L0.fu_col = reinterpret_cast<const int32_t *>(base + o_fuc);
+            L0.fd_ptr = reinterpret_cast<const int32_t *>(base + o_fdp);
+            L0.fd_col = reinterpret_cast<const int32_t *>(base + o_fdc);
+            L0.f_q = reinterpret_cast<const double2 *>(base + o_fq);
+            L0.f_ab = reinterpret_cast<cplx<T> *>(base + (sizeof(T) == 4 ? o_fab32 : o_fab64));
+        }
     };
     fill(h->mg32, 0.0f);
     fill(h->mg64, 0.0);
@@ -1229,12 +1304,13 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
                          ozaki_tall_work_bytes(n, L, L);
     // multigrid (mg_coarse > 0): Z block, level blocks r/z/t and Jacobi
     // diagonals (the levels below the finest hold at most n/2 rows together),
-    // transfers and Galerkin pencils (bounded by the fine pattern), coarsest
-    // eigenvectors and shifted inverses
+    // transfers and Galerkin pencils (bounded by the fine pattern) and the
+    // finest level's fused transfer pairs F (up to ~100 B per stored entry of
+    // A), coarsest eigenvectors and shifted inverses
     size_t mgb = 0;
     if (mg_coarse > 0) {
         const size_t nh = (size_t)n / 2 + 1, nc = (size_t)mg_coarse;
-        mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 96 * (size_t)nnz + nc * nc * 12 +
+        mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 200 * (size_t)nnz + nc * nc * 12 +
               nc * N * 2 * ts + 16 * 4096 + 768 * 768 * 12 + 768 * (size_t)N * 2 * ts;
     }
     // BiCGStab keeps five more n x W blocks (r^, v, y, z, t)
@@ -1248,6 +1324,54 @@ int slrf::handle_device(const slrf_handle *h) { return h->device; }
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace {
+template <typename T>
+slrf_status precond_apply_t(slrf_handle *h, const slrf_filter *f, KrylovDims &d, const cplx<T> *Rb, cplx<T> *Zb,
+                            cplx<T> *mu, int32_t *mg_levels) {
+    Ctx &ctx = h->ctx;
+    const int W = d.W(), N = d.N;
+    const int64_t n = d.n;
+    KrylovBuffers<T> kb{};
+    kb.gy = krylov_row_groups(ctx, d, sizeof(T) == 4);
+    CKS(ensure(h, h->kDinv, (size_t)n * N * sizeof(cplx<T>)));
+    CKS(ensure(h, h->kPart, (size_t)kb.gy * W * 4 * sizeof(T)));
+    CKS(ensure(h, h->kSig, SLRF_MAX_POLES * sizeof(cplx<T>)));
+    CKS(ensure(h, h->kFlags, (size_t)W * 2 * sizeof(int32_t) + 64));
+    kb.dinv = as<cplx<T>>(h->kDinv);
+    kb.s.part = as<T>(h->kPart);
+    kb.s.flag = as<int32_t>(h->kFlags);
+    std::vector<int32_t> flags(W);
+    for (int col = 0; col < W; ++col) flags[col] = (col % d.Lp) < d.m ? 1 : 0;
+    std::vector<cplx<T>> sg(SLRF_MAX_POLES);
+    for (int j = 0; j < N; ++j) sg[j] = mk((T)f->sigma_re[j], (T)f->sigma_im[j]);
+    CK(cudaMemcpyAsync(kb.s.flag, flags.data(), W * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
+    CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
+    const cplx<T> *sig = as<cplx<T>>(h->kSig);
+    h->ctx.reset_counters();
+    bool use_mg = uses_mg(h);
+    if (use_mg) {
+        bool usable = true;
+        CKS(mg_prepare<T>(h, f, d, kb, h->opts.precond == SLRF_PRECOND_AUTO, &usable));
+        use_mg = usable;
+    }
+    if (use_mg) {
+        MgSolve<T> &mg = mg_of<T>(h);
+        if (mg.nlev == 1) CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
+        mg_apply<T>(ctx, d, mg, sig, kb.s.flag, kb.s.part, kb.gy, Rb, Zb, mg.nlev == 1 ? as<cplx<T>>(h->kQ) : nullptr);
+    } else {
+        krylov_dinv<T>(ctx, h->A, make_poleset<T>(f),
+                       h->opts.precond == SLRF_PRECOND_NONE ? SLRF_PRECOND_NONE : SLRF_PRECOND_JACOBI, kb.dinv);
+        bicgstab_precond_jacobi<T>(ctx, d, kb, Rb, Zb);
+        mg_rz<T>(ctx, d, kb.gy, Rb, Zb, kb.s.flag, kb.s.part);
+    }
+    if (mu) krylov_reduce_mu<T>(ctx, d, kb.s.part, kb.gy, mu);
+    if (mg_levels) *mg_levels = use_mg ? mg_of<T>(h).nlev : 0;
+    CK(cudaStreamSynchronize(ctx.stream));   // the host vectors above are pageable
+    CK(cudaGetLastError());
+    return SLRF_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char *slrf_status_str(slrf_status s) {
@@ -1361,6 +1485,39 @@ slrf_status slrf_mg_describe(const slrf_pencil *p, const slrf_opts *o, int32_t *
                 if (coarse_b) coarse_b[(size_t)i * nc + cc[k]] = cb[k];
             }
     }
+    return SLRF_OK;
+}
+
+slrf_status slrf_mg_transfer(const slrf_pencil *p, const slrf_opts *o, int32_t level, int32_t *n_rows,
+                             int32_t *n_cols, int64_t *nnz, double *rho, int32_t *ptr, int32_t *col, double *val) {
+    if (!p || p->on_device || !n_rows || !n_cols || !nnz || !rho || level < 0) return SLRF_EINVAL;
+    if (p->n < 1 || p->n > (1LL << 31) - 2 || p->nnz < p->n || p->nnz > (1LL << 31) - 1 || !p->row_ptr ||
+        !p->col_idx || !p->a_val || !p->b_val)
+        return SLRF_EINVAL;
+    slrf_opts def;
+    slrf_opts_default(&def);
+    if (!o) o = &def;
+    CKS(check_opts(o));
+    const int64_t n = p->n, nnzA = p->nnz;
+    std::vector<int32_t> rp(p->row_ptr, p->row_ptr + n + 1), ci(p->col_idx, p->col_idx + nnzA);
+    std::vector<double> av(p->a_val, p->a_val + nnzA), bv(p->b_val, p->b_val + nnzA);
+    if (!pencil_valid(n, nnzA, rp, ci, av, bv)) return SLRF_EINVAL;
+    HostHierarchy H;
+    const std::string err =
+        mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(*o, mg_block_for(*o, n, rp, ci)), H);
+    if (!err.empty()) {
+        g_last_error = err;
+        return SLRF_BREAKDOWN;
+    }
+    if (level > (int)H.lv.size() - 2) return SLRF_EINVAL;
+    const HostCsr &P = H.lv[level].P;
+    *n_rows = P.n_rows;
+    *n_cols = P.n_cols;
+    *nnz = (int64_t)P.col.size();
+    *rho = H.lv[level].rho;
+    if (ptr) std::copy(P.ptr.begin(), P.ptr.end(), ptr);
+    if (col) std::copy(P.col.begin(), P.col.end(), col);
+    if (val) std::copy(P.val.begin(), P.val.end(), val);
     return SLRF_OK;
 }
 
@@ -1638,6 +1795,22 @@ slrf_status slrf_shifted_spmm(slrf_handle *h, const slrf_filter *f, int32_t prec
     CK(cudaStreamSynchronize(ctx.stream));
     CK(cudaGetLastError());
     return SLRF_OK;
+}
+
+slrf_status slrf_precond_apply(slrf_handle *h, const slrf_filter *f, int32_t prec, int32_t m, int32_t ldp,
+                               const void *R, void *Z, void *mu, int32_t *mg_levels) {
+    if (!h || !R || !Z || m < 1 || ldp < m || (ldp & 1)) return SLRF_EINVAL;
+    CKS(check_filter(f));
+    KrylovDims d;
+    d.n = h->A.n;
+    d.N = f->n_poles;
+    d.Lp = ldp;
+    d.m = m;
+    if (prec == SLRF_PREC_MIXED)
+        return precond_apply_t<float>(h, f, d, (const float2 *)R, (float2 *)Z, (float2 *)mu, mg_levels);
+    if (prec == SLRF_PREC_FP64)
+        return precond_apply_t<double>(h, f, d, (const double2 *)R, (double2 *)Z, (double2 *)mu, mg_levels);
+    return SLRF_EINVAL;
 }
 
 slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx, double *Y, int64_t ldy, double *Z,

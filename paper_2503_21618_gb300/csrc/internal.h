@@ -156,6 +156,16 @@ template <typename T> struct MgLevel {
     const T *pval = nullptr, *rval = nullptr;
     cplx<T> *r = nullptr, *z = nullptr, *t = nullptr, *dinv = nullptr;
     double rho = 1.0;                         // spectral radius of D^{-1} A on this level
+    // level 0 with a next level: F = (M - D^{-1}) P in pair form (F_a, F_b),
+    // F_a = A P - (rho/omega) diag(a) P, F_b = B P - (rho/omega) diag(b) P,
+    // by fine row groups (the R rows of the level's groups, union coarse
+    // columns, R pairs per entry: "up") and by coarse rows (F^T: "down").
+    // f_q holds the unfolded FP64 pieces (A P, B P) and (a_ii P, b_ii P) per
+    // stored pair, up entries first; f_ab the folded pairs in that order.
+    int64_t fu_nnz = 0, fd_nnz = 0;
+    const int32_t *fu_ptr = nullptr, *fu_col = nullptr, *fd_ptr = nullptr, *fd_col = nullptr;
+    const double2 *f_q = nullptr;
+    cplx<T> *f_ab = nullptr;
 };
 template <typename T> struct MgSolve {
     int nlev = 0, nc = 0;
@@ -168,10 +178,14 @@ template <typename T> struct MgSolve {
 template <typename T>
 void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps);
 // Z0 = cycle(R0) for all active columns of the state; T0 is an n x W
-// scratch block; part receives the partial sums r^T z (slots 0, 1).
+// scratch block (used only by a single-level hierarchy); part receives the
+// partial sums r^T z (slots 0, 1).
 template <typename T>
 void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig, const int32_t *flag, T *part,
               int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0);
+// part = partial sums r^T z per column (slots 0, 1) of two state blocks
+template <typename T>
+void mg_rz(Ctx &ctx, const KrylovDims &d, int gy, const cplx<T> *R, const cplx<T> *Z, const int32_t *flag, T *part);
 
 // ---------------------------------------------------------------- dense.cu
 // Y = A X and/or Z = B X, FP64, row-major n x m.

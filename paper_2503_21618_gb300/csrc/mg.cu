@@ -3,20 +3,24 @@
 // One cycle is applied to all (pole, column) systems at once: every level
 // keeps the column-block layout of the Krylov state (complex n_l x W, row
 // stride W, pole j in columns [j*Lp, j*Lp + Lp)), the level operator of pole
-// j is A_l - sigma_j B_l with the Galerkin pencil of mg_setup.cpp, and the
-// smoother is damped Jacobi, D_lj = omega_l / (a_ii - sigma_j b_ii) with
+// j is M_l = A_l - sigma_j B_l with the Galerkin pencil of mg_setup.cpp, and
+// the smoother is damped Jacobi, D_lj = omega_l / (a_ii - sigma_j b_ii) with
 // omega_l = omega / rho(D_l^{-1} A_l) (4/3 by default: the high-frequency
 // modes are damped whatever the level's diagonal dominance).  With
 // R_l = P_l^T, equal pre- and post-smoothing and the exact coarsest solve
 // V (Lambda - sigma_j)^{-1} V^T, the cycle is a complex symmetric linear
 // operator, as COCG requires of its preconditioner.
 //
-// Finest level (one sweep each side, the pre-smoothing from zero folded in):
-//   t  = r - M (D r)                  k_mg_sspmm<RESID0>
-//   r1 = P^T t                        k_mg_xfer<RESTRICT>
-//   e  = cycle(1, r1)
-//   z1 = D r + P e                    k_mg_xfer<PROLONG0>
-//   z  = z1 + D (r - M z1), r^T z     k_mg_sspmm<SMOOTH>  (+ partial dots)
+// Finest level, one sweep each side with the pre-smoothing from zero:
+//   x = D r,  r1 = P^T (r - M x),  e = cycle(1, r1),
+//   z1 = x + P e,  z = z1 + D (r - M z1).
+// With F = (M - D^{-1}) P (a pair matrix like the pencil's: F_a - sigma F_b)
+// the two ends fold into one gathered product each, and neither the fine
+// residual nor z1 is ever stored:
+//   r1 = -F^T (D r)                         k_mg_sspmm<DOWN>  (coarse rows)
+//   z  = D (2 r - M (D r) - F e),  r^T z    k_mg_sspmm<UP>    (fine row groups)
+// (P^T (I - M D) = -((M - D^{-1}) P)^T D and (I - D M) P = -D F.)  The fine
+// level is read twice and written once per cycle.
 // Coarser levels run nu sweeps on each side and gamma coarse visits
 // (gamma = 2: W-cycle) with materialised iterates.
 #include <cuda_runtime.h>
@@ -55,8 +59,8 @@ __device__ __forceinline__ CV<double, 1> ldcv(const double2 *p) {
 }
 __device__ __forceinline__ void stcv(double2 *p, const CV<double, 1> &a) { *p = a.v[0]; }
 
-enum { MG_RESID0 = 0, MG_RESID = 1, MG_SMOOTH = 2 };
-enum { MG_RESTRICT = 0, MG_PROLONG0 = 1, MG_PROLONG_ADD = 2 };
+enum { MG_RESID = 0, MG_SMOOTH = 1, MG_DOWN = 2, MG_UP = 3 };
+enum { MG_RESTRICT = 0, MG_PROLONG_ADD = 1 };
 
 // Column group of a thread: VC consecutive columns of one pole (Lp is even).
 template <int VC>
@@ -67,23 +71,75 @@ __device__ __forceinline__ bool col_active(const int32_t *flag, int c0) {
     return a;
 }
 
+// One segment of a row group's union column list [e0, e1): gathers x_k = X[k]
+// (times D_kj if SCALE) and accumulates sa[r] += a_rk x_k, sb[r] += b_rk x_k.
+// measured on the 2D bench: 2-deep gathers at 6 CTAs per SM beat 4-deep at 4
+// (125 vs 134 ms per solve) and 8-deep (155 ms)
+template <typename T, int VC, int R, bool SCALE>
+__device__ __forceinline__ void seg_accum(int e0, int e1, const int32_t *__restrict__ ucol,
+                                          const cplx<T> *__restrict__ uab, const cplx<T> *__restrict__ X, int W,
+                                          int c0, const cplx<T> *__restrict__ dinv, int N, int j,
+                                          cplx<T> (&sa)[R][VC], cplx<T> (&sb)[R][VC]) {
+    using C = cplx<T>;
+    constexpr int UNR = 2;
+    for (int e = e0; e < e1; e += UNR) {
+        int cc[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) cc[u] = (e + u < e1) ? __ldg(ucol + e + u) : -1;
+        CV<T, VC> x[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (cc[u] >= 0) {
+                x[u] = ldcv(X + (int64_t)cc[u] * W + c0);
+                if (SCALE) {
+                    const C dk = dinv[(int64_t)cc[u] * N + j];
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) x[u].v[v] = cmul(dk, x[u].v[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < VC; ++v) x[u].v[v] = mk((T)0, (T)0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (cc[u] < 0) break;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const C w = __ldg(uab + (int64_t)(e + u) * R + r);
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    sa[r][v].x = fma(w.x, x[u].v[v].x, sa[r][v].x);
+                    sa[r][v].y = fma(w.x, x[u].v[v].y, sa[r][v].y);
+                    sb[r][v].x = fma(w.y, x[u].v[v].x, sb[r][v].x);
+                    sb[r][v].y = fma(w.y, x[u].v[v].y, sb[r][v].y);
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Shifted level product in row-group form (R rows per group share one union
-// column list with R (a, b) pairs per entry; R = 1 is plain CSR):
-//   RESID0: out = r - M (D r)   (gathers r and D of the neighbour rows)
+// column list with R (a, b) pairs per entry; R = 1 is plain CSR), with
+// y = (sa - sigma sb) the gathered shifted product of the group's rows:
 //   RESID : out = r - M x
 //   SMOOTH: out = x + D (r - M x), optional partial r^T out per column
+//   DOWN  : out = -F^T (D x)               (rows: coarse; gathers: fine x, D)
+//   UP    : out = D (2 r - M (D r) - F e),  (x = r; second list: F over e)
+//           optional partial r^T out
 // ---------------------------------------------------------------------------
 template <typename T, int VC, int R, int MODE>
 __global__ void __launch_bounds__(32 * TY, 6)
 k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__ gptr,
            const int32_t *__restrict__ ucol, const cplx<T> *__restrict__ uab, const cplx<T> *__restrict__ sig,
            const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ X, const cplx<T> *__restrict__ Rv,
-           cplx<T> *__restrict__ Out, const int32_t *__restrict__ flag, T *__restrict__ part) {
+           cplx<T> *__restrict__ Out, const int32_t *__restrict__ flag, T *__restrict__ part,
+           const int32_t *__restrict__ g2ptr, const int32_t *__restrict__ u2col, const cplx<T> *__restrict__ u2ab,
+           const cplx<T> *__restrict__ X2) {
     using C = cplx<T>;
-    // measured on the 2D bench: 2-deep gathers at 6 CTAs per SM beat 4-deep at 4
-    // (125 vs 134 ms per solve) and 8-deep (155 ms)
-    constexpr int UNR = 2;
+    constexpr bool DOTS = MODE == MG_SMOOTH || MODE == MG_UP;
+    constexpr bool SCALE = MODE == MG_DOWN || MODE == MG_UP;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int ng = W / VC;
     const int cg = blockIdx.x * 32 + tx;
@@ -106,72 +162,49 @@ k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__
     // 2D solve)
     if (act) {
         for (int g = blockIdx.y * TY + ty; g < ngroups; g += gridDim.y * TY) {
-            const int e0 = __ldg(gptr + g), e1 = __ldg(gptr + g + 1);
             C sa[R][VC], sb[R][VC];
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int v = 0; v < VC; ++v) sa[r][v] = sb[r][v] = mk((T)0, (T)0);
-            for (int e = e0; e < e1; e += UNR) {
-                int cc[UNR];
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) cc[u] = (e + u < e1) ? __ldg(ucol + e + u) : -1;
-                CV<T, VC> x[UNR];
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) {
-                    if (cc[u] >= 0) {
-                        x[u] = ldcv(X + (int64_t)cc[u] * W + c0);
-                        if (MODE == MG_RESID0) {
-                            const C dk = dinv[(int64_t)cc[u] * N + j];
-#pragma unroll
-                            for (int v = 0; v < VC; ++v) x[u].v[v] = cmul(dk, x[u].v[v]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < VC; ++v) x[u].v[v] = mk((T)0, (T)0);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) {
-                    if (cc[u] < 0) break;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const C w = __ldg(uab + (int64_t)(e + u) * R + r);
-#pragma unroll
-                        for (int v = 0; v < VC; ++v) {
-                            sa[r][v].x = fma(w.x, x[u].v[v].x, sa[r][v].x);
-                            sa[r][v].y = fma(w.x, x[u].v[v].y, sa[r][v].y);
-                            sb[r][v].x = fma(w.y, x[u].v[v].x, sb[r][v].x);
-                            sb[r][v].y = fma(w.y, x[u].v[v].y, sb[r][v].y);
-                        }
-                    }
-                }
-            }
+            seg_accum<T, VC, R, SCALE>(__ldg(gptr + g), __ldg(gptr + g + 1), ucol, uab, X, W, c0, dinv, N, j, sa, sb);
+            if constexpr (MODE == MG_UP)
+                seg_accum<T, VC, R, false>(__ldg(g2ptr + g), __ldg(g2ptr + g + 1), u2col, u2ab, X2, W, c0, dinv, N, j,
+                                           sa, sb);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int row = g * R + r;
                 if (row >= n) break;
                 const int64_t base = (int64_t)row * W + c0;
-                const CV<T, VC> rr = ldcv(Rv + base);
                 CV<T, VC> o;
-                if (MODE == MG_SMOOTH) {
-                    const CV<T, VC> xr = ldcv(X + base);
-                    const C d = dinv[(int64_t)row * N + j];
+                if constexpr (MODE == MG_DOWN) {
 #pragma unroll
-                    for (int v = 0; v < VC; ++v) {
-                        const C y = csub(sa[r][v], cmul(s, sb[r][v]));
-                        o.v[v] = cfma(d, csub(rr.v[v], y), xr.v[v]);
-                        rz[v] = cfma(rr.v[v], o.v[v], rz[v]);
-                    }
+                    for (int v = 0; v < VC; ++v) o.v[v] = csub(cmul(s, sb[r][v]), sa[r][v]);
                 } else {
+                    const CV<T, VC> rr = ldcv(Rv + base);
+                    if constexpr (MODE == MG_RESID) {
 #pragma unroll
-                    for (int v = 0; v < VC; ++v) o.v[v] = csub(rr.v[v], csub(sa[r][v], cmul(s, sb[r][v])));
+                        for (int v = 0; v < VC; ++v) o.v[v] = csub(rr.v[v], csub(sa[r][v], cmul(s, sb[r][v])));
+                    } else {
+                        const C d = dinv[(int64_t)row * N + j];
+                        CV<T, VC> xr;
+                        if constexpr (MODE == MG_SMOOTH) xr = ldcv(X + base);
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
+                            const C y = csub(sa[r][v], cmul(s, sb[r][v]));
+                            if constexpr (MODE == MG_SMOOTH)
+                                o.v[v] = cfma(d, csub(rr.v[v], y), xr.v[v]);
+                            else
+                                o.v[v] = cmul(d, csub(cadd(rr.v[v], rr.v[v]), y));
+                            rz[v] = cfma(rr.v[v], o.v[v], rz[v]);
+                        }
+                    }
                 }
                 stcv(Out + base, o);
             }
         }
     }
-    if constexpr (MODE == MG_SMOOTH) {
+    if constexpr (DOTS) {
         if (part == nullptr) return;   // uniform over the block
         __shared__ T red[TY][32][VC * 2];
 #pragma unroll
@@ -197,17 +230,15 @@ k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Grid transfers with a real CSR matrix (P or P^T), all W columns:
+// Grid transfers below the finest level with a real CSR matrix (P or P^T),
+// all W columns:
 //   RESTRICT   : out = M x
-//   PROLONG0   : out = D r + M x
 //   PROLONG_ADD: out += M x           (out is the level iterate, updated in place)
 // ---------------------------------------------------------------------------
 template <typename T, int VC, int MODE>
 __global__ void __launch_bounds__(32 * TY)
-k_mg_xfer(int n_out, int W, int Lp, int N, int rows_per_block, const int32_t *__restrict__ ptr,
-          const int32_t *__restrict__ col, const T *__restrict__ val, const cplx<T> *__restrict__ X,
-          const cplx<T> *__restrict__ Rv, const cplx<T> *__restrict__ dinv, cplx<T> *Out,
-          const int32_t *__restrict__ flag) {
+k_mg_xfer(int n_out, int W, int rows_per_block, const int32_t *__restrict__ ptr, const int32_t *__restrict__ col,
+          const T *__restrict__ val, const cplx<T> *__restrict__ X, cplx<T> *Out, const int32_t *__restrict__ flag) {
     using C = cplx<T>;
     constexpr int UNR = 4;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -216,7 +247,6 @@ k_mg_xfer(int n_out, int W, int Lp, int N, int rows_per_block, const int32_t *__
     if (cg >= ng) return;
     const int c0 = cg * VC;
     if (!col_active<VC>(flag, c0)) return;
-    const int j = c0 / Lp;
     const int r_begin = blockIdx.y * rows_per_block;
     const int r_end = min(n_out, r_begin + rows_per_block);
     for (int row = r_begin + ty; row < r_end; row += TY) {
@@ -256,11 +286,6 @@ k_mg_xfer(int n_out, int W, int Lp, int N, int rows_per_block, const int32_t *__
         if (MODE == MG_RESTRICT) {
 #pragma unroll
             for (int v = 0; v < VC; ++v) o.v[v] = acc[v];
-        } else if (MODE == MG_PROLONG0) {
-            const CV<T, VC> rr = ldcv(Rv + base);
-            const C d = dinv[(int64_t)row * N + j];
-#pragma unroll
-            for (int v = 0; v < VC; ++v) o.v[v] = cfma(d, rr.v[v], acc[v]);
         } else {
             o = ldcv(Out + base);
 #pragma unroll
@@ -405,6 +430,17 @@ __global__ void k_mg_dinv(int n, int N, const double *__restrict__ da, const dou
     dinv[i] = r;
 }
 
+// F = (M - D^{-1}) P of the finest level in pair form for the current damping:
+// per stored pair, q = (A P, B P) and (a_ii P, b_ii P); out = first - kappa
+// second with kappa = rho_0 / omega (D^{-1} = (rho_0 / omega) (a_ii - sigma b_ii)).
+template <typename T>
+__global__ void k_mg_fold(int64_t ns, const double2 *__restrict__ q, double kappa, cplx<T> *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const double2 a = q[2 * i], b = q[2 * i + 1];
+    out[i] = mk((T)(a.x - kappa * b.x), (T)(a.y - kappa * b.y));
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -413,20 +449,31 @@ double vec_bytes(const KrylovDims &d, int n) {
     return (double)n * d.W() * d.frac * sizeof(cplx<T>);
 }
 
+// One level product.  Bytes: the pattern and pairs once, the gathered input
+// block once (its own rows are part of it), the other vector blocks read or
+// written once, the Jacobi diagonals of the gathered rows; for UP also F and
+// the coarse iterate.
 template <typename T, int MODE>
-void launch_sspmm(Ctx &ctx, const KrylovDims &d, const MgLevel<T> &L, int gy, const cplx<T> *sig,
-                  const cplx<T> *X, const cplx<T> *Rv, cplx<T> *Out, const int32_t *flag, T *part) {
+void launch_sspmm(Ctx &ctx, const KrylovDims &d, int kc, int n_rows, int R, int ngroups, const int32_t *gptr,
+                  const int32_t *gcol, const cplx<T> *ab, int64_t nnz_union, int n_in, int gy, const cplx<T> *sig,
+                  const cplx<T> *dinv, const cplx<T> *X, const cplx<T> *Rv, cplx<T> *Out, const int32_t *flag,
+                  T *part, const int32_t *g2ptr = nullptr, const int32_t *g2col = nullptr,
+                  const cplx<T> *ab2 = nullptr, int64_t nnz2 = 0, const cplx<T> *X2 = nullptr, int n2 = 0) {
     constexpr int VC = VecN<T>::VC;
     const int W = d.W();
+    // gy is used as given: with partial dots every one of the gy partial rows
+    // must be written (CTAs without row groups write zeros)
     dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
-    const double vb = vec_bytes<T>(d, L.n);
-    const double bytes = 4.0 * (L.ngroups + 1) + (double)L.nnz_union * (4 + L.R * sizeof(cplx<T>)) +
-                         (MODE == MG_SMOOTH ? 4 : 3) * vb + (double)L.n * d.N * sizeof(cplx<T>);
-    ctx.before(L.n == d.n ? KC_MG_FINE : KC_MG_COARSE, bytes, 8.0 * (double)L.nnz_union * L.R * W * d.frac);
-#define SSP(RR)                                                                                                   \
-    k_mg_sspmm<T, VC, RR, MODE><<<grid, block, 0, ctx.stream>>>(L.n, W, d.Lp, d.N, L.ngroups, L.gptr, L.gcol,      \
-                                                               L.ab, sig, L.dinv, X, Rv, Out, flag, part)
-    switch (L.R) {
+    const double vin = vec_bytes<T>(d, n_in), vout = vec_bytes<T>(d, n_rows);
+    double bytes = 4.0 * (ngroups + 1) + (double)nnz_union * (4 + R * sizeof(cplx<T>)) + vin + vout;
+    if (MODE == MG_RESID || MODE == MG_SMOOTH) bytes += vout;                // r of the rows (UP: r is x)
+    if (MODE != MG_RESID) bytes += (double)n_in * d.N * sizeof(cplx<T>);   // D of the gathered rows
+    if (MODE == MG_UP) bytes += 4.0 * (ngroups + 1) + (double)nnz2 * (4 + R * sizeof(cplx<T>)) + vec_bytes<T>(d, n2);
+    ctx.before(kc, bytes, 8.0 * (double)(nnz_union + nnz2) * R * W * d.frac);
+#define SSP(RR)                                                                                                     \
+    k_mg_sspmm<T, VC, RR, MODE><<<grid, block, 0, ctx.stream>>>(n_rows, W, d.Lp, d.N, ngroups, gptr, gcol, ab, sig, \
+                                                               dinv, X, Rv, Out, flag, part, g2ptr, g2col, ab2, X2)
+    switch (R) {
         case 1: SSP(1); break;
         case 2: SSP(2); break;
         case 3: SSP(3); break;
@@ -436,10 +483,17 @@ void launch_sspmm(Ctx &ctx, const KrylovDims &d, const MgLevel<T> &L, int gy, co
     ctx.after();
 }
 
+// RESID / SMOOTH on a level below the finest
+template <typename T, int MODE>
+void level_sspmm(Ctx &ctx, const KrylovDims &d, const MgLevel<T> &L, int gy, const cplx<T> *sig, const cplx<T> *X,
+                 const cplx<T> *Rv, cplx<T> *Out, const int32_t *flag) {
+    launch_sspmm<T, MODE>(ctx, d, KC_MG_COARSE, L.n, L.R, L.ngroups, L.gptr, L.gcol, L.ab, L.nnz_union, L.n, gy, sig,
+                          L.dinv, X, Rv, Out, flag, nullptr);
+}
+
 template <typename T, int MODE>
 void launch_xfer(Ctx &ctx, const KrylovDims &d, int n_out, int n_in, int64_t nnz, const int32_t *ptr,
-                 const int32_t *col, const T *val, int gy, const cplx<T> *X, const cplx<T> *Rv, const cplx<T> *dinv,
-                 cplx<T> *Out, const int32_t *flag) {
+                 const int32_t *col, const T *val, int gy, const cplx<T> *X, cplx<T> *Out, const int32_t *flag) {
     constexpr int VC = VecN<T>::VC;
     const int W = d.W();
     int gyy = std::min(gy, (n_out + TY - 1) / TY);
@@ -447,11 +501,9 @@ void launch_xfer(Ctx &ctx, const KrylovDims &d, int n_out, int n_in, int64_t nnz
     dim3 grid((W / VC + 31) / 32, gyy), block(32, TY);
     const int rpb = (n_out + gyy - 1) / gyy;
     const double bytes = 4.0 * (n_out + 1) + (double)nnz * (4 + sizeof(T)) + vec_bytes<T>(d, n_in) +
-                         (MODE == MG_RESTRICT ? 1 : 2) * vec_bytes<T>(d, n_out) +
-                         (MODE == MG_PROLONG0 ? (double)n_out * d.N * sizeof(cplx<T>) : 0.0);
+                         (MODE == MG_RESTRICT ? 1 : 2) * vec_bytes<T>(d, n_out);
     ctx.before(KC_MG_TRANSFER, bytes, 4.0 * (double)nnz * W * d.frac);
-    k_mg_xfer<T, VC, MODE><<<grid, block, 0, ctx.stream>>>(n_out, W, d.Lp, d.N, rpb, ptr, col, val, X, Rv, dinv, Out,
-                                                          flag);
+    k_mg_xfer<T, VC, MODE><<<grid, block, 0, ctx.stream>>>(n_out, W, rpb, ptr, col, val, X, Out, flag);
     ctx.after();
 }
 
@@ -467,6 +519,17 @@ void coarse_solve(Ctx &ctx, const KrylovDims &d, const MgSolve<T> &mg, const cpl
     ctx.after();
     ctx.before(KC_MG_COARSE, bytes, flops);
     k_mg_coarse_gemm<T><<<grid, block, 0, ctx.stream>>>(nc, W, d.Lp, d.N, 0, mg.V, Y, nullptr, Z, flag);
+    ctx.after();
+}
+
+template <typename T>
+void launch_rz(Ctx &ctx, const KrylovDims &d, int gy, const cplx<T> *R, const cplx<T> *Z, const int32_t *flag,
+               T *part) {
+    constexpr int VC = VecN<T>::VC;
+    const int W = d.W();
+    dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
+    ctx.before(KC_MG_TRANSFER, 2 * vec_bytes<T>(d, d.n), 0);
+    k_mg_rz<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, R, Z, flag, part);
     ctx.after();
 }
 
@@ -487,25 +550,23 @@ cplx<T> *cycle(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, int l, int gy, con
     {
         const int W = d.W();
         dim3 grid((W / VC + 31) / 32, gyl), block(32, TY);
-        ctx.before(KC_MG_TRANSFER, 2 * vec_bytes<T>(d, L.n), 0);
+        ctx.before(KC_MG_TRANSFER, 2 * vec_bytes<T>(d, L.n) + (double)L.n * d.N * sizeof(cplx<T>), 0);
         k_mg_jacobi0<T, VC><<<grid, block, 0, ctx.stream>>>(L.n, W, d.Lp, d.N, L.dinv, L.r, z, flag);
         ctx.after();
     }
     for (int s = 1; s < mg.nu; ++s) {
-        launch_sspmm<T, MG_SMOOTH>(ctx, d, L, gyl, sig, z, L.r, t, flag, nullptr);
+        level_sspmm<T, MG_SMOOTH>(ctx, d, L, gyl, sig, z, L.r, t, flag);
         std::swap(z, t);
     }
     const MgLevel<T> &Lc = mg.lv[l + 1];
     for (int v = 0; v < mg.gamma; ++v) {
-        launch_sspmm<T, MG_RESID>(ctx, d, L, gyl, sig, z, L.r, t, flag, nullptr);
-        launch_xfer<T, MG_RESTRICT>(ctx, d, Lc.n, L.n, L.r_nnz, L.rptr, L.rcol, L.rval, gy, t, nullptr, nullptr,
-                                    Lc.r, flag);
+        level_sspmm<T, MG_RESID>(ctx, d, L, gyl, sig, z, L.r, t, flag);
+        launch_xfer<T, MG_RESTRICT>(ctx, d, Lc.n, L.n, L.r_nnz, L.rptr, L.rcol, L.rval, gy, t, Lc.r, flag);
         cplx<T> *e = cycle<T>(ctx, d, mg, l + 1, gy, sig, flag);
-        launch_xfer<T, MG_PROLONG_ADD>(ctx, d, L.n, Lc.n, L.p_nnz, L.pptr, L.pcol, L.pval, gy, e, nullptr, nullptr,
-                                       z, flag);
+        launch_xfer<T, MG_PROLONG_ADD>(ctx, d, L.n, Lc.n, L.p_nnz, L.pptr, L.pcol, L.pval, gy, e, z, flag);
     }
     for (int s = 0; s < mg.nu; ++s) {
-        launch_sspmm<T, MG_SMOOTH>(ctx, d, L, gyl, sig, z, L.r, t, flag, nullptr);
+        level_sspmm<T, MG_SMOOTH>(ctx, d, L, gyl, sig, z, L.r, t, flag);
         std::swap(z, t);
     }
     return z;
@@ -524,35 +585,45 @@ void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps) {
                                                                               mg.omega / L.rho, L.dinv);
         ctx.after();
     }
+    MgLevel<T> &L0 = mg.lv[0];
+    if (mg.nlev > 1) {
+        const int64_t ns = L0.fu_nnz * L0.R + L0.fd_nnz;
+        ctx.before(KC_KRYLOV_INIT, (double)ns * (32 + sizeof(cplx<T>)), 0);
+        k_mg_fold<T><<<(unsigned)((ns + 255) / 256), 256, 0, ctx.stream>>>(ns, L0.f_q, L0.rho / mg.omega, L0.f_ab);
+        ctx.after();
+    }
 }
 
 template <typename T>
 void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig, const int32_t *flag, T *part,
               int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0) {
-    constexpr int VC = VecN<T>::VC;
-    const int W = d.W();
     if (mg.nlev == 1) {
         coarse_solve<T>(ctx, d, mg, R0, T0, Z0, flag);
-        dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
-        ctx.before(KC_MG_TRANSFER, 2 * vec_bytes<T>(d, d.n), 0);
-        k_mg_rz<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, R0, Z0, flag, part);
-        ctx.after();
+        launch_rz<T>(ctx, d, gy, R0, Z0, flag, part);
         return;
     }
-    MgLevel<T> &L = mg.lv[0];
+    const MgLevel<T> &L = mg.lv[0];
     const MgLevel<T> &Lc = mg.lv[1];
-    launch_sspmm<T, MG_RESID0>(ctx, d, L, gy, sig, R0, R0, T0, flag, nullptr);
-    launch_xfer<T, MG_RESTRICT>(ctx, d, Lc.n, L.n, L.r_nnz, L.rptr, L.rcol, L.rval, gy, T0, nullptr, nullptr, Lc.r,
-                                flag);
+    // r1 = -F^T (D r)
+    const int gyd = std::max(1, std::min(gy, (Lc.n + TY - 1) / TY));
+    launch_sspmm<T, MG_DOWN>(ctx, d, KC_MG_FINE, Lc.n, 1, Lc.n, L.fd_ptr, L.fd_col, L.f_ab + L.fu_nnz * L.R,
+                             L.fd_nnz, L.n, gyd, sig, L.dinv, R0, nullptr, Lc.r, flag, nullptr);
     cplx<T> *e = cycle<T>(ctx, d, mg, 1, gy, sig, flag);
-    launch_xfer<T, MG_PROLONG0>(ctx, d, L.n, Lc.n, L.p_nnz, L.pptr, L.pcol, L.pval, gy, e, R0, L.dinv, T0, flag);
-    launch_sspmm<T, MG_SMOOTH>(ctx, d, L, gy, sig, T0, R0, Z0, flag, part);
+    // z = D (2 r - M (D r) - F e), r^T z
+    launch_sspmm<T, MG_UP>(ctx, d, KC_MG_FINE, L.n, L.R, L.ngroups, L.gptr, L.gcol, L.ab, L.nnz_union, L.n, gy, sig,
+                           L.dinv, R0, R0, Z0, flag, part, L.fu_ptr, L.fu_col, L.f_ab, L.fu_nnz, e, Lc.n);
+}
+
+template <typename T>
+void mg_rz(Ctx &ctx, const KrylovDims &d, int gy, const cplx<T> *R, const cplx<T> *Z, const int32_t *flag, T *part) {
+    launch_rz<T>(ctx, d, gy, R, Z, flag, part);
 }
 
 #define INST(T)                                                                                                  \
     template void mg_dinv<T>(Ctx &, MgSolve<T> &, const PoleSet<T> &);                                           \
     template void mg_apply<T>(Ctx &, const KrylovDims &, MgSolve<T> &, const cplx<T> *, const int32_t *, T *,  \
-                              int, const cplx<T> *, cplx<T> *, cplx<T> *);
+                              int, const cplx<T> *, cplx<T> *, cplx<T> *);                                      \
+    template void mg_rz<T>(Ctx &, const KrylovDims &, int, const cplx<T> *, const cplx<T> *, const int32_t *, T *);
 INST(float)
 INST(double)
 #undef INST

@@ -36,6 +36,13 @@ struct HostLevel {
     // transfer to the next level (empty on the coarsest level)
     HostCsr P;    // n x n_next
     HostCsr Rt;   // n_next x n, the transpose of P
+    // level 0 only (when it has a next level): the products A P and B P on
+    // their common pattern (rows sorted by column) with P's values on that
+    // pattern (zero where P has no entry; supp P is inside it since a_ii > 0).
+    // The device folds them into the pair matrix (M - D^{-1}) P of the fused
+    // finest-level restriction and prolongation.
+    std::vector<int32_t> fptr, fcol;
+    std::vector<double> fp, fap, fbp;
 };
 
 struct MgParams {

@@ -471,6 +471,21 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
                 for (int32_t t = P.ptr[j]; t < P.ptr[j + 1]; ++t) add(P.col[t], ca[k] * P.val[t], cb[k] * P.val[t]);
             }
         }, APr);
+        if (H.lv.size() == 1) {   // finest level: keep (P, A P, B P) on the pattern of A P
+            L.fptr = APr.ptr;
+            L.fcol = APr.col;
+            L.fap = APr.a;
+            L.fbp = APr.b;
+            L.fp.assign(L.fcol.size(), 0.0);
+            for (int i = 0; i < cn; ++i) {
+                int32_t k = L.fptr[i];
+                for (int32_t t = P.ptr[i]; t < P.ptr[i + 1]; ++t) {
+                    while (k < L.fptr[i + 1] && L.fcol[k] < P.col[t]) ++k;
+                    if (k < L.fptr[i + 1] && L.fcol[k] == P.col[t]) L.fp[k] = P.val[t];
+                    else return "multigrid setup: prolongator entry outside the pattern of A P";
+                }
+            }
+        }
         HostLevel next;
         next.n = nc;
         RowsOut Cr;

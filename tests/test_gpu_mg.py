@@ -179,3 +179,141 @@ def test_unattainable_tolerance_ends_in_stagnation_after_fp64(api):
 def lam_max_1d(n):
     from oracle import inertia
     return float(inertia.lambda_1d(n, np.array([n]))[0])
+
+
+# ---------------------------------------------------------------------------
+# one cycle, compared with a plain scipy model of it
+# ---------------------------------------------------------------------------
+def _hierarchy_model(api, p, o):
+    """Level pencils (A_l, B_l) chained by Galerkin products of the library's
+    prolongators, and the rho_l of its Jacobi damping."""
+    import scipy.sparse as sp
+    As, Bs, Ps, rhos = [p.A().tocsr()], [p.B().tocsr()], [], []
+    for l in range(len(api.mg_describe(p, o)["levels"]) - 1):
+        (ptr, col, val, nr, nc), rho = api.mg_transfer(p, l, o)
+        P = sp.csr_matrix((val, col, ptr), shape=(nr, nc))
+        Ps.append(P)
+        rhos.append(rho)
+        As.append((P.T @ As[-1] @ P).tocsr())
+        Bs.append((P.T @ Bs[-1] @ P).tocsr())
+    return As, Bs, Ps, rhos
+
+
+def _cycle_model(H, o, sig, r, l, c):
+    """The cycle as written in the textbook: damped Jacobi D = (omega/rho_l) /
+    diag(A_l - sigma B_l), nu sweeps per side below the finest level (one
+    there), gamma coarse visits, exact solve on level c."""
+    As, Bs, Ps, rhos = H
+    M = (As[l] - sig * Bs[l]).tocsr()
+    if l == c:
+        return np.linalg.solve(M.toarray(), r)
+    D = (o.mg_omega / rhos[l]) / (As[l].diagonal() - sig * Bs[l].diagonal())
+    P = Ps[l]
+    if l == 0:
+        x = D * r
+        e = _cycle_model(H, o, sig, P.T @ (r - M @ x), 1, c)
+        z1 = x + P @ e
+        return z1 + D * (r - M @ z1)
+    z = D * r
+    for _ in range(o.mg_nu - 1):
+        z = z + D * (r - M @ z)
+    for _ in range(o.mg_cycle):
+        z = z + P @ _cycle_model(H, o, sig, P.T @ (r - M @ z), l + 1, c)
+    for _ in range(o.mg_nu):
+        z = z + D * (r - M @ z)
+    return z
+
+
+def _apply_case(api, p, o, s, w, prec, m=3, ldp=4, seed=0):
+    N = len(s)
+    rng = np.random.default_rng(seed)
+    R = rng.standard_normal((p.n, N * ldp)) + 1j * rng.standard_normal((p.n, N * ldp))
+    dt = torch.complex128 if prec == api.PREC_FP64 else torch.complex64
+    Rd = torch.from_numpy(R).to(dt).cuda()
+    mu = torch.zeros(N * m, dtype=dt, device="cuda")
+    h = api.Handle(p, o)
+    Z, lv = h.precond_apply(api.Filter(s, w), Rd, m, ldp, prec=prec, mu=mu)
+    R = Rd.cpu().numpy().astype(np.complex128)     # the model starts from the same (rounded) input
+    return R, Z.cpu().numpy().astype(np.complex128), mu.cpu().numpy().astype(np.complex128), lv
+
+
+@pytest.mark.parametrize("variant", [
+    dict(),                                           # two levels (441, 57): exact solve on 57
+    dict(mg_coarse=16),                               # three levels, V-cycle
+    dict(mg_coarse=16, mg_cycle=2),                   # W-cycle
+    dict(mg_coarse=16, mg_nu=1, mg_omega=1.0),
+    dict(mg_coarse=16, mg_nu=3, mg_shift_limit=100.0),
+])
+def test_precond_apply_fp64_is_the_cycle(api, variant):
+    p = pencil_2d_q1(22, seed=9)
+    _, _, s, w = _filter_case(p, 15)
+    o = api.default_opts(precision=api.PREC_FP64, precond=api.PRECOND_MG, **variant)
+    H = _hierarchy_model(api, p, o)
+    m, ldp = 3, 4
+    R, Z, mu, lv = _apply_case(api, p, o, s, w, api.PREC_FP64, m, ldp)
+    assert 2 <= lv <= len(H[0])
+    for j, sig in enumerate(s):
+        for c in range(m):
+            col = j * ldp + c
+            ref = _cycle_model(H, o, sig, R[:, col], 0, lv - 1)
+            assert np.linalg.norm(Z[:, col] - ref) <= 1e-12 * np.linalg.norm(ref)
+            assert abs(mu[j * m + c] - R[:, col] @ ref) <= 1e-12 * np.linalg.norm(R[:, col]) * np.linalg.norm(ref)
+
+
+def test_precond_apply_mixed_is_the_cycle_in_fp32(api):
+    p = pencil_2d_q1(40, seed=5)                      # n = 1521, three levels
+    _, _, s, w = _filter_case(p, 25)
+    o = api.default_opts(precond=api.PRECOND_MG, mg_coarse=64)
+    H = _hierarchy_model(api, p, o)
+    R, Z, mu, lv = _apply_case(api, p, o, s, w, api.PREC_MIXED, m=5, ldp=6, seed=2)
+    assert 2 <= lv <= len(H[0])
+    for j, sig in enumerate(s):
+        for c in range(5):
+            col = j * 6 + c
+            ref = _cycle_model(H, o, sig, R[:, col], 0, lv - 1)
+            assert np.linalg.norm(Z[:, col] - ref) <= 2e-5 * np.linalg.norm(ref)
+
+
+def test_precond_apply_is_complex_symmetric(api):
+    # x^T C y = y^T C x (unconjugated), the property COCG needs of C
+    p = pencil_2d_q1(30, seed=4)
+    _, _, s, w = _filter_case(p, 20)
+    o = api.default_opts(precision=api.PREC_FP64, precond=api.PRECOND_MG, mg_coarse=16, mg_cycle=2)
+    R, Z, _, _ = _apply_case(api, p, o, s, w, api.PREC_FP64, m=2, ldp=2, seed=3)
+    for j in range(len(s)):
+        x, y = R[:, 2 * j], R[:, 2 * j + 1]
+        Cx, Cy = Z[:, 2 * j], Z[:, 2 * j + 1]
+        assert abs(x @ Cy - y @ Cx) <= 1e-12 * abs(x @ Cy)
+
+
+def test_precond_apply_truncated_cycle(api):
+    # deep shift: the cycle stops at level 1 (725 unknowns) and solves it exactly
+    p = pencil_2d_q1(80, seed=7)
+    s, w = poles.slrf_poles(4, 1.0, 0.01, 3500.0)
+    o = api.default_opts(precision=api.PREC_FP64, precond=api.PRECOND_MG)
+    H = _hierarchy_model(api, p, o)
+    R, Z, _, lv = _apply_case(api, p, o, s, w, api.PREC_FP64, m=2, ldp=2, seed=5)
+    assert lv == 2
+    for j, sig in enumerate(s):
+        ref = _cycle_model(H, o, sig, R[:, 2 * j + 1], 0, 1)
+        assert np.linalg.norm(Z[:, 2 * j + 1] - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_precond_apply_single_level_and_jacobi(api):
+    p = pencil_1d(200)                                # one level: the exact shifted solve
+    _, _, s, w = _filter_case(p, 8)
+    A, B = p.A().tocsr(), p.B().tocsr()
+    for pc in (api.PRECOND_MG, api.PRECOND_JACOBI, api.PRECOND_NONE):
+        o = api.default_opts(precision=api.PREC_FP64, precond=pc)
+        R, Z, mu, lv = _apply_case(api, p, o, s, w, api.PREC_FP64, m=2, ldp=2, seed=6)
+        assert lv == (1 if pc == api.PRECOND_MG else 0)
+        for j, sig in enumerate(s):
+            r = R[:, 2 * j]
+            if pc == api.PRECOND_MG:
+                ref = np.linalg.solve((A - sig * B).toarray(), r)
+            elif pc == api.PRECOND_JACOBI:
+                ref = r / (A.diagonal() - sig * B.diagonal())
+            else:
+                ref = r
+            assert np.linalg.norm(Z[:, 2 * j] - ref) <= 1e-12 * np.linalg.norm(ref)
+            assert abs(mu[2 * j] - r @ ref) <= 1e-12 * np.linalg.norm(r) * np.linalg.norm(ref)

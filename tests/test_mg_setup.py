@@ -110,3 +110,95 @@ def test_describe_rejects_bad_input(api, lib):
     o.mg_omega = 2.5
     ok = api.slrf_pencil(p.n, keep[1].size, *[a.ctypes.data for a in keep], 0)
     assert lib.slrf_mg_describe(C.byref(ok), C.byref(o), C.byref(nl), ln, lz, None, None, None, None) == api.EINVAL
+
+
+def _prolongators(api, p, o):
+    import scipy.sparse as sp
+    Ps, rhos = [], []
+    for l in range(len(api.mg_describe(p, o)["levels"]) - 1):
+        (ptr, col, val, nr, nc), rho = api.mg_transfer(p, l, o)
+        Ps.append(sp.csr_matrix((val, col, ptr), shape=(nr, nc)))
+        rhos.append(rho)
+    return Ps, rhos
+
+
+@pytest.mark.parametrize("pencil,opts", [(lambda: pencil_2d_q1(22, seed=9), dict(mg_coarse=16)),
+                                         (lambda: pencil_1d(2000), dict()),
+                                         (lambda: pencil_3d_elasticity(5), dict(mg_coarse=30))])
+def test_prolongators_reproduce_the_galerkin_coarse_pencil(api, pencil, opts):
+    # P_l^T A_l P_l chained from the exported prolongators (scipy) must give the
+    # coarsest pencil the library formed itself; rho_l must be the spectral
+    # radius of diag(A_l)^{-1} A_l to within the few percent that its 30
+    # power-iteration steps reach (the damping omega / rho_l needs no more)
+    p = pencil()
+    o = api.default_opts(**opts)
+    d = api.mg_describe(p, o, coarse=True)
+    Ps, rhos = _prolongators(api, p, o)
+    A, B = p.A().tocsr(), p.B().tocsr()
+    for l, P in enumerate(Ps):
+        assert P.shape == (d["levels"][l], d["levels"][l + 1])
+        Dinv_A = (A.multiply(1.0 / A.diagonal()[:, None])).toarray()
+        lam_max = np.max(np.abs(np.linalg.eigvals(Dinv_A))) if A.shape[0] <= 2000 else None
+        if lam_max is not None:
+            assert abs(rhos[l] - lam_max) <= 0.05 * lam_max
+        A, B = (P.T @ A @ P).tocsr(), (P.T @ B @ P).tocsr()
+    scale = np.abs(d["coarse_A"]).max()
+    np.testing.assert_allclose(A.toarray(), d["coarse_A"], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(B.toarray(), d["coarse_B"], rtol=0, atol=1e-12 * np.abs(d["coarse_B"]).max())
+
+
+def test_prolongator_is_a_smoothed_piecewise_constant(api):
+    # P = (I - 4/(3 rho) diag(A)^{-1} A) T with T piecewise constant on the
+    # aggregates (T 1 = 1/sqrt(|aggregate|) per row).  In 1D the aggregates
+    # are a node and its two strong neighbours (n = 300 -> 100 aggregates;
+    # the first and the last differ), so T 1 = 1/sqrt(3) and A T 1 = 0 a few
+    # nodes away from the ends: P 1 = T 1 there
+    p = pencil_1d(300)
+    (ptr, col, val, nr, nc), rho = api.mg_transfer(p, 0)
+    import scipy.sparse as sp
+    P = sp.csr_matrix((val, col, ptr), shape=(nr, nc))
+    assert nc == 100
+    rows = np.asarray(P.sum(axis=1)).ravel()
+    np.testing.assert_allclose(rows[4:-6], 1 / np.sqrt(3), rtol=1e-13)
+    assert np.all(np.diff(P.indptr) <= 2)           # a node touches at most two aggregates
+
+
+def test_fused_finest_level_equals_the_two_grid_steps(api):
+    # The cycle's finest level restricts and prolongs through F = (M - D^{-1}) P:
+    # r1 = -F^T (D r) and z = D (2 r - M (D r) - F e) are the textbook steps
+    # x = D r, r1 = P^T (r - M x), z1 = x + P e, z = z1 + D (r - M z1)
+    import scipy.sparse as sp
+    from oracle import poles
+    p = pencil_2d_q1(22, seed=9)
+    o = api.default_opts(mg_coarse=16)
+    Ps, rhos = _prolongators(api, p, o)
+    P = Ps[0]
+    A, B = p.A().tocsr(), p.B().tocsr()
+    s, _ = poles.slrf_poles(4, 1.0, 0.01, 3000.0)
+    rng = np.random.default_rng(1)
+    for sig in s:
+        M = (A - sig * B).tocsr()
+        Dd = (o.mg_omega / rhos[0]) / (A.diagonal() - sig * B.diagonal())
+        D = sp.diags(Dd)
+        Mc = (P.T @ M @ P).toarray()
+        r = rng.standard_normal(p.n) + 1j * rng.standard_normal(p.n)
+        x = D @ r
+        r1 = P.T @ (r - M @ x)
+        e = np.linalg.solve(Mc, r1)
+        z1 = x + P @ e
+        z = z1 + D @ (r - M @ z1)
+        F = (M - sp.diags(1.0 / Dd)) @ P
+        r1f = -(F.T @ (D @ r))
+        zf = D @ (2 * r - M @ (D @ r) - F @ np.linalg.solve(Mc, r1f))
+        assert np.linalg.norm(r1f - r1) <= 1e-13 * np.linalg.norm(r1)
+        assert np.linalg.norm(zf - z) <= 1e-13 * np.linalg.norm(z)
+
+
+def test_transfer_rejects_bad_levels(api):
+    p = pencil_2d_q1(22, seed=9)
+    o = api.default_opts(mg_coarse=16)
+    nlev = len(api.mg_describe(p, o)["levels"])
+    with pytest.raises(api.SlrfError):
+        api.mg_transfer(p, nlev - 1, o)
+    with pytest.raises(api.SlrfError):
+        api.mg_transfer(p, -1, o)
