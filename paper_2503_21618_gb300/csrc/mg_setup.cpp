@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -128,6 +130,7 @@ HostCsr transpose(const HostCsr &M) {
 }
 
 // Strong node neighbours: ||A_IJ||_F >= theta * sqrt(||A_II||_F ||A_JJ||_F).
+// Node ranges in parallel; each node's list is formed by one thread, sorted.
 void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, int bs, double theta,
               std::vector<int32_t> &sptr, std::vector<int32_t> &scol) {
     const int nn = n / bs;
@@ -135,28 +138,44 @@ void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, in
     for (int i = 0; i < n; ++i)
         for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k)
             if (col[k] / bs == i / bs) dnorm[i / bs] += a[k] * a[k];
+    const int nt = n_threads(ptr[n]);
+    std::vector<std::vector<int32_t>> len(nt), out(nt);
+    const double th2 = theta * theta;
+    parallel_for_rows(nn, nt, [&](int I0, int I1, int t) {
+        std::vector<int32_t> mark(nn, -1), nb;
+        std::vector<double> acc(nn, 0.0);
+        for (int I = I0; I < I1; ++I) {
+            nb.clear();
+            for (int i = I * bs; i < I * bs + bs; ++i)
+                for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+                    const int J = col[k] / bs;
+                    if (J == I) continue;
+                    if (mark[J] != I) {
+                        mark[J] = I;
+                        acc[J] = 0.0;
+                        nb.push_back(J);
+                    }
+                    acc[J] += a[k] * a[k];
+                }
+            std::sort(nb.begin(), nb.end());
+            int32_t cnt = 0;
+            for (int J : nb)
+                if (acc[J] >= th2 * std::sqrt(dnorm[I] * dnorm[J])) {
+                    out[t].push_back(J);
+                    ++cnt;
+                }
+            len[t].push_back(cnt);
+        }
+    });
     sptr.assign(nn + 1, 0);
     scol.clear();
-    std::vector<int32_t> mark(nn, -1), nb;
-    std::vector<double> acc(nn, 0.0);
-    const double th2 = theta * theta;
-    for (int I = 0; I < nn; ++I) {
-        nb.clear();
-        for (int i = I * bs; i < I * bs + bs; ++i)
-            for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-                const int J = col[k] / bs;
-                if (J == I) continue;
-                if (mark[J] != I) {
-                    mark[J] = I;
-                    acc[J] = 0.0;
-                    nb.push_back(J);
-                }
-                acc[J] += a[k] * a[k];
-            }
-        std::sort(nb.begin(), nb.end());
-        for (int J : nb)
-            if (acc[J] >= th2 * std::sqrt(dnorm[I] * dnorm[J])) scol.push_back(J);
-        sptr[I + 1] = (int32_t)scol.size();
+    int I = 0;
+    for (int t = 0; t < nt; ++t) {
+        for (int32_t l : len[t]) {
+            sptr[I + 1] = sptr[I] + l;
+            ++I;
+        }
+        scol.insert(scol.end(), out[t].begin(), out[t].end());
     }
 }
 
@@ -195,29 +214,88 @@ int aggregate(int nn, const std::vector<int32_t> &sptr, const std::vector<int32_
     return na;
 }
 
+// Reusable barrier for a fixed team of threads.
+class Barrier {
+  public:
+    explicit Barrier(int n) : n_(n), left_(n) {}
+    void wait() {
+        std::unique_lock<std::mutex> lk(m_);
+        const int64_t g = gen_;
+        if (--left_ == 0) {
+            ++gen_;
+            left_ = n_;
+            cv_.notify_all();
+        } else {
+            cv_.wait(lk, [&] { return gen_ != g; });
+        }
+    }
+
+  private:
+    std::mutex m_;
+    std::condition_variable cv_;
+    const int n_;
+    int left_;
+    int64_t gen_ = 0;
+};
+
 // Largest |eigenvalue| of D^{-1} A by power iteration (deterministic start).
+// One team of threads runs all the steps on fixed row chunks; the squared
+// norms are summed per chunk and the chunks added in order by every thread,
+// so the estimate does not depend on the thread count.
 double rho_dinv_a(int n, const int32_t *ptr, const int32_t *col, const double *a, const std::vector<double> &d) {
-    std::vector<double> x(n), y(n);
+    constexpr int NIT = 30, NCH = 64;
+    std::vector<double> buf[2] = {std::vector<double>(n), std::vector<double>(n)};
     uint64_t s = 0x9E3779B97F4A7C15ull;
     for (int i = 0; i < n; ++i) {
         s = s * 6364136223846793005ull + 1442695040888963407ull;
-        x[i] = 0.5 + (double)(s >> 11) * (1.0 / 9007199254740992.0);
+        buf[0][i] = 0.5 + (double)(s >> 11) * (1.0 / 9007199254740992.0);
     }
-    double lam = 0.0;
-    for (int it = 0; it < 30; ++it) {
-        double nx = 0.0, ny = 0.0;
-        for (int i = 0; i < n; ++i) {
-            double t = 0.0;
-            for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) t += a[k] * x[col[k]];
-            y[i] = t / d[i];
-            nx += x[i] * x[i];
-            ny += y[i] * y[i];
+    // step it: y = (D^{-1} A x) * scale with x = buf[it & 1] the previous,
+    // unnormalised iterate and scale = 1 / ||x_prev||; the normalised x has
+    // squared norm sum (scale x_i)^2 over its rows
+    std::vector<double> part[2] = {std::vector<double>(2 * NCH), std::vector<double>(2 * NCH)};
+    auto chunk = [&](int c) { return (int)((int64_t)n * c / NCH); };
+    const int nt = n_threads(ptr[n]);
+    Barrier bar(nt);
+    double lam_out = 0.0;
+    auto team = [&](int c0, int c1, int tid) {
+        double scale = 1.0, lam = 0.0;
+        for (int it = 0; it < NIT; ++it) {
+            const std::vector<double> &x = buf[it & 1];
+            std::vector<double> &y = buf[(it + 1) & 1];
+            std::vector<double> &pp = part[it & 1];
+            for (int c = c0; c < c1; ++c) {
+                double sx = 0.0, sy = 0.0;
+                for (int i = chunk(c); i < chunk(c + 1); ++i) {
+                    double t = 0.0;
+                    for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) t += a[k] * x[col[k]];
+                    const double yi = t / d[i] * scale, xi = x[i] * scale;
+                    y[i] = yi;
+                    sx += xi * xi;
+                    sy += yi * yi;
+                }
+                pp[2 * c] = sx;
+                pp[2 * c + 1] = sy;
+            }
+            bar.wait();
+            double nx = 0.0, ny = 0.0;
+            for (int c = 0; c < NCH; ++c) {
+                nx += pp[2 * c];
+                ny += pp[2 * c + 1];
+            }
+            lam = std::sqrt(ny / nx);
+            scale = 1.0 / std::sqrt(ny);
         }
-        lam = std::sqrt(ny / nx);
-        const double inv = 1.0 / std::sqrt(ny);
-        for (int i = 0; i < n; ++i) x[i] = y[i] * inv;
+        if (tid == 0) lam_out = lam;
+    };
+    if (nt <= 1) {
+        team(0, NCH, 0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) th.emplace_back(team, NCH * t / nt, NCH * (t + 1) / nt, t);
+        for (auto &x : th) x.join();
     }
-    return lam;
+    return lam_out;
 }
 
 // In-place dense Cholesky S = L L^T (lower, row-major); false if not SPD.
@@ -258,22 +336,27 @@ std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector
             Bd[(size_t)i * n + j] = Bd[(size_t)j * n + i] = sb;
         }
     if (!cholesky_lower(n, Bd)) return "multigrid setup: coarse mass matrix is not positive definite";
-    // X = L^{-1} A_c (forward substitution, column by column of A_c)
+    // Y <- L^{-1} Y by forward substitution, one row of Y at a time (the
+    // inner loops run along rows of the row-major arrays)
+    auto forward = [&](std::vector<double> &Y) {
+        for (int i = 0; i < n; ++i) {
+            double *__restrict yi = &Y[(size_t)i * n];
+            for (int k = 0; k < i; ++k) {
+                const double l = Bd[(size_t)i * n + k];
+                const double *__restrict yk = &Y[(size_t)k * n];
+                for (int c = 0; c < n; ++c) yi[c] -= l * yk[c];
+            }
+            const double inv = 1.0 / Bd[(size_t)i * n + i];
+            for (int c = 0; c < n; ++c) yi[c] *= inv;
+        }
+    };
+    // X = L^{-1} A_c, then C = L^{-1} X^T (= L^{-1} A_c L^{-T})
     std::vector<double> X(Ad);
-    for (int c = 0; c < n; ++c)
-        for (int i = 0; i < n; ++i) {
-            double t = X[(size_t)i * n + c];
-            for (int k = 0; k < i; ++k) t -= Bd[(size_t)i * n + k] * X[(size_t)k * n + c];
-            X[(size_t)i * n + c] = t / Bd[(size_t)i * n + i];
-        }
-    // C = L^{-1} X^T  (= L^{-1} A_c L^{-T})
+    forward(X);
     std::vector<double> C((size_t)n * n);
-    for (int c = 0; c < n; ++c)
-        for (int i = 0; i < n; ++i) {
-            double t = X[(size_t)c * n + i];
-            for (int k = 0; k < i; ++k) t -= Bd[(size_t)i * n + k] * C[(size_t)k * n + c];
-            C[(size_t)i * n + c] = t / Bd[(size_t)i * n + i];
-        }
+    for (int i = 0; i < n; ++i)
+        for (int c = 0; c < n; ++c) C[(size_t)i * n + c] = X[(size_t)c * n + i];
+    forward(C);
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < i; ++j) {
             const double s = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
@@ -281,14 +364,18 @@ std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector
         }
     std::vector<double> Q;
     host_syev(n, C, lam, Q);
-    // V = L^{-T} Q (back substitution)
-    V.assign((size_t)n * n, 0.0);
-    for (int c = 0; c < n; ++c)
-        for (int i = n - 1; i >= 0; --i) {
-            double t = Q[(size_t)i * n + c];
-            for (int k = i + 1; k < n; ++k) t -= Bd[(size_t)k * n + i] * V[(size_t)k * n + c];
-            V[(size_t)i * n + c] = t / Bd[(size_t)i * n + i];
+    // V = L^{-T} Q (back substitution, one row of V at a time)
+    V = Q;
+    for (int i = n - 1; i >= 0; --i) {
+        double *__restrict vi = &V[(size_t)i * n];
+        for (int k = i + 1; k < n; ++k) {
+            const double l = Bd[(size_t)k * n + i];
+            const double *__restrict vk = &V[(size_t)k * n];
+            for (int c = 0; c < n; ++c) vi[c] -= l * vk[c];
         }
+        const double inv = 1.0 / Bd[(size_t)i * n + i];
+        for (int c = 0; c < n; ++c) vi[c] *= inv;
+    }
     return "";
 }
 
@@ -324,9 +411,14 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
         for (int i = 0; i < m; ++i) vp += v[i] * p[i];
         const double K = vp / vv;
         for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
-        for (int i = 0; i < m; ++i) {
-            double *row = &S[(size_t)(k + 1 + i) * n + k + 1];
-            for (int j = 0; j < m; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+        {
+            const double *__restrict vp_ = v.data();
+            const double *__restrict qp_ = q.data();
+            for (int i = 0; i < m; ++i) {
+                double *__restrict row = &S[(size_t)(k + 1 + i) * n + k + 1];
+                const double vi = vp_[i], qi = qp_[i];
+                for (int j = 0; j < m; ++j) row[j] -= vi * qp_[j] + qi * vp_[j];
+            }
         }
         S[(size_t)(k + 1) * n + k] = S[(size_t)k * n + k + 1] = alpha;
         for (int i = 1; i < m; ++i) S[(size_t)(k + 1 + i) * n + k] = S[(size_t)k * n + k + 1 + i] = 0.0;
@@ -338,10 +430,16 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
             qv[r] = beta * t;
         }
         for (int r = 0; r < n; ++r) {
-            double *row = &Q[(size_t)r * n + k + 1];
-            for (int j = 0; j < m; ++j) row[j] -= qv[r] * v[j];
+            double *__restrict row = &Q[(size_t)r * n + k + 1];
+            const double *__restrict vp_ = v.data();
+            const double f = qv[r];
+            for (int j = 0; j < m; ++j) row[j] -= f * vp_[j];
         }
     }
+    // the QR phase rotates pairs of eigenvector columns: keep them as rows of Q^T
+    std::vector<double> Qt((size_t)n * n);
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) Qt[(size_t)c * n + r] = Q[(size_t)r * n + c];
     std::vector<double> d(n), e(n > 0 ? n : 1, 0.0);
     for (int i = 0; i < n; ++i) d[i] = S[(size_t)i * n + i];
     for (int i = 0; i + 1 < n; ++i) e[i] = S[(size_t)(i + 1) * n + i];
@@ -384,11 +482,12 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
                 bulge = s * e[k + 1];
                 e[k + 1] = c * e[k + 1];
             }
+            double *__restrict qk = &Qt[(size_t)k * n];
+            double *__restrict qk1 = &Qt[(size_t)(k + 1) * n];
             for (int row = 0; row < n; ++row) {
-                double *qr = &Q[(size_t)row * n];
-                const double zk = qr[k], zk1 = qr[k + 1];
-                qr[k] = c * zk + s * zk1;
-                qr[k + 1] = -s * zk + c * zk1;
+                const double zk = qk[row], zk1 = qk1[row];
+                qk[row] = c * zk + s * zk1;
+                qk1[row] = -s * zk + c * zk1;
             }
         }
     }
@@ -400,7 +499,7 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
     std::vector<double> Qs((size_t)n * n);
     for (int c = 0; c < n; ++c) {
         w[c] = d[idx[c]];
-        for (int r = 0; r < n; ++r) Qs[(size_t)r * n + c] = Q[(size_t)r * n + idx[c]];
+        for (int r = 0; r < n; ++r) Qs[(size_t)r * n + c] = Qt[(size_t)idx[c] * n + r];
     }
     Q.swap(Qs);
 }
@@ -471,21 +570,6 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
                 for (int32_t t = P.ptr[j]; t < P.ptr[j + 1]; ++t) add(P.col[t], ca[k] * P.val[t], cb[k] * P.val[t]);
             }
         }, APr);
-        if (H.lv.size() == 1) {   // finest level: keep (P, A P, B P) on the pattern of A P
-            L.fptr = APr.ptr;
-            L.fcol = APr.col;
-            L.fap = APr.a;
-            L.fbp = APr.b;
-            L.fp.assign(L.fcol.size(), 0.0);
-            for (int i = 0; i < cn; ++i) {
-                int32_t k = L.fptr[i];
-                for (int32_t t = P.ptr[i]; t < P.ptr[i + 1]; ++t) {
-                    while (k < L.fptr[i + 1] && L.fcol[k] < P.col[t]) ++k;
-                    if (k < L.fptr[i + 1] && L.fcol[k] == P.col[t]) L.fp[k] = P.val[t];
-                    else return "multigrid setup: prolongator entry outside the pattern of A P";
-                }
-            }
-        }
         HostLevel next;
         next.n = nc;
         RowsOut Cr;
@@ -497,6 +581,21 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
                 for (int32_t k = APr.ptr[i]; k < APr.ptr[i + 1]; ++k) add(APr.col[k], r * APr.a[k], r * APr.b[k]);
             }
         }, Cr);
+        if (H.lv.size() == 1) {   // finest level: keep (P, A P, B P) on the pattern of A P
+            L.fptr = std::move(APr.ptr);
+            L.fcol = std::move(APr.col);
+            L.fap = std::move(APr.a);
+            L.fbp = std::move(APr.b);
+            L.fp.assign(L.fcol.size(), 0.0);
+            for (int i = 0; i < cn; ++i) {
+                int32_t k = L.fptr[i];
+                for (int32_t t = P.ptr[i]; t < P.ptr[i + 1]; ++t) {
+                    while (k < L.fptr[i + 1] && L.fcol[k] < P.col[t]) ++k;
+                    if (k < L.fptr[i + 1] && L.fcol[k] == P.col[t]) L.fp[k] = P.val[t];
+                    else return "multigrid setup: prolongator entry outside the pattern of A P";
+                }
+            }
+        }
         next.ptr = std::move(Cr.ptr);
         next.col = std::move(Cr.col);
         next.a = std::move(Cr.a);
