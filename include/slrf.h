@@ -112,7 +112,8 @@ typedef struct {
     int32_t eig_refine;     /* small eigensolver: 1 = FP32 Jacobi + FP64 refinement,
                                0 = FP64 Jacobi                                     (1) */
     int64_t mem_budget;     /* workspace byte cap, 0 = none                       (0) */
-    int32_t profile;        /* 1: time each kernel class with CUDA events         (0) */
+    int32_t profile;        /* 1: time kernel classes with CUDA events around
+                               each launch (those selected by profile_mask)      (0) */
     int32_t spmm_rows;      /* rows per group of the shifted SpMM (1..4); 0 = auto:
                                3 for 3-dof node-block patterns, else 2             (0) */
     int32_t gram_ozaki;     /* Grams and tall products (Q1 = U T1, X = Q1 M) of the
@@ -139,7 +140,10 @@ typedef struct {
                                wanted residual (of all Ritz pairs while none is
                                wanted) after which slrf_subspace_iterate stops
                                with SLRF_STAGNATION; 0 = never                  (8) */
-    int32_t reserved[3];
+    uint32_t profile_mask;  /* profile == 1: bit c times kernel class c
+                               (slrf_kernel_class_name), 0 = every class; timing
+                               fewer classes records fewer events               (0) */
+    int32_t reserved[2];
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

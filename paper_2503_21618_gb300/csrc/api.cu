@@ -92,7 +92,8 @@ void Ctx::before(int kc, double b, double f) {
     launches[kc] += 1;
     bytes[kc] += b;
     flops[kc] += f;
-    if (profile) {
+    rec = profile && ((profile_mask >> kc) & 1u);
+    if (rec) {
         if (used == pool.size()) {
             EvPair p;
             cudaEventCreate(&p.a);
@@ -106,10 +107,11 @@ void Ctx::before(int kc, double b, double f) {
     }
 }
 void Ctx::after() {
-    if (profile) {
+    if (rec) {
         cudaEventRecord(pool[used].b, stream);
         ++used;
     }
+    rec = false;
 }
 void Ctx::harvest(double ms_out[SLRF_NKERNEL_CLASSES]) {
     if (!profile || used == 0) return;
@@ -1526,6 +1528,7 @@ slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
     CKS(check_opts(o));
     h->opts = *o;
     h->ctx.profile = o->profile != 0;
+    h->ctx.profile_mask = o->profile_mask ? o->profile_mask : ~0u;
     return SLRF_OK;
 }
 
@@ -1594,6 +1597,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     h->node_blocks = blocks;
     h->ctx.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     h->ctx.profile = o->profile != 0;
+    h->ctx.profile_mask = o->profile_mask ? o->profile_mask : ~0u;
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->ctx.sm_count, cudaDevAttrMultiProcessorCount, h->device);
     h->A.n = (int)n;

@@ -16,6 +16,8 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 152;
     bool profile = false;
+    uint32_t profile_mask = ~0u;  // classes timed when profile is set
+    bool rec = false;             // the current launch is being timed
     int64_t launches[SLRF_NKERNEL_CLASSES] = {};
     double bytes[SLRF_NKERNEL_CLASSES] = {};
     double flops[SLRF_NKERNEL_CLASSES] = {};

@@ -317,3 +317,22 @@ def test_precond_apply_single_level_and_jacobi(api):
                 ref = r
             assert np.linalg.norm(Z[:, 2 * j] - ref) <= 1e-12 * np.linalg.norm(ref)
             assert abs(mu[2 * j] - r @ ref) <= 1e-12 * np.linalg.norm(r) * np.linalg.norm(ref)
+
+
+def test_profile_mask_times_only_the_selected_classes(api):
+    p = pencil_2d_q1(40, seed=5)
+    _, _, s, w = _filter_case(p, 20)
+    V = torch.from_numpy(start_block(p.n, 12, 2)).cuda()
+    names = [api.class_name(i) for i in range(api.NKERNEL_CLASSES)]
+    sel = {"mg_fine", "shifted_spmm"}
+    mask = sum(1 << i for i, nm in enumerate(names) if nm in sel)
+    h = api.Handle(p, api.default_opts(profile=1, profile_mask=mask))
+    _, st, rep = h.filter_apply(api.Filter(s, w), V)
+    assert st == api.OK
+    k = rep.as_dict()["kernels"]
+    assert all(v["ms"] > 0 for nm, v in k.items() if nm in sel)
+    assert all(v["ms"] == 0 for nm, v in k.items() if nm not in sel)
+    assert {"krylov_update", "mg_coarse"} <= set(k)           # launches are counted either way
+    h.set_opts(profile_mask=0)                                # 0: every class
+    _, _, rep = h.filter_apply(api.Filter(s, w), V)
+    assert all(v["ms"] > 0 for v in rep.as_dict()["kernels"].values())
