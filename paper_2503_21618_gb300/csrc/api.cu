@@ -455,62 +455,13 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
     const int nc = H.lv.back().n;
     const size_t v32 = take((size_t)nc * nc * 4), v64 = take((size_t)nc * nc * 8);
     // fused finest-level transfers: F by fine row groups ("up") and by coarse rows ("down")
-    const HostLevel &H0 = H.lv[0];
-    const int R0 = h->A.rg_rows > 1 ? h->A.rg_rows : 1;
-    const int64_t n0 = H0.n, ng0 = (n0 + R0 - 1) / R0;
-    std::vector<int32_t> fu_ptr, fu_col, fd_ptr, fd_col;
-    std::vector<double2> fq;   // per stored pair: (A P, B P), (a_ii P, b_ii P)
-    if (nlev > 1) {
-        const int n1 = H.lv[1].n;
-        auto slot = [&](int64_t i, int32_t k, bool hit) {
-            if (!hit) {
-                fq.push_back(make_double2(0.0, 0.0));
-                fq.push_back(make_double2(0.0, 0.0));
-                return;
-            }
-            fq.push_back(make_double2(H0.fap[k], H0.fbp[k]));
-            fq.push_back(make_double2(H0.fp[k] * H0.diag_a[i], H0.fp[k] * H0.diag_b[i]));
-        };
-        fu_ptr.assign(ng0 + 1, 0);
-        std::vector<int32_t> u;
-        for (int64_t g = 0; g < ng0; ++g) {
-            const int64_t r0 = g * R0, r1 = std::min<int64_t>(n0, r0 + R0);
-            u.clear();
-            for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), H0.fcol.begin() + H0.fptr[r], H0.fcol.begin() + H0.fptr[r + 1]);
-            std::sort(u.begin(), u.end());
-            u.erase(std::unique(u.begin(), u.end()), u.end());
-            for (int32_t c : u) {
-                fu_col.push_back(c);
-                for (int r = 0; r < R0; ++r) {
-                    const int64_t row = r0 + r;
-                    if (row >= n0) {
-                        slot(0, 0, false);
-                        continue;
-                    }
-                    const auto b = H0.fcol.begin() + H0.fptr[row], e = H0.fcol.begin() + H0.fptr[row + 1];
-                    const auto it = std::lower_bound(b, e, c);
-                    slot(row, (int32_t)(it - H0.fcol.begin()), it != e && *it == c);
-                }
-            }
-            fu_ptr[g + 1] = (int32_t)fu_col.size();
-        }
-        // F^T: coarse row c lists the fine rows i with an entry (i, c), ascending
-        fd_ptr.assign(n1 + 1, 0);
-        for (int32_t c : H0.fcol) fd_ptr[c + 1]++;
-        for (int c = 0; c < n1; ++c) fd_ptr[c + 1] += fd_ptr[c];
-        fd_col.resize(H0.fcol.size());
-        std::vector<int32_t> fill(fd_ptr.begin(), fd_ptr.end() - 1), src(H0.fcol.size());
-        for (int64_t i = 0; i < n0; ++i)
-            for (int32_t k = H0.fptr[i]; k < H0.fptr[i + 1]; ++k) {
-                const int32_t dst = fill[H0.fcol[k]]++;
-                fd_col[dst] = (int32_t)i;
-                src[dst] = k;
-            }
-        for (size_t e = 0; e < fd_col.size(); ++e) slot(fd_col[e], src[e], true);
-    }
-    const size_t nslot = fq.size() / 2;
+    FusedLayout FL;
+    if (nlev > 1) mg_fused_layout(H.lv[0], H.lv[1].n, h->A.rg_rows > 1 ? h->A.rg_rows : 1, FL);
+    const std::vector<int32_t> &fu_ptr = FL.up_ptr, &fu_col = FL.up_col, &fd_ptr = FL.down_ptr,
+                               &fd_col = FL.down_col;
+    const size_t nslot = FL.q.size() / 4;   // 4 doubles = two double2 per stored pair
     const size_t o_fup = take(fu_ptr.size() * 4), o_fuc = take(fu_col.size() * 4), o_fdp = take(fd_ptr.size() * 4),
-                 o_fdc = take(fd_col.size() * 4), o_fq = take(fq.size() * sizeof(double2)),
+                 o_fdc = take(fd_col.size() * 4), o_fq = take(FL.q.size() * sizeof(double)),
                  o_fab32 = take(nslot * sizeof(float2)), o_fab64 = take(nslot * sizeof(double2));
     std::vector<char> stage(off);
     auto put = [&](size_t o, const void *src, size_t bytes) {
@@ -556,7 +507,7 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
     put(o_fuc, fu_col.data(), fu_col.size() * 4);
     put(o_fdp, fd_ptr.data(), fd_ptr.size() * 4);
     put(o_fdc, fd_col.data(), fd_col.size() * 4);
-    put(o_fq, fq.data(), fq.size() * sizeof(double2));
+    put(o_fq, FL.q.data(), FL.q.size() * sizeof(double));
     CKS(ensure(h, h->mgStatic, off));
     char *base = reinterpret_cast<char *>(h->mgStatic.p);
     CK(cudaMemcpyAsync(base, stage.data(), off, cudaMemcpyHostToDevice, h->ctx.stream));

@@ -59,6 +59,21 @@ struct HostHierarchy {
     double ms_setup = 0.0;
 };
 
+// The finest level's pair matrix F = (M - D^{-1}) P in the two layouts of the
+// fused restriction (coarse rows of F^T: "down") and prolongation (groups of R
+// fine rows with the union of their coarse columns, R pairs per entry: "up"),
+// unfolded: per stored pair q holds (A P, B P, a_ii P, b_ii P), and for a
+// damping D = (omega / rho_0) / (a_ii - sigma b_ii),
+// F = (q0 - kappa q2) - sigma (q1 - kappa q3), kappa = rho_0 / omega.
+struct FusedLayout {
+    int R = 1;
+    std::vector<int32_t> up_ptr, up_col;       // ceil(n / R) + 1 groups; coarse columns
+    std::vector<int32_t> down_ptr, down_col;   // n_c + 1 coarse rows; fine columns
+    std::vector<double> q;                     // 4 per stored pair: up pairs (R per entry), then down
+};
+// From level 0 of a hierarchy with at least two levels (L0.fptr non-empty).
+void mg_fused_layout(const HostLevel &L0, int n_coarse, int R, FusedLayout &out);
+
 // Build the hierarchy of the n x n pencil given in CSR with shared pattern
 // (a = A values, b = B values).  Returns an empty string on success, else a
 // description of the failure (non-positive diagonal, coarse mass matrix not

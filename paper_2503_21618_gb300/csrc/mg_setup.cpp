@@ -504,6 +504,59 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
     Q.swap(Qs);
 }
 
+void mg_fused_layout(const HostLevel &L0, int n_coarse, int R, FusedLayout &out) {
+    out = FusedLayout();
+    out.R = R;
+    const int64_t n0 = L0.n, ng = (n0 + R - 1) / R;
+    auto slot = [&](int64_t i, int32_t k, bool hit) {
+        if (!hit) {
+            out.q.insert(out.q.end(), 4, 0.0);
+            return;
+        }
+        out.q.push_back(L0.fap[k]);
+        out.q.push_back(L0.fbp[k]);
+        out.q.push_back(L0.fp[k] * L0.diag_a[i]);
+        out.q.push_back(L0.fp[k] * L0.diag_b[i]);
+    };
+    // up: groups of R fine rows, sorted union of their coarse columns
+    out.up_ptr.assign(ng + 1, 0);
+    std::vector<int32_t> u;
+    for (int64_t g = 0; g < ng; ++g) {
+        const int64_t r0 = g * R, r1 = std::min<int64_t>(n0, r0 + R);
+        u.clear();
+        for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), L0.fcol.begin() + L0.fptr[r], L0.fcol.begin() + L0.fptr[r + 1]);
+        std::sort(u.begin(), u.end());
+        u.erase(std::unique(u.begin(), u.end()), u.end());
+        for (int32_t c : u) {
+            out.up_col.push_back(c);
+            for (int r = 0; r < R; ++r) {
+                const int64_t row = r0 + r;
+                if (row >= n0) {
+                    slot(0, 0, false);
+                    continue;
+                }
+                const auto b = L0.fcol.begin() + L0.fptr[row], e = L0.fcol.begin() + L0.fptr[row + 1];
+                const auto it = std::lower_bound(b, e, c);
+                slot(row, (int32_t)(it - L0.fcol.begin()), it != e && *it == c);
+            }
+        }
+        out.up_ptr[g + 1] = (int32_t)out.up_col.size();
+    }
+    // down: F^T, coarse row c lists the fine rows i with an entry (i, c), ascending
+    out.down_ptr.assign(n_coarse + 1, 0);
+    for (int32_t c : L0.fcol) out.down_ptr[c + 1]++;
+    for (int c = 0; c < n_coarse; ++c) out.down_ptr[c + 1] += out.down_ptr[c];
+    out.down_col.resize(L0.fcol.size());
+    std::vector<int32_t> fill(out.down_ptr.begin(), out.down_ptr.end() - 1), src(L0.fcol.size());
+    for (int64_t i = 0; i < n0; ++i)
+        for (int32_t k = L0.fptr[i]; k < L0.fptr[i + 1]; ++k) {
+            const int32_t d = fill[L0.fcol[k]]++;
+            out.down_col[d] = (int32_t)i;
+            src[d] = k;
+        }
+    for (size_t e = 0; e < out.down_col.size(); ++e) slot(out.down_col[e], src[e], true);
+}
+
 std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double *a, const double *b,
                      const MgParams &prm, HostHierarchy &H) {
     const auto t0 = std::chrono::steady_clock::now();
