@@ -316,6 +316,10 @@ bool cholesky_lower(int n, std::vector<double> &S) {
     return true;
 }
 
+// Threads for the O(n^3) steps of an n x n dense problem (one below n = 320,
+// where the per-step barriers of the reduction would cost more than they save).
+int dense_threads(int n) { return n >= 320 ? n_threads((int64_t)n * n * n) : 1; }
+
 }  // namespace
 
 // V^T A_l V = diag(lam), V^T B_l V = I.
@@ -337,18 +341,22 @@ std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector
         }
     if (!cholesky_lower(n, Bd)) return "multigrid setup: coarse mass matrix is not positive definite";
     // Y <- L^{-1} Y by forward substitution, one row of Y at a time (the
-    // inner loops run along rows of the row-major arrays)
+    // inner loops run along rows of the row-major arrays); the columns of Y
+    // are independent, so threads take column ranges
+    const int nt = dense_threads(n);
     auto forward = [&](std::vector<double> &Y) {
-        for (int i = 0; i < n; ++i) {
-            double *__restrict yi = &Y[(size_t)i * n];
-            for (int k = 0; k < i; ++k) {
-                const double l = Bd[(size_t)i * n + k];
-                const double *__restrict yk = &Y[(size_t)k * n];
-                for (int c = 0; c < n; ++c) yi[c] -= l * yk[c];
+        parallel_for_rows(n, nt, [&](int c0, int c1, int) {
+            for (int i = 0; i < n; ++i) {
+                double *__restrict yi = &Y[(size_t)i * n];
+                for (int k = 0; k < i; ++k) {
+                    const double l = Bd[(size_t)i * n + k];
+                    const double *__restrict yk = &Y[(size_t)k * n];
+                    for (int c = c0; c < c1; ++c) yi[c] -= l * yk[c];
+                }
+                const double inv = 1.0 / Bd[(size_t)i * n + i];
+                for (int c = c0; c < c1; ++c) yi[c] *= inv;
             }
-            const double inv = 1.0 / Bd[(size_t)i * n + i];
-            for (int c = 0; c < n; ++c) yi[c] *= inv;
-        }
+        });
     };
     // X = L^{-1} A_c, then C = L^{-1} X^T (= L^{-1} A_c L^{-T})
     std::vector<double> X(Ad);
@@ -364,78 +372,110 @@ std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector
         }
     std::vector<double> Q;
     host_syev(n, C, lam, Q);
-    // V = L^{-T} Q (back substitution, one row of V at a time)
+    // V = L^{-T} Q (back substitution, one row of V at a time, column ranges
+    // in parallel)
     V = Q;
-    for (int i = n - 1; i >= 0; --i) {
-        double *__restrict vi = &V[(size_t)i * n];
-        for (int k = i + 1; k < n; ++k) {
-            const double l = Bd[(size_t)k * n + i];
-            const double *__restrict vk = &V[(size_t)k * n];
-            for (int c = 0; c < n; ++c) vi[c] -= l * vk[c];
+    parallel_for_rows(n, nt, [&](int c0, int c1, int) {
+        for (int i = n - 1; i >= 0; --i) {
+            double *__restrict vi = &V[(size_t)i * n];
+            for (int k = i + 1; k < n; ++k) {
+                const double l = Bd[(size_t)k * n + i];
+                const double *__restrict vk = &V[(size_t)k * n];
+                for (int c = c0; c < c1; ++c) vi[c] -= l * vk[c];
+            }
+            const double inv = 1.0 / Bd[(size_t)i * n + i];
+            for (int c = c0; c < c1; ++c) vi[c] *= inv;
         }
-        const double inv = 1.0 / Bd[(size_t)i * n + i];
-        for (int c = 0; c < n; ++c) vi[c] *= inv;
-    }
+    });
     return "";
 }
 
 void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vector<double> &Q) {
     Q.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
-    std::vector<double> v(n), p(n), q(n), qv(n);
+    std::vector<double> v(n), p(n), q(n);
     // Householder reduction to tridiagonal form: S <- H S H on the trailing
-    // block, Q <- Q H, for each column k.
-    for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;   // length of the sub-column
-        double xn = 0.0;
-        for (int i = 0; i < m; ++i) {
-            v[i] = S[(size_t)(k + 1 + i) * n + k];
-            xn += v[i] * v[i];
-        }
-        xn = std::sqrt(xn);
-        if (xn == 0.0) continue;
-        const double alpha = v[0] > 0 ? -xn : xn;
-        v[0] -= alpha;
-        double vv = 0.0;
-        for (int i = 0; i < m; ++i) vv += v[i] * v[i];
-        if (!(vv > 0.0)) continue;
-        const double beta = 2.0 / vv;
-        // p = beta * S22 v
-        for (int i = 0; i < m; ++i) {
-            double t = 0.0;
-            const double *row = &S[(size_t)(k + 1 + i) * n + k + 1];
-            for (int j = 0; j < m; ++j) t += row[j] * v[j];
-            p[i] = beta * t;
-        }
-        double vp = 0.0;
-        for (int i = 0; i < m; ++i) vp += v[i] * p[i];
-        const double K = vp / vv;
-        for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
-        {
-            const double *__restrict vp_ = v.data();
-            const double *__restrict qp_ = q.data();
-            for (int i = 0; i < m; ++i) {
-                double *__restrict row = &S[(size_t)(k + 1 + i) * n + k + 1];
-                const double vi = vp_[i], qi = qp_[i];
-                for (int j = 0; j < m; ++j) row[j] -= vi * qp_[j] + qi * vp_[j];
+    // block, Q <- Q H, for each column k.  One team of threads: thread 0 forms
+    // the reflector, all threads update row ranges between barriers; every
+    // entry is computed by one thread in the same order whatever the team size.
+    struct Refl {
+        bool skip = true;
+        double alpha = 0.0, beta = 0.0, vv = 0.0;
+    } rf[2];
+    const int nt = dense_threads(n);
+    Barrier bar(nt);
+    auto range = [&](int m, int t, int &r0, int &r1) {
+        r0 = (int)((int64_t)m * t / nt);
+        r1 = (int)((int64_t)m * (t + 1) / nt);
+    };
+    auto reduce = [&](int, int, int tid) {
+        for (int k = 0; k + 2 < n; ++k) {
+            const int m = n - k - 1;   // length of the sub-column
+            Refl &R = rf[k & 1];
+            if (tid == 0) {
+                double xn = 0.0;
+                for (int i = 0; i < m; ++i) {
+                    v[i] = S[(size_t)(k + 1 + i) * n + k];
+                    xn += v[i] * v[i];
+                }
+                xn = std::sqrt(xn);
+                R.skip = xn == 0.0;
+                if (!R.skip) {
+                    R.alpha = v[0] > 0 ? -xn : xn;
+                    v[0] -= R.alpha;
+                    R.vv = 0.0;
+                    for (int i = 0; i < m; ++i) R.vv += v[i] * v[i];
+                    R.skip = !(R.vv > 0.0);
+                    R.beta = R.skip ? 0.0 : 2.0 / R.vv;
+                }
             }
+            bar.wait();
+            if (R.skip) continue;
+            int r0, r1;
+            range(m, tid, r0, r1);
+            // p = beta * S22 v
+            for (int i = r0; i < r1; ++i) {
+                double t = 0.0;
+                const double *row = &S[(size_t)(k + 1 + i) * n + k + 1];
+                for (int j = 0; j < m; ++j) t += row[j] * v[j];
+                p[i] = R.beta * t;
+            }
+            bar.wait();
+            if (tid == 0) {
+                double vp = 0.0;
+                for (int i = 0; i < m; ++i) vp += v[i] * p[i];
+                const double K = vp / R.vv;
+                for (int i = 0; i < m; ++i) q[i] = p[i] - K * v[i];
+            }
+            bar.wait();
+            {
+                const double *__restrict vp_ = v.data();
+                const double *__restrict qp_ = q.data();
+                for (int i = r0; i < r1; ++i) {
+                    double *__restrict row = &S[(size_t)(k + 1 + i) * n + k + 1];
+                    const double vi = vp_[i], qi = qp_[i];
+                    for (int j = 0; j < m; ++j) row[j] -= vi * qp_[j] + qi * vp_[j];
+                }
+            }
+            // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T
+            int q0, q1;
+            range(n, tid, q0, q1);
+            for (int r = q0; r < q1; ++r) {
+                double t = 0.0;
+                double *__restrict row = &Q[(size_t)r * n + k + 1];
+                const double *__restrict vp_ = v.data();
+                for (int j = 0; j < m; ++j) t += row[j] * vp_[j];
+                const double f = R.beta * t;
+                for (int j = 0; j < m; ++j) row[j] -= f * vp_[j];
+            }
+            if (tid == 0) {
+                S[(size_t)(k + 1) * n + k] = S[(size_t)k * n + k + 1] = R.alpha;
+                for (int i = 1; i < m; ++i) S[(size_t)(k + 1 + i) * n + k] = S[(size_t)k * n + k + 1 + i] = 0.0;
+            }
+            bar.wait();
         }
-        S[(size_t)(k + 1) * n + k] = S[(size_t)k * n + k + 1] = alpha;
-        for (int i = 1; i < m; ++i) S[(size_t)(k + 1 + i) * n + k] = S[(size_t)k * n + k + 1 + i] = 0.0;
-        // Q[:, k+1:] -= beta (Q[:, k+1:] v) v^T
-        for (int r = 0; r < n; ++r) {
-            double t = 0.0;
-            const double *row = &Q[(size_t)r * n + k + 1];
-            for (int j = 0; j < m; ++j) t += row[j] * v[j];
-            qv[r] = beta * t;
-        }
-        for (int r = 0; r < n; ++r) {
-            double *__restrict row = &Q[(size_t)r * n + k + 1];
-            const double *__restrict vp_ = v.data();
-            const double f = qv[r];
-            for (int j = 0; j < m; ++j) row[j] -= f * vp_[j];
-        }
-    }
+    };
+    parallel_for_rows(nt, nt, [&](int t0, int, int) { reduce(0, 0, t0); });
     // the QR phase rotates pairs of eigenvector columns: keep them as rows of Q^T
     std::vector<double> Qt((size_t)n * n);
     for (int r = 0; r < n; ++r)
@@ -445,7 +485,10 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
     for (int i = 0; i + 1 < n; ++i) e[i] = S[(size_t)(i + 1) * n + i];
     // Implicit symmetric QR steps with Wilkinson shifts on the unreduced
     // trailing block; each Givens rotation R on (k, k+1) maps T -> R T R^T
-    // and Q -> Q R^T.
+    // and Q -> Q R^T.  The rotations are recorded and applied to Q^T at the
+    // end, each thread to its own range of components (in the same order).
+    std::vector<int32_t> rot_k;
+    std::vector<double> rot_c, rot_s;
     const double eps = 2.220446049250313e-16;
     int hi = n - 1;
     int64_t guard = 0;
@@ -482,15 +525,23 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
                 bulge = s * e[k + 1];
                 e[k + 1] = c * e[k + 1];
             }
-            double *__restrict qk = &Qt[(size_t)k * n];
-            double *__restrict qk1 = &Qt[(size_t)(k + 1) * n];
-            for (int row = 0; row < n; ++row) {
+            rot_k.push_back(k);
+            rot_c.push_back(c);
+            rot_s.push_back(s);
+        }
+    }
+    parallel_for_rows(n, dense_threads(n), [&](int c0, int c1, int) {
+        for (size_t t = 0; t < rot_k.size(); ++t) {
+            const double c = rot_c[t], s = rot_s[t];
+            double *__restrict qk = &Qt[(size_t)rot_k[t] * n];
+            double *__restrict qk1 = qk + n;
+            for (int row = c0; row < c1; ++row) {
                 const double zk = qk[row], zk1 = qk1[row];
                 qk[row] = c * zk + s * zk1;
                 qk1[row] = -s * zk + c * zk1;
             }
         }
-    }
+    });
     // ascending order
     std::vector<int> idx(n);
     std::iota(idx.begin(), idx.end(), 0);

@@ -1,8 +1,9 @@
-// Test harness (host only): builds the multigrid hierarchy of a pencil read
-// from raw files and writes the finest level's fused-transfer layouts
-// (mg_fused_layout) as raw files, for the CPU test that compares them with
-// scipy products of the exported prolongator.
-//   mg_layout_dump <dir> <block> <R>
+// Test harness (host only) for the multigrid setup code, which it links
+// directly: reads a pencil from raw files, builds the hierarchy and writes
+//   mg_host_dump <dir> layout <block> <R>: the finest level's fused-transfer
+//       layouts (mg_fused_layout);
+//   mg_host_dump <dir> eig <block> <level>: that level's dense pencil and its
+//       eigendecomposition by mg_level_eig (V^T A V = diag(lam), V^T B V = I).
 // <dir>/hdr.bin: int64 n, nnz; rp.bin, ci.bin (int32); a.bin, b.bin (float64).
 #include <cstdio>
 #include <string>
@@ -29,8 +30,8 @@ template <class T> static bool wr(const std::string &f, const std::vector<T> &v)
 }
 
 int main(int argc, char **argv) {
-    if (argc != 4) return 2;
-    const std::string dir = argv[1];
+    if (argc != 5) return 2;
+    const std::string dir = argv[1], mode = argv[2];
     std::vector<long long> hdr;
     if (!rd(dir + "/hdr.bin", hdr, 2)) return 3;
     const int n = (int)hdr[0];
@@ -41,15 +42,33 @@ int main(int argc, char **argv) {
         !rd(dir + "/b.bin", b, nnz))
         return 3;
     MgParams prm;
-    prm.block = std::stoi(argv[2]);
+    prm.block = std::stoi(argv[3]);
     HostHierarchy H;
     const std::string err = mg_build(n, rp.data(), ci.data(), a.data(), b.data(), prm, H);
     if (!err.empty() || H.lv.size() < 2) {
         fprintf(stderr, "%s\n", err.c_str());
         return 4;
     }
+    if (mode == "eig") {
+        const size_t l = (size_t)std::stoi(argv[4]);
+        if (l < 1 || l >= H.lv.size()) return 2;
+        const HostLevel &Lv = H.lv[l];
+        const size_t m = (size_t)Lv.n;
+        std::vector<double> Ad(m * m, 0.0), Bd(m * m, 0.0), V, lam;
+        for (size_t i = 0; i < m; ++i)
+            for (int32_t k = Lv.ptr[i]; k < Lv.ptr[i + 1]; ++k) {
+                Ad[i * m + Lv.col[k]] = Lv.a[k];
+                Bd[i * m + Lv.col[k]] = Lv.b[k];
+            }
+        const std::string e2 = mg_level_eig(Lv, V, lam);
+        if (!e2.empty()) return 4;
+        return wr(dir + "/Ad.bin", Ad) && wr(dir + "/Bd.bin", Bd) && wr(dir + "/V.bin", V) && wr(dir + "/lam.bin", lam)
+                   ? 0
+                   : 5;
+    }
+    if (mode != "layout") return 2;
     FusedLayout L;
-    mg_fused_layout(H.lv[0], H.lv[1].n, std::stoi(argv[3]), L);
+    mg_fused_layout(H.lv[0], H.lv[1].n, std::stoi(argv[4]), L);
     const std::vector<long long> out_hdr = {H.lv[1].n, (long long)L.up_col.size(), (long long)L.down_col.size()};
     return wr(dir + "/out_hdr.bin", out_hdr) && wr(dir + "/up_ptr.bin", L.up_ptr) && wr(dir + "/up_col.bin", L.up_col) &&
                    wr(dir + "/down_ptr.bin", L.down_ptr) && wr(dir + "/down_col.bin", L.down_col) &&

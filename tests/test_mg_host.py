@@ -1,15 +1,21 @@
-"""CPU check of the host logic that lays out the finest multigrid level's
-fused transfers (mg_fused_layout, host C++ compiled here with g++): the
-"up" layout (groups of R fine rows, union of their coarse columns, R pairs
-per entry) and the "down" layout (coarse rows of F^T) must both hold exactly
-the products A P, B P, diag(a) P, diag(b) P of the library's prolongator P
-(exported by slrf_mg_transfer, multiplied here by scipy)."""
+"""CPU checks of host multigrid setup code that has no entry point of its
+own, compiled here with g++ into a small harness (tests/mg_host_dump.cpp):
+
+* the layouts of the finest level's fused transfers (mg_fused_layout): the
+  "up" layout (groups of R fine rows, union of their coarse columns, R pairs
+  per entry) and the "down" layout (coarse rows of F^T) must both hold
+  exactly the products A P, B P, diag(a) P, diag(b) P of the library's
+  prolongator P (exported by slrf_mg_transfer, multiplied here by scipy);
+* the eigendecomposition of a level pencil (mg_level_eig), whose
+  eigenvectors the coarsest solve applies: V^T A V = diag(lambda),
+  V^T B V = I, lambda ascending and equal to LAPACK's."""
 import os
 import shutil
 import subprocess
 
 import numpy as np
 import pytest
+import scipy.linalg as sla
 import scipy.sparse as sp
 
 from workloads import pencil_1d, pencil_2d_q1, pencil_3d_elasticity
@@ -29,19 +35,23 @@ def dump_tool(tmp_path_factory):
     gxx = shutil.which(os.environ.get("CXX", "g++"))
     if gxx is None:
         pytest.skip("no C++ compiler")
-    exe = str(tmp_path_factory.mktemp("mgl") / "mg_layout_dump")
-    subprocess.run([gxx, "-O1", "-std=c++17", "-I" + CSRC, os.path.join(ROOT, "tests", "mg_layout_dump.cpp"),
+    exe = str(tmp_path_factory.mktemp("mgh") / "mg_host_dump")
+    subprocess.run([gxx, "-O2", "-std=c++17", "-I" + CSRC, os.path.join(ROOT, "tests", "mg_host_dump.cpp"),
                     os.path.join(CSRC, "mg_setup.cpp"), "-lpthread", "-o", exe], check=True)
     return exe
 
 
-def _dump(exe, p, block, R, d):
+def _write_pencil(p, d):
     np.asarray([p.n, len(p.col_idx)], np.int64).tofile(os.path.join(d, "hdr.bin"))
     np.asarray(p.row_ptr, np.int32).tofile(os.path.join(d, "rp.bin"))
     np.asarray(p.col_idx, np.int32).tofile(os.path.join(d, "ci.bin"))
     np.asarray(p.a_val, np.float64).tofile(os.path.join(d, "a.bin"))
     np.asarray(p.b_val, np.float64).tofile(os.path.join(d, "b.bin"))
-    subprocess.run([exe, d, str(block), str(R)], check=True)
+
+
+def _dump(exe, p, block, R, d):
+    _write_pencil(p, d)
+    subprocess.run([exe, d, "layout", str(block), str(R)], check=True)
     rd = lambda name, dt: np.fromfile(os.path.join(d, name), dtype=dt)  # noqa: E731
     n1, nu, nd = rd("out_hdr.bin", np.int64)
     return (int(n1), rd("up_ptr.bin", np.int32), rd("up_col.bin", np.int32), rd("down_ptr.bin", np.int32),
@@ -94,3 +104,25 @@ def test_fused_layouts_hold_the_products_of_p(api, dump_tool, tmp_path, case):
                 got[t][down_col[e], c] = qd[e, t]
     for t in range(4):
         np.testing.assert_allclose(got[t], want[t], rtol=0, atol=1e-13 * scale[t])
+
+
+@pytest.mark.parametrize("case", ["226", "725"])
+def test_level_eigendecomposition(dump_tool, tmp_path, case):
+    # 226: the coarsest level of a 2D hierarchy (one thread); 725: the level
+    # a deep shift solves exactly (the threaded path)
+    if case == "226":
+        p, level = pencil_2d_q1(120, seed=7), 2
+    else:
+        p, level = pencil_2d_q1(80, seed=7), 1
+    d = str(tmp_path)
+    _write_pencil(p, d)
+    subprocess.run([dump_tool, d, "eig", "1", str(level)], check=True)
+    lam = np.fromfile(os.path.join(d, "lam.bin"))
+    m = lam.size
+    A = np.fromfile(os.path.join(d, "Ad.bin")).reshape(m, m)
+    B = np.fromfile(os.path.join(d, "Bd.bin")).reshape(m, m)
+    V = np.fromfile(os.path.join(d, "V.bin")).reshape(m, m)
+    assert np.all(np.diff(lam) >= 0)
+    np.testing.assert_allclose(lam, sla.eigh(A, B, eigvals_only=True), rtol=1e-10)
+    np.testing.assert_allclose(V.T @ A @ V, np.diag(lam), rtol=0, atol=1e-13 * np.abs(lam).max())
+    np.testing.assert_allclose(V.T @ B @ V, np.eye(m), rtol=0, atol=1e-13)

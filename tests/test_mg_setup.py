@@ -42,6 +42,17 @@ def test_coarse_eigensolver_matches_lapack(api, name):
     np.testing.assert_allclose(lam, ref, rtol=1e-10)
 
 
+def test_large_coarse_level_eigensolver_matches_lapack(api):
+    # a 725-unknown coarsest level: the size at which the solve of a deep
+    # shift stops the cycle; the eigensolver runs on several threads there
+    p = pencil_2d_q1(80, seed=7)
+    o = api.default_opts(mg_coarse=800)
+    d = api.mg_describe(p, o, coarse=True)
+    assert d["levels"] == [6241, 725]
+    ref = sla.eigh(d["coarse_A"], d["coarse_B"], eigvals_only=True)
+    np.testing.assert_allclose(d["coarse_lambda"], ref, rtol=1e-10)
+
+
 def test_coarse_ritz_values_bound_the_1d_spectrum(api):
     n = 2000
     d = api.mg_describe(pencil_1d(n), coarse=True)
