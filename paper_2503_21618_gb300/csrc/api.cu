@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <complex>
+#include <future>
 #include <mutex>
 #include <type_traits>
 #include <string>
@@ -1538,6 +1539,30 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
     // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
     const bool blocks = has_node_blocks(n, rp, ci, 3);
+    // The multigrid hierarchy (host) is built on its own thread while the row
+    // groups are formed and the pencil is uploaded; the guard waits for it on
+    // every return, before the host copies it reads go out of scope.
+    const slrf_opts opts_copy = *o;
+    const bool want_mg = o->precond == SLRF_PRECOND_MG || (o->precond == SLRF_PRECOND_AUTO && !blocks);
+    const int mg_blk = want_mg ? mg_block_for(opts_copy, n, rp, ci) : 0;
+    std::future<std::pair<std::string, HostHierarchy>> mg_fut;
+    struct Join {
+        std::future<std::pair<std::string, HostHierarchy>> &f;
+        ~Join() {
+            if (f.valid()) f.wait();
+        }
+    } mg_join{mg_fut};
+    auto build_mg = [&rp, &ci, &av, &bv, &opts_copy, n, mg_blk] {
+        std::pair<std::string, HostHierarchy> r;
+        r.first = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(opts_copy, mg_blk), r.second);
+        return r;
+    };
+    if (want_mg) {
+        try {
+            mg_fut = std::async(std::launch::async, build_mg);
+        } catch (...) {   // no thread: built synchronously below
+        }
+    }
     int R = o->spmm_rows;
     if (R == 0) R = blocks ? 3 : 2;
     std::vector<int32_t> gptr, ucol;
@@ -1614,8 +1639,18 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         slrf_destroy(h);
         return SLRF_ECUDA;
     }
-    if (uses_mg(h)) {
-        const slrf_status st = mg_build_upload(h, rp, ci, av, bv);
+    if (want_mg) {
+        std::pair<std::string, HostHierarchy> built;
+        try {
+            built = mg_fut.valid() ? mg_fut.get() : build_mg();
+        } catch (const std::exception &ex) {
+            built.first = std::string("multigrid setup: ") + ex.what();
+        }
+        slrf_status st = SLRF_BREAKDOWN;
+        if (built.first.empty())
+            st = mg_upload(h, built.second, mg_blk);
+        else
+            g_last_error = built.first;
         if (st != SLRF_OK) {
             slrf_destroy(h);
             return st;
