@@ -373,6 +373,11 @@ const char *slrf_noalloc_last_error(void);
 
 /* ---- multigrid hierarchy (inspection) -------------------------------------- */
 
+/* The multigrid hierarchy is built on the host with up to 16 threads per
+ * step (the environment variable SLRF_HOST_THREADS, read once, sets another
+ * cap, e.g. when many handles are created at once); every value it produces
+ * is formed in a fixed order, so the hierarchy does not depend on the count. */
+
 #define SLRF_MG_MAX_LEVELS 16
 /* Build the SLRF_PRECOND_MG hierarchy of a HOST pencil (p->on_device must be
  * 0) with the mg_* fields of *o (NULL = defaults), on the host only, and

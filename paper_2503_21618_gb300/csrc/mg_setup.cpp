@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -23,11 +24,19 @@
 namespace slrf {
 namespace {
 
+// Host threads for a setup step: up to 16 (or SLRF_HOST_THREADS, read once),
+// one for small work.  No result depends on the count.
 int n_threads(int64_t work) {
-    unsigned hc = std::thread::hardware_concurrency();
-    int t = (int)std::min<unsigned>(hc ? hc : 1, 16u);
-    if (work < 200000) t = 1;
-    return std::max(1, t);
+    static const int cap = [] {
+        unsigned hc = std::thread::hardware_concurrency();
+        int t = (int)std::min<unsigned>(hc ? hc : 1, 16u);
+        if (const char *env = std::getenv("SLRF_HOST_THREADS")) {
+            const int v = std::atoi(env);
+            if (v >= 1) t = std::min(v, 64);
+        }
+        return t;
+    }();
+    return work < 200000 ? 1 : cap;
 }
 
 // Run fn(r0, r1, tid) over contiguous row ranges in parallel.

@@ -126,3 +126,21 @@ def test_level_eigendecomposition(dump_tool, tmp_path, case):
     np.testing.assert_allclose(lam, sla.eigh(A, B, eigvals_only=True), rtol=1e-10)
     np.testing.assert_allclose(V.T @ A @ V, np.diag(lam), rtol=0, atol=1e-13 * np.abs(lam).max())
     np.testing.assert_allclose(V.T @ B @ V, np.eye(m), rtol=0, atol=1e-13)
+
+
+def test_setup_does_not_depend_on_the_thread_count(dump_tool, tmp_path):
+    # power iteration, strength graph, row products, level eigensolver and
+    # layouts on 1 and on 4 host threads: byte-identical outputs
+    p = pencil_2d_q1(80, seed=7)                      # levels 6241, 725, 107
+    outs = {}
+    for nt in (1, 4):
+        d = str(tmp_path / f"t{nt}")
+        os.makedirs(d)
+        _write_pencil(p, d)
+        env = dict(os.environ, SLRF_HOST_THREADS=str(nt))
+        subprocess.run([dump_tool, d, "eig", "1", "1"], check=True, env=env)
+        subprocess.run([dump_tool, d, "layout", "1", "2"], check=True, env=env)
+        outs[nt] = {f: open(os.path.join(d, f), "rb").read()
+                    for f in ("lam.bin", "V.bin", "Ad.bin", "Bd.bin", "up_col.bin", "down_col.bin", "q.bin")}
+    for f in outs[1]:
+        assert outs[1][f] == outs[4][f], f
