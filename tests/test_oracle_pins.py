@@ -9,7 +9,7 @@ import scipy.linalg as la
 
 from oracle import filter as ofilt
 from oracle import inertia, poles, rr, subspace
-from workloads import pencil_1d, pencil_2d_q1, start_block
+from workloads import pencil_1d, pencil_2d_q1, pencil_3d_elasticity, start_block
 
 
 # --------------------------------------------------------------------------
@@ -238,3 +238,76 @@ def test_algorithm1_brute_force_small_2d():
         res = subspace.subspace_iterate(p.A(), p.B(), s, w, gamma, start_block(p.n, 18, 3), tol=1e-10)
         assert res.converged and res.n_wanted == 12
         np.testing.assert_allclose(res.theta[:12], lam[:12], rtol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# lowest_eigs through its sparse (ARPACK shift-invert) branch, and the sparse
+# inertia count on a node-block elasticity pencil.  These two functions write
+# the stored 2D/3D spectra and counts that every full-size parity test uses.
+#
+# Tolerance: 1e-10 relative, the eigenvalue tolerance of the parity tests.
+# FP64 rounding alone puts the lowest eigenvalues of these pencils ~1e-11 from
+# the exact ones (dense LAPACK eigh and ARPACK differ by 3e-11 on the 2D
+# pencil below; the 1D closed form sits 3e-11 from either), so a tighter gate
+# would test rounding, not the routine.  A wrong mass operand, a wrong
+# inverse operator or a dropped eigenvalue moves some lambda_k by at least
+# the relative gap to its neighbour (>= 1e-4 here), far above the gate.
+# --------------------------------------------------------------------------
+def _check_lowest(p, k, lam_ref, lam, X):
+    np.testing.assert_allclose(lam, lam_ref, rtol=1e-10, atol=0)
+    A, B = p.A(), p.B()
+    # B-orthonormal eigenvectors (Section 2: x^T B x = 1) with small residuals
+    np.testing.assert_allclose(X.T @ (B @ X), np.eye(k), atol=1e-10)
+    # backward-error form of the residual: a backward-stable eigenpair has
+    # ||A x - lambda B x|| <= c eps (||A|| + |lambda| ||B||) ||x||; a wrong
+    # operand gives an O(1) residual
+    R = A @ X - (B @ X) * lam[None, :]
+    nA = abs(A).sum(axis=1).max()
+    nB = abs(B).sum(axis=1).max()
+    bound = 100 * np.finfo(float).eps * (nA + np.abs(lam) * nB) * np.linalg.norm(X, axis=0)
+    assert np.all(np.linalg.norm(R, axis=0) <= bound), (np.linalg.norm(R, axis=0) / bound).max()
+    # nothing dropped or doubled: the inertia count of A - gamma B at the gap
+    # above lambda_k equals k (Sylvester's law, as in Algorithm 1's ENSURE)
+    gamma = 0.5 * (lam_ref[k - 1] + lam_ref[k]) if len(lam_ref) > k else None
+    return gamma
+
+
+def test_lowest_eigs_sparse_branch_1d_closed_form():
+    n, k = 5000, 30
+    p = pencil_1d(n)
+    lam, X = inertia.lowest_eigs(p.A(), p.B(), k, dense_limit=1000)   # forces ARPACK
+    exact = inertia.lambda_1d(n)
+    _check_lowest(p, k, exact[:k], lam, X)
+    gamma = 0.5 * (exact[k - 1] + exact[k])
+    assert inertia.count_below_1d(n, gamma) == k
+    assert inertia.count_below_sparse(p.A(), p.B(), gamma) == k
+
+
+def test_lowest_eigs_sparse_branch_2d_lognormal_against_dense():
+    p = pencil_2d_q1(70, seed=17)          # n = 4761, lognormal coefficient
+    k = 40
+    ref = la.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True, subset_by_index=[0, k])
+    lam, X = inertia.lowest_eigs(p.A(), p.B(), k, dense_limit=1000)
+    _check_lowest(p, k, ref[:k], lam, X)
+    gamma = 0.5 * (ref[k - 1] + ref[k])
+    assert inertia.count_below_sparse(p.A(), p.B(), gamma) == k
+
+
+def test_lowest_eigs_sparse_branch_3d_elasticity_against_dense():
+    p = pencil_3d_elasticity(12, seed=19)  # 12^3 nodes, face x=0 clamped: n = 4752
+    assert p.n == 4752
+    k = 40
+    ref = la.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True, subset_by_index=[0, k])
+    lam, X = inertia.lowest_eigs(p.A(), p.B(), k, dense_limit=1000)
+    _check_lowest(p, k, ref[:k], lam, X)
+
+
+def test_sparse_count_on_elasticity_pencil_matches_dense():
+    # node-block (3 dof per node) pencil: the case where diagonal-pivot-only
+    # symmetric LU is most fragile; checked against a Bunch-Kaufman LDL^T.
+    p = pencil_3d_elasticity(8, seed=23)   # n = 8*8*7*3 = 1344
+    lam = la.eigh(p.A().toarray(), p.B().toarray(), eigvals_only=True)
+    for k in (1, 6, 25, 90, 400, 1000):
+        gamma = 0.5 * (lam[k - 1] + lam[k])
+        assert inertia.count_below_dense(p.A(), p.B(), gamma) == k
+        assert inertia.count_below_sparse(p.A(), p.B(), gamma) == k
