@@ -361,7 +361,10 @@ void slrf_server_destroy(slrf_server *s);
  * held by every GPU that loads the library; m*m*8 must fit in it (m <= 724),
  * larger m returns SLRF_EINVAL (message in slrf_noalloc_last_error()).
  * The first call on a device looks up that array's device address (with that
- * device current), so make the first call before any stream capture.  All
+ * device current), so make the first call before any stream capture: a first
+ * call on a capturing stream returns SLRF_EINVAL.  The address is that of the
+ * device's primary context (the CUDA runtime's), so call from that context
+ * only, and not after cudaDeviceReset in the same process.  All
  * calls share the scratch: calls that overlap on the GPU (concurrent streams)
  * race.  Work is enqueued on cuda_stream (a cudaStream_t); returns after
  * enqueuing. */
@@ -370,6 +373,19 @@ slrf_status slrf_gram_noalloc(int64_t n, int32_t m, const double *X, int64_t ldx
                               int64_t ldy, double *G, void *cuda_stream);
 /* Text of the last error of slrf_gram_noalloc on this thread ("" if none). */
 const char *slrf_noalloc_last_error(void);
+
+/* ---- measurement ----------------------------------------------------------- */
+
+/* Measured fused multiply-add throughput of the current device in flop/s
+ * (2 flops per FMA), FP32 for precision = SLRF_PREC_MIXED, FP64 for
+ * SLRF_PREC_FP64: the peak against which kernels bound by plain ALU
+ * arithmetic are reported (the paper has no counterpart; it reports no
+ * timings).  Runs a register-only FMA kernel that fills every SM on
+ * cuda_stream (a cudaStream_t), best of three timed repetitions after one
+ * warm-up; synchronises the stream.  *flops_per_s is written on SLRF_OK.
+ * SLRF_EINVAL for a NULL output or another precision, SLRF_ECUDA if a CUDA
+ * call fails. */
+slrf_status slrf_fma_peak(int32_t precision, double *flops_per_s, void *cuda_stream);
 
 /* ---- multigrid hierarchy (inspection) -------------------------------------- */
 

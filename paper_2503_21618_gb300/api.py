@@ -115,6 +115,7 @@ _SIGNATURES = {
     "slrf_server_destroy": (None, [_P]),
     "slrf_gram_noalloc": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, _P]),
     "slrf_noalloc_last_error": (C.c_char_p, []),
+    "slrf_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), _P]),
     "slrf_mg_describe": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P, _P]),
     "slrf_mg_transfer": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.c_int32, C.POINTER(C.c_int32),
@@ -206,6 +207,13 @@ def filter_eval(f: Filter, x) -> np.ndarray:
     _check(load().slrf_filter_eval(C.byref(f.c), x.ctypes.data_as(C.POINTER(C.c_double)), x.size,
                                    out.ctypes.data_as(C.POINTER(C.c_double))), "slrf_filter_eval")
     return out
+
+
+def fma_peak(precision: int = PREC_MIXED, stream=None) -> float:
+    """Measured FP32 (PREC_MIXED) or FP64 (PREC_FP64) FMA throughput, flop/s."""
+    v = C.c_double()
+    _check(load().slrf_fma_peak(precision, C.byref(v), _stream_ptr(stream)), "slrf_fma_peak")
+    return v.value
 
 
 def mg_describe(pencil, opts: slrf_opts | None = None, coarse: bool = False) -> dict:

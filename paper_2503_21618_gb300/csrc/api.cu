@@ -1037,7 +1037,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
     k_symmetrize<<<(unsigned)((m2 + 255) / 256), 256, 0, ctx.stream>>>(m, Ah);
     ctx.after();
-    small_syev(ctx, m, Ah, theta, Sm, syw, h->opts.eig_refine);
+    CK(small_syev(ctx, m, Ah, theta, Sm, syw, h->opts.eig_refine));
     // X = Q1 (T2 S); AX, BX by SpMM
     dgemm(ctx, 0, 0, m, m, m, T2, m, Sm, m, 0.0, Mm, m, 1, nullptr, KC_SMALL_DENSE);
     CKS(tall_product(h, n, m, m, Q1, m, nullptr, Mm, m, X, ldx));
@@ -1828,7 +1828,7 @@ slrf_status slrf_syev(slrf_handle *h, int32_t m, const double *S, double *lam, d
     h->ctx.before(KC_SMALL_DENSE, 16.0 * m * m, 0);
     k_symmetrize<<<(unsigned)(((size_t)m * m + 255) / 256), 256, 0, h->ctx.stream>>>(m, Sc);
     h->ctx.after();
-    small_syev(h->ctx, m, Sc, lam, Q, w, h->opts.eig_refine);
+    CK(small_syev(h->ctx, m, Sc, lam, Q, w, h->opts.eig_refine));
     CK(cudaGetLastError());
     return SLRF_OK;
 }

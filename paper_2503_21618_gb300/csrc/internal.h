@@ -240,7 +240,7 @@ void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv);
 void small_scale_rows(Ctx &ctx, int m, const double *s, double *T);  // T = diag(s) T
 // Symmetric eigensolver: lam ascending, Q eigenvectors (columns).  mode 1:
 // FP32 Jacobi followed by FP64 refinement; 0: FP64 Jacobi.
-void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode);
+cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode);
 size_t small_syev_work_bytes(int m);
 
 // ---------------------------------------------------------------- api.cu

@@ -13,7 +13,9 @@
 // loads this library holds that array until the process exits.  In host code
 // the array's name is only a host-side stand-in, so its device address is
 // looked up once per device with cudaGetSymbolAddress (with that device
-// current) on the first call made on that device.
+// current) on the first call made on that device.  That address belongs to
+// the device's primary context (the one the CUDA runtime uses): calls must
+// come from that context, and not after cudaDeviceReset in this process.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -65,6 +67,18 @@ extern "C" slrf_status slrf_gram_noalloc(int64_t n, int32_t m, const double *X, 
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
         if (!g_scratch_ptr[dev]) {
+            // The set-up below (symbol lookup, possibly lazy module loading)
+            // must not happen while the stream is being captured into a graph.
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            e = cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(cuda_stream), &cap);
+            if (e != cudaSuccess) {
+                g_noalloc_error = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e);
+                return SLRF_ECUDA;
+            }
+            if (cap != cudaStreamCaptureStatusNone) {
+                g_noalloc_error = "the first call on a device must not be made during stream capture";
+                return SLRF_EINVAL;
+            }
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_scratch);
             if (e != cudaSuccess || !ptr) {

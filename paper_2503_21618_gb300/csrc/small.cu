@@ -481,8 +481,11 @@ size_t small_syev_work_bytes(int m) {
 // so two partially resident cooperative grids can never wait on each other.
 static std::mutex g_coop_mutex;
 
-static void coop_jacobi(Ctx &ctx, int m, double *A, double *V, double *lam, int max_sweeps, const double *normA,
-                        int *cnt) {
+// Returns the launch's or the wait's error: a refused cooperative launch (too
+// few co-resident blocks, say) must not leave the caller polishing an
+// unrotated matrix.
+static cudaError_t coop_jacobi(Ctx &ctx, int m, double *A, double *V, double *lam, int max_sweeps,
+                               const double *normA, int *cnt) {
     static const int per_sm = [] {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_jacobi_coop, 256, 0);
@@ -494,16 +497,25 @@ static void coop_jacobi(Ctx &ctx, int m, double *A, double *V, double *lam, int 
     int32_t *info = nullptr;
     void *args[] = {&m, &A, &V, &lam, &max_sweeps, (void *)&normA, &cnt, &info};
     thread_local cudaEvent_t done = nullptr;
-    if (!done) cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    if (!done) {
+        const cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            done = nullptr;
+            return e;
+        }
+    }
     std::lock_guard<std::mutex> lock(g_coop_mutex);
     ctx.before(KC_SMALL_DENSE, 24.0 * m * m, 9.0 * (double)m * m * m * 3);
-    cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(blocks), dim3(256), args, 0, ctx.stream);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_jacobi_coop, dim3(blocks), dim3(256), args, 0,
+                                                ctx.stream);
     ctx.after();
-    cudaEventRecord(done, ctx.stream);
-    cudaEventSynchronize(done);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(done, ctx.stream);
+    if (e != cudaSuccess) return e;
+    return cudaEventSynchronize(done);
 }
 
-void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode) {
+cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double *work, int mode) {
     const size_t m2 = (size_t)m * m;
     const size_t mp = (size_t)(m + (m & 1));
     char *w = reinterpret_cast<char *>(work);
@@ -532,11 +544,12 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
     const int use_smem = smem <= 200 * 1024;
     if (mode == 0 || !use_smem) {
         cudaMemcpyAsync(Tm, S, m2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream);
-        coop_jacobi(ctx, m, Tm, Vm, lam0, 60, normA, cnt);
+        const cudaError_t e = coop_jacobi(ctx, m, Tm, Vm, lam0, 60, normA, cnt);
+        if (e != cudaSuccess) return e;
         ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
         k_sort_eig<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, lam0, Vm, lam, Q);
         ctx.after();
-        return;
+        return cudaGetLastError();
     }
     // stage 1: FP32 Jacobi in shared memory
     raise_smem_limits();
@@ -552,11 +565,13 @@ void small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q, double
     // T = S1^T A S1, then polish T by FP64 Jacobi, S = S1 V
     dgemm(ctx, 0, 0, m, m, m, S, m, S1, m, 0.0, Ym, m, 1, nullptr, KC_SMALL_DENSE);
     dgemm(ctx, 1, 0, m, m, m, S1, m, Ym, m, 0.0, Tm, m, 1, nullptr, KC_SMALL_DENSE);
-    coop_jacobi(ctx, m, Tm, Vm, lam0, 20, normA, cnt);
+    const cudaError_t e = coop_jacobi(ctx, m, Tm, Vm, lam0, 20, normA, cnt);
+    if (e != cudaSuccess) return e;
     dgemm(ctx, 0, 0, m, m, m, S1, m, Vm, m, 0.0, S0, m, 1, nullptr, KC_SMALL_DENSE);
     ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
     k_sort_eig<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, lam0, S0, lam, Q);
     ctx.after();
+    return cudaGetLastError();
 }
 
 // Kernel attributes are process-wide: a handle lowering a kernel's dynamic

@@ -172,3 +172,13 @@ def test_rayleigh_ritz_survives_dependent_columns(api):
     # six Ritz values reproduce lambda_1..6; the seventh comes from the noise direction
     hits = [np.min(np.abs(th - l)) / l for l in lam[:6]]
     assert max(hits) < 1e-9
+
+
+def test_fma_peak_is_plausible(api):
+    # 152 SMs x 128 FP32 lanes x 2 flops x ~2 GHz ~ 80 TFLOP/s nominal; FP64
+    # runs far slower on this part.  A broken timer or a dead-code-eliminated
+    # loop reads far outside these ranges.
+    f32 = api.fma_peak(api.PREC_MIXED)
+    f64 = api.fma_peak(api.PREC_FP64)
+    assert 20e12 < f32 < 120e12, f32
+    assert 0.1e12 < f64 < 0.5 * f32, f64

@@ -53,6 +53,23 @@ def test_noalloc_gram_matches_handle_gram_twice(api):
         assert np.abs(got - X.T @ Y).max() <= tol
 
 
+def test_noalloc_gram_at_the_largest_accepted_size(api):
+    # m = 724 is the largest m whose m x m partial product fits the scratch:
+    # one K slice only, so the unsplit product path runs
+    n, m = 20000, 724
+    X = start_block(n, m, 31)
+    Y = start_block(n, m, 32)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    h = api.Handle(pencil_1d(n))
+    ref = h.gram(Xd, Yd).cpu().numpy()
+    h.close()
+    tol = 1e-13 * np.abs(X).max() * np.abs(Y).max() * n
+    for _ in range(2):
+        got = _noalloc_gram(api, Xd, Yd)
+        assert np.abs(got - ref).max() <= tol
+        assert np.abs(got - X.T @ Y).max() <= tol
+
+
 def test_noalloc_gram_rejects_m_beyond_scratch(api):
     m = 725
     X = torch.zeros((4, m), dtype=torch.float64, device="cuda")
