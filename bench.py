@@ -387,6 +387,7 @@ def bench_3d(pkg, fp32_peak):
     ach = k["flops"] / (k["ms"] / 1e3) if k["ms"] else None
     return {"workload": name, "n": p.n, "nnz": p.nnz, "L": iv["L"], "nev": iv["nev"], "n_poles": iv["n_poles"],
             "precision": "mixed", "precond": "jacobi (AUTO on 3-dof node-block pencils)",
+            "spmm_kernel": int(rep.spmm_kernel),
             "value": (int(nc) if st == pkg.OK else 0) / t, "unit": UNIT, "seconds": t, "status": int(st),
             "converged": int(nc), "outer_iters": rep.outer_iters, "max_resid": rep.max_resid,
             "max_rel_eig_err_vs_oracle": float(np.max(np.abs(th - lam) / lam)) if int(nc) == iv["nev"] else None,
@@ -598,6 +599,8 @@ def main():
                        "filter": "SLRF alpha=1 beta=0.01 (library designer)", "precision": "mixed",
                        "inner_tol": opts.inner_tol, "tol": TOL, "parallelism": f"replicas x{world}",
                        "precond": "multigrid (smoothed aggregation)" if "mg_fine" in tot else "jacobi",
+                       "spmm_kernel": {1: "row groups", 2: "staged (bulk copies to shared memory)"}.get(
+                           reps[0]["spmm_kernel"], str(reps[0]["spmm_kernel"])) if reps else None,
                        "l2": "inputs larger than L2 (Krylov state 1.29 GB per solve)"},
             "converged_per_step": conv, "outer_iters": outer,
             "gpu_launches": int(launches),

@@ -117,8 +117,11 @@ typedef struct {
     int32_t spmm_rows;      /* rows per group of the shifted SpMM (1..4); 0 = auto:
                                3 for 3-dof node-block patterns, else 2             (0) */
     int32_t gram_ozaki;     /* Grams and tall products (Q1 = U T1, X = Q1 M) of the
-                               projection step: 1 = FP64-accurate int8 tensor-core
-                               products (Ozaki splitting), 0 = FP64 CUDA cores     (1) */
+                               projection step, FP64-accurate from exact integer
+                               digit products (Ozaki splitting): 2 = Grams on the
+                               tcgen05 tensor cores (bf16 digits, FP32 TMEM
+                               accumulators), tall products as with 1; 1 = int8
+                               mma.sync digits for both; 0 = FP64 CUDA cores    (2) */
     int32_t mg_nu;          /* MG: Jacobi sweeps per side on the levels below the
                                finest (the finest always takes one)                (2) */
     int32_t mg_cycle;       /* MG: coarse visits per level, 1 = V-, 2 = W-cycle    (1) */
@@ -143,7 +146,15 @@ typedef struct {
     uint32_t profile_mask;  /* profile == 1: bit c times kernel class c
                                (slrf_kernel_class_name), 0 = every class; timing
                                fewer classes records fewer events               (0) */
-    int32_t reserved[2];
+    int32_t spmm_kernel;    /* FP32 shifted product kernel: 1 = row groups gathered
+                               through L1/L2 by every warp; 2 = staged: a producer
+                               warp moves the gathered rows into shared memory by
+                               bulk copies (TMA engine) and consumer warps only
+                               multiply; 0 = chosen per pattern and column count
+                               by timing both on the first solve (the choice is
+                               kept for the process; the two differ only in the
+                               rounding order of the partial dot products)    (0) */
+    int32_t reserved;
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the
@@ -173,6 +184,8 @@ typedef struct {
                                      (0: Jacobi or no preconditioner)           */
     int32_t krylov_fp64;          /* MIXED: 1 if the solve switched its Krylov
                                      solves to FP64 after the FP32 ones stagnated */
+    int32_t spmm_kernel;          /* FP32 shifted product kernel used (the value
+                                     of slrf_opts.spmm_kernel, resolved when 0) */
 } slrf_report;
 
 /* ---- library -------------------------------------------------------- */

@@ -20,6 +20,7 @@ NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PENDING =
 PREC_FP64, PREC_MIXED = 0, 1
 KRYLOV_COCG, KRYLOV_BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG, PRECOND_AUTO = 0, 1, 2, 3
+SPMM_AUTO, SPMM_ROWGROUP, SPMM_STAGED = 0, 1, 2
 RULE_MIDPOINT, RULE_GAUSS_LEGENDRE, RULE_GAUSS_CHEBYSHEV, RULE_SLRF = 0, 1, 2, 3
 RULES = {"midpoint": 0, "gauss_legendre": 1, "gauss_chebyshev": 2, "slrf": 3}
 MAX_POLES = 16
@@ -45,7 +46,7 @@ class slrf_opts(C.Structure):
                 ("mg_nu", C.c_int32), ("mg_cycle", C.c_int32), ("mg_coarse", C.c_int32), ("mg_block", C.c_int32),
                 ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("mg_shift_limit", C.c_double),
                 ("stagnation_window", C.c_int32),
-                ("profile_mask", C.c_uint32), ("reserved", C.c_int32 * 2)]
+                ("profile_mask", C.c_uint32), ("spmm_kernel", C.c_int32), ("reserved", C.c_int32)]
 
 
 class slrf_report(C.Structure):
@@ -55,7 +56,8 @@ class slrf_report(C.Structure):
                 ("kernel_launches", C.c_int64), ("ms_total", C.c_double), ("ms_krylov", C.c_double),
                 ("ms_rr", C.c_double), ("k_launches", C.c_int64 * NKERNEL_CLASSES),
                 ("k_ms", C.c_double * NKERNEL_CLASSES), ("k_bytes", C.c_double * NKERNEL_CLASSES),
-                ("k_flops", C.c_double * NKERNEL_CLASSES), ("mg_levels", C.c_int32), ("krylov_fp64", C.c_int32)]
+                ("k_flops", C.c_double * NKERNEL_CLASSES), ("mg_levels", C.c_int32), ("krylov_fp64", C.c_int32),
+                ("spmm_kernel", C.c_int32)]
 
     def as_dict(self, lib=None) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("k_") and k != "iters_per_pole"}

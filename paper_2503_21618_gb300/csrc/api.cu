@@ -6,8 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <complex>
 #include <future>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <string>
@@ -760,6 +762,69 @@ struct KStats {
     int mg_levels = 0;            // multigrid levels used (0: none)
 };
 
+// Kernel choice of the FP32 shifted product (slrf_opts.spmm_kernel = 0):
+// both kernels are timed on this solve's blocks (one warm launch, then three
+// timed ones each) and the faster is kept, per device, pattern and column
+// count, for the rest of the process.
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 6>, int> g_tune;
+
+template <typename T>
+slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffers<T> &kb, const cplx<T> *sig) {
+    DevPencil &A = h->A;
+    if (sizeof(T) != 4 || A.spmm_kind != 0) return SLRF_OK;
+    if (spmm_staged_smem(A) == 0) {
+        A.spmm_kind = SPMM_ROWGROUP;
+        return SLRF_OK;
+    }
+    const std::array<int64_t, 6> key = {h->device, A.n, A.nnz, A.rg_rows, A.rg_nnz, d.W()};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            A.spmm_kind = it->second;
+            return SLRF_OK;
+        }
+    }
+    Ctx &ctx = h->ctx;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        g_last_error = "autotune: event creation failed";
+        return SLRF_ECUDA;
+    }
+    float best = 0.f;
+    int pick = SPMM_ROWGROUP;
+    for (int kind : {SPMM_ROWGROUP, SPMM_STAGED}) {
+        A.spmm_kind = kind;
+        krylov_spmm<T>(ctx, d, A, sig, kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
+        cudaEventRecord(e0, ctx.stream);
+        for (int r = 0; r < 3; ++r) krylov_spmm<T>(ctx, d, A, sig, kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
+        cudaEventRecord(e1, ctx.stream);
+        float ms = 0.f;
+        const cudaError_t err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess || *(volatile int32_t *)(h->h_pin + 1) != 0) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            g_last_error = err != cudaSuccess ? std::string("autotune: ") + cudaGetErrorString(err)
+                                              : std::string("autotune: a bounded device wait gave up");
+            return err != cudaSuccess ? SLRF_ECUDA : SLRF_ETIMEOUT;
+        }
+        if (kind == SPMM_ROWGROUP || ms < best) {
+            best = ms;
+            pick = kind;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A.spmm_kind = pick;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = pick;
+    return SLRF_OK;
+}
+
 template <typename T>
 slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const double *rhs, int64_t ldr,
                          const std::vector<int> &col_active, const std::vector<cd> &coef, double tol, int maxit,
@@ -773,6 +838,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     const int W = d.W();
     const int64_t n = d.n;
     kb.gy = krylov_row_groups(ctx, d, sizeof(T) == 4);
+    *(volatile int32_t *)(h->h_pin + 1) = 0;   // device-side wait timeouts of this solve
     CKS(ensure(h, h->kP, (size_t)n * W * sizeof(cplx<T>)));
     CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
     CKS(ensure(h, h->kR, (size_t)n * W * sizeof(cplx<T>)));
@@ -866,6 +932,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         krylov_direction<T>(ctx, d, kb, 1);
     }
     krylov_reduce_init<T>(ctx, d, kb);
+    CKS(resolve_spmm_kernel<T>(h, d, kb, sig));
 
     int n_active = 0;
     for (int col = 0; col < W; ++col) n_active += flags[col] == 1;
@@ -905,6 +972,10 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         CK(cudaEventRecord(h->ev_poll, ctx.stream));
         CK(cudaEventSynchronize(h->ev_poll));
         n_active = *(volatile int32_t *)h->h_pin;
+        if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
+            g_last_error = "shifted product: a bounded device wait gave up";
+            return SLRF_ETIMEOUT;
+        }
         d.frac = (double)n_active / W;
         if (n_active == 0) break;
     }
@@ -933,14 +1004,16 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
     return SLRF_OK;
 }
 
-// G = X^T Y with the handle's Gram method (int8 tensor-core Ozaki or FP64)
-// (symmetric: Y = B X with B symmetric, so only the upper tiles are computed)
+// G = X^T Y with the handle's Gram method (Ozaki digits on the tcgen05 or the
+// mma.sync tensor path, or FP64) (symmetric: Y = B X with B symmetric, so only
+// the upper tiles are computed)
 slrf_status gram(slrf_handle *h, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
                  double *G, bool symmetric = false) {
     Ctx &ctx = h->ctx;
     if (h->opts.gram_ozaki) {
         CKS(ensure(h, h->rOz, ozaki_gram_work_bytes(n, m, ctx.sm_count)));
-        ozaki_gram(ctx, n, m, X, ldx, Y, ldy, G, h->rOz.p, symmetric);
+        ozaki_gram(ctx, n, m, X, ldx, Y, ldy, G, h->rOz.p, symmetric,
+                   h->opts.gram_ozaki == 2 ? h->d_pin + 1 : nullptr);
         return SLRF_OK;
     }
     const int split = gram_split(ctx, m, n);
@@ -972,6 +1045,7 @@ slrf_status tall_product(slrf_handle *h, int64_t n, int k, int m, const double *
 slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double *theta, double *X, int64_t ldx,
                     double *AX, double *BX, int32_t *chol_status) {
     Ctx &ctx = h->ctx;
+    *(volatile int32_t *)(h->h_pin + 1) = 0;   // device-side wait timeouts of this step
     const int64_t n = h->A.n;
     const size_t m2 = (size_t)m * m;
     const int split = gram_split(ctx, m, n);
@@ -1048,6 +1122,10 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
         CK(cudaStreamSynchronize(ctx.stream));
         chol_status[0] = chol_status[0] > 0 ? chol_status[0] : (chol_status[1] > 0 ? chol_status[1] : 0);
         chol_status[1] = 0;
+        if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
+            g_last_error = "Gram: a bounded device wait gave up";
+            return SLRF_ETIMEOUT;
+        }
     }
     return SLRF_OK;
 }
@@ -1234,6 +1312,7 @@ slrf_status subspace_core(slrf_handle *h, const slrf_filter *f, double gamma, in
         rep->spmv = spmv;
         rep->mg_levels = st.mg_levels;
         rep->krylov_fp64 = k64 ? 1 : 0;
+        rep->spmm_kernel = h->A.spmm_kind;
         for (int j = 0; j < N; ++j) rep->iters_per_pole[j] = outer ? ipp[j] / outer : 0.0;
     }
     return status;
@@ -1287,6 +1366,7 @@ slrf_status precond_apply_t(slrf_handle *h, const slrf_filter *f, KrylovDims &d,
     const int64_t n = d.n;
     KrylovBuffers<T> kb{};
     kb.gy = krylov_row_groups(ctx, d, sizeof(T) == 4);
+    *(volatile int32_t *)(h->h_pin + 1) = 0;   // device-side wait timeouts of this solve
     CKS(ensure(h, h->kDinv, (size_t)n * N * sizeof(cplx<T>)));
     CKS(ensure(h, h->kPart, (size_t)kb.gy * W * 4 * sizeof(T)));
     CKS(ensure(h, h->kSig, SLRF_MAX_POLES * sizeof(cplx<T>)));
@@ -1366,7 +1446,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->mem_budget = 0;
     o->profile = 0;
     o->spmm_rows = 0;
-    o->gram_ozaki = 1;
+    o->gram_ozaki = 2;
     o->mg_nu = 2;
     o->mg_cycle = 1;
     o->mg_coarse = 256;
@@ -1390,6 +1470,8 @@ static slrf_status check_opts(const slrf_opts *o) {
         return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
+    if (o->spmm_kernel < 0 || o->spmm_kernel > 2) return SLRF_EINVAL;
+    if (o->gram_ozaki < 0 || o->gram_ozaki > 2) return SLRF_EINVAL;
     return SLRF_OK;
 }
 
@@ -1481,6 +1563,7 @@ slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
     h->opts = *o;
     h->ctx.profile = o->profile != 0;
     h->ctx.profile_mask = o->profile_mask ? o->profile_mask : ~0u;
+    h->A.spmm_kind = o->spmm_kernel;
     return SLRF_OK;
 }
 
@@ -1495,8 +1578,9 @@ void slrf_destroy(slrf_handle *h) {
                    &h->mg_eig[12].dev, &h->mg_eig[13].dev, &h->mg_eig[14].dev, &h->mg_eig[15].dev};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
-    void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,      h->A.ab32,   h->A.ab64,
-                   h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64};
+    void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,       h->A.ab32,   h->A.ab64,
+                   h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64,
+                   h->A.rg_ab4, h->A.rg_dpos};
     for (void *p : pen)
         if (p) cudaFreeAsync(p, h->ctx.stream);
     cudaStreamSynchronize(h->ctx.stream);
@@ -1602,6 +1686,8 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         slrf_destroy(h);
         return SLRF_ENOMEM;
     }
+    h->A.dev_err = h->d_pin + 1;   // second word of the handle's pinned poll slot
+    h->A.spmm_kind = o->spmm_kernel;
     cudaEventCreate(&h->ev_poll);
     cudaEventCreate(&h->ev_t0);
     cudaEventCreate(&h->ev_t1);
@@ -1626,6 +1712,33 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         h->A.rg_rows = R;
         h->A.rg_ngroups = (int)(gptr.size() - 1);
         h->A.rg_nnz = U;
+        // staged-kernel form: packed (a, a, b, b) pairs and own-column positions
+        int emax = 0;
+        for (size_t g = 0; g + 1 < gptr.size(); ++g) emax = std::max(emax, gptr[g + 1] - gptr[g]);
+        h->A.rg_emax = emax;
+        if (emax <= 255) {
+            const int64_t ng = (int64_t)gptr.size() - 1;
+            std::vector<float4> ab4(uab.size());
+            for (size_t i = 0; i < uab.size(); ++i) {
+                const float a = (float)uab[i].x, b = (float)uab[i].y;
+                ab4[i] = make_float4(a, a, b, b);
+            }
+            std::vector<uint8_t> dpos((size_t)ng * R, 0);
+            for (int64_t g = 0; g < ng; ++g)
+                for (int r = 0; r < R; ++r) {
+                    const int64_t row = g * R + r;
+                    if (row >= n) break;
+                    const auto b = ucol.begin() + gptr[g], e = ucol.begin() + gptr[g + 1];
+                    dpos[(size_t)g * R + r] = (uint8_t)(std::lower_bound(b, e, (int32_t)row) - b);
+                }
+            // optional: without these arrays the row-group kernel runs
+            if (alloc((void **)&h->A.rg_ab4, ab4.size() * 16) && alloc((void **)&h->A.rg_dpos, dpos.size())) {
+                cudaMemcpyAsync(h->A.rg_ab4, ab4.data(), ab4.size() * 16, cudaMemcpyHostToDevice, s);
+                cudaMemcpyAsync(h->A.rg_dpos, dpos.data(), dpos.size(), cudaMemcpyHostToDevice, s);
+                // pageable sources: complete before they go out of scope
+                cudaStreamSynchronize(s);
+            }
+        }
         // stream-ordered after the allocations; pageable sources are staged
         // before each call returns
         cudaMemcpyAsync(h->A.rg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice, s);
@@ -1765,6 +1878,8 @@ slrf_status slrf_shifted_spmm(slrf_handle *h, const slrf_filter *f, int32_t prec
     for (int col = 0; col < W; ++col) flags[col] = (col % ldp) < m ? 1 : 0;
     CK(cudaMemcpyAsync(h->kFlags.p, flags.data(), W * 4, cudaMemcpyHostToDevice, ctx.stream));
     h->ctx.reset_counters();
+    CK(cudaStreamSynchronize(ctx.stream));
+    *(volatile int32_t *)(h->h_pin + 1) = 0;
     if (prec == SLRF_PREC_MIXED) {
         std::vector<float2> sg(d.N);
         for (int j = 0; j < d.N; ++j) sg[j] = make_float2((float)f->sigma_re[j], (float)f->sigma_im[j]);
@@ -1784,6 +1899,10 @@ slrf_status slrf_shifted_spmm(slrf_handle *h, const slrf_filter *f, int32_t prec
     }
     CK(cudaStreamSynchronize(ctx.stream));
     CK(cudaGetLastError());
+    if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
+        g_last_error = "shifted product: a bounded device wait gave up";
+        return SLRF_ETIMEOUT;
+    }
     return SLRF_OK;
 }
 
@@ -1814,8 +1933,15 @@ slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx
 slrf_status slrf_gram(slrf_handle *h, int32_t m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
                       double *G) {
     if (!h || !X || !Y || !G || m < 1 || ldx < m || ldy < m) return SLRF_EINVAL;
+    CK(cudaStreamSynchronize(h->ctx.stream));
+    *(volatile int32_t *)(h->h_pin + 1) = 0;
     CKS(gram(h, h->A.n, m, X, ldx, Y, ldy, G));
+    CK(cudaStreamSynchronize(h->ctx.stream));
     CK(cudaGetLastError());
+    if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
+        g_last_error = "Gram: a bounded device wait gave up";
+        return SLRF_ETIMEOUT;
+    }
     return SLRF_OK;
 }
 

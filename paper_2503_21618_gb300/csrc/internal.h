@@ -58,7 +58,23 @@ struct DevPencil {
     int32_t *rg_ptr = nullptr, *rg_col = nullptr;
     float2 *rg_ab32 = nullptr;
     double2 *rg_ab64 = nullptr;
+    // staged form of the FP32 row-group product: per union entry and row the
+    // pair as (a, a, b, b) (the operand layout of the packed FP32x2 FMA), the
+    // position of each row's own column in its group's union list, and the
+    // longest union list
+    float4 *rg_ab4 = nullptr;
+    uint8_t *rg_dpos = nullptr;
+    int rg_emax = 0;
+    // shifted product kernel: SPMM_ROWGROUP or SPMM_STAGED, and the staged
+    // kernel's row groups per CTA; dev_err receives a device-side wait timeout
+    int spmm_kind = 0;
+    int spmm_gpb = 0;
+    int32_t *dev_err = nullptr;
 };
+enum { SPMM_ROWGROUP = 1, SPMM_STAGED = 2 };
+// Dynamic shared memory of the staged kernel for this pencil (0: the staged
+// kernel cannot run it: no row groups, or a union list too long).
+size_t spmm_staged_smem(const DevPencil &A);
 
 // ---------------------------------------------------------------- krylov.cu
 // Column-block layout of the Krylov state: complex n x W, W = N * Lp, row
@@ -220,8 +236,10 @@ void copy_block(Ctx &ctx, int n, int m, const double *src, int64_t lds, double *
 size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count);
 // symmetric: X^T Y is known to be symmetric (Y = B X with B symmetric): only
 // the tiles on and above the diagonal are computed and mirrored.
+// tc_err != nullptr selects the tensor-core (tcgen05, bf16 digits) form; it
+// receives a nonzero code if one of that kernel's bounded waits gives up.
 void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
-                void *work, bool symmetric = false);
+                void *work, bool symmetric = false, int32_t *tc_err = nullptr);
 // C = (A diag(cs)) B, A n x k, B k x m, C n x m (row-major, leading dims),
 // cs = nullptr for no column scaling; FP64-accurate from int8 digit products.
 size_t ozaki_tall_work_bytes(int64_t n, int k, int m);

@@ -23,6 +23,8 @@
 // residual-corrected one), so the per-pole solutions are never stored.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace slrf {
@@ -378,6 +380,284 @@ k_spmm_shifted_rg(int n, int W, int Lp, int ngroups, int groups_per_block, const
 }
 
 // ---------------------------------------------------------------------------
+// Staged (warp-specialized) variant of the FP32 row-group product.
+//
+// The row-group kernel above is latency-bound: every warp waits on its own
+// gathers from L2, and a third of its instructions are index loads and
+// address arithmetic.  Here one producer warp per CTA moves the gathered rows
+// with bulk copies (the TMA engine) into shared-memory slots, and NC consumer
+// warps only read shared memory and multiply:
+//   * a CTA owns one column chunk (CW = 32 VC complex columns) of a range of
+//     row groups; task t (one row group) goes to consumer warp t % NC, which
+//     has NS private slots used in turn;
+//   * a slot holds the group's gathered rows (union entry e at row e of the
+//     slot, CW columns each) and its coefficient pairs in the packed layout
+//     (a, a, b, b), so each entry costs one shared load of the rows, R of the
+//     pairs and 2 R VC packed FP32x2 FMAs;
+//   * slot handover uses two mbarriers per slot: "full" completes when the
+//     producer's copies have landed (transaction count), "empty" when the
+//     consumer is done with it.  Every wait is bounded (1 s); a wait that
+//     gives up sets *err and the kernel winds down.
+// The product and the partial sums mu = p^T q per column are those of the
+// row-group kernel (same union lists, same per-column order of the FMAs
+// within a row), so both kernels satisfy the same parity tests.
+// ---------------------------------------------------------------------------
+template <int R, int VC, int NC, int NS>
+__global__ void __launch_bounds__(32 * (NC + 1), 1)
+k_spmm_staged(int n, int W, int Lp, int ngroups, int gpb, int emax, const int32_t *__restrict__ gptr,
+              const int32_t *__restrict__ ucol, const float4 *__restrict__ ab4, const uint8_t *__restrict__ dpos,
+              const float2 *__restrict__ sig, const float2 *__restrict__ P, float2 *__restrict__ Q,
+              const int32_t *__restrict__ flag, float *__restrict__ part, int gy_part, int32_t *__restrict__ err) {
+    constexpr int CW = 32 * VC;
+    constexpr unsigned long long LIMIT_NS = 1000000000ull;
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem);   // full[NC][NS], empty[NC][NS]
+    const size_t slot_bytes = ((size_t)emax * CW * 8 + (size_t)emax * R * 16 + 127) & ~(size_t)127;
+    unsigned char *slots = smem + 128 * ((2 * NC * NS * 8 + 127) / 128);
+    float *red = reinterpret_cast<float *>(slots + NC * NS * slot_bytes);   // [NC][32][2 VC]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * CW;
+    const int cw = min(CW, W - c0);
+    const int cl = c0 + lane * VC;   // first column of this lane (consumers)
+    const bool live = lane * VC < cw;
+    const int g_begin = blockIdx.y * gpb;
+    const int T = max(0, min(ngroups, g_begin + gpb) - g_begin);
+    bool act = false;
+    if (warp < NC && live) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) act |= flag[cl + v] == 1;
+    }
+    // The partial sums have gy_part rows (the layout the reductions read);
+    // this grid has gridDim.y <= gy_part of them, and the CTAs of row 0 zero
+    // the rest for their columns.
+    if (blockIdx.y == 0 && warp == 0 && live)
+        for (int yy = gridDim.y; yy < gy_part; ++yy)
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                float *o = part + ((int64_t)yy * W + cl + v) * 4;
+                o[0] = 0.f;
+                o[1] = 0.f;
+            }
+    if (!__syncthreads_or(act)) {
+        // no active column in the chunk: zero partial sums keep the per-column sums complete
+        if (warp == 0 && live)
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                float *o = part + ((int64_t)blockIdx.y * W + cl + v) * 4;
+                o[0] = 0.f;
+                o[1] = 0.f;
+            }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 * NC * NS; ++i) mbar_init(bars + i, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == NC) {   // ---- producer
+        // Rounds of NC consecutive groups (one per consumer, slot k % NS).  A
+        // round's union entries are one contiguous range of the lists, so the
+        // lanes load its column indices together (coalesced) and each lane
+        // issues the copies of every 32nd entry; lane w < NC handles the
+        // slot handshake and the coefficient copy of consumer w.
+        const unsigned row_bytes = (unsigned)cw * 8u;
+        const int rounds = (T + NC - 1) / NC;
+        for (int k = 0; k < rounds; ++k) {
+            const int s = k % NS, u = k / NS;
+            const int t = k * NC + lane;                 // this lane's task (lane < NC)
+            const bool mine = lane < NC && t < T;
+            int e0 = 0, ne = 0;
+            if (mine) {
+                const int g = g_begin + t;
+                e0 = __ldg(gptr + g);
+                ne = __ldg(gptr + g + 1) - e0;
+            }
+            int ok = 1;
+            if (mine && u > 0) ok = mbar_wait_bounded(bars + NC * NS + lane * NS + s, (u - 1) & 1, LIMIT_NS);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            unsigned long long *full = bars + lane * NS + s;
+            if (mine) mbar_expect_tx(full, row_bytes * (unsigned)ne + (unsigned)ne * R * 16u);
+            // entry prefix over the round's groups (lanes 0..NC-1 hold ne)
+            int pre = ne;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, pre, off);
+                if (lane >= off) pre += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, pre, 31);
+            const int ebase = __shfl_sync(0xffffffffu, e0, 0);   // first entry of the round
+            int pq[NC];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) pq[q] = __shfl_sync(0xffffffffu, pre, q);
+            __syncwarp();
+            for (int j = lane; j < total; j += 32) {
+                // consumer w of entry j: pq[w - 1] <= j < pq[w]
+                int w = 0, start = 0;
+#pragma unroll
+                for (int q = 0; q < NC - 1; ++q)
+                    if (pq[q] <= j) {
+                        w = q + 1;
+                        start = pq[q];
+                    }
+                unsigned char *slot = slots + (size_t)(w * NS + s) * slot_bytes;
+                bulk_g2s(slot + (size_t)(j - start) * CW * 8, P + (int64_t)__ldg(ucol + ebase + j) * W + c0, row_bytes,
+                         bars + w * NS + s);
+            }
+            if (mine)
+                bulk_g2s(slots + (size_t)(lane * NS + s) * slot_bytes + (size_t)emax * CW * 8, ab4 + (int64_t)e0 * R,
+                         (unsigned)ne * R * 16u, full);
+        }
+        return;
+    }
+
+    // ---- consumers
+    const float2 sg = sig[min(cl, W - 1) / Lp];
+    float2 mu[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) mu[v] = make_float2(0.f, 0.f);
+    for (int k = 0;; ++k) {
+        const int t = warp + k * NC;
+        if (t >= T) break;
+        const int s = k % NS, u = k / NS;
+        unsigned long long *full = bars + warp * NS + s;
+        unsigned long long *empty = bars + NC * NS + warp * NS + s;
+        const bool ok = mbar_wait_bounded(full, u & 1, LIMIT_NS);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) atomicExch(err, 2);
+            break;
+        }
+        const int g = g_begin + t;
+        const int ne = __ldg(gptr + g + 1) - __ldg(gptr + g);
+        const unsigned char *slot = slots + (size_t)(warp * NS + s) * slot_bytes;
+        const float2 *xs = reinterpret_cast<const float2 *>(slot) + lane * VC;
+        const float4 *ws = reinterpret_cast<const float4 *>(slot + (size_t)emax * CW * 8);
+        float2 sa[R][VC], sb[R][VC];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int v = 0; v < VC; ++v) sa[r][v] = sb[r][v] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int e = 0; e < ne; ++e) {
+            float2 x[VC];
+            if constexpr (VC == 2) {
+                const float4 t4 = *reinterpret_cast<const float4 *>(xs + (size_t)e * CW);
+                x[0] = make_float2(t4.x, t4.y);
+                x[1] = make_float2(t4.z, t4.w);
+            } else {
+                x[0] = xs[(size_t)e * CW];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float4 w4 = ws[e * R + r];
+                const float2 aa = make_float2(w4.x, w4.y), bb = make_float2(w4.z, w4.w);
+#pragma unroll
+                for (int v = 0; v < VC; ++v) {
+                    ffma2(sa[r][v], aa, x[v]);
+                    ffma2(sb[r][v], bb, x[v]);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = g * R + r;
+            if (row >= n) break;
+            const int dp = __ldg(dpos + (int64_t)g * R + r);
+            float2 q[VC];
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                q[v] = csub(sa[r][v], cmul(sg, sb[r][v]));
+                const float2 pr = xs[(size_t)dp * CW + v];
+                mu[v] = cfma(pr, q[v], mu[v]);
+            }
+            if (live) {
+                if constexpr (VC == 2)
+                    *reinterpret_cast<float4 *>(Q + (int64_t)row * W + cl) = make_float4(q[0].x, q[0].y, q[1].x, q[1].y);
+                else
+                    Q[(int64_t)row * W + cl] = q[0];
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty);
+    }
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        red[(warp * 32 + lane) * 2 * VC + 2 * v] = mu[v].x;
+        red[(warp * 32 + lane) * 2 * VC + 2 * v + 1] = mu[v].y;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(NC * 32) : "memory");   // consumers only
+    if (warp == 0 && live) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            float s0 = 0.f, s1 = 0.f;
+            for (int w = 0; w < NC; ++w) {
+                s0 += red[(w * 32 + lane) * 2 * VC + 2 * v];
+                s1 += red[(w * 32 + lane) * 2 * VC + 2 * v + 1];
+            }
+            float *o = part + ((int64_t)blockIdx.y * W + cl + v) * 4;
+            o[0] = s0;
+            o[1] = s1;
+        }
+    }
+}
+
+// Shapes of the staged kernel by rows per group: two complex columns per
+// lane and 8 consumers for R <= 2; one column per lane and 4 consumers for
+// longer groups (3-dof elasticity: 81 union entries per group).
+template <int R> struct StagedShape;
+template <> struct StagedShape<2> { static constexpr int VC = 2, NC = 8, NS = 2; };
+template <> struct StagedShape<3> { static constexpr int VC = 1, NC = 4, NS = 2; };
+template <> struct StagedShape<4> { static constexpr int VC = 1, NC = 4, NS = 2; };
+
+template <int R>
+static size_t staged_smem_bytes(int emax) {
+    using S = StagedShape<R>;
+    const size_t slot = ((size_t)emax * 32 * S::VC * 8 + (size_t)emax * R * 16 + 127) & ~(size_t)127;
+    return 128 * ((2 * S::NC * S::NS * 8 + 127) / 128) + S::NC * S::NS * slot + (size_t)S::NC * 32 * 2 * S::VC * 4;
+}
+
+size_t spmm_staged_smem(const DevPencil &A) {
+    if (A.rg_rows < 2 || A.rg_rows > 4 || !A.rg_ab4 || !A.rg_dpos || A.rg_emax < 1 || A.rg_emax > 255) return 0;
+    size_t b = 0;
+    if (A.rg_rows == 2) b = staged_smem_bytes<2>(A.rg_emax);
+    else if (A.rg_rows == 3) b = staged_smem_bytes<3>(A.rg_emax);
+    else b = staged_smem_bytes<4>(A.rg_emax);
+    return b <= 227 * 1024 ? b : 0;
+}
+
+template <int R>
+static void launch_staged(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const float2 *sig, const float2 *P,
+                          float2 *Q, const int32_t *flag, float *part, int gy) {
+    using S = StagedShape<R>;
+    constexpr int CW = 32 * S::VC;
+    const int W = d.W();
+    const size_t smem = staged_smem_bytes<R>(A.rg_emax);
+    static bool raised[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !raised[dev]) {   // per device, before the first launch there
+        cudaFuncSetAttribute(k_spmm_staged<R, S::VC, S::NC, S::NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+        raised[dev] = true;
+    }
+    // about two waves of CTAs, each streaming a long contiguous range of row
+    // groups (long producer/consumer pipelines); at most gy rows of partials
+    const int gx = (W + CW - 1) / CW;
+    const int per_sm = std::max(1, (int)((228 * 1024) / (smem + 1024)));
+    int gy2 = A.spmm_gpb > 0 ? (A.rg_ngroups + A.spmm_gpb - 1) / A.spmm_gpb
+                             : (2 * per_sm * ctx.sm_count + gx - 1) / gx;
+    gy2 = std::max(1, std::min(gy2, std::min(gy, A.rg_ngroups)));
+    const int gpb = (A.rg_ngroups + gy2 - 1) / gy2;
+    dim3 grid(gx, gy2);
+    k_spmm_staged<R, S::VC, S::NC, S::NS><<<grid, 32 * (S::NC + 1), smem, ctx.stream>>>(
+        d.n, W, d.Lp, A.rg_ngroups, gpb, A.rg_emax, A.rg_ptr, A.rg_col, A.rg_ab4, A.rg_dpos, sig, P, Q, flag, part,
+        gy, A.dev_err);
+}
+
+// ---------------------------------------------------------------------------
 // update: r -= alpha q ; U += Re(ua p) ; partial |r|^2 and, with the Jacobi
 // preconditioner (JAC), z = M^{-1} r and partial r^T z (with multigrid the
 // cycle that follows forms z and r^T z).
@@ -705,6 +985,16 @@ void krylov_spmm(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const cplx<T
     const auto *abp =
         reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.ab32 : (const void *)A.ab64);
     ctx.before(KC_SHIFTED_SPMM, bytes, flops);
+    if constexpr (sizeof(T) == 4) {
+        if (A.spmm_kind == SPMM_STAGED && spmm_staged_smem(A) > 0) {
+            const float2 *s2 = reinterpret_cast<const float2 *>(sig);
+            if (A.rg_rows == 2) launch_staged<2>(ctx, d, A, s2, P, Q, flag, part, gy);
+            else if (A.rg_rows == 3) launch_staged<3>(ctx, d, A, s2, P, Q, flag, part, gy);
+            else launch_staged<4>(ctx, d, A, s2, P, Q, flag, part, gy);
+            ctx.after();
+            return;
+        }
+    }
     if (A.rg_rows > 1) {
         const int gpb = (A.rg_ngroups + gy - 1) / gy;
         const auto *uab = reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.rg_ab32

@@ -17,6 +17,7 @@
 //  * the int32 sums are converted to FP64 once per (CTA, d) and the K-slices
 //    are reduced in a fixed order.
 // With S = 7 the truncation error is ~2^-50 relative to max|X_a| max|Y_b| n.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -224,16 +225,292 @@ __global__ void k_oz_reduce(int m, int split, const double *__restrict__ work, c
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-core (tcgen05) form of the same Gram.
+//
+// The digits are the seven balanced base-128 digits above, stored as bf16
+// (|D| <= 64 is exact in bf16) and multiplied by tcgen05.mma (kind::f16, bf16
+// operands, FP32 accumulation in tensor memory).  A digit product is at most
+// 2^12 and a diagonal d sums at most 7 of them per row of K, so with K-slices
+// of at most 512 rows every partial sum stays below 2^24 and the FP32
+// accumulation is exact; the seven diagonals live in seven TMEM accumulators
+// and are combined in FP64 once per K-slice, then the K-slices are reduced in
+// a fixed order (k_oz_reduce).
+//
+// Operand "panel" layout (UMMA canonical K-major, no swizzle): an operand
+// with R rows (the M or N side) and depth K is stored per digit s, K-step of
+// 32, and 64-row panel as 8 x 4 core matrices of 8 rows x 8 K-elements
+// (128 contiguous bytes, row r at 16 r):
+//   [s][ks][panel][row%64 / 8][k%32 / 8][row%8][k%8]
+// so one (digit, K-step) block of consecutive panels is contiguous, the
+// 8-row groups of consecutive panels are 512 bytes apart (the descriptor's
+// stride offset) and K-adjacent cores 128 bytes apart (its leading offset).
+// ---------------------------------------------------------------------------
+constexpr int TC_KSTEP = 32;        // K rows per pipeline stage
+constexpr int TC_KSLICE = 512;      // K rows per CTA (exact FP32 accumulation)
+constexpr int TC_TM = 128, TC_TN = 64;
+constexpr unsigned TC_STAGE_A = OZ_S * 8192u, TC_STAGE_B = OZ_S * 4096u;
+constexpr int TC_NS = 2;
+// (16 KB of slack after the stages: no operand read can leave the allocation)
+constexpr size_t TC_SMEM = 1024 + TC_NS * (size_t)(TC_STAGE_A + TC_STAGE_B) + 16384;
+
+// digits of X (rows i < n, columns a < m, exponents e[a]) into the panel
+// layout with K = rows of X and the panel rows = columns a; zero padding to
+// ntr panels and nks K-steps.  One thread per (a, 8 consecutive i).
+__global__ void __launch_bounds__(256)
+k_oz_split_panel(int64_t n, int m, const double *__restrict__ X, int64_t ldx, const int *__restrict__ e, int64_t nks,
+                 int ntr, __nv_bfloat16 *__restrict__ out) {
+    const int a = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (a >= ntr * 64) return;
+    const int ea = a < m ? e[a] : 0;
+    for (int64_t i8 = blockIdx.y * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i8 < nks * 4;
+         i8 += (int64_t)gridDim.y * (blockDim.x >> 5)) {
+        int8_t d[8][OZ_S];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t i = i8 * 8 + k;
+            const double x = (i < n && a < m) ? X[i * ldx + a] : 0.0;
+            oz_digits(x, ea, d[k]);
+        }
+        const int64_t ks = i8 >> 2;
+        const int kc = (int)(i8 & 3);
+        const int panel = a >> 6, mg = (a & 63) >> 3, r = a & 7;
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) {
+            const int64_t core = (((int64_t)s * nks + ks) * ntr + panel) * 32 + mg * 4 + kc;
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __int2bfloat16_rn((int)d[k][s]);
+            *reinterpret_cast<uint4 *>(out + core * 64 + r * 8) = *reinterpret_cast<const uint4 *>(v);
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t umma_desc(unsigned smem_byte_addr) {
+    // K-major, no swizzle: leading offset 128 B (next K core), stride offset
+    // 512 B (next 8-row group), descriptor version 1 (bits 46-47)
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_byte_addr >> 4) & 0x3fff);
+    d |= (uint64_t)((128u >> 4) & 0x3fff) << 16;
+    d |= (uint64_t)((512u >> 4) & 0x3fff) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// M = 128, N = 64, bf16 x bf16 -> FP32, both operands K-major
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_TN >> 3) << 17) |
+                              ((uint32_t)(TC_TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(void *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// One CTA: output block a in [128 ta, +128), b in [64 tb, +64) of K-slice z
+// (rows [512 z, 512 z + 512)).  Warp 0: TMEM allocation and the bulk copies
+// of the digit panels; warp 1 lane 0: the MMAs; all four warps: epilogue
+// (thread = TMEM lane = row a).  work[z][a][b] (m x m per slice) receives
+// sum_d 2^(-7(d+2)) sum_{s+t=d} D_s^T E_t for a, b < m.
+__global__ void __launch_bounds__(128, 1)
+k_oz_gram_tc(int m, int nta, int ntb, int64_t nks, int ntrx, int ntry, const __nv_bfloat16 *__restrict__ PX,
+             const __nv_bfloat16 *__restrict__ PY, double *__restrict__ work, int symmetric, int32_t *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int ta = blockIdx.x / ntb, tb = blockIdx.x % ntb;
+    if (symmetric && tb < 2 * ta) return;   // block entirely below the diagonal
+    const int z = blockIdx.y;
+    const int64_t ks0 = (int64_t)z * (TC_KSLICE / TC_KSTEP);
+    const int nsteps = (int)min((int64_t)(TC_KSLICE / TC_KSTEP), nks - ks0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr unsigned long long LIMIT_NS = 1000000000ull;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem);   // full[2], empty[2], done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 64);
+    unsigned char *stA = smem + 1024;
+    unsigned char *stB = stA + TC_NS * TC_STAGE_A;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 * TC_NS + 1; ++i) mbar_init(bars + i, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tmem_slot);
+    unsigned long long *full = bars, *empty = bars + TC_NS, *done = bars + 2 * TC_NS;
+
+    if (warp == 0) {   // ---- producer: 7 A blocks (8 KB) and 7 B blocks (4 KB) per stage
+        for (int it = 0; it < nsteps; ++it) {
+            const int st = it % TC_NS, u = it / TC_NS;
+            int ok = 1;
+            if (u > 0 && lane == 0) ok = mbar_wait_bounded(empty + st, (u - 1) & 1, LIMIT_NS);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                if (lane == 0) atomicExch(err, 3);
+                break;
+            }
+            if (lane == 0) mbar_expect_tx(full + st, TC_STAGE_A + TC_STAGE_B);
+            __syncwarp();
+            const int64_t ks = ks0 + it;
+            if (lane < OZ_S) {
+                const __nv_bfloat16 *src = PX + ((((int64_t)lane * nks + ks) * ntrx + 2 * ta) * 32) * 64;
+                bulk_g2s(stA + st * TC_STAGE_A + lane * 8192u, src, 8192u, full + st);
+            } else if (lane < 2 * OZ_S) {
+                const int t = lane - OZ_S;
+                const __nv_bfloat16 *src = PY + ((((int64_t)t * nks + ks) * ntry + tb) * 32) * 64;
+                bulk_g2s(stB + st * TC_STAGE_B + t * 4096u, src, 4096u, full + st);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {   // ---- MMA issuer
+        bool first = true;
+        for (int it = 0; it < nsteps; ++it) {
+            const int st = it % TC_NS, u = it / TC_NS;
+            if (!mbar_wait_bounded(full + st, u & 1, LIMIT_NS)) {
+                atomicExch(err, 4);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned a0 = smem_addr(stA + st * TC_STAGE_A), b0 = smem_addr(stB + st * TC_STAGE_B);
+            for (int d = 0; d < OZ_S; ++d)
+                for (int sd = 0; sd <= d; ++sd)
+#pragma unroll
+                    for (int k16 = 0; k16 < 2; ++k16) {
+                        const uint64_t ad = umma_desc(a0 + sd * 8192u + k16 * 256u);
+                        const uint64_t bd = umma_desc(b0 + (d - sd) * 4096u + k16 * 256u);
+                        umma_bf16(tmem + (uint32_t)(d * TC_TN), ad, bd, (first && sd == 0 && k16 == 0) ? 0u : 1u);
+                    }
+            first = false;
+            umma_commit(empty + st);   // stage free once these MMAs have read it
+        }
+        umma_commit(done);             // accumulators final once every MMA above completes
+    }
+    __syncwarp();
+    // ---- epilogue: thread = row a of the block (TMEM lane 32 warp + lane)
+    const bool ok = mbar_wait_bounded(done, 0, LIMIT_NS);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int a = ta * TC_TM + warp * 32 + lane;
+    double *W = work + (int64_t)z * m * m;
+    if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) atomicExch(err, 5);
+    } else {
+        for (int c16 = 0; c16 < TC_TN / 16; ++c16) {
+            double acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+            for (int d = 0; d < OZ_S; ++d) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TC_TN + c16 * 16), v);
+                const double scale = ldexp(1.0, -7 * (d + 2));
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = fma((double)v[j], scale, acc[j]);
+            }
+            if (a < m)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int b = tb * TC_TN + c16 * 16 + j;
+                    if (b < m) W[(int64_t)a * m + b] = acc[j];
+                }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+static void ozaki_gram_tc(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                          double *G, void *work, bool symmetric, int32_t *err) {
+    const int64_t nks = (n + TC_KSTEP - 1) / TC_KSTEP;
+    const int nta = (m + TC_TM - 1) / TC_TM, ntb = (m + TC_TN - 1) / TC_TN;
+    const int ntrx = 2 * nta, ntry = ntb;
+    const int nz = (int)((nks * TC_KSTEP + TC_KSLICE - 1) / TC_KSLICE);
+    char *w = reinterpret_cast<char *>(work);
+    __nv_bfloat16 *PX = reinterpret_cast<__nv_bfloat16 *>(w);
+    __nv_bfloat16 *PY = PX + (size_t)OZ_S * nks * ntrx * 2048;
+    char *tail = reinterpret_cast<char *>(PY + (size_t)OZ_S * nks * ntry * 2048);
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(tail);
+    int *ex = reinterpret_cast<int *>(mb + 2 * m);
+    int *ey = ex + m;
+    double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(ey + m) + 16 - ((uintptr_t)(ey + m) & 15));
+    static bool raised[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !raised[dev]) {
+        cudaFuncSetAttribute(k_oz_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        raised[dev] = true;
+    }
+    cudaMemsetAsync(mb, 0, 2 * (size_t)m * sizeof(unsigned long long), ctx.stream);
+    const dim3 cgrid((m + 31) / 32, 64), cblock(32, 8);
+    ctx.before(KC_GRAM, 8.0 * (double)n * m * 2, 0);
+    k_oz_colmax<<<cgrid, cblock, 0, ctx.stream>>>(n, m, X, ldx, mb);
+    k_oz_colmax<<<cgrid, cblock, 0, ctx.stream>>>(n, m, Y, ldy, mb + m);
+    k_oz_exponent<<<(2 * m + 127) / 128, 128, 0, ctx.stream>>>(2 * m, mb, ex);
+    ctx.after();
+    const unsigned gy_split = (unsigned)std::min<int64_t>((nks * 4 + 7) / 8, 8192);
+    ctx.before(KC_GRAM, 8.0 * (double)n * m * 2 + 2.0 * OZ_S * nks * TC_KSTEP * 64.0 * (ntrx + ntry), 0);
+    k_oz_split_panel<<<dim3(ntrx * 2, gy_split), 256, 0, ctx.stream>>>(n, m, X, ldx, ex, nks, ntrx, PX);
+    k_oz_split_panel<<<dim3(ntry * 2, gy_split), 256, 0, ctx.stream>>>(n, m, Y, ldy, ey, nks, ntry, PY);
+    ctx.after();
+    const int live = symmetric ? [&] {
+        int c = 0;
+        for (int a = 0; a < nta; ++a)
+            for (int b = 0; b < ntb; ++b) c += b >= 2 * a;
+        return c;
+    }() : nta * ntb;
+    const double pairs = OZ_S * (OZ_S + 1) / 2.0;
+    ctx.before(KC_GRAM, 2.0 * OZ_S * (double)nks * TC_KSTEP * 64.0 * (2.0 * live + live) + 8.0 * nz * m * m,
+               2.0 * pairs * (double)live * TC_TM * TC_TN * nks * TC_KSTEP);
+    k_oz_gram_tc<<<dim3(nta * ntb, nz), 128, TC_SMEM, ctx.stream>>>(m, nta, ntb, nks, ntrx, ntry, PX, PY, part,
+                                                                    symmetric ? 1 : 0, err);
+    ctx.after();
+    ctx.before(KC_GRAM, 8.0 * (double)nz * m * m, 0);
+    k_oz_reduce<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, ctx.stream>>>(m, nz, part, ex, ey, G, m,
+                                                                                    symmetric ? 1 : 0);
+    ctx.after();
+}
+
+// ---------------------------------------------------------------------------
 size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count) {
     const int64_t npad = (n + 63) / 64 * 64;
     const int mpad = (m + OZ_TM - 1) / OZ_TM * OZ_TM;
     const size_t slices = 2 * (size_t)OZ_S * mpad * npad;
     const size_t split = (size_t)sm_count * 4;
-    return slices + split * m * m * sizeof(double) + 2 * (size_t)m * (sizeof(int) + 8) + 1024;
+    const size_t mma_sync = slices + split * m * m * sizeof(double) + 2 * (size_t)m * (sizeof(int) + 8) + 1024;
+    // tensor-core form: bf16 digit panels of both operands and one m x m partial per 512-row slice
+    const int64_t nks = (n + TC_KSTEP - 1) / TC_KSTEP;
+    const int nta = (m + TC_TM - 1) / TC_TM, ntb = (m + TC_TN - 1) / TC_TN;
+    const int64_t nz = (nks * TC_KSTEP + TC_KSLICE - 1) / TC_KSLICE;
+    const size_t tc = (size_t)OZ_S * nks * (2 * nta + ntb) * 2048 * sizeof(__nv_bfloat16) +
+                      (size_t)nz * m * m * sizeof(double) + 2 * (size_t)m * (sizeof(int) + 8) + 1024;
+    return std::max(mma_sync, tc);
 }
 
 void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
-                void *work, bool symmetric) {
+                void *work, bool symmetric, int32_t *tc_err) {
+    if (tc_err) {   // tensor-core form (tcgen05)
+        ozaki_gram_tc(ctx, n, m, X, ldx, Y, ldy, G, work, symmetric, tc_err);
+        return;
+    }
     const int64_t npad = (n + 63) / 64 * 64;
     const int mpad = (m + OZ_TM - 1) / OZ_TM * OZ_TM;
     char *w = reinterpret_cast<char *>(work);

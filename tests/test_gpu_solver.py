@@ -9,7 +9,7 @@ import scipy.linalg as la
 
 from oracle import filter as ofilt
 from oracle import inertia, poles
-from workloads import config_pencil, interval_for, pencil_1d, pencil_2d_q1, start_block
+from workloads import config_pencil, interval_for, pencil_1d, pencil_2d_q1, pencil_3d_elasticity, start_block
 
 pytestmark = pytest.mark.gpu
 
@@ -110,14 +110,48 @@ def test_subspace_1d_config(api, prec):
     np.testing.assert_allclose(Xh[:, :20].T @ (p.B() @ Xh[:, :20]), np.eye(20), atol=1e-10)
 
 
-def test_subspace_2d_small_matches_dense(api):
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_subspace_2d_small_matches_dense(api, kernel):
+    # shifted product kernel 0 = autotuned, 1 = row groups, 2 = staged
     p = pencil_2d_q1(40, seed=21)          # n = 1521
     lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
     nev = 30
     gamma = 0.5 * (lam[nev - 1] + lam[nev])
     s, w = poles.slrf_poles(4, 1.0, 0.01, gamma)
     V0 = start_block(p.n, 45, 7)
-    h = api.Handle(p)
+    h = api.Handle(p, api.default_opts(spmm_kernel=kernel))
+    theta, X, resid, nconv, st, rep = h.subspace_iterate(api.Filter(s, w), gamma, torch.from_numpy(V0).cuda())
+    assert st == api.OK and nconv == nev == inertia.count_below_sparse(p.A(), p.B(), gamma)
+    _check_eigs(theta.cpu().numpy(), resid.cpu().numpy(), lam, nev)
+
+
+@pytest.mark.parametrize("ozaki", [2, 1, 0])
+def test_subspace_2d_each_gram_path_matches_dense(api, ozaki):
+    # projection Grams on tcgen05 (2), mma.sync (1) or FP64 CUDA cores (0)
+    p = pencil_2d_q1(36, seed=5)           # n = 1225
+    lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
+    nev = 25
+    gamma = 0.5 * (lam[nev - 1] + lam[nev])
+    s, w = poles.slrf_poles(4, 1.0, 0.01, gamma)
+    V0 = start_block(p.n, 38, 9)
+    h = api.Handle(p, api.default_opts(gram_ozaki=ozaki))
+    theta, X, resid, nconv, st, rep = h.subspace_iterate(api.Filter(s, w), gamma, torch.from_numpy(V0).cuda())
+    assert st == api.OK and nconv == nev
+    _check_eigs(theta.cpu().numpy(), resid.cpu().numpy(), lam, nev)
+    Xh = X.cpu().numpy()[:, :nev]
+    np.testing.assert_allclose(Xh.T @ (p.B() @ Xh), np.eye(nev), atol=1e-10)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_subspace_3d_small_matches_dense(api, kernel):
+    # 3-dof node groups (81 union entries each): the staged kernel's long-list shape
+    p = pencil_3d_elasticity(7, seed=13)   # n = 7 * 7 * 6 * 3 = 882
+    lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
+    nev = 24
+    gamma = 0.5 * (lam[nev - 1] + lam[nev])
+    s, w = poles.slrf_poles(4, 1.0, 0.01, gamma)
+    V0 = start_block(p.n, 36, 8)
+    h = api.Handle(p, api.default_opts(spmm_kernel=kernel))
     theta, X, resid, nconv, st, rep = h.subspace_iterate(api.Filter(s, w), gamma, torch.from_numpy(V0).cuda())
     assert st == api.OK and nconv == nev == inertia.count_below_sparse(p.A(), p.B(), gamma)
     _check_eigs(theta.cpu().numpy(), resid.cpu().numpy(), lam, nev)

@@ -28,16 +28,19 @@ def _cplx_block(n, N, m, ldp, seed):
     return P
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec,kernel", [("fp32", 1), ("fp32", 2), ("fp64", 1)])
 @pytest.mark.parametrize("pencil,N,m,rows", [("2d", 3, 37, 0), ("3d", 2, 10, 0), ("1d", 1, 1, 0), ("2d", 9, 5, 0),
-                                             ("2d", 2, 12, 1), ("2d", 2, 12, 3), ("2d", 4, 6, 4), ("3d", 1, 4, 2)])
-def test_shifted_spmm_matches_oracle(api, prec, pencil, N, m, rows):
+                                             ("2d", 2, 12, 1), ("2d", 2, 12, 3), ("2d", 4, 6, 4), ("3d", 1, 4, 2),
+                                             ("2d", 4, 150, 0), ("3d", 3, 33, 0)])
+def test_shifted_spmm_matches_oracle(api, prec, kernel, pencil, N, m, rows):
+    # kernel 1: row groups gathered by every warp; 2: staged (bulk copies into
+    # shared memory by a producer warp); both against the oracle's product
     p = {"2d": lambda: pencil_2d_q1(23, seed=4), "3d": lambda: pencil_3d_elasticity(5, seed=2),
          "1d": lambda: pencil_1d(77)}[pencil]()
     s, w = poles.quadrature_poles("gauss_legendre", N, 300.0)
     ldp = m + (m & 1)
     P = _cplx_block(p.n, N, m, ldp, 1)
-    h = api.Handle(p, api.default_opts(spmm_rows=rows))
+    h = api.Handle(p, api.default_opts(spmm_rows=rows, spmm_kernel=kernel))
     f = api.Filter(s, w)
     cdt = np.complex64 if prec == "fp32" else np.complex128
     Pd = torch.from_numpy(P.astype(cdt).view(np.float32 if prec == "fp32" else np.float64).copy()).cuda()
@@ -69,8 +72,8 @@ def test_spmm_ab_matches_scipy(api, m):
     np.testing.assert_allclose(Z.cpu().numpy(), p.B() @ X, rtol=1e-13, atol=1e-13 * np.abs(p.B() @ X).max())
 
 
-@pytest.mark.parametrize("ozaki", [1, 0])
-@pytest.mark.parametrize("n,m", [(1000, 1), (5000, 64), (20011, 150), (3001, 77), (70000, 65)])
+@pytest.mark.parametrize("ozaki", [2, 1, 0])
+@pytest.mark.parametrize("n,m", [(1000, 1), (5000, 64), (20011, 150), (3001, 77), (70000, 65), (4099, 300)])
 def test_gram_matches_numpy(api, n, m, ozaki):
     p = pencil_1d(n)
     X = start_block(n, m, 1)
@@ -81,14 +84,15 @@ def test_gram_matches_numpy(api, n, m, ozaki):
     assert np.abs(G - ref).max() <= 1e-13 * np.abs(X).max() * np.abs(Y).max() * n
 
 
-def test_ozaki_gram_graded_columns(api):
+@pytest.mark.parametrize("ozaki", [2, 1])
+def test_ozaki_gram_graded_columns(api, ozaki):
     # columns spanning 16 orders of magnitude, zero and subnormal-free tiny columns
     n, m = 9000, 40
     rng = np.random.default_rng(3)
     X = start_block(n, m, 4) * 10.0 ** rng.uniform(-8, 8, m)[None, :]
     Y = start_block(n, m, 5) * 10.0 ** rng.uniform(-8, 8, m)[None, :]
     X[:, 3] = 0.0
-    h = api.Handle(pencil_1d(n), api.default_opts(gram_ozaki=1))
+    h = api.Handle(pencil_1d(n), api.default_opts(gram_ozaki=ozaki))
     G = h.gram(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()).cpu().numpy()
     ref = X.T @ Y
     bound = 1e-13 * np.abs(X).max(axis=0)[:, None] * np.abs(Y).max(axis=0)[None, :] * n
