@@ -916,6 +916,8 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         if (!bcg) {
             CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
             kb.Z = as<cplx<T>>(h->kZ);
+            // the update forms the cycle's gathered block y = D r (finest level)
+            if (mg_of<T>(h).nlev > 1) kb.mgd = mg_of<T>(h).lv[0].dinv;
         }
     } else {
         const PoleSet<T> ps = make_poleset<T>(f);
@@ -963,7 +965,7 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
             krylov_spmm<T>(ctx, d, h->A, sig, kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
             krylov_reduce_alpha<T>(ctx, d, kb);
             krylov_update<T>(ctx, d, kb);
-            if (use_mg) mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q);
+            if (use_mg) mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q, kb.Q);
             krylov_reduce_beta<T>(ctx, d, kb, tol2, maxit);
             krylov_direction<T>(ctx, d, kb);
         }
@@ -1390,8 +1392,8 @@ slrf_status precond_apply_t(slrf_handle *h, const slrf_filter *f, KrylovDims &d,
     }
     if (use_mg) {
         MgSolve<T> &mg = mg_of<T>(h);
-        if (mg.nlev == 1) CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
-        mg_apply<T>(ctx, d, mg, sig, kb.s.flag, kb.s.part, kb.gy, Rb, Zb, mg.nlev == 1 ? as<cplx<T>>(h->kQ) : nullptr);
+        CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
+        mg_apply<T>(ctx, d, mg, sig, kb.s.flag, kb.s.part, kb.gy, Rb, Zb, as<cplx<T>>(h->kQ));
     } else {
         krylov_dinv<T>(ctx, h->A, make_poleset<T>(f),
                        h->opts.precond == SLRF_PRECOND_NONE ? SLRF_PRECOND_NONE : SLRF_PRECOND_JACOBI, kb.dinv);

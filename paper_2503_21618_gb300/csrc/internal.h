@@ -102,6 +102,8 @@ struct KrylovBuffers {
     cplx<T> *dinv;                       // n x N Jacobi inverse diagonal
     T *Uacc;                             // n x Lp accumulation of the filter output
     cplx<T> *Z = nullptr;                // n x W preconditioned residual (multigrid); nullptr: Jacobi
+    const cplx<T> *mgd = nullptr;        // multigrid: finest damped Jacobi diagonal (n x N); the
+                                         // update then also writes y = mgd r into Q (Q is dead there)
     KrylovScalars<T> s;
     int gy;                              // row groups of the kernels
 };
@@ -195,12 +197,14 @@ template <typename T> struct MgSolve {
 };
 template <typename T>
 void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps);
-// Z0 = cycle(R0) for all active columns of the state; T0 is an n x W
-// scratch block (used only by a single-level hierarchy); part receives the
-// partial sums r^T z (slots 0, 1).
+// Z0 = cycle(R0) for all active columns of the state; part receives the
+// partial sums r^T z (slots 0, 1).  Y0 = D R0 with the finest level's
+// damped Jacobi diagonal (mg.lv[0].dinv), if the caller has it (the COCG
+// update forms it); otherwise it is formed into T0, an n x W scratch block
+// (also the scratch of a single-level hierarchy).
 template <typename T>
 void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig, const int32_t *flag, T *part,
-              int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0);
+              int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0, const cplx<T> *Y0 = nullptr);
 // part = partial sums r^T z per column (slots 0, 1) of two state blocks
 template <typename T>
 void mg_rz(Ctx &ctx, const KrylovDims &d, int gy, const cplx<T> *R, const cplx<T> *Z, const int32_t *flag, T *part);

@@ -664,10 +664,13 @@ static void launch_staged(Ctx &ctx, const KrylovDims &d, const DevPencil &A, con
 // One thread owns VC columns of one pole-slot c and walks all N poles, so the
 // pole sum of the filter is formed in registers.
 // ---------------------------------------------------------------------------
-template <typename T, int VC, int NP, bool JAC>
+// With the multigrid preconditioner (MGY) the update also writes y = D r
+// (D: the cycle's finest damped Jacobi diagonal) over Q, which is dead once
+// read here: the block the cycle's gathered products read.
+template <typename T, int VC, int NP, bool JAC, bool MGY>
 __global__ void __launch_bounds__(32 * TY)
 k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__restrict__ P,
-         const cplx<T> *__restrict__ Q, const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ alpha,
+         cplx<T> *__restrict__ Q, const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ alpha,
          const cplx<T> *__restrict__ ua, const int32_t *__restrict__ flag, T *__restrict__ U,
          T *__restrict__ part) {
     using C = cplx<T>;
@@ -706,7 +709,7 @@ k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__
                 const CV<T, VC> p = ldcv(P + base);
                 const CV<T, VC> q = ldcv(Q + base);
                 C dv = mk((T)0, (T)0);
-                if (JAC) dv = dinv[(int64_t)row * N + j];
+                if (JAC || MGY) dv = dinv[(int64_t)row * N + j];
 #pragma unroll
                 for (int v = 0; v < VC; ++v) {
                     if (!(mj & (1u << v))) continue;
@@ -723,6 +726,12 @@ k_update(int n, int W, int Lp, int N, cplx<T> *__restrict__ R, const cplx<T> *__
                     acc[j][v][2] += cabs2(r.v[v]);
                 }
                 stcv(R + base, r);
+                if (MGY) {
+                    CV<T, VC> y;
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) y.v[v] = cmul(dv, r.v[v]);
+                    stcv(Q + base, y);
+                }
             }
 #pragma unroll
             for (int v = 0; v < VC; ++v) {
@@ -1028,14 +1037,21 @@ static void launch_update(Ctx &ctx, const KrylovDims &d, KrylovBuffers<T> &kb) {
     const int W = d.W();
     dim3 grid((d.Lp / VC + 31) / 32, kb.gy), block(32, TY);
     const double vb = (double)d.n * W * d.frac * sizeof(cplx<T>);
-    ctx.before(KC_KRYLOV_UPDATE, 4 * vb + 2.0 * d.n * d.Lp * sizeof(T) + (double)d.n * d.N * sizeof(cplx<T>),
+    ctx.before(KC_KRYLOV_UPDATE,
+               (kb.mgd ? 5 : 4) * vb + 2.0 * d.n * d.Lp * sizeof(T) + (double)d.n * d.N * sizeof(cplx<T>),
                16.0 * d.n * W * d.frac);
-    if (kb.Z)
-        k_update<T, VC, NP, false><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv,
-                                                                    kb.s.alpha, kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
+    if (kb.Z && kb.mgd)
+        k_update<T, VC, NP, false, true><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.mgd,
+                                                                          kb.s.alpha, kb.s.ua, kb.s.flag, kb.Uacc,
+                                                                          kb.s.part);
+    else if (kb.Z)
+        k_update<T, VC, NP, false, false><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q,
+                                                                           kb.dinv, kb.s.alpha, kb.s.ua, kb.s.flag,
+                                                                           kb.Uacc, kb.s.part);
     else
-        k_update<T, VC, NP, true><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv,
-                                                                   kb.s.alpha, kb.s.ua, kb.s.flag, kb.Uacc, kb.s.part);
+        k_update<T, VC, NP, true, false><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, kb.R, kb.P, kb.Q, kb.dinv,
+                                                                          kb.s.alpha, kb.s.ua, kb.s.flag, kb.Uacc,
+                                                                          kb.s.part);
     ctx.after();
 }
 

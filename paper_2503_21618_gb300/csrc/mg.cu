@@ -17,8 +17,9 @@
 // With F = (M - D^{-1}) P (a pair matrix like the pencil's: F_a - sigma F_b)
 // the two ends fold into one gathered product each, and neither the fine
 // residual nor z1 is ever stored:
-//   r1 = -F^T (D r)                         k_mg_sspmm<DOWN>  (coarse rows)
-//   z  = D (2 r - M (D r) - F e),  r^T z    k_mg_sspmm<UP>    (fine row groups)
+//   r1 = -F^T y                             k_mg_sspmm<DOWN>  (coarse rows)
+//   z  = D (2 r - M y - F e),  r^T z        k_mg_sspmm<UP>    (fine row groups)
+// with y = D r formed once (fused into the Krylov update that produces r).
 // (P^T (I - M D) = -((M - D^{-1}) P)^T D and (I - D M) P = -D F.)  The fine
 // level is read twice and written once per cycle.
 // Coarser levels run nu sweeps on each side and gamma coarse visits
@@ -72,38 +73,25 @@ __device__ __forceinline__ bool col_active(const int32_t *flag, int c0) {
 }
 
 // One segment of a row group's union column list [e0, e1): gathers x_k = X[k]
-// (times D_kj if SCALE) and accumulates sa[r] += a_rk x_k, sb[r] += b_rk x_k.
-// measured on the 2D bench: 2-deep gathers at 6 CTAs per SM beat 4-deep at 4
-// (125 vs 134 ms per solve) and 8-deep (155 ms)
-template <typename T, int VC, int R, bool SCALE>
+// and accumulates sa[r] += a_rk x_k, sb[r] += b_rk x_k.  Full batches of UNR
+// entries issue all their index loads, then all their gathers, then the FMAs
+// (UNR gathers in flight per warp), and a remainder loop takes the rest.
+template <typename T, int VC, int R, int UNR>
 __device__ __forceinline__ void seg_accum(int e0, int e1, const int32_t *__restrict__ ucol,
                                           const cplx<T> *__restrict__ uab, const cplx<T> *__restrict__ X, int W,
-                                          int c0, const cplx<T> *__restrict__ dinv, int N, int j,
-                                          cplx<T> (&sa)[R][VC], cplx<T> (&sb)[R][VC]) {
+                                          int c0, cplx<T> (&sa)[R][VC], cplx<T> (&sb)[R][VC]) {
     using C = cplx<T>;
-    constexpr int UNR = 2;
-    for (int e = e0; e < e1; e += UNR) {
+    const cplx<T> *Xc = X + c0;
+    int e = e0;
+    for (; e + UNR <= e1; e += UNR) {
         int cc[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) cc[u] = (e + u < e1) ? __ldg(ucol + e + u) : -1;
+        for (int u = 0; u < UNR; ++u) cc[u] = __ldg(ucol + e + u);
         CV<T, VC> x[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            if (cc[u] >= 0) {
-                x[u] = ldcv(X + (int64_t)cc[u] * W + c0);
-                if (SCALE) {
-                    const C dk = dinv[(int64_t)cc[u] * N + j];
+        for (int u = 0; u < UNR; ++u) x[u] = ldcv(Xc + (int64_t)cc[u] * W);
 #pragma unroll
-                    for (int v = 0; v < VC; ++v) x[u].v[v] = cmul(dk, x[u].v[v]);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < VC; ++v) x[u].v[v] = mk((T)0, (T)0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            if (cc[u] < 0) break;
+        for (int u = 0; u < UNR; ++u)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const C w = __ldg(uab + (int64_t)(e + u) * R + r);
@@ -115,6 +103,19 @@ __device__ __forceinline__ void seg_accum(int e0, int e1, const int32_t *__restr
                     sb[r][v].y = fma(w.y, x[u].v[v].y, sb[r][v].y);
                 }
             }
+    }
+    for (; e < e1; ++e) {
+        const CV<T, VC> x = ldcv(Xc + (int64_t)__ldg(ucol + e) * W);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const C w = __ldg(uab + (int64_t)e * R + r);
+#pragma unroll
+            for (int v = 0; v < VC; ++v) {
+                sa[r][v].x = fma(w.x, x.v[v].x, sa[r][v].x);
+                sa[r][v].y = fma(w.x, x.v[v].y, sa[r][v].y);
+                sb[r][v].x = fma(w.y, x.v[v].x, sb[r][v].x);
+                sb[r][v].y = fma(w.y, x.v[v].y, sb[r][v].y);
+            }
         }
     }
 }
@@ -125,10 +126,15 @@ __device__ __forceinline__ void seg_accum(int e0, int e1, const int32_t *__restr
 // y = (sa - sigma sb) the gathered shifted product of the group's rows:
 //   RESID : out = r - M x
 //   SMOOTH: out = x + D (r - M x), optional partial r^T out per column
-//   DOWN  : out = -F^T (D x)               (rows: coarse; gathers: fine x, D)
-//   UP    : out = D (2 r - M (D r) - F e),  (x = r; second list: F over e)
-//           optional partial r^T out
+//   DOWN  : out = -F^T y                   (rows: coarse; gathers: fine y = D r)
+//   UP    : out = D (2 r - M y - F e),      (gathers y = D r and, by the
+//           second list, F over e), optional partial r^T out
+// The finest-level block y = D r is formed once per cycle (by the Krylov
+// update, or k_mg_scale), so the gathers carry no per-entry diagonal.
 // ---------------------------------------------------------------------------
+// 40 registers, 6 resident CTAs per SM: measured on the 2D bench, the finest
+// UP product of row groups runs faster there (282 us per launch, with some
+// spills) than at 64 registers and 4 CTAs without spills (323 us).
 template <typename T, int VC, int R, int MODE>
 __global__ void __launch_bounds__(32 * TY, 6)
 k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__ gptr,
@@ -139,7 +145,7 @@ k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__
            const cplx<T> *__restrict__ X2) {
     using C = cplx<T>;
     constexpr bool DOTS = MODE == MG_SMOOTH || MODE == MG_UP;
-    constexpr bool SCALE = MODE == MG_DOWN || MODE == MG_UP;
+    constexpr int UNR = (MODE == MG_DOWN) ? 4 : 2;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int ng = W / VC;
     const int cg = blockIdx.x * 32 + tx;
@@ -167,10 +173,9 @@ k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int v = 0; v < VC; ++v) sa[r][v] = sb[r][v] = mk((T)0, (T)0);
-            seg_accum<T, VC, R, SCALE>(__ldg(gptr + g), __ldg(gptr + g + 1), ucol, uab, X, W, c0, dinv, N, j, sa, sb);
+            seg_accum<T, VC, R, UNR>(__ldg(gptr + g), __ldg(gptr + g + 1), ucol, uab, X, W, c0, sa, sb);
             if constexpr (MODE == MG_UP)
-                seg_accum<T, VC, R, false>(__ldg(g2ptr + g), __ldg(g2ptr + g + 1), u2col, u2ab, X2, W, c0, dinv, N, j,
-                                           sa, sb);
+                seg_accum<T, VC, R, UNR>(__ldg(g2ptr + g), __ldg(g2ptr + g + 1), u2col, u2ab, X2, W, c0, sa, sb);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int row = g * R + r;
@@ -311,6 +316,28 @@ k_mg_jacobi0(int n, int W, int Lp, int N, const cplx<T> *__restrict__ dinv, cons
         const int64_t base = (int64_t)row * W + c0;
         const cplx<T> d = dinv[(int64_t)row * N + j];
         CV<T, VC> o = ldcv(Rv + base);
+#pragma unroll
+        for (int v = 0; v < VC; ++v) o.v[v] = cmul(d, o.v[v]);
+        stcv(Out + base, o);
+    }
+}
+
+// y = D x on the finest level (the block the DOWN / UP products gather)
+template <typename T, int VC>
+__global__ void __launch_bounds__(32 * TY)
+k_mg_scale(int n, int W, int Lp, int N, const cplx<T> *__restrict__ dinv, const cplx<T> *__restrict__ Xv,
+           cplx<T> *__restrict__ Out, const int32_t *__restrict__ flag) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    if (cg >= ng) return;
+    const int c0 = cg * VC;
+    if (!col_active<VC>(flag, c0)) return;
+    const int j = c0 / Lp;
+    for (int row = blockIdx.y * TY + ty; row < n; row += gridDim.y * TY) {
+        const int64_t base = (int64_t)row * W + c0;
+        const cplx<T> d = dinv[(int64_t)row * N + j];
+        CV<T, VC> o = ldcv(Xv + base);
 #pragma unroll
         for (int v = 0; v < VC; ++v) o.v[v] = cmul(d, o.v[v]);
         stcv(Out + base, o);
@@ -466,8 +493,8 @@ void launch_sspmm(Ctx &ctx, const KrylovDims &d, int kc, int n_rows, int R, int 
     dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
     const double vin = vec_bytes<T>(d, n_in), vout = vec_bytes<T>(d, n_rows);
     double bytes = 4.0 * (ngroups + 1) + (double)nnz_union * (4 + R * sizeof(cplx<T>)) + vin + vout;
-    if (MODE == MG_RESID || MODE == MG_SMOOTH) bytes += vout;                // r of the rows (UP: r is x)
-    if (MODE != MG_RESID) bytes += (double)n_in * d.N * sizeof(cplx<T>);   // D of the gathered rows
+    if (MODE == MG_RESID || MODE == MG_SMOOTH || MODE == MG_UP) bytes += vout;   // r of the rows
+    if (MODE == MG_SMOOTH || MODE == MG_UP) bytes += (double)n_rows * d.N * sizeof(cplx<T>);   // D of the rows
     if (MODE == MG_UP) bytes += 4.0 * (ngroups + 1) + (double)nnz2 * (4 + R * sizeof(cplx<T>)) + vec_bytes<T>(d, n2);
     ctx.before(kc, bytes, 8.0 * (double)(nnz_union + nnz2) * R * W * d.frac);
 #define SSP(RR)                                                                                                     \
@@ -595,8 +622,19 @@ void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps) {
 }
 
 template <typename T>
+void mg_scale(Ctx &ctx, const KrylovDims &d, const MgSolve<T> &mg, int gy, const cplx<T> *X, cplx<T> *Y,
+              const int32_t *flag) {
+    constexpr int VC = VecN<T>::VC;
+    const int W = d.W();
+    dim3 grid((W / VC + 31) / 32, gy), block(32, TY);
+    ctx.before(KC_MG_TRANSFER, 2 * vec_bytes<T>(d, d.n) + (double)d.n * d.N * sizeof(cplx<T>), 0);
+    k_mg_scale<T, VC><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, d.N, mg.lv[0].dinv, X, Y, flag);
+    ctx.after();
+}
+
+template <typename T>
 void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig, const int32_t *flag, T *part,
-              int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0) {
+              int gy, const cplx<T> *R0, cplx<T> *Z0, cplx<T> *T0, const cplx<T> *Y0) {
     if (mg.nlev == 1) {
         coarse_solve<T>(ctx, d, mg, R0, T0, Z0, flag);
         launch_rz<T>(ctx, d, gy, R0, Z0, flag, part);
@@ -604,14 +642,18 @@ void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig,
     }
     const MgLevel<T> &L = mg.lv[0];
     const MgLevel<T> &Lc = mg.lv[1];
-    // r1 = -F^T (D r)
+    if (!Y0) {   // y = D r into the scratch block
+        mg_scale<T>(ctx, d, mg, gy, R0, T0, flag);
+        Y0 = T0;
+    }
+    // r1 = -F^T y
     const int gyd = std::max(1, std::min(gy, (Lc.n + TY - 1) / TY));
     launch_sspmm<T, MG_DOWN>(ctx, d, KC_MG_FINE, Lc.n, 1, Lc.n, L.fd_ptr, L.fd_col, L.f_ab + L.fu_nnz * L.R,
-                             L.fd_nnz, L.n, gyd, sig, L.dinv, R0, nullptr, Lc.r, flag, nullptr);
+                             L.fd_nnz, L.n, gyd, sig, L.dinv, Y0, nullptr, Lc.r, flag, nullptr);
     cplx<T> *e = cycle<T>(ctx, d, mg, 1, gy, sig, flag);
-    // z = D (2 r - M (D r) - F e), r^T z
+    // z = D (2 r - M y - F e), r^T z
     launch_sspmm<T, MG_UP>(ctx, d, KC_MG_FINE, L.n, L.R, L.ngroups, L.gptr, L.gcol, L.ab, L.nnz_union, L.n, gy, sig,
-                           L.dinv, R0, R0, Z0, flag, part, L.fu_ptr, L.fu_col, L.f_ab, L.fu_nnz, e, Lc.n);
+                           L.dinv, Y0, R0, Z0, flag, part, L.fu_ptr, L.fu_col, L.f_ab, L.fu_nnz, e, Lc.n);
 }
 
 template <typename T>
@@ -622,7 +664,7 @@ void mg_rz(Ctx &ctx, const KrylovDims &d, int gy, const cplx<T> *R, const cplx<T
 #define INST(T)                                                                                                  \
     template void mg_dinv<T>(Ctx &, MgSolve<T> &, const PoleSet<T> &);                                           \
     template void mg_apply<T>(Ctx &, const KrylovDims &, MgSolve<T> &, const cplx<T> *, const int32_t *, T *,  \
-                              int, const cplx<T> *, cplx<T> *, cplx<T> *);                                      \
+                              int, const cplx<T> *, cplx<T> *, cplx<T> *, const cplx<T> *);                     \
     template void mg_rz<T>(Ctx &, const KrylovDims &, int, const cplx<T> *, const cplx<T> *, const int32_t *, T *);
 INST(float)
 INST(double)
