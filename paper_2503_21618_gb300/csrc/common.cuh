@@ -95,6 +95,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
+// Prefetch [p, p + bytes) into L2 with bulk prefetches of at most 32 KB, one
+// per lane of the calling (converged) warp; p 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void l2_prefetch_warp(const void *p, int64_t bytes, int lane) {
+    const char *c = reinterpret_cast<const char *>(p);
+    for (int64_t off = (int64_t)lane * 32768; off < bytes; off += 32 * 32768) {
+        const unsigned sz = (unsigned)((bytes - off) < 32768 ? (bytes - off) : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(sz) : "memory");
+    }
+}
+
 // ---------------------------------------------------------------------------
 // kernel classes (profiling buckets of slrf_report)
 // ---------------------------------------------------------------------------

@@ -298,6 +298,12 @@ k_spmm_shifted_rg(int n, int W, int Lp, int ngroups, int groups_per_block, const
     for (int v = 0; v < VC; ++v) mu[v] = mk((T)0, (T)0);
     const int g_begin = blockIdx.y * groups_per_block;
     const int g_end = min(ngroups, g_begin + groups_per_block);
+    if (blockIdx.x == 0 && ty == 0 && g_end > g_begin) {
+        // this CTA's slab of rows (whole rows, every column chunk) into L2 up
+        // front: their first gathers then hit L2 instead of DRAM
+        const int64_t r0 = (int64_t)g_begin * R, r1 = min((int64_t)n, (int64_t)g_end * R);
+        l2_prefetch_warp(P + r0 * W, (r1 - r0) * W * (int64_t)sizeof(C), tx);
+    }
     if (act) {
         for (int g = g_begin + ty; g < g_end; g += TY) {
             const int e0 = __ldg(gptr + g), e1 = __ldg(gptr + g + 1);

@@ -168,6 +168,17 @@ k_mg_sspmm(int n, int W, int Lp, int N, int ngroups, const int32_t *__restrict__
     // 2D solve)
     if (act) {
         for (int g = blockIdx.y * TY + ty; g < ngroups; g += gridDim.y * TY) {
+            if constexpr (MODE == MG_UP) {
+                // the grid's next band of row groups: this CTA's part of it,
+                // whole rows of the gathered block, moved into L2 ahead of use
+                if (blockIdx.x == 0 && ty == 0) {
+                    const int64_t gn = (int64_t)g + (int64_t)gridDim.y * TY;
+                    if (gn < ngroups) {
+                        const int64_t r0 = gn * R, r1 = min((int64_t)n, r0 + (int64_t)TY * R);
+                        l2_prefetch_warp(X + r0 * W, (r1 - r0) * W * (int64_t)sizeof(C), tx);
+                    }
+                }
+            }
             C sa[R][VC], sb[R][VC];
 #pragma unroll
             for (int r = 0; r < R; ++r)
