@@ -154,7 +154,12 @@ typedef struct {
                                by timing both on the first solve (the choice is
                                kept for the process; the two differ only in the
                                rounding order of the partial dot products)    (0) */
-    int32_t reserved;
+    int32_t mg_exact;       /* MG, FP32 Krylov: the first level below the finest with
+                               at most this many unknowns (above the coarsest) ends
+                               the cycle and is solved exactly by its dense shifted
+                               inverses (A_l - sigma_j B_l)^{-1}, formed per solve on
+                               the GPU (N n_l^2 complex FP32 values); 0 = off, the
+                               cycle then descends to the coarsest level     (1536) */
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

@@ -46,7 +46,7 @@ class slrf_opts(C.Structure):
                 ("mg_nu", C.c_int32), ("mg_cycle", C.c_int32), ("mg_coarse", C.c_int32), ("mg_block", C.c_int32),
                 ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("mg_shift_limit", C.c_double),
                 ("stagnation_window", C.c_int32),
-                ("profile_mask", C.c_uint32), ("spmm_kernel", C.c_int32), ("reserved", C.c_int32)]
+                ("profile_mask", C.c_uint32), ("spmm_kernel", C.c_int32), ("mg_exact", C.c_int32)]
 
 
 class slrf_report(C.Structure):

@@ -1,5 +1,6 @@
 // C ABI of the slrf library: handle lifetime, workspace, and the drivers of
 // the hot path (Krylov solve loop, Cholesky-QR2 + Rayleigh-Ritz, Algorithm 1).
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -181,6 +182,13 @@ struct slrf_handle {
     const double *mg_fullV64 = nullptr;
     slrf::MgSolve<float> mg32;
     slrf::MgSolve<double> mg64;
+    Buf mgInv;                  // FP32 cycles: dense shifted inverses of the exact level + their work
+    // the poles, level and hierarchy the inverses in mgInv were formed for:
+    // the outer steps of one call reuse them instead of inverting again
+    std::vector<double> inv_key;
+    const void *inv_buf = nullptr;
+    int64_t mg_gen = 0;
+    cublasHandle_t cublas = nullptr;   // created on first use (coarse-level GEMMs)
     int32_t *h_pin = nullptr;   // pinned host words for polls
     int32_t *d_pin = nullptr;   // device alias of h_pin
     cudaEvent_t ev_poll = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
@@ -244,6 +252,8 @@ struct CallScope {
     slrf_handle *h;
     slrf_report *rep;
     explicit CallScope(slrf_handle *h_, slrf_report *r) : h(h_), rep(r) {
+        // every call forms its own exact-level inverses (reused by its outer steps only)
+        h->inv_key.clear();
         h->ctx.reset_counters();
         h->phase_k_used = h->phase_r_used = 0;
         cudaEventRecord(h->ev_t0, h->ctx.stream);
@@ -602,6 +612,7 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
     h->mg_coarse = h->opts.mg_coarse;
     h->mg_theta = h->opts.mg_theta;
     h->mg_ready = true;
+    ++h->mg_gen;
     return SLRF_OK;
 }
 
@@ -669,9 +680,19 @@ slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d
             c = l;
             break;
         }
+    // FP32 cycles: the first level below the finest (not the coarsest) with
+    // at most mg_exact unknowns ends the cycle with its dense shifted inverses
+    int e_inv = -1;
+    if (sizeof(T) == 4 && h->opts.mg_exact > 0)
+        for (int l = 1; l <= c && l < nfull - 1; ++l)
+            if (h->mg_host_lv[l].n <= h->opts.mg_exact) {
+                e_inv = l;
+                break;
+            }
+    if (e_inv >= 0) c = e_inv;
     const std::vector<double> *lam = &h->mg_lam;
     const T *V = reinterpret_cast<const T *>(sizeof(T) == 4 ? (const void *)h->mg_fullV32 : (const void *)h->mg_fullV64);
-    if (c < nfull - 1) {
+    if (e_inv < 0 && c < nfull - 1) {
         auto &E = h->mg_eig[c];
         const int ncl = h->mg_host_lv[c].n;
         if (E.lam.empty() && ncl > kMgExactMax) {
@@ -736,6 +757,44 @@ slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d
         mg.lv[l].dinv = l < mg.nlev - 1 ? reinterpret_cast<cplx<T> *>(base + o_d[l]) : nullptr;
     }
     mg.cinv = reinterpret_cast<cplx<T> *>(base + o_c);
+    mg.Minv = nullptr;
+    if (e_inv >= 0) {
+        if constexpr (sizeof(T) == 4) {
+            if (!h->cublas) {
+                if (cublasCreate(&h->cublas) != CUBLAS_STATUS_SUCCESS) {
+                    h->cublas = nullptr;
+                    g_last_error = "cublasCreate failed";
+                    return SLRF_ECUDA;
+                }
+            }
+            const size_t inv_bytes = (size_t)N * nc * nc * sizeof(cplx<T>);
+            const size_t inv_off = (inv_bytes + 255) / 256 * 256;
+            CKS(ensure(h, h->mgInv, inv_off + coarse_inverse_work_bytes(nc, N)));
+            float2 *Minv = reinterpret_cast<float2 *>(h->mgInv.p);
+            std::vector<double> key = {(double)e_inv, (double)nc, (double)h->mg_gen, (double)N};
+            for (int j = 0; j < N; ++j) {
+                key.push_back(f->sigma_re[j]);
+                key.push_back(f->sigma_im[j]);
+            }
+            if (key != h->inv_key || h->inv_buf != h->mgInv.p) {
+                const MgLevel<T> &Le = mg.lv[e_inv];
+                const int rc = coarse_inverse(h->ctx, h->cublas, nc, make_poleset<float>(f), Le.gptr, Le.gcol,
+                                              reinterpret_cast<const float2 *>(Le.ab), Minv,
+                                              reinterpret_cast<char *>(h->mgInv.p) + inv_off);
+                if (rc != 0) {
+                    h->inv_key.clear();
+                    g_last_error = "coarse inverse: cuBLAS status " + std::to_string(rc);
+                    return SLRF_ECUDA;
+                }
+                h->inv_key = key;
+                h->inv_buf = h->mgInv.p;
+            }
+            mg.Minv = reinterpret_cast<const cplx<T> *>(Minv);
+            mg.cublas = h->cublas;
+        }
+        mg_dinv<T>(h->ctx, mg, make_poleset<T>(f));
+        return SLRF_OK;
+    }
     // the previous solve of this handle synchronised before returning, so the
     // staging vector is free to be rewritten
     h->mg_cinv_host.resize((size_t)nc * N * sizeof(cplx<T>));
@@ -1347,6 +1406,12 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
         const size_t nh = (size_t)n / 2 + 1, nc = (size_t)mg_coarse;
         mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 200 * (size_t)nnz + nc * nc * 12 +
               nc * N * 2 * ts + 16 * 4096 + 768 * 768 * 12 + 768 * (size_t)N * 2 * ts;
+        // FP32 cycles ending at a level of at most mg_exact (1536) unknowns: its
+        // dense shifted inverses and their elimination work
+        if (precision == SLRF_PREC_MIXED) {
+            const size_t ne = std::min<size_t>(1536, (size_t)n);
+            mgb += (size_t)N * ne * ne * 8 + coarse_inverse_work_bytes((int)ne, N);
+        }
     }
     // BiCGStab keeps five more n x W blocks (r^, v, y, z, t)
     const size_t bcg = krylov == SLRF_KRYLOV_BICGSTAB ? 5 * (size_t)n * W * 2 * ts + 2 * W * 2 * ts : 0;
@@ -1383,6 +1448,7 @@ slrf_status precond_apply_t(slrf_handle *h, const slrf_filter *f, KrylovDims &d,
     CK(cudaMemcpyAsync(kb.s.flag, flags.data(), W * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
     CK(cudaMemcpyAsync(h->kSig.p, sg.data(), N * sizeof(cplx<T>), cudaMemcpyHostToDevice, ctx.stream));
     const cplx<T> *sig = as<cplx<T>>(h->kSig);
+    h->inv_key.clear();
     h->ctx.reset_counters();
     bool use_mg = uses_mg(h);
     if (use_mg) {
@@ -1457,6 +1523,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->mg_theta = 0.0;
     o->mg_shift_limit = 0.8;
     o->stagnation_window = 8;
+    o->mg_exact = 1536;
     return SLRF_OK;
 }
 
@@ -1474,6 +1541,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
     if (o->spmm_kernel < 0 || o->spmm_kernel > 2) return SLRF_EINVAL;
     if (o->gram_ozaki < 0 || o->gram_ozaki > 2) return SLRF_EINVAL;
+    if (o->mg_exact < 0 || o->mg_exact > 4096) return SLRF_EINVAL;
     return SLRF_OK;
 }
 
@@ -1580,6 +1648,8 @@ void slrf_destroy(slrf_handle *h) {
                    &h->mg_eig[12].dev, &h->mg_eig[13].dev, &h->mg_eig[14].dev, &h->mg_eig[15].dev};
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
+    if (h->mgInv.p) cudaFreeAsync(h->mgInv.p, h->ctx.stream);
+    if (h->cublas) cublasDestroy(h->cublas);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,       h->A.ab32,   h->A.ab64,
                    h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64,
                    h->A.rg_ab4, h->A.rg_dpos};

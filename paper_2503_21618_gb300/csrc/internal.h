@@ -194,9 +194,25 @@ template <typename T> struct MgSolve {
     MgLevel<T> lv[MG_MAX_LEVELS];
     const T *V = nullptr;         // coarsest eigenvectors, nc x nc row-major
     cplx<T> *cinv = nullptr;      // nc x N: 1 / (lambda_k - sigma_j)
+    // FP32 cycles may instead stop at a level solved by its dense shifted
+    // inverses (N matrices nc x nc, formed per solve by coarse_inverse);
+    // cublas is the handle's cuBLAS handle for their GEMMs
+    const cplx<T> *Minv = nullptr;
+    void *cublas = nullptr;
 };
 template <typename T>
 void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps);
+
+// ---------------------------------------------------------------- coarse.cu
+// Dense shifted inverses of one level: Minv_j = (A - sigma_j B)^{-1}, j < N,
+// n x n each (symmetric), from the level's CSR pairs, by blocked Gauss-Jordan
+// (GEMMs through cuBLAS handle `cublas`); work: coarse_inverse_work_bytes.
+size_t coarse_inverse_work_bytes(int n, int N);
+int coarse_inverse(Ctx &ctx, void *cublas, int n, const PoleSet<float> &ps, const int32_t *ptr, const int32_t *col,
+                   const float2 *ab, float2 *Minv, void *work);
+// Z_j = Minv_j R_j for every pole's columns of the level block (layout of the state)
+int coarse_inverse_apply(Ctx &ctx, void *cublas, const KrylovDims &d, int n, const float2 *Minv, const float2 *R,
+                         float2 *Z);
 // Z0 = cycle(R0) for all active columns of the state; part receives the
 // partial sums r^T z (slots 0, 1).  Y0 = D R0 with the finest level's
 // damped Jacobi diagonal (mg.lv[0].dinv), if the caller has it (the COCG

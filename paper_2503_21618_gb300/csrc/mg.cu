@@ -548,6 +548,12 @@ void launch_xfer(Ctx &ctx, const KrylovDims &d, int n_out, int n_in, int64_t nnz
 template <typename T>
 void coarse_solve(Ctx &ctx, const KrylovDims &d, const MgSolve<T> &mg, const cplx<T> *Rv, cplx<T> *Y, cplx<T> *Z,
                   const int32_t *flag) {
+    if constexpr (sizeof(T) == 4) {
+        if (mg.Minv) {   // dense shifted inverses of this level (FP32 cycles)
+            coarse_inverse_apply(ctx, mg.cublas, d, mg.nc, mg.Minv, Rv, Z);
+            return;
+        }
+    }
     const int nc = mg.nc, W = d.W();
     dim3 grid((W + 31) / 32, (nc + 31) / 32), block(32, 8);
     const double bytes = (double)nc * nc * sizeof(T) + 2.0 * vec_bytes<T>(d, nc);
