@@ -94,7 +94,17 @@ enum { SLRF_KRYLOV_COCG = 0, SLRF_KRYLOV_BICGSTAB = 1 };
  * not pay off for shifts deep inside the spectrum.  The paper's own solver
  * is ILU-preconditioned BiCGStab (Section 4.2.1); every option keeps the
  * preconditioner complex symmetric, as COCG requires. */
-enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1, SLRF_PRECOND_MG = 2, SLRF_PRECOND_AUTO = 3 };
+enum { SLRF_PRECOND_NONE = 0, SLRF_PRECOND_JACOBI = 1, SLRF_PRECOND_MG = 2, SLRF_PRECOND_AUTO = 3,
+       SLRF_PRECOND_ILU = 4 };
+/* ILU: incomplete factorisation of each shifted matrix A - sigma_j B on the
+ * pencil's own pattern (no fill), in the symmetric form L D L^T (L unit lower
+ * triangular, unconjugated transpose), built on the GPU per solve by
+ * ilu_sweeps fixed-point (Chow-Patel) sweeps from L = strict lower part
+ * scaled by the diagonal, D = diag; applied as z = P^T D^{-1} P r with
+ * P = I - N + N^2 - ... (ilu_tri_sweeps Jacobi sweeps of each triangular
+ * solve, N = L - I), a fixed complex symmetric operator.  The paper's solver
+ * is BiCGStab with ILU (drop tolerance 1e-4, RCM order; Section 4.2.1);
+ * this is its GPU-native no-fill form (no sequential triangular solves). */
 enum { SLRF_RULE_MIDPOINT = 0, SLRF_RULE_GAUSS_LEGENDRE = 1, SLRF_RULE_GAUSS_CHEBYSHEV = 2,
        SLRF_RULE_SLRF = 3 };
 
@@ -160,6 +170,8 @@ typedef struct {
                                inverses (A_l - sigma_j B_l)^{-1}, formed per solve on
                                the GPU (N n_l^2 complex FP32 values); 0 = off, the
                                cycle then descends to the coarsest level     (1536) */
+    int32_t ilu_sweeps;     /* ILU: fixed-point sweeps building the factors     (3) */
+    int32_t ilu_tri_sweeps; /* ILU: Jacobi sweeps of each triangular solve      (3) */
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

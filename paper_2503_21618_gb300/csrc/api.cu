@@ -182,6 +182,9 @@ struct slrf_handle {
     const double *mg_fullV64 = nullptr;
     slrf::MgSolve<float> mg32;
     slrf::MgSolve<double> mg64;
+    Buf iluPat, iluFac, kIluY;  // ILU preconditioner: pattern (once), factors (per call), sweep scratch
+    slrf::IluPattern ilu_pat;
+    bool ilu_ready = false;
     Buf mgInv;                  // FP32 cycles: dense shifted inverses of the exact level + their work
     // the poles, level and hierarchy the inverses in mgInv were formed for:
     // the outer steps of one call reuse them instead of inverting again
@@ -821,6 +824,35 @@ struct KStats {
     int mg_levels = 0;            // multigrid levels used (0: none)
 };
 
+// ILU preconditioner of one call: the pattern arrays once per handle (host
+// build from the device CSR), the factors of this call's poles.
+template <typename T>
+slrf_status ilu_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d, IluFactor<T> &fac) {
+    Ctx &ctx = h->ctx;
+    const int n = h->A.n;
+    if (!h->ilu_ready) {
+        std::vector<int32_t> rp(n + 1), ci(h->A.nnz);
+        CK(cudaMemcpyAsync(rp.data(), h->A.rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaMemcpyAsync(ci.data(), h->A.col, h->A.nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));
+        int64_t nnzl = 0;
+        const std::vector<int32_t> v = ilu_pattern_host(n, rp, ci, &nnzl);
+        CKS(ensure(h, h->iluPat, v.size() * sizeof(int32_t)));
+        CK(cudaMemcpyAsync(h->iluPat.p, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
+        CK(cudaStreamSynchronize(ctx.stream));   // pageable source
+        ilu_pattern_views(as<int32_t>(h->iluPat), n, nnzl, h->ilu_pat);
+        h->ilu_ready = true;
+    }
+    const int N = f->n_poles;
+    const size_t work = (ilu_factor_work_bytes(h->ilu_pat, N) + 255) / 256 * 256;
+    const size_t outb = ((size_t)N * h->ilu_pat.nnzl + (size_t)n * N) * sizeof(cplx<T>);
+    CKS(ensure(h, h->iluFac, work + outb));
+    CKS(ensure(h, h->kIluY, (size_t)n * d.W() * sizeof(cplx<T>)));
+    ilu_factor<T>(ctx, h->A, h->ilu_pat, make_poleset<double>(f), h->opts.ilu_sweeps, h->iluFac.p,
+                  reinterpret_cast<cplx<T> *>(reinterpret_cast<char *>(h->iluFac.p) + work), fac);
+    return SLRF_OK;
+}
+
 // Kernel choice of the FP32 shifted product (slrf_opts.spmm_kernel = 0):
 // both kernels are timed on this solve's blocks (one warm launch, then three
 // timed ones each) and the faster is kept, per device, pattern and column
@@ -971,13 +1003,17 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         CKS(mg_prepare<T>(h, f, d, kb, h->opts.precond == SLRF_PRECOND_AUTO, &usable));
         use_mg = usable;
     }
+    const bool use_ilu = !use_mg && h->opts.precond == SLRF_PRECOND_ILU;
+    IluFactor<T> ilu{};
+    if (use_ilu) CKS(ilu_prepare<T>(h, f, d, ilu));
+    cplx<T> *ilu_y = use_ilu ? as<cplx<T>>(h->kIluY) : nullptr;
+    if ((use_mg || use_ilu) && !bcg) {
+        CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
+        kb.Z = as<cplx<T>>(h->kZ);
+    }
     if (use_mg) {
-        if (!bcg) {
-            CKS(ensure(h, h->kZ, (size_t)n * W * sizeof(cplx<T>)));
-            kb.Z = as<cplx<T>>(h->kZ);
-            // the update forms the cycle's gathered block y = D r (finest level)
-            if (mg_of<T>(h).nlev > 1) kb.mgd = mg_of<T>(h).lv[0].dinv;
-        }
+        // the update forms the cycle's gathered block y = D r (finest level)
+        if (!bcg && mg_of<T>(h).nlev > 1) kb.mgd = mg_of<T>(h).lv[0].dinv;
     } else {
         const PoleSet<T> ps = make_poleset<T>(f);
         krylov_dinv<T>(ctx, h->A, ps, h->opts.precond == SLRF_PRECOND_NONE ? SLRF_PRECOND_NONE : SLRF_PRECOND_JACOBI,
@@ -990,6 +1026,10 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
         bicgstab_init<T>(ctx, d, kb, bb);
     } else if (use_mg) {
         mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q);
+        krylov_direction<T>(ctx, d, kb, 1);
+    } else if (use_ilu) {
+        ilu_apply<T>(ctx, d, h->ilu_pat, ilu, h->opts.ilu_tri_sweeps, kb.gy, kb.s.flag, kb.R, kb.Z, kb.Q, ilu_y,
+                     kb.s.part);
         krylov_direction<T>(ctx, d, kb, 1);
     }
     krylov_reduce_init<T>(ctx, d, kb);
@@ -1008,12 +1048,18 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
             // x, r ; rho', beta ; p
             if (use_mg)
                 mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.P, bb.Y, bb.Tt);
+            else if (use_ilu)
+                ilu_apply<T>(ctx, d, h->ilu_pat, ilu, h->opts.ilu_tri_sweeps, kb.gy, kb.s.flag, kb.P, bb.Y, bb.Tt,
+                             ilu_y, nullptr);
             else
                 bicgstab_precond_jacobi<T>(ctx, d, kb, kb.P, bb.Y);
             krylov_spmm<T>(ctx, d, h->A, sig, bb.Y, bb.V, kb.s.flag, kb.s.part, kb.gy);
             bicgstab_alpha<T>(ctx, d, kb, bb);
-            bicgstab_s<T>(ctx, d, kb, bb, !use_mg);
+            bicgstab_s<T>(ctx, d, kb, bb, !use_mg && !use_ilu);
             if (use_mg) mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, bb.Z, bb.Tt);
+            if (use_ilu)
+                ilu_apply<T>(ctx, d, h->ilu_pat, ilu, h->opts.ilu_tri_sweeps, kb.gy, kb.s.flag, kb.R, bb.Z, bb.Tt,
+                             ilu_y, nullptr);
             krylov_spmm<T>(ctx, d, h->A, sig, bb.Z, bb.Tt, kb.s.flag, kb.s.part, kb.gy);
             bicgstab_omega<T>(ctx, d, kb, bb);
             bicgstab_update<T>(ctx, d, kb, bb);
@@ -1025,6 +1071,9 @@ slrf_status krylov_solve(slrf_handle *h, const slrf_filter *f, int m, const doub
             krylov_reduce_alpha<T>(ctx, d, kb);
             krylov_update<T>(ctx, d, kb);
             if (use_mg) mg_apply<T>(ctx, d, mg_of<T>(h), sig, kb.s.flag, kb.s.part, kb.gy, kb.R, kb.Z, kb.Q, kb.Q);
+            if (use_ilu)
+                ilu_apply<T>(ctx, d, h->ilu_pat, ilu, h->opts.ilu_tri_sweeps, kb.gy, kb.s.flag, kb.R, kb.Z, kb.Q,
+                             ilu_y, kb.s.part);
             krylov_reduce_beta<T>(ctx, d, kb, tol2, maxit);
             krylov_direction<T>(ctx, d, kb);
         }
@@ -1460,6 +1509,12 @@ slrf_status precond_apply_t(slrf_handle *h, const slrf_filter *f, KrylovDims &d,
         MgSolve<T> &mg = mg_of<T>(h);
         CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
         mg_apply<T>(ctx, d, mg, sig, kb.s.flag, kb.s.part, kb.gy, Rb, Zb, as<cplx<T>>(h->kQ));
+    } else if (h->opts.precond == SLRF_PRECOND_ILU) {
+        IluFactor<T> ilu{};
+        CKS(ilu_prepare<T>(h, f, d, ilu));
+        CKS(ensure(h, h->kQ, (size_t)n * W * sizeof(cplx<T>)));
+        ilu_apply<T>(ctx, d, h->ilu_pat, ilu, h->opts.ilu_tri_sweeps, kb.gy, kb.s.flag, Rb, Zb, as<cplx<T>>(h->kQ),
+                     as<cplx<T>>(h->kIluY), kb.s.part);
     } else {
         krylov_dinv<T>(ctx, h->A, make_poleset<T>(f),
                        h->opts.precond == SLRF_PRECOND_NONE ? SLRF_PRECOND_NONE : SLRF_PRECOND_JACOBI, kb.dinv);
@@ -1524,6 +1579,8 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->mg_shift_limit = 0.8;
     o->stagnation_window = 8;
     o->mg_exact = 1536;
+    o->ilu_sweeps = 3;
+    o->ilu_tri_sweeps = 3;
     return SLRF_OK;
 }
 
@@ -1531,7 +1588,9 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (!o) return SLRF_EINVAL;
     if (o->precision != SLRF_PREC_FP64 && o->precision != SLRF_PREC_MIXED) return SLRF_EINVAL;
     if (o->krylov != SLRF_KRYLOV_COCG && o->krylov != SLRF_KRYLOV_BICGSTAB) return SLRF_EINVAL;
-    if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_AUTO) return SLRF_EINVAL;
+    if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_ILU) return SLRF_EINVAL;
+    if (o->ilu_sweeps < 0 || o->ilu_sweeps > 32 || o->ilu_tri_sweeps < 1 || o->ilu_tri_sweeps > 32)
+        return SLRF_EINVAL;
     if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
         o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
         !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0) || o->stagnation_window < 0 ||
@@ -1649,6 +1708,8 @@ void slrf_destroy(slrf_handle *h) {
     for (Buf *b : bufs)
         if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     if (h->mgInv.p) cudaFreeAsync(h->mgInv.p, h->ctx.stream);
+    for (Buf *b : {&h->iluPat, &h->iluFac, &h->kIluY})
+        if (b->p) cudaFreeAsync(b->p, h->ctx.stream);
     if (h->cublas) cublasDestroy(h->cublas);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,       h->A.ab32,   h->A.ab64,
                    h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64,

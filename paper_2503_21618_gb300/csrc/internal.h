@@ -225,6 +225,44 @@ void mg_apply(Ctx &ctx, const KrylovDims &d, MgSolve<T> &mg, const cplx<T> *sig,
 template <typename T>
 void mg_rz(Ctx &ctx, const KrylovDims &d, int gy, const cplx<T> *R, const cplx<T> *Z, const int32_t *flag, T *part);
 
+// ---------------------------------------------------------------- ilu.cu
+// No-fill incomplete L D L^T of every shifted matrix A - sigma_j B (pencil
+// pattern), built per solve by fixed-point sweeps and applied by Jacobi
+// sweeps of the two triangular solves.  Pattern arrays are built once per
+// handle (lower part by rows and by columns), factor values per solve.
+struct IluPattern {
+    int n = 0;
+    int64_t nnzl = 0;                          // strictly lower entries
+    const int32_t *lptr = nullptr, *lcol = nullptr;  // lower part by rows (CSR, sorted columns)
+    const int32_t *lrow = nullptr;             // row of each lower entry
+    const int32_t *lsrc = nullptr;             // pencil CSR index of each lower entry
+    const int32_t *tptr = nullptr, *trow = nullptr;  // lower part by columns (rows of L^T)
+    const int32_t *tidx = nullptr;             // lower-entry index of each L^T entry
+};
+// Host build of the pattern arrays from the pencil's CSR, concatenated in
+// the order lptr (n+1), lcol, lrow, lsrc (nnzl each), tptr (n+1), trow, tidx.
+std::vector<int32_t> ilu_pattern_host(int n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                                      int64_t *nnzl);
+// Device views of the concatenated arrays.
+void ilu_pattern_views(const int32_t *dev, int n, int64_t nnzl, IluPattern &pat);
+template <typename T> struct IluFactor {
+    int N = 0;
+    const cplx<T> *L = nullptr;    // N x nnzl, pole-major
+    const cplx<T> *Dinv = nullptr; // n x N, 1 / d
+};
+size_t ilu_factor_work_bytes(const IluPattern &pat, int N);
+// Factor values of all poles (FP64 sweeps; stored as T in `out`, sized
+// N * nnzl + n * N complex T, after the FP64 work in `work`).
+template <typename T>
+void ilu_factor(Ctx &ctx, const DevPencil &A, const IluPattern &pat, const PoleSet<double> &ps, int sweeps,
+                void *work, cplx<T> *out, IluFactor<T> &fac);
+// Out = P^T D^{-1} P In (tri_sweeps each side) for the active columns;
+// F and Ys are n x W scratch blocks; part receives In^T Out partials when
+// non-null.
+template <typename T>
+void ilu_apply(Ctx &ctx, const KrylovDims &d, const IluPattern &pat, const IluFactor<T> &fac, int tri_sweeps,
+               int gy, const int32_t *flag, const cplx<T> *In, cplx<T> *Out, cplx<T> *F, cplx<T> *Ys, T *part);
+
 // ---------------------------------------------------------------- dense.cu
 // Y = A X and/or Z = B X, FP64, row-major n x m.
 void spmm_real(Ctx &ctx, const DevPencil &A, int m, const double *X, int64_t ldx, double *Y,
