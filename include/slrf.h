@@ -160,10 +160,17 @@ typedef struct {
                                through L1/L2 by every warp; 2 = staged: a producer
                                warp moves the gathered rows into shared memory by
                                bulk copies (TMA engine) and consumer warps only
-                               multiply; 0 = chosen per pattern and column count
-                               by timing both on the first solve (the choice is
-                               kept for the process; the two differ only in the
-                               rounding order of the partial dot products)    (0) */
+                               multiply; 3 = node blocks (3-dof pencils whose
+                               nodes' rows share one pattern of whole neighbour
+                               nodes and whose mass couples equal dofs only, as
+                               consistent vector-element mass does): one index
+                               and one 3 x 3 stiffness block per neighbour node,
+                               the zero off-dof mass entries skipped; a pencil
+                               not of that form runs kernel 1; 0 = chosen per
+                               pattern and column count by timing the available
+                               kernels on the first solve (the choice is kept
+                               for the process; the kernels differ only in the
+                               rounding order of their sums)                 (0) */
     int32_t mg_exact;       /* MG, FP32 Krylov: the first level below the finest with
                                at most this many unknowns (above the coarsest) ends
                                the cycle and is solved exactly by its dense shifted

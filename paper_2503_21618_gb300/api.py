@@ -20,7 +20,7 @@ NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PENDING =
 PREC_FP64, PREC_MIXED = 0, 1
 KRYLOV_COCG, KRYLOV_BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG, PRECOND_AUTO, PRECOND_ILU = 0, 1, 2, 3, 4
-SPMM_AUTO, SPMM_ROWGROUP, SPMM_STAGED = 0, 1, 2
+SPMM_AUTO, SPMM_ROWGROUP, SPMM_STAGED, SPMM_NODEBLOCK = 0, 1, 2, 3
 RULE_MIDPOINT, RULE_GAUSS_LEGENDRE, RULE_GAUSS_CHEBYSHEV, RULE_SLRF = 0, 1, 2, 3
 RULES = {"midpoint": 0, "gauss_legendre": 1, "gauss_chebyshev": 2, "slrf": 3}
 MAX_POLES = 16

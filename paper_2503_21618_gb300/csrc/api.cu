@@ -389,6 +389,43 @@ void build_rowgroups(int R, int64_t n, const std::vector<int32_t> &rp, const std
     }
 }
 
+// Node-block form of a 3-dof pencil (rows of a node share one pattern, made
+// of whole neighbour nodes, and the mass couples equal dofs only): per node
+// the neighbour nodes and, per neighbour, the 3 x 3 stiffness block and the 3
+// mass weights in three float4.  False (nothing built) when the pencil is
+// not of that form.
+bool build_nodeblocks(int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                      const std::vector<double> &av, const std::vector<double> &bv, std::vector<int32_t> &nptr,
+                      std::vector<int32_t> &nnode, std::vector<float4> &coef) {
+    if (n % 3 || !has_node_blocks(n, rp, ci, 3)) return false;
+    const int64_t nn = n / 3;
+    nptr.assign(nn + 1, 0);
+    nnode.clear();
+    coef.clear();
+    for (int64_t g = 0; g < nn; ++g) {
+        const int64_t k0 = rp[3 * g], k1 = rp[3 * g + 1];
+        if ((k1 - k0) % 3) return false;
+        for (int64_t k = k0; k < k1; k += 3) {
+            if (ci[k] % 3 || ci[k + 1] != ci[k] + 1 || ci[k + 2] != ci[k] + 2) return false;
+            float a[3][3], b[3];
+            for (int r = 0; r < 3; ++r) {
+                const int64_t kr = rp[3 * g + r] + (k - k0);
+                for (int c = 0; c < 3; ++c) {
+                    a[r][c] = (float)av[kr + c];
+                    if (c == r) b[r] = (float)bv[kr + c];
+                    else if (bv[kr + c] != 0.0) return false;
+                }
+            }
+            nnode.push_back(ci[k] / 3);
+            coef.push_back(make_float4(a[0][0], a[0][1], a[0][2], a[1][0]));
+            coef.push_back(make_float4(a[1][1], a[1][2], a[2][0], a[2][1]));
+            coef.push_back(make_float4(a[2][2], b[0], b[1], b[2]));
+        }
+        nptr[g + 1] = (int32_t)nnode.size();
+    }
+    return true;
+}
+
 // CSR monotone with sorted, in-range columns, finite values and a positive
 // diagonal in every row (SPD pencils have one).
 bool pencil_valid(int64_t n, int64_t nnz, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
@@ -854,17 +891,26 @@ slrf_status ilu_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &
 }
 
 // Kernel choice of the FP32 shifted product (slrf_opts.spmm_kernel = 0):
-// both kernels are timed on this solve's blocks (one warm launch, then three
-// timed ones each) and the faster is kept, per device, pattern and column
-// count, for the rest of the process.
+// the candidate kernels are timed on this solve's blocks (one warm launch,
+// then three timed ones each) and the fastest is kept, per device, pattern
+// and column count, for the rest of the process.
 std::mutex g_tune_mu;
 std::map<std::array<int64_t, 6>, int> g_tune;
 
 template <typename T>
 slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffers<T> &kb, const cplx<T> *sig) {
     DevPencil &A = h->A;
-    if (sizeof(T) != 4 || A.spmm_kind != 0) return SLRF_OK;
-    if (spmm_staged_smem(A) == 0) {
+    if (sizeof(T) != 4) return SLRF_OK;
+    // a requested form the pencil does not have runs as the row-group kernel
+    if ((A.spmm_kind == SPMM_STAGED && spmm_staged_smem(A) == 0) || (A.spmm_kind == SPMM_NODEBLOCK && !A.nb_coef))
+        A.spmm_kind = SPMM_ROWGROUP;
+    if (A.spmm_kind != 0) return SLRF_OK;
+    // node pencils: row groups against node blocks (the staged kernel,
+    // bulk-copying 81-entry union lists, measured ~10x slower than either)
+    std::vector<int> kinds = {SPMM_ROWGROUP};
+    if (A.nb_coef) kinds.push_back(SPMM_NODEBLOCK);
+    else if (spmm_staged_smem(A) > 0) kinds.push_back(SPMM_STAGED);
+    if (kinds.size() == 1) {
         A.spmm_kind = SPMM_ROWGROUP;
         return SLRF_OK;
     }
@@ -887,7 +933,7 @@ slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffe
     }
     float best = 0.f;
     int pick = SPMM_ROWGROUP;
-    for (int kind : {SPMM_ROWGROUP, SPMM_STAGED}) {
+    for (int kind : kinds) {
         A.spmm_kind = kind;
         krylov_spmm<T>(ctx, d, A, sig, kb.P, kb.Q, kb.s.flag, kb.s.part, kb.gy);
         cudaEventRecord(e0, ctx.stream);
@@ -1598,7 +1644,7 @@ static slrf_status check_opts(const slrf_opts *o) {
         return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
-    if (o->spmm_kernel < 0 || o->spmm_kernel > 2) return SLRF_EINVAL;
+    if (o->spmm_kernel < 0 || o->spmm_kernel > 3) return SLRF_EINVAL;
     if (o->gram_ozaki < 0 || o->gram_ozaki > 2) return SLRF_EINVAL;
     if (o->mg_exact < 0 || o->mg_exact > 4096) return SLRF_EINVAL;
     return SLRF_OK;
@@ -1713,7 +1759,7 @@ void slrf_destroy(slrf_handle *h) {
     if (h->cublas) cublasDestroy(h->cublas);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,       h->A.ab32,   h->A.ab64,
                    h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64,
-                   h->A.rg_ab4, h->A.rg_dpos};
+                   h->A.rg_ab4, h->A.rg_dpos, h->A.nb_ptr, h->A.nb_node, h->A.nb_coef};
     for (void *p : pen)
         if (p) cudaFreeAsync(p, h->ctx.stream);
     cudaStreamSynchronize(h->ctx.stream);
@@ -1872,6 +1918,23 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
                 cudaStreamSynchronize(s);
             }
         }
+        // node-block form (optional: without it the row-group kernel runs)
+        std::vector<int32_t> nptr, nnode;
+        std::vector<float4> ncoef;
+        if (R == 3 && build_nodeblocks(n, rp, ci, av, bv, nptr, nnode, ncoef) &&
+            alloc((void **)&h->A.nb_ptr, nptr.size() * 4) && alloc((void **)&h->A.nb_node, nnode.size() * 4) &&
+            alloc((void **)&h->A.nb_coef, ncoef.size() * 16)) {
+            cudaMemcpyAsync(h->A.nb_ptr, nptr.data(), nptr.size() * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(h->A.nb_node, nnode.data(), nnode.size() * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(h->A.nb_coef, ncoef.data(), ncoef.size() * 16, cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+        } else {
+            for (void **q : {(void **)&h->A.nb_ptr, (void **)&h->A.nb_node, (void **)&h->A.nb_coef})
+                if (*q) {
+                    cudaFreeAsync(*q, s);
+                    *q = nullptr;
+                }
+        }
         // stream-ordered after the allocations; pageable sources are staged
         // before each call returns
         cudaMemcpyAsync(h->A.rg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice, s);
@@ -1945,6 +2008,7 @@ slrf_status slrf_filter_apply(slrf_handle *h, const slrf_filter *f, const double
         for (int j = 0; j < N; ++j) rep->iters_per_pole[j] = st.iters_per_pole[j];
         rep->status_detail = st.n_fail + st.n_breakdown;
         rep->mg_levels = st.mg_levels;
+        rep->spmm_kernel = h->A.spmm_kind;
     }
     scope.finish();
     CK(cudaGetLastError());

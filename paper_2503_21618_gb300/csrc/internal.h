@@ -70,8 +70,15 @@ struct DevPencil {
     int spmm_kind = 0;
     int spmm_gpb = 0;
     int32_t *dev_err = nullptr;
+    // node-block form (3-dof nodes whose mass couples equal dofs only, as the
+    // consistent mass of vector Lagrange elements does): per row group (node)
+    // the neighbour nodes, and per neighbour the 3 x 3 stiffness block and
+    // the 3 mass weights, packed as 3 float4 (a00 a01 a02 a10 | a11 a12 a20
+    // a21 | a22 b0 b1 b2)
+    int32_t *nb_ptr = nullptr, *nb_node = nullptr;
+    float4 *nb_coef = nullptr;
 };
-enum { SPMM_ROWGROUP = 1, SPMM_STAGED = 2 };
+enum { SPMM_ROWGROUP = 1, SPMM_STAGED = 2, SPMM_NODEBLOCK = 3 };
 // Dynamic shared memory of the staged kernel for this pencil (0: the staged
 // kernel cannot run it: no row groups, or a union list too long).
 size_t spmm_staged_smem(const DevPencil &A);

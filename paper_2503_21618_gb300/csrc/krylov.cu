@@ -386,6 +386,119 @@ k_spmm_shifted_rg(int n, int W, int Lp, int ngroups, int groups_per_block, const
 }
 
 // ---------------------------------------------------------------------------
+// Node-block variant (FP32) for 3-dof pencils whose mass couples equal dofs
+// only: per neighbour node j one index, the three gathered rows 3j..3j+2 of
+// P, the 3 x 3 stiffness block and three mass weights.  Against the
+// row-group kernel on the same pattern: a third of the index loads, a third
+// of the coefficient loads and two thirds of the mass FMAs (the zero
+// off-dof mass entries are skipped).  Same FMA order per row and column
+// within the stiffness and the mass sums as the row-group kernel.
+// ---------------------------------------------------------------------------
+template <int UNR>
+__global__ void __launch_bounds__(32 * TY)
+k_spmm_shifted_nb(int n, int W, int Lp, int ngroups, int groups_per_block, const int32_t *__restrict__ nptr,
+                  const int32_t *__restrict__ node, const float4 *__restrict__ coef, const float2 *__restrict__ sig,
+                  const float2 *__restrict__ P, float2 *__restrict__ Q, const int32_t *__restrict__ flag,
+                  float *__restrict__ part) {
+    constexpr int VC = 2;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    const int c0 = cg * VC;
+    bool act = false;
+    float2 s = make_float2(0.f, 0.f);
+    if (cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) act |= flag[c0 + v] == 1;
+        s = sig[c0 / Lp];
+    }
+    float2 mu[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) mu[v] = make_float2(0.f, 0.f);
+    const int g_begin = blockIdx.y * groups_per_block;
+    const int g_end = min(ngroups, g_begin + groups_per_block);
+    if (blockIdx.x == 0 && ty == 0 && g_end > g_begin) {
+        const int64_t r0 = (int64_t)g_begin * 3, r1 = min((int64_t)n, (int64_t)g_end * 3);
+        l2_prefetch_warp(P + r0 * W, (r1 - r0) * W * (int64_t)sizeof(float2), tx);
+    }
+    if (act) {
+        const float2 *Pc = P + c0;
+        for (int g = g_begin + ty; g < g_end; g += TY) {
+            const int t0 = __ldg(nptr + g), t1 = __ldg(nptr + g + 1);
+            float2 sa[3][VC], sb[3][VC];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int v = 0; v < VC; ++v) sa[r][v] = sb[r][v] = make_float2(0.f, 0.f);
+            for (int t = t0; t < t1; t += UNR) {
+                CV<float, VC> p[UNR][3];
+                float4 w[UNR][3];
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    if (t + u < t1) {
+                        const int64_t j3 = 3 * (int64_t)__ldg(node + t + u);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            p[u][c] = ldcv(Pc + (j3 + c) * W);
+                            w[u][c] = __ldg(coef + (int64_t)(t + u) * 3 + c);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    if (t + u >= t1) break;
+                    const float a[3][3] = {{w[u][0].x, w[u][0].y, w[u][0].z},
+                                           {w[u][0].w, w[u][1].x, w[u][1].y},
+                                           {w[u][1].z, w[u][1].w, w[u][2].x}};
+                    const float b[3] = {w[u][2].y, w[u][2].z, w[u][2].w};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
+                            const float2 x = p[u][c].v[v];
+#pragma unroll
+                            for (int r = 0; r < 3; ++r) ffma2(sa[r][v], make_float2(a[r][c], a[r][c]), x);
+                            ffma2(sb[c][v], make_float2(b[c], b[c]), x);
+                        }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int row = g * 3 + r;
+                if (row >= n) break;
+                CV<float, VC> q;
+#pragma unroll
+                for (int v = 0; v < VC; ++v) q.v[v] = csub(sa[r][v], cmul(s, sb[r][v]));
+                stcv(Q + (int64_t)row * W + c0, q);
+                const CV<float, VC> pr = ldcv(P + (int64_t)row * W + c0);
+#pragma unroll
+                for (int v = 0; v < VC; ++v) mu[v] = cfma(pr.v[v], q.v[v], mu[v]);
+            }
+        }
+    }
+    __shared__ float red[TY][32][VC * 2];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        red[ty][tx][2 * v] = mu[v].x;
+        red[ty][tx][2 * v + 1] = mu[v].y;
+    }
+    __syncthreads();
+    if (ty == 0 && cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            float s0 = 0.f, s1 = 0.f;
+            for (int y = 0; y < TY; ++y) {
+                s0 += red[y][tx][2 * v];
+                s1 += red[y][tx][2 * v + 1];
+            }
+            float *o = part + ((int64_t)blockIdx.y * W + c0 + v) * 4;
+            o[0] = s0;
+            o[1] = s1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Staged (warp-specialized) variant of the FP32 row-group product.
 //
 // The row-group kernel above is latency-bound: every warp waits on its own
@@ -1001,6 +1114,16 @@ void krylov_spmm(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const cplx<T
         reinterpret_cast<const typename ABT<T>::type *>(sizeof(T) == 4 ? (const void *)A.ab32 : (const void *)A.ab64);
     ctx.before(KC_SHIFTED_SPMM, bytes, flops);
     if constexpr (sizeof(T) == 4) {
+        if (A.spmm_kind == SPMM_NODEBLOCK && A.nb_coef) {
+            const int gpb = (A.rg_ngroups + gy - 1) / gy;
+            // one neighbour node in flight per warp (three 16-B gathers and
+            // three coefficient loads): two in flight measured 30% slower
+            k_spmm_shifted_nb<1><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, A.rg_ngroups, gpb, A.nb_ptr, A.nb_node,
+                                                                 A.nb_coef, reinterpret_cast<const float2 *>(sig), P,
+                                                                 Q, flag, part);
+            ctx.after();
+            return;
+        }
         if (A.spmm_kind == SPMM_STAGED && spmm_staged_smem(A) > 0) {
             const float2 *s2 = reinterpret_cast<const float2 *>(sig);
             if (A.rg_rows == 2) launch_staged<2>(ctx, d, A, s2, P, Q, flag, part, gy);

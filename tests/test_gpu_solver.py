@@ -142,9 +142,10 @@ def test_subspace_2d_each_gram_path_matches_dense(api, ozaki):
     np.testing.assert_allclose(Xh.T @ (p.B() @ Xh), np.eye(nev), atol=1e-10)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_subspace_3d_small_matches_dense(api, kernel):
-    # 3-dof node groups (81 union entries each): the staged kernel's long-list shape
+    # 3-dof node groups (81 union entries each): the staged kernel's long-list
+    # shape; kernel 3 takes them as 27 neighbour nodes with 3 x 3 blocks
     p = pencil_3d_elasticity(7, seed=13)   # n = 7 * 7 * 6 * 3 = 882
     lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
     nev = 24

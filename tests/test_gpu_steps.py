@@ -28,13 +28,14 @@ def _cplx_block(n, N, m, ldp, seed):
     return P
 
 
-@pytest.mark.parametrize("prec,kernel", [("fp32", 1), ("fp32", 2), ("fp64", 1)])
+@pytest.mark.parametrize("prec,kernel", [("fp32", 1), ("fp32", 2), ("fp32", 3), ("fp64", 1)])
 @pytest.mark.parametrize("pencil,N,m,rows", [("2d", 3, 37, 0), ("3d", 2, 10, 0), ("1d", 1, 1, 0), ("2d", 9, 5, 0),
                                              ("2d", 2, 12, 1), ("2d", 2, 12, 3), ("2d", 4, 6, 4), ("3d", 1, 4, 2),
                                              ("2d", 4, 150, 0), ("3d", 3, 33, 0)])
 def test_shifted_spmm_matches_oracle(api, prec, kernel, pencil, N, m, rows):
     # kernel 1: row groups gathered by every warp; 2: staged (bulk copies into
-    # shared memory by a producer warp); both against the oracle's product
+    # shared memory by a producer warp); 3: node blocks (3-dof pencils; others
+    # run kernel 1); each against the oracle's product
     p = {"2d": lambda: pencil_2d_q1(23, seed=4), "3d": lambda: pencil_3d_elasticity(5, seed=2),
          "1d": lambda: pencil_1d(77)}[pencil]()
     s, w = poles.quadrature_poles("gauss_legendre", N, 300.0)
@@ -59,6 +60,44 @@ def test_shifted_spmm_matches_oracle(api, prec, kernel, pencil, N, m, rows):
         assert np.abs(Qh[:, j, :m] - ref).max() <= tol * scale
         muref = np.sum(Pq[:, j, :m] * ref, axis=0)
         assert np.abs(muh[j] - muref).max() <= tol * scale * np.abs(Pq).max() * p.n
+
+
+@pytest.mark.parametrize("pencil,rows,want", [("3d", 0, 3), ("3d", 2, 1), ("2d", 0, 1), ("1d", 0, 1)])
+def test_node_block_kernel_runs_only_on_node_pencils(api, pencil, rows, want):
+    # the node-block form exists for 3-dof pencils grouped by node; elsewhere
+    # the request resolves to the row-group kernel, and the report says so
+    p = {"2d": lambda: pencil_2d_q1(15, seed=4), "3d": lambda: pencil_3d_elasticity(4, seed=2),
+         "1d": lambda: pencil_1d(90)}[pencil]()
+    s, w = poles.quadrature_poles("gauss_legendre", 2, 300.0)
+    h = api.Handle(p, api.default_opts(spmm_rows=rows, spmm_kernel=3, inner_tol=1e-4))
+    V = torch.from_numpy(start_block(p.n, 4, 1)).cuda()
+    U, st, rep = h.filter_apply(api.Filter(s, w), V)
+    assert st == api.OK and rep.spmm_kernel == want
+
+
+def test_node_block_kernel_on_graded_3d_pencil(api):
+    # a larger elasticity pencil (several node groups per block, lognormal
+    # stiffness), every column active, against the oracle's product
+    p = pencil_3d_elasticity(9, seed=7)
+    s, w = poles.slrf_poles(3, 1.0, 0.01, 40.0)
+    N, m = len(s), 24
+    P = _cplx_block(p.n, N, m, m, 5)
+    out = {}
+    for kernel in (1, 3):
+        h = api.Handle(p, api.default_opts(spmm_kernel=kernel))
+        Pd = torch.from_numpy(P.astype(np.complex64).view(np.float32).copy()).cuda()
+        Q = torch.zeros_like(Pd)
+        mu = torch.zeros(2 * N * m, dtype=Pd.dtype, device="cuda")
+        h.shifted_spmm(api.Filter(s, w), Pd, m, m, prec=api.PREC_MIXED, Q=Q, mu=mu)
+        torch.cuda.synchronize()
+        out[kernel] = Q.cpu().numpy().view(np.complex64).reshape(p.n, N, m).astype(complex)
+    A, B = p.A(), p.B()
+    Pq = P.astype(np.complex64).astype(complex)
+    for j in range(N):
+        ref = ofilt.shifted_product(A, B, s[j], Pq[:, j])
+        scale = np.abs(A).sum(axis=1).max() * np.abs(Pq).max() * (1 + abs(s[j]))
+        for kernel in (1, 3):
+            assert np.abs(out[kernel][:, j] - ref).max() <= 2e-6 * scale
 
 
 @pytest.mark.parametrize("m", [1, 30, 65])
