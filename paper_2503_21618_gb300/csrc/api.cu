@@ -11,6 +11,7 @@
 #include <complex>
 #include <future>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <type_traits>
 #include <string>
@@ -465,23 +466,35 @@ MgParams mg_params(const slrf_opts &o, int block) {
 // Pack the hierarchy into one device buffer: level pencils (levels
 // 1 .. nlev-2; the coarsest is solved exactly), transfers P and P^T (FP32 and
 // FP64 values), coarsest eigenvectors (FP32 and FP64).
-slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
+// Device image of a host hierarchy, laid out and filled on the host (the
+// setup thread does this while the pencil uploads): byte offsets of every
+// array in one buffer.
+struct MgLvOff {
+    size_t ptr = 0, col = 0, ab32 = 0, ab64 = 0, da = 0, db = 0;
+    size_t pptr = 0, pcol = 0, pv32 = 0, pv64 = 0, rptr = 0, rcol = 0, rv32 = 0, rv64 = 0;
+};
+struct MgStaged {
+    std::unique_ptr<char[]> stage;   // the uploaded part of the image (uninitialised padding)
+    size_t upload_bytes = 0, total_bytes = 0;
+    std::vector<MgLvOff> lo;
+    size_t v32 = 0, v64 = 0, o_fup = 0, o_fuc = 0, o_fdp = 0, o_fdc = 0, o_fq = 0, o_fab32 = 0, o_fab64 = 0;
+    int64_t fu_nnz = 0, fd_nnz = 0;
+};
+
+// Lays out and fills the image of every level but the coarsest level's
+// eigenvectors (mg_stage_v, once they exist).  R0: rows per group of the
+// finest level's row-group form (1 = plain rows).  The folded pairs f_ab
+// come last and are not uploaded: every solve writes them from f_q.
+void mg_stage(const HostHierarchy &H, int R0, MgStaged &S) {
     const int nlev = (int)H.lv.size();
-    if (nlev > MG_MAX_LEVELS) {
-        g_last_error = "multigrid setup: too many levels";
-        return SLRF_BREAKDOWN;
-    }
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    struct LvOff {
-        size_t ptr = 0, col = 0, ab32 = 0, ab64 = 0, da = 0, db = 0;
-        size_t pptr = 0, pcol = 0, pv32 = 0, pv64 = 0, rptr = 0, rcol = 0, rv32 = 0, rv64 = 0;
-    };
-    std::vector<LvOff> lo(nlev);
+    std::vector<MgLvOff> &lo = S.lo;
+    lo.assign(nlev, MgLvOff());
     for (int l = 0; l < nlev; ++l) {
         const HostLevel &L = H.lv[l];
         if (l >= 1 && l < nlev - 1) {
@@ -506,19 +519,28 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
         }
     }
     const int nc = H.lv.back().n;
-    const size_t v32 = take((size_t)nc * nc * 4), v64 = take((size_t)nc * nc * 8);
+    S.v32 = take((size_t)nc * nc * 4);
+    S.v64 = take((size_t)nc * nc * 8);
     // fused finest-level transfers: F by fine row groups ("up") and by coarse rows ("down")
     FusedLayout FL;
-    if (nlev > 1) mg_fused_layout(H.lv[0], H.lv[1].n, h->A.rg_rows > 1 ? h->A.rg_rows : 1, FL);
-    const std::vector<int32_t> &fu_ptr = FL.up_ptr, &fu_col = FL.up_col, &fd_ptr = FL.down_ptr,
-                               &fd_col = FL.down_col;
-    const size_t nslot = FL.q.size() / 4;   // 4 doubles = two double2 per stored pair
-    const size_t o_fup = take(fu_ptr.size() * 4), o_fuc = take(fu_col.size() * 4), o_fdp = take(fd_ptr.size() * 4),
-                 o_fdc = take(fd_col.size() * 4), o_fq = take(FL.q.size() * sizeof(double)),
-                 o_fab32 = take(nslot * sizeof(float2)), o_fab64 = take(nslot * sizeof(double2));
-    std::vector<char> stage(off);
+    if (nlev > 1) mg_fused_pattern(H.lv[0], H.lv[1].n, R0, FL);
+    const size_t nq = nlev > 1 ? FL.q_count() : 0;
+    const size_t nslot = nq / 4;   // 4 doubles = two double2 per stored pair
+    S.o_fup = take(FL.up_ptr.size() * 4);
+    S.o_fuc = take(FL.up_col.size() * 4);
+    S.o_fdp = take(FL.down_ptr.size() * 4);
+    S.o_fdc = take(FL.down_col.size() * 4);
+    S.o_fq = take(nq * sizeof(double));
+    S.upload_bytes = off;
+    S.o_fab32 = take(nslot * sizeof(float2));
+    S.o_fab64 = take(nslot * sizeof(double2));
+    S.total_bytes = off;
+    S.fu_nnz = (int64_t)FL.up_col.size();
+    S.fd_nnz = (int64_t)FL.down_col.size();
+    S.stage.reset(new char[S.upload_bytes]);
+    char *stage = S.stage.get();
     auto put = [&](size_t o, const void *src, size_t bytes) {
-        if (bytes) memcpy(stage.data() + o, src, bytes);
+        if (bytes) memcpy(stage + o, src, bytes);
     };
     for (int l = 0; l < nlev; ++l) {
         const HostLevel &L = H.lv[l];
@@ -526,8 +548,8 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
             const size_t nz = L.col.size();
             put(lo[l].ptr, L.ptr.data(), (L.n + 1) * 4);
             put(lo[l].col, L.col.data(), nz * 4);
-            float2 *a32 = reinterpret_cast<float2 *>(stage.data() + lo[l].ab32);
-            double2 *a64 = reinterpret_cast<double2 *>(stage.data() + lo[l].ab64);
+            float2 *a32 = reinterpret_cast<float2 *>(stage + lo[l].ab32);
+            double2 *a64 = reinterpret_cast<double2 *>(stage + lo[l].ab64);
             for (size_t k = 0; k < nz; ++k) {
                 a32[k] = make_float2((float)L.a[k], (float)L.b[k]);
                 a64[k] = make_double2(L.a[k], L.b[k]);
@@ -543,28 +565,40 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
             put(lo[l].rptr, L.Rt.ptr.data(), (L.Rt.n_rows + 1) * 4);
             put(lo[l].rcol, L.Rt.col.data(), pz * 4);
             put(lo[l].rv64, L.Rt.val.data(), pz * 8);
-            float *p32 = reinterpret_cast<float *>(stage.data() + lo[l].pv32);
-            float *r32 = reinterpret_cast<float *>(stage.data() + lo[l].rv32);
+            float *p32 = reinterpret_cast<float *>(stage + lo[l].pv32);
+            float *r32 = reinterpret_cast<float *>(stage + lo[l].rv32);
             for (size_t k = 0; k < pz; ++k) {
                 p32[k] = (float)L.P.val[k];
                 r32[k] = (float)L.Rt.val[k];
             }
         }
     }
-    {
-        float *V32 = reinterpret_cast<float *>(stage.data() + v32);
-        for (size_t k = 0; k < (size_t)nc * nc; ++k) V32[k] = (float)H.V[k];
-        put(v64, H.V.data(), (size_t)nc * nc * 8);
+    put(S.o_fup, FL.up_ptr.data(), FL.up_ptr.size() * 4);
+    put(S.o_fuc, FL.up_col.data(), FL.up_col.size() * 4);
+    put(S.o_fdp, FL.down_ptr.data(), FL.down_ptr.size() * 4);
+    put(S.o_fdc, FL.down_col.data(), FL.down_col.size() * 4);
+    if (nq) mg_fused_values(H.lv[0], FL, reinterpret_cast<double *>(stage + S.o_fq));
+}
+
+void mg_stage_v(const HostHierarchy &H, MgStaged &S) {
+    const size_t nc = (size_t)H.lv.back().n;
+    float *V32 = reinterpret_cast<float *>(S.stage.get() + S.v32);
+    for (size_t k = 0; k < nc * nc; ++k) V32[k] = (float)H.V[k];
+    memcpy(S.stage.get() + S.v64, H.V.data(), nc * nc * 8);
+}
+
+slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, const MgStaged &S, int block) {
+    const int nlev = (int)H.lv.size();
+    if (nlev > MG_MAX_LEVELS) {
+        g_last_error = "multigrid setup: too many levels";
+        return SLRF_BREAKDOWN;
     }
-    put(o_fup, fu_ptr.data(), fu_ptr.size() * 4);
-    put(o_fuc, fu_col.data(), fu_col.size() * 4);
-    put(o_fdp, fd_ptr.data(), fd_ptr.size() * 4);
-    put(o_fdc, fd_col.data(), fd_col.size() * 4);
-    put(o_fq, FL.q.data(), FL.q.size() * sizeof(double));
-    CKS(ensure(h, h->mgStatic, off));
+    const int nc = H.lv.back().n;
+    const std::vector<MgLvOff> &lo = S.lo;
+    CKS(ensure(h, h->mgStatic, S.total_bytes));
     char *base = reinterpret_cast<char *>(h->mgStatic.p);
-    CK(cudaMemcpyAsync(base, stage.data(), off, cudaMemcpyHostToDevice, h->ctx.stream));
-    CK(cudaStreamSynchronize(h->ctx.stream));   // the staging vector is pageable and local
+    CK(cudaMemcpyAsync(base, S.stage.get(), S.upload_bytes, cudaMemcpyHostToDevice, h->ctx.stream));
+    CK(cudaStreamSynchronize(h->ctx.stream));   // the staging vector is pageable
     auto fill = [&](auto &mg, auto tag) {
         using T = decltype(tag);
         mg = std::remove_reference_t<decltype(mg)>();
@@ -608,16 +642,16 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, int block) {
                 L.rval = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? lo[l].rv32 : lo[l].rv64));
             }
         }
-        mg.V = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? v32 : v64));
+        mg.V = reinterpret_cast<const T *>(base + (sizeof(T) == 4 ? S.v32 : S.v64));
         if (nlev > 1) {
-            L0.fu_nnz = (int64_t)fu_col.size();
-            L0.fd_nnz = (int64_t)fd_col.size();
-            L0.fu_ptr = reinterpret_cast<const int32_t *>(base + o_fup);
-            L0.fu_col = reinterpret_cast<const int32_t *>(base + o_fuc);
-            L0.fd_ptr = reinterpret_cast<const int32_t *>(base + o_fdp);
-            L0.fd_col = reinterpret_cast<const int32_t *>(base + o_fdc);
-            L0.f_q = reinterpret_cast<const double2 *>(base + o_fq);
-            L0.f_ab = reinterpret_cast<cplx<T> *>(base + (sizeof(T) == 4 ? o_fab32 : o_fab64));
+            L0.fu_nnz = S.fu_nnz;
+            L0.fd_nnz = S.fd_nnz;
+            L0.fu_ptr = reinterpret_cast<const int32_t *>(base + S.o_fup);
+            L0.fu_col = reinterpret_cast<const int32_t *>(base + S.o_fuc);
+            L0.fd_ptr = reinterpret_cast<const int32_t *>(base + S.o_fdp);
+            L0.fd_col = reinterpret_cast<const int32_t *>(base + S.o_fdc);
+            L0.f_q = reinterpret_cast<const double2 *>(base + S.o_fq);
+            L0.f_ab = reinterpret_cast<cplx<T> *>(base + (sizeof(T) == 4 ? S.o_fab32 : S.o_fab64));
         }
     };
     fill(h->mg32, 0.0f);
@@ -665,7 +699,10 @@ slrf_status mg_build_upload(slrf_handle *h, const std::vector<int32_t> &rp, cons
         g_last_error = err;
         return SLRF_BREAKDOWN;
     }
-    return mg_upload(h, H, block);
+    MgStaged S;
+    mg_stage(H, h->A.rg_rows > 1 ? h->A.rg_rows : 1, S);
+    mg_stage_v(H, S);
+    return mg_upload(h, H, S, block);
 }
 
 // Build the hierarchy if the options ask for one it does not have yet (from
@@ -1802,22 +1839,43 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
     // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
     const bool blocks = has_node_blocks(n, rp, ci, 3);
-    // The multigrid hierarchy (host) is built on its own thread while the row
-    // groups are formed and the pencil is uploaded; the guard waits for it on
-    // every return, before the host copies it reads go out of scope.
+    int R = o->spmm_rows;
+    if (R == 0) R = blocks ? 3 : 2;
+    // The multigrid hierarchy (host) is built, and its device image laid out,
+    // on its own thread while the row groups are formed and the pencil is
+    // uploaded; the guard waits for it on every return, before the host
+    // copies it reads go out of scope.
     const slrf_opts opts_copy = *o;
     const bool want_mg = o->precond == SLRF_PRECOND_MG || (o->precond == SLRF_PRECOND_AUTO && !blocks);
     const int mg_blk = want_mg ? mg_block_for(opts_copy, n, rp, ci) : 0;
-    std::future<std::pair<std::string, HostHierarchy>> mg_fut;
+    struct MgBuilt {
+        std::string err;
+        HostHierarchy H;
+        MgStaged S;
+    };
+    std::future<MgBuilt> mg_fut;
     struct Join {
-        std::future<std::pair<std::string, HostHierarchy>> &f;
+        std::future<MgBuilt> &f;
         ~Join() {
             if (f.valid()) f.wait();
         }
     } mg_join{mg_fut};
-    auto build_mg = [&rp, &ci, &av, &bv, &opts_copy, n, mg_blk] {
-        std::pair<std::string, HostHierarchy> r;
-        r.first = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(opts_copy, mg_blk), r.second);
+    auto build_mg = [&rp, &ci, &av, &bv, &opts_copy, n, mg_blk, R] {
+        MgBuilt r;
+        MgParams prm = mg_params(opts_copy, mg_blk);
+        prm.defer_coarse_eig = true;
+        r.err = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), prm, r.H);
+        if (!r.err.empty()) return r;
+        // the coarsest level's eigenvectors on a second thread while the
+        // image of the other levels is laid out and filled
+        std::future<std::string> eig;
+        try {
+            eig = std::async(std::launch::async, [&r] { return mg_coarse_eig(r.H); });
+        } catch (...) {   // no thread: in line
+        }
+        mg_stage(r.H, R > 1 ? R : 1, r.S);
+        r.err = eig.valid() ? eig.get() : mg_coarse_eig(r.H);
+        if (r.err.empty()) mg_stage_v(r.H, r.S);
         return r;
     };
     if (want_mg) {
@@ -1826,8 +1884,6 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         } catch (...) {   // no thread: built synchronously below
         }
     }
-    int R = o->spmm_rows;
-    if (R == 0) R = blocks ? 3 : 2;
     std::vector<int32_t> gptr, ucol;
     std::vector<double2> uab;
     if (R > 1) build_rowgroups(R, n, rp, ci, av, bv, gptr, ucol, uab);
@@ -1949,17 +2005,17 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         return SLRF_ECUDA;
     }
     if (want_mg) {
-        std::pair<std::string, HostHierarchy> built;
+        MgBuilt built;
         try {
             built = mg_fut.valid() ? mg_fut.get() : build_mg();
         } catch (const std::exception &ex) {
-            built.first = std::string("multigrid setup: ") + ex.what();
+            built.err = std::string("multigrid setup: ") + ex.what();
         }
         slrf_status st = SLRF_BREAKDOWN;
-        if (built.first.empty())
-            st = mg_upload(h, built.second, mg_blk);
+        if (built.err.empty())
+            st = mg_upload(h, built.H, built.S, mg_blk);
         else
-            g_last_error = built.first;
+            g_last_error = built.err;
         if (st != SLRF_OK) {
             slrf_destroy(h);
             return st;
@@ -1968,6 +2024,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     *out = h;
     return SLRF_OK;
 }
+
 
 slrf_status slrf_filter_apply(slrf_handle *h, const slrf_filter *f, const double *V, int64_t ldv, int32_t m,
                               double *U, int64_t ldu, slrf_report *rep) {
@@ -2035,6 +2092,41 @@ slrf_status slrf_subspace_iterate(slrf_handle *h, const slrf_filter *f, double g
     return s;
 }
 
+// Copies between a contiguous device block (rows x width bytes) and a host
+// block of row pitch ldh bytes.  A pitched copy to or from pageable host
+// memory runs row by row in the driver (measured ~90 ms for 89 401 rows of
+// 1.2 KB on GB300, against ~4 ms for one contiguous copy), so a pitched
+// pageable host block goes through one contiguous copy and a host-side row
+// gather or scatter; pinned host blocks keep the pitched DMA copy.
+static bool host_is_pinned(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+static cudaError_t copy_rows_h2d(void *dev, const void *host, size_t ldh, size_t width, size_t rows, cudaStream_t s) {
+    if (ldh == width) return cudaMemcpyAsync(dev, host, width * rows, cudaMemcpyHostToDevice, s);
+    if (host_is_pinned(host)) return cudaMemcpy2DAsync(dev, width, host, ldh, width, rows, cudaMemcpyHostToDevice, s);
+    std::vector<char> tmp(width * rows);
+    for (size_t r = 0; r < rows; ++r) memcpy(tmp.data() + r * width, (const char *)host + r * ldh, width);
+    const cudaError_t e = cudaMemcpyAsync(dev, tmp.data(), width * rows, cudaMemcpyHostToDevice, s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(s);
+}
+
+static cudaError_t copy_rows_d2h(void *host, size_t ldh, const void *dev, size_t width, size_t rows, cudaStream_t s) {
+    if (ldh == width) return cudaMemcpyAsync(host, dev, width * rows, cudaMemcpyDeviceToHost, s);
+    if (host_is_pinned(host)) return cudaMemcpy2DAsync(host, ldh, dev, width, width, rows, cudaMemcpyDeviceToHost, s);
+    std::vector<char> tmp(width * rows);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), dev, width * rows, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    for (size_t r = 0; r < rows; ++r) memcpy((char *)host + r * ldh, tmp.data() + r * width, width);
+    return cudaSuccess;
+}
+
 slrf_status slrf_subspace_iterate_host(slrf_handle *h, const slrf_filter *f, double gamma, int32_t L,
                                        const double *V0, int64_t ldv, double tol, int32_t max_outer, double *theta,
                                        double *X, int64_t ldx, double *resid, int32_t *n_conv, slrf_report *rep) {
@@ -2045,10 +2137,10 @@ slrf_status slrf_subspace_iterate_host(slrf_handle *h, const slrf_filter *f, dou
     double *dV = as<double>(h->hostV), *dX = as<double>(h->hostX);
     double *dth = dX + (size_t)n * L, *dres = dth + L;
     cudaStream_t s = h->ctx.stream;
-    CK(cudaMemcpy2DAsync(dV, (size_t)L * 8, V0, (size_t)ldv * 8, (size_t)L * 8, (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(copy_rows_h2d(dV, V0, (size_t)ldv * 8, (size_t)L * 8, (size_t)n, s));
     const slrf_status st = slrf_subspace_iterate(h, f, gamma, L, dV, L, tol, max_outer, dth, dX, L, dres, n_conv, rep);
     if (st == SLRF_EINVAL || st == SLRF_ECUDA || st == SLRF_ENOMEM || st == SLRF_EBUDGET) return st;
-    CK(cudaMemcpy2DAsync(X, (size_t)ldx * 8, dX, (size_t)L * 8, (size_t)L * 8, (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(copy_rows_d2h(X, (size_t)ldx * 8, dX, (size_t)L * 8, (size_t)n, s));
     CK(cudaMemcpyAsync(theta, dth, L * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(resid, dres, L * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

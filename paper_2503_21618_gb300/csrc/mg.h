@@ -50,6 +50,7 @@ struct MgParams {
     int coarse_target = 256; // stop coarsening at or below this size
     int max_levels = 10;
     double theta = 0.08;     // strength-of-connection threshold
+    bool defer_coarse_eig = false;   // leave V, lam to mg_coarse_eig (run concurrently)
 };
 
 struct HostHierarchy {
@@ -69,10 +70,14 @@ struct FusedLayout {
     int R = 1;
     std::vector<int32_t> up_ptr, up_col;       // ceil(n / R) + 1 groups; coarse columns
     std::vector<int32_t> down_ptr, down_col;   // n_c + 1 coarse rows; fine columns
-    std::vector<double> q;                     // 4 per stored pair: up pairs (R per entry), then down
+    std::vector<int32_t> down_src;             // per down entry: its position in A P's pattern
+    // doubles of the values: 4 per stored pair, up pairs (R per entry), then down
+    size_t q_count() const { return (up_col.size() * (size_t)R + down_col.size()) * 4; }
 };
-// From level 0 of a hierarchy with at least two levels (L0.fptr non-empty).
-void mg_fused_layout(const HostLevel &L0, int n_coarse, int R, FusedLayout &out);
+// From level 0 of a hierarchy with at least two levels (L0.fptr non-empty):
+// the two patterns, then the values written to q (q_count() doubles).
+void mg_fused_pattern(const HostLevel &L0, int n_coarse, int R, FusedLayout &out);
+void mg_fused_values(const HostLevel &L0, const FusedLayout &FL, double *q);
 
 // Build the hierarchy of the n x n pencil given in CSR with shared pattern
 // (a = A values, b = B values).  Returns an empty string on success, else a
@@ -85,6 +90,10 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
 // row-major V, lam ascending); used for the coarsest level and, on demand, for
 // the level at which a deep shift truncates the cycle.
 std::string mg_level_eig(const HostLevel &L, std::vector<double> &V, std::vector<double> &lam);
+
+// The coarsest level's V, lam of a hierarchy built with defer_coarse_eig
+// (and the release of a single level's pencil copy).
+std::string mg_coarse_eig(HostHierarchy &H);
 
 // Dense symmetric eigensolver (FP64, host): S = Q diag(w) Q^T, w ascending,
 // Q row-major n x n with the eigenvectors in its columns.  S is overwritten.

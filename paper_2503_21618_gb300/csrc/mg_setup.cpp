@@ -539,7 +539,9 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
             rot_s.push_back(s);
         }
     }
-    parallel_for_rows(n, dense_threads(n), [&](int c0, int c1, int) {
+    // one parallel region without barriers: worth threads well below the
+    // size at which the reduction's per-step barriers pay
+    parallel_for_rows(n, n >= 64 ? n_threads((int64_t)rot_k.size() * n) : 1, [&](int c0, int c1, int) {
         for (size_t t = 0; t < rot_k.size(); ++t) {
             const double c = rot_c[t], s = rot_s[t];
             double *__restrict qk = &Qt[(size_t)rot_k[t] * n];
@@ -564,57 +566,92 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
     Q.swap(Qs);
 }
 
-void mg_fused_layout(const HostLevel &L0, int n_coarse, int R, FusedLayout &out) {
+void mg_fused_pattern(const HostLevel &L0, int n_coarse, int R, FusedLayout &out) {
     out = FusedLayout();
     out.R = R;
     const int64_t n0 = L0.n, ng = (n0 + R - 1) / R;
-    auto slot = [&](int64_t i, int32_t k, bool hit) {
-        if (!hit) {
-            out.q.insert(out.q.end(), 4, 0.0);
-            return;
+    // up: groups of R fine rows, sorted union of their coarse columns.  Group
+    // ranges in parallel: unions per thread, then one prefix sum; the layout
+    // does not depend on the thread count.
+    const int nt = n_threads((int64_t)L0.fcol.size() * 4);
+    std::vector<std::vector<int32_t>> ucat(nt);
+    std::vector<int32_t> glen(ng);
+    parallel_for_rows((int)ng, nt, [&](int g0, int g1, int t) {
+        std::vector<int32_t> u;
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t r0 = g * R, r1 = std::min<int64_t>(n0, r0 + R);
+            u.clear();
+            for (int64_t r = r0; r < r1; ++r)
+                u.insert(u.end(), L0.fcol.begin() + L0.fptr[r], L0.fcol.begin() + L0.fptr[r + 1]);
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            glen[g] = (int32_t)u.size();
+            ucat[t].insert(ucat[t].end(), u.begin(), u.end());
         }
-        out.q.push_back(L0.fap[k]);
-        out.q.push_back(L0.fbp[k]);
-        out.q.push_back(L0.fp[k] * L0.diag_a[i]);
-        out.q.push_back(L0.fp[k] * L0.diag_b[i]);
-    };
-    // up: groups of R fine rows, sorted union of their coarse columns
+    });
     out.up_ptr.assign(ng + 1, 0);
-    std::vector<int32_t> u;
-    for (int64_t g = 0; g < ng; ++g) {
-        const int64_t r0 = g * R, r1 = std::min<int64_t>(n0, r0 + R);
-        u.clear();
-        for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), L0.fcol.begin() + L0.fptr[r], L0.fcol.begin() + L0.fptr[r + 1]);
-        std::sort(u.begin(), u.end());
-        u.erase(std::unique(u.begin(), u.end()), u.end());
-        for (int32_t c : u) {
-            out.up_col.push_back(c);
-            for (int r = 0; r < R; ++r) {
-                const int64_t row = r0 + r;
-                if (row >= n0) {
-                    slot(0, 0, false);
-                    continue;
-                }
-                const auto b = L0.fcol.begin() + L0.fptr[row], e = L0.fcol.begin() + L0.fptr[row + 1];
-                const auto it = std::lower_bound(b, e, c);
-                slot(row, (int32_t)(it - L0.fcol.begin()), it != e && *it == c);
-            }
-        }
-        out.up_ptr[g + 1] = (int32_t)out.up_col.size();
+    for (int64_t g = 0; g < ng; ++g) out.up_ptr[g + 1] = out.up_ptr[g] + glen[g];
+    out.up_col.resize(out.up_ptr[ng]);
+    for (int t = 0, g0 = 0; t < nt; ++t) {
+        std::copy(ucat[t].begin(), ucat[t].end(), out.up_col.begin() + out.up_ptr[g0]);
+        g0 = (int)(ng * (t + 1) / nt);
     }
-    // down: F^T, coarse row c lists the fine rows i with an entry (i, c), ascending
+    // down: F^T, coarse row c lists the fine rows i with an entry (i, c),
+    // ascending (counting sort)
+    const int64_t nz = (int64_t)L0.fcol.size();
     out.down_ptr.assign(n_coarse + 1, 0);
     for (int32_t c : L0.fcol) out.down_ptr[c + 1]++;
     for (int c = 0; c < n_coarse; ++c) out.down_ptr[c + 1] += out.down_ptr[c];
-    out.down_col.resize(L0.fcol.size());
-    std::vector<int32_t> fill(out.down_ptr.begin(), out.down_ptr.end() - 1), src(L0.fcol.size());
+    out.down_col.resize(nz);
+    out.down_src.resize(nz);
+    std::vector<int32_t> fill(out.down_ptr.begin(), out.down_ptr.end() - 1);
     for (int64_t i = 0; i < n0; ++i)
         for (int32_t k = L0.fptr[i]; k < L0.fptr[i + 1]; ++k) {
             const int32_t d = fill[L0.fcol[k]]++;
             out.down_col[d] = (int32_t)i;
-            src[d] = k;
+            out.down_src[d] = k;
         }
-    for (size_t e = 0; e < out.down_col.size(); ++e) slot(out.down_col[e], src[e], true);
+}
+
+void mg_fused_values(const HostLevel &L0, const FusedLayout &FL, double *q_out) {
+    const int R = FL.R;
+    const int64_t n0 = L0.n, ng = (int64_t)FL.up_ptr.size() - 1, nz = (int64_t)FL.down_col.size();
+    // the four values of one stored pair (fine row i, entry k of A P's
+    // pattern), or zeros for a padding slot
+    auto slot = [&](double *q, int64_t i, int32_t k, bool hit) {
+        if (!hit) {
+            q[0] = q[1] = q[2] = q[3] = 0.0;
+            return;
+        }
+        q[0] = L0.fap[k];
+        q[1] = L0.fbp[k];
+        q[2] = L0.fp[k] * L0.diag_a[i];
+        q[3] = L0.fp[k] * L0.diag_b[i];
+    };
+    const int nt = n_threads((int64_t)L0.fcol.size() * 4);
+    double *q_up = q_out, *q_dn = q_out + FL.up_col.size() * (size_t)R * 4;
+    parallel_for_rows((int)ng, nt, [&](int g0, int g1, int) {
+        for (int64_t g = g0; g < g1; ++g) {
+            const int64_t r0 = g * R;
+            for (int32_t e = FL.up_ptr[g]; e < FL.up_ptr[g + 1]; ++e) {
+                const int32_t c = FL.up_col[e];
+                for (int r = 0; r < R; ++r) {
+                    double *q = q_up + ((size_t)e * R + r) * 4;
+                    const int64_t row = r0 + r;
+                    if (row >= n0) {
+                        slot(q, 0, 0, false);
+                        continue;
+                    }
+                    const auto b = L0.fcol.begin() + L0.fptr[row], e1 = L0.fcol.begin() + L0.fptr[row + 1];
+                    const auto it = std::lower_bound(b, e1, c);
+                    slot(q, row, (int32_t)(it - L0.fcol.begin()), it != e1 && *it == c);
+                }
+            }
+        }
+    });
+    parallel_for_rows((int)nz, nt, [&](int d0, int d1, int) {
+        for (int64_t d = d0; d < d1; ++d) slot(q_dn + (size_t)d * 4, FL.down_col[d], FL.down_src[d], true);
+    });
 }
 
 std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double *a, const double *b,
@@ -729,6 +766,16 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         Lc.b.assign(b, b + ptr[n]);
     }
     if (Lc.n > 4096) return "multigrid setup: coarsening stalled at " + std::to_string(Lc.n) + " unknowns";
+    if (!prm.defer_coarse_eig) {
+        std::string err = mg_coarse_eig(H);
+        if (!err.empty()) return err;
+    }
+    H.ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return "";
+}
+
+std::string mg_coarse_eig(HostHierarchy &H) {
+    HostLevel &Lc = H.lv.back();
     std::string err = mg_level_eig(Lc, H.V, H.lam);
     if (!err.empty()) return err;
     if (H.lv.size() == 1) {   // level 0 keeps no pencil copy
@@ -737,7 +784,6 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         Lc.a.clear();
         Lc.b.clear();
     }
-    H.ms_setup = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return "";
 }
 

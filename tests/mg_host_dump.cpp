@@ -68,11 +68,13 @@ int main(int argc, char **argv) {
     }
     if (mode != "layout") return 2;
     FusedLayout L;
-    mg_fused_layout(H.lv[0], H.lv[1].n, std::stoi(argv[4]), L);
+    mg_fused_pattern(H.lv[0], H.lv[1].n, std::stoi(argv[4]), L);
+    std::vector<double> q(L.q_count());
+    mg_fused_values(H.lv[0], L, q.data());
     const std::vector<long long> out_hdr = {H.lv[1].n, (long long)L.up_col.size(), (long long)L.down_col.size()};
     return wr(dir + "/out_hdr.bin", out_hdr) && wr(dir + "/up_ptr.bin", L.up_ptr) && wr(dir + "/up_col.bin", L.up_col) &&
                    wr(dir + "/down_ptr.bin", L.down_ptr) && wr(dir + "/down_col.bin", L.down_col) &&
-                   wr(dir + "/q.bin", L.q)
+                   wr(dir + "/q.bin", q)
                ? 0
                : 5;
 }

@@ -172,6 +172,44 @@ def test_subspace_host_entry_equals_device_entry(api):
     np.testing.assert_array_equal(X_d.cpu().numpy(), X_h)
 
 
+@pytest.mark.parametrize("pinned", [False, True])
+def test_subspace_host_entry_pitched_blocks(api, pinned):
+    # V0 and X with row pitches above L, in pageable or pinned host memory
+    # (the pageable pitched blocks go through one contiguous copy and a host
+    # row gather/scatter, the pinned ones through a pitched copy): the same
+    # bits as the contiguous call, and the padding columns left untouched
+    import ctypes as C
+    p = pencil_2d_q1(24, seed=2)
+    lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
+    gamma = 0.5 * (lam[9] + lam[10])
+    f = api.Filter(*poles.quadrature_poles("gauss_legendre", 4, gamma))
+    L = 16
+    V0 = start_block(p.n, L, 3)
+    h = api.Handle(p)
+    th_c, X_c, r_c, nc_c, st_c, _ = h.subspace_iterate_host(f, gamma, V0)
+
+    def host(shape, fill):
+        if pinned:
+            a = torch.full(shape, fill, dtype=torch.float64).pin_memory().numpy()
+        else:
+            a = np.full(shape, fill)
+        return a
+    ldv, ldx = L + 3, L + 5
+    Vp = host((p.n, ldv), 7.0)
+    Vp[:, :L] = V0
+    Xp = host((p.n, ldx), -3.0)
+    th, res = np.zeros(L), np.zeros(L)
+    nconv = C.c_int32(0)
+    rep = api.slrf_report()
+    st = h.lib.slrf_subspace_iterate_host(h.h, C.byref(f.c), gamma, L, Vp.ctypes.data, ldv, 1e-8, 50,
+                                          th.ctypes.data, Xp.ctypes.data, ldx, res.ctypes.data, C.byref(nconv),
+                                          C.byref(rep))
+    assert st == st_c == api.OK and nconv.value == nc_c
+    np.testing.assert_array_equal(th, th_c)
+    np.testing.assert_array_equal(Xp[:, :L], X_c)
+    assert np.all(Xp[:, L:] == -3.0) and np.all(Vp[:, L:] == 7.0)
+
+
 def test_subspace_too_small_is_reported(api):
     p = pencil_1d(300)
     lam = inertia.lambda_1d(300)
