@@ -218,6 +218,13 @@ typedef struct {
 const char *slrf_status_str(slrf_status s);
 /* Text of the last CUDA error seen by this thread ("" if none). */
 const char *slrf_last_error(void);
+/* Device memory of handles comes from one pool per device that keeps what
+ * destroyed handles release reserved for later handles of the process (so
+ * creating the next handle maps no new memory).  This returns the unused
+ * part of device `device`'s pool to the driver; memory held by live handles
+ * stays.  SLRF_OK also when the pool was never created; SLRF_ECUDA if the
+ * trim fails. */
+slrf_status slrf_release_cached_memory(int32_t device);
 /* Name of a kernel class index of slrf_report.k_*; NULL if out of range. */
 const char *slrf_kernel_class_name(int32_t k);
 /* Fill *o with the defaults listed in slrf_opts. */

@@ -119,6 +119,7 @@ _SIGNATURES = {
     "slrf_gram_noalloc": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, _P]),
     "slrf_noalloc_last_error": (C.c_char_p, []),
     "slrf_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), _P]),
+    "slrf_release_cached_memory": (C.c_int, [C.c_int32]),
     "slrf_mg_describe": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P, _P]),
     "slrf_mg_transfer": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.c_int32, C.POINTER(C.c_int32),
@@ -217,6 +218,12 @@ def fma_peak(precision: int = PREC_MIXED, stream=None) -> float:
     v = C.c_double()
     _check(load().slrf_fma_peak(precision, C.byref(v), _stream_ptr(stream)), "slrf_fma_peak")
     return v.value
+
+
+def release_cached_memory(device: int = 0) -> None:
+    """Return the unused part of the library's device memory pool (memory
+    released by destroyed handles, kept for later handles) to the driver."""
+    _check(load().slrf_release_cached_memory(device), "slrf_release_cached_memory")
 
 
 def mg_describe(pencil, opts: slrf_opts | None = None, coarse: bool = False) -> dict:

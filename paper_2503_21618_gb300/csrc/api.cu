@@ -202,6 +202,40 @@ struct slrf_handle {
 
 namespace {
 
+// Device memory of handles comes from one stream-ordered pool per device,
+// created by the library, that keeps what destroyed handles free reserved
+// for the next ones: the default pool hands freed memory back to the driver
+// at every synchronisation, and mapping it again on the next handle costs
+// milliseconds per GB.  slrf_release_cached_memory() trims it.
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaMemPool_t handle_pool(int device) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    auto it = g_pools.find(device);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPool_t pool = nullptr;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        pool = nullptr;   // the device's default pool is used instead
+    } else {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    g_pools[device] = pool;
+    return pool;
+}
+
+cudaError_t dev_alloc(slrf_handle *h, void **ptr, size_t bytes) {
+    cudaMemPool_t pool = handle_pool(h->device);
+    return pool ? cudaMallocFromPoolAsync(ptr, bytes, pool, h->ctx.stream) : cudaMallocAsync(ptr, bytes, h->ctx.stream);
+}
+
 slrf_status ensure(slrf_handle *h, Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return SLRF_OK;
@@ -216,7 +250,7 @@ slrf_status ensure(slrf_handle *h, Buf &b, size_t bytes) {
         b.p = nullptr;
         b.bytes = 0;
     }
-    if (cudaMallocAsync(&b.p, bytes, h->ctx.stream) != cudaSuccess) {
+    if (dev_alloc(h, &b.p, bytes) != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
         g_last_error = "device allocation of " + std::to_string(bytes) + " bytes failed";
@@ -1638,6 +1672,18 @@ const char *slrf_kernel_class_name(int32_t k) {
     return (k >= 0 && k < SLRF_NKERNEL_CLASSES) ? kKernelClassNames[k] : nullptr;
 }
 
+slrf_status slrf_release_cached_memory(int32_t device) {
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        auto it = g_pools.find(device);
+        if (it != g_pools.end()) pool = it->second;
+    }
+    if (!pool) return SLRF_OK;
+    CK(cudaMemPoolTrimTo(pool, 0));
+    return SLRF_OK;
+}
+
 slrf_status slrf_opts_default(slrf_opts *o) {
     if (!o) return SLRF_EINVAL;
     memset(o, 0, sizeof(*o));
@@ -1903,7 +1949,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         return SLRF_EBUDGET;
     }
     auto alloc = [&](void **ptr, size_t bytes) -> bool {
-        if (cudaMallocAsync(ptr, bytes, h->ctx.stream) != cudaSuccess) {
+        if (dev_alloc(h, ptr, bytes) != cudaSuccess) {
             *ptr = nullptr;
             cudaGetLastError();
             return false;

@@ -210,6 +210,25 @@ def test_subspace_host_entry_pitched_blocks(api, pinned):
     assert np.all(Xp[:, L:] == -3.0) and np.all(Vp[:, L:] == 7.0)
 
 
+def test_release_cached_memory(api):
+    # a destroyed handle's memory stays in the library's pool for the next
+    # handle; the trim hands it back, and the next handle solves as before
+    p = pencil_2d_q1(24, seed=2)
+    lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
+    gamma = 0.5 * (lam[9] + lam[10])
+    f = api.Filter(*poles.quadrature_poles("gauss_legendre", 4, gamma))
+    V0 = start_block(p.n, 16, 3)
+    out = []
+    for _ in range(2):
+        h = api.Handle(p)
+        out.append(h.subspace_iterate_host(f, gamma, V0))
+        h.close()
+        api.release_cached_memory(torch.cuda.current_device())
+    assert out[0][4] == out[1][4] == api.OK
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    api.release_cached_memory(torch.cuda.device_count() + 5)   # no pool there: nothing to do
+
+
 def test_subspace_too_small_is_reported(api):
     p = pencil_1d(300)
     lam = inertia.lambda_1d(300)
