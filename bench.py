@@ -353,6 +353,30 @@ def class_mask(pkg, names):
     return m
 
 
+def spmm_formats(pkg, p, f, V0, hbm_peak):
+    """The 2D workload's shifted product in its CSR row-group form against
+    SELL-C-sigma (two chunk/sorting-window shapes): one filter application per
+    form with every shifted-product launch timed by CUDA events; algorithmic
+    bytes as in the roofline (pattern + FP32 pairs once, P read and Q written
+    for the active columns)."""
+    import torch
+    out = {}
+    for name, kw in (("csr_rowgroup", dict(spmm_kernel=1)),
+                     ("sell_c32_sigma256", dict(spmm_kernel=4, sell_c=32, sell_sigma=256)),
+                     ("sell_c8_sigma1", dict(spmm_kernel=4, sell_c=8, sell_sigma=1))):
+        h = pkg.Handle(p, pkg.default_opts(profile=1, profile_mask=class_mask(pkg, {"shifted_spmm"}), **kw))
+        h.filter_apply(f, V0)                       # warm-up
+        torch.cuda.synchronize()
+        _, st, rep = h.filter_apply(f, V0)
+        k = rep.as_dict()["kernels"].get("shifted_spmm", {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        h.close()
+        gbs = k["bytes"] / (k["ms"] / 1e3) / 1e9 if k["ms"] else None
+        out[name] = {"spmm_kernel": int(rep.spmm_kernel), "launches": k["launches"],
+                     "avg_launch_us": k["ms"] / k["launches"] * 1e3 if k["launches"] else None,
+                     "achieved_gbs": gbs, "frac": gbs / hbm_peak if gbs and hbm_peak else None}
+    return out
+
+
 def bench_3d(pkg, fp32_peak):
     """One timed solve of the 3D elasticity workload (40^3 nodes x 3 dof,
     n = 187 200, 200 eigenpairs, L = 300, N = 4, mixed precision), after a
@@ -599,7 +623,8 @@ def main():
                        "filter": "SLRF alpha=1 beta=0.01 (library designer)", "precision": "mixed",
                        "inner_tol": opts.inner_tol, "tol": TOL, "parallelism": f"replicas x{world}",
                        "precond": "multigrid (smoothed aggregation)" if "mg_fine" in tot else "jacobi",
-                       "spmm_kernel": {1: "row groups", 2: "staged (bulk copies to shared memory)"}.get(
+                       "spmm_kernel": {1: "row groups", 2: "staged (bulk copies to shared memory)",
+                                       3: "node blocks", 4: "SELL-C-sigma"}.get(
                            reps[0]["spmm_kernel"], str(reps[0]["spmm_kernel"])) if reps else None,
                        "l2": "inputs larger than L2 (Krylov state 1.29 GB per solve)"},
             "converged_per_step": conv, "outer_iters": outer,
@@ -629,6 +654,7 @@ def main():
                                      "peak_source": f"{peak_src} hbm_gbs", "launches": ks["launches"],
                                      "avg_launch_us": ks["ms"] / ks["launches"] * 1e3}
         if not args.no_extra:
+            line["spmm_formats"] = spmm_formats(pkg, p, f, V0, peaks.get("hbm_gbs"))
             line["configs"] = {}
             fp32_peak = pkg.api.fma_peak(pkg.PREC_MIXED)
             line["fp32_fma_peak_tflops"] = fp32_peak / 1e12

@@ -166,7 +166,9 @@ typedef struct {
                                consistent vector-element mass does): one index
                                and one 3 x 3 stiffness block per neighbour node,
                                the zero off-dof mass entries skipped; a pencil
-                               not of that form runs kernel 1; 0 = chosen per
+                               not of that form runs kernel 1; 4 = SELL-C-sigma
+                               (sell_c, sell_sigma): one warp per permuted row
+                               walking its chunk's slot-major entries; 0 = chosen per
                                pattern and column count by timing the available
                                kernels on the first solve (the choice is kept
                                for the process; the kernels differ only in the
@@ -179,6 +181,11 @@ typedef struct {
                                cycle then descends to the coarsest level     (1536) */
     int32_t ilu_sweeps;     /* ILU: fixed-point sweeps building the factors     (3) */
     int32_t ilu_tri_sweeps; /* ILU: Jacobi sweeps of each triangular solve      (3) */
+    int32_t sell_c;         /* SELL-C-sigma form of the pencil (spmm_kernel 4):
+                               rows per chunk, one of 4, 8, 16, 32, 64; 0 = 32 */
+    int32_t sell_sigma;     /* SELL-C-sigma: rows are sorted by length within
+                               windows of this many rows (1 = natural order);
+                               0 = 256                                         */
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

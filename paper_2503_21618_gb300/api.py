@@ -20,7 +20,7 @@ NOT_CONVERGED, STAGNATION, BREAKDOWN, SUBSPACE_TOO_SMALL, CHOLQR_FAIL, PENDING =
 PREC_FP64, PREC_MIXED = 0, 1
 KRYLOV_COCG, KRYLOV_BICGSTAB = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MG, PRECOND_AUTO, PRECOND_ILU = 0, 1, 2, 3, 4
-SPMM_AUTO, SPMM_ROWGROUP, SPMM_STAGED, SPMM_NODEBLOCK = 0, 1, 2, 3
+SPMM_AUTO, SPMM_ROWGROUP, SPMM_STAGED, SPMM_NODEBLOCK, SPMM_SELL = 0, 1, 2, 3, 4
 RULE_MIDPOINT, RULE_GAUSS_LEGENDRE, RULE_GAUSS_CHEBYSHEV, RULE_SLRF = 0, 1, 2, 3
 RULES = {"midpoint": 0, "gauss_legendre": 1, "gauss_chebyshev": 2, "slrf": 3}
 MAX_POLES = 16
@@ -47,7 +47,8 @@ class slrf_opts(C.Structure):
                 ("mg_omega", C.c_double), ("mg_theta", C.c_double), ("mg_shift_limit", C.c_double),
                 ("stagnation_window", C.c_int32),
                 ("profile_mask", C.c_uint32), ("spmm_kernel", C.c_int32), ("mg_exact", C.c_int32),
-                ("ilu_sweeps", C.c_int32), ("ilu_tri_sweeps", C.c_int32)]
+                ("ilu_sweeps", C.c_int32), ("ilu_tri_sweeps", C.c_int32), ("sell_c", C.c_int32),
+                ("sell_sigma", C.c_int32)]
 
 
 class slrf_report(C.Structure):

@@ -461,6 +461,55 @@ bool build_nodeblocks(int64_t n, const std::vector<int32_t> &rp, const std::vect
     return true;
 }
 
+// SELL-C-sigma form of the pencil (FP32 pairs): rows sorted by length,
+// longest first, within windows of sigma rows (stable, so equal lengths keep
+// their order), chunks of C permuted rows, each padded to its longest row and
+// stored slot-major.  Padding slots hold the row's own column and zero
+// coefficients.
+bool build_sell(int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                const std::vector<double> &av, const std::vector<double> &bv, int C, int sigma,
+                std::vector<int32_t> &cptr, std::vector<int32_t> &col, std::vector<float2> &ab,
+                std::vector<int32_t> &perm, std::vector<int32_t> &rlen) {
+    perm.resize(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    auto len = [&](int32_t r) { return rp[r + 1] - rp[r]; };
+    for (int64_t w0 = 0; w0 < n; w0 += sigma)
+        std::stable_sort(perm.begin() + w0, perm.begin() + std::min<int64_t>(n, w0 + sigma),
+                         [&](int32_t x, int32_t y) { return len(x) > len(y); });
+    rlen.resize(n);
+    for (int64_t i = 0; i < n; ++i) rlen[i] = len(perm[i]);
+    const int64_t nch = (n + C - 1) / C;
+    cptr.assign(nch + 1, 0);
+    int64_t tot = 0;
+    for (int64_t c = 0; c < nch; ++c) {
+        int32_t K = 0;
+        for (int64_t r = c * C; r < std::min<int64_t>(n, (c + 1) * C); ++r) K = std::max(K, rlen[r]);
+        tot += (int64_t)K * C;
+        if (tot > (1LL << 31) - 1) return false;   // slots addressed by int32 offsets
+        cptr[c + 1] = (int32_t)tot;
+    }
+    col.assign(cptr[nch], 0);
+    ab.assign(cptr[nch], make_float2(0.f, 0.f));
+    for (int64_t c = 0; c < nch; ++c) {
+        const int32_t K = (cptr[c + 1] - cptr[c]) / C;
+        for (int r = 0; r < C; ++r) {
+            const int64_t pr = c * C + r;
+            const int32_t row = pr < n ? perm[pr] : 0;
+            for (int32_t k = 0; k < K; ++k) {
+                const int64_t e = cptr[c] + (int64_t)k * C + r;
+                if (pr < n && k < rlen[pr]) {
+                    const int64_t src = rp[row] + k;
+                    col[e] = ci[src];
+                    ab[e] = make_float2((float)av[src], (float)bv[src]);
+                } else {
+                    col[e] = row;
+                }
+            }
+        }
+    }
+    return true;
+}
+
 // CSR monotone with sorted, in-range columns, finite values and a positive
 // diagonal in every row (SPD pencils have one).
 bool pencil_valid(int64_t n, int64_t nnz, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
@@ -966,14 +1015,15 @@ slrf_status ilu_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &
 // then three timed ones each) and the fastest is kept, per device, pattern
 // and column count, for the rest of the process.
 std::mutex g_tune_mu;
-std::map<std::array<int64_t, 6>, int> g_tune;
+std::map<std::array<int64_t, 7>, int> g_tune;
 
 template <typename T>
 slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffers<T> &kb, const cplx<T> *sig) {
     DevPencil &A = h->A;
     if (sizeof(T) != 4) return SLRF_OK;
     // a requested form the pencil does not have runs as the row-group kernel
-    if ((A.spmm_kind == SPMM_STAGED && spmm_staged_smem(A) == 0) || (A.spmm_kind == SPMM_NODEBLOCK && !A.nb_coef))
+    if ((A.spmm_kind == SPMM_STAGED && spmm_staged_smem(A) == 0) || (A.spmm_kind == SPMM_NODEBLOCK && !A.nb_coef) ||
+        (A.spmm_kind == SPMM_SELL && !A.sell_ab))
         A.spmm_kind = SPMM_ROWGROUP;
     if (A.spmm_kind != 0) return SLRF_OK;
     // node pencils: row groups against node blocks (the staged kernel,
@@ -981,11 +1031,13 @@ slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffe
     std::vector<int> kinds = {SPMM_ROWGROUP};
     if (A.nb_coef) kinds.push_back(SPMM_NODEBLOCK);
     else if (spmm_staged_smem(A) > 0) kinds.push_back(SPMM_STAGED);
+    if (A.sell_ab) kinds.push_back(SPMM_SELL);
     if (kinds.size() == 1) {
         A.spmm_kind = SPMM_ROWGROUP;
         return SLRF_OK;
     }
-    const std::array<int64_t, 6> key = {h->device, A.n, A.nnz, A.rg_rows, A.rg_nnz, d.W()};
+    const std::array<int64_t, 7> key = {h->device, A.n, A.nnz, A.rg_rows, A.rg_nnz, d.W(),
+                                        (int64_t)A.sell_c * 1000000 + A.sell_sigma};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(key);
@@ -1727,7 +1779,10 @@ static slrf_status check_opts(const slrf_opts *o) {
         return SLRF_EINVAL;
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
-    if (o->spmm_kernel < 0 || o->spmm_kernel > 3) return SLRF_EINVAL;
+    if (o->spmm_kernel < 0 || o->spmm_kernel > 4) return SLRF_EINVAL;
+    if (o->sell_c != 0 && o->sell_c != 4 && o->sell_c != 8 && o->sell_c != 16 && o->sell_c != 32 && o->sell_c != 64)
+        return SLRF_EINVAL;
+    if (o->sell_sigma < 0) return SLRF_EINVAL;
     if (o->gram_ozaki < 0 || o->gram_ozaki > 2) return SLRF_EINVAL;
     if (o->mg_exact < 0 || o->mg_exact > 4096) return SLRF_EINVAL;
     return SLRF_OK;
@@ -1842,7 +1897,8 @@ void slrf_destroy(slrf_handle *h) {
     if (h->cublas) cublasDestroy(h->cublas);
     void *pen[] = {h->A.rowptr, h->A.col,    h->A.a,      h->A.b,       h->A.ab32,   h->A.ab64,
                    h->A.diag_a, h->A.diag_b, h->A.rg_ptr, h->A.rg_col, h->A.rg_ab32, h->A.rg_ab64,
-                   h->A.rg_ab4, h->A.rg_dpos, h->A.nb_ptr, h->A.nb_node, h->A.nb_coef};
+                   h->A.rg_ab4, h->A.rg_dpos, h->A.nb_ptr, h->A.nb_node, h->A.nb_coef,
+                   h->A.sell_cptr, h->A.sell_col, h->A.sell_ab, h->A.sell_perm, h->A.sell_rlen};
     for (void *p : pen)
         if (p) cudaFreeAsync(p, h->ctx.stream);
     cudaStreamSynchronize(h->ctx.stream);
@@ -2043,6 +2099,34 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         cudaMemcpyAsync(h->A.rg_col, ucol.data(), U * 4, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(h->A.rg_ab32, uab32.data(), uab32.size() * 8, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(h->A.rg_ab64, uab.data(), uab.size() * 16, cudaMemcpyHostToDevice, s);
+    }
+    // SELL-C-sigma form (optional: without it the row-group kernel runs)
+    {
+        const int C = o->sell_c ? o->sell_c : 32, sg = o->sell_sigma ? o->sell_sigma : 256;
+        std::vector<int32_t> cptr, scol, perm, rlen;
+        std::vector<float2> sab;
+        if (build_sell(n, rp, ci, av, bv, C, sg, cptr, scol, sab, perm, rlen) &&
+            alloc((void **)&h->A.sell_cptr, cptr.size() * 4) && alloc((void **)&h->A.sell_col, scol.size() * 4) &&
+            alloc((void **)&h->A.sell_ab, sab.size() * 8) && alloc((void **)&h->A.sell_perm, perm.size() * 4) &&
+            alloc((void **)&h->A.sell_rlen, rlen.size() * 4)) {
+            cudaMemcpyAsync(h->A.sell_cptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(h->A.sell_col, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(h->A.sell_ab, sab.data(), sab.size() * 8, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(h->A.sell_perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(h->A.sell_rlen, rlen.data(), rlen.size() * 4, cudaMemcpyHostToDevice, s);
+            h->A.sell_c = C;
+            h->A.sell_sigma = sg;
+            h->A.sell_nchunks = (int)(cptr.size() - 1);
+            h->A.sell_slots = cptr.back();
+            cudaStreamSynchronize(s);
+        } else {
+            for (void **q : {(void **)&h->A.sell_cptr, (void **)&h->A.sell_col, (void **)&h->A.sell_ab,
+                             (void **)&h->A.sell_perm, (void **)&h->A.sell_rlen})
+                if (*q) {
+                    cudaFreeAsync(*q, s);
+                    *q = nullptr;
+                }
+        }
     }
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -77,8 +77,17 @@ struct DevPencil {
     // a21 | a22 b0 b1 b2)
     int32_t *nb_ptr = nullptr, *nb_node = nullptr;
     float4 *nb_coef = nullptr;
+    // SELL-C-sigma form (FP32): rows permuted by length within windows of
+    // sigma rows, chunks of C rows padded to their longest row, entries
+    // slot-major within a chunk (entry k of the chunk's row r at
+    // sell_cptr[chunk] + k C + r); per permuted row its original index and
+    // length
+    int sell_c = 0, sell_sigma = 0, sell_nchunks = 0;
+    int64_t sell_slots = 0;
+    int32_t *sell_cptr = nullptr, *sell_col = nullptr, *sell_perm = nullptr, *sell_rlen = nullptr;
+    float2 *sell_ab = nullptr;
 };
-enum { SPMM_ROWGROUP = 1, SPMM_STAGED = 2, SPMM_NODEBLOCK = 3 };
+enum { SPMM_ROWGROUP = 1, SPMM_STAGED = 2, SPMM_NODEBLOCK = 3, SPMM_SELL = 4 };
 // Dynamic shared memory of the staged kernel for this pencil (0: the staged
 // kernel cannot run it: no row groups, or a union list too long).
 size_t spmm_staged_smem(const DevPencil &A);

@@ -499,6 +499,110 @@ k_spmm_shifted_nb(int n, int W, int Lp, int ngroups, int groups_per_block, const
 }
 
 // ---------------------------------------------------------------------------
+// SELL-C-sigma variant (FP32).  The chunks of C permuted rows are split
+// between the CTAs of a column slice; warp ty takes rows ty, ty + TY, ... of
+// each chunk and walks its row's slots k = 0 .. len-1 at cptr + k C + r (the
+// padding slots of shorter rows are skipped, not multiplied).  Results go to
+// the row's original position.
+// ---------------------------------------------------------------------------
+template <int UNR>
+__global__ void __launch_bounds__(32 * TY)
+k_spmm_shifted_sell(int n, int W, int Lp, int C, int nchunks, int chunks_per_block, const int32_t *__restrict__ cptr,
+                    const int32_t *__restrict__ col, const float2 *__restrict__ ab, const int32_t *__restrict__ perm,
+                    const int32_t *__restrict__ rlen, const float2 *__restrict__ sig, const float2 *__restrict__ P,
+                    float2 *__restrict__ Q, const int32_t *__restrict__ flag, float *__restrict__ part) {
+    constexpr int VC = 2;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int ng = W / VC;
+    const int cg = blockIdx.x * 32 + tx;
+    const int c0 = cg * VC;
+    bool act = false;
+    float2 s = make_float2(0.f, 0.f);
+    if (cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) act |= flag[c0 + v] == 1;
+        s = sig[c0 / Lp];
+    }
+    float2 mu[VC];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) mu[v] = make_float2(0.f, 0.f);
+    const int ch_begin = blockIdx.y * chunks_per_block;
+    const int ch_end = min(nchunks, ch_begin + chunks_per_block);
+    if (act) {
+        const float2 *Pc = P + c0;
+        for (int ch = ch_begin; ch < ch_end; ++ch) {
+            const int64_t base = __ldg(cptr + ch);
+            for (int r = ty; r < C; r += TY) {
+                const int prow = ch * C + r;
+                if (prow >= n) break;
+                const int row = __ldg(perm + prow), len = __ldg(rlen + prow);
+                float2 sa[VC], sb[VC];
+#pragma unroll
+                for (int v = 0; v < VC; ++v) sa[v] = sb[v] = make_float2(0.f, 0.f);
+                int k = 0;
+                for (; k + UNR <= len; k += UNR) {
+                    int cc[UNR];
+                    float2 w[UNR];
+#pragma unroll
+                    for (int u = 0; u < UNR; ++u) {
+                        const int64_t e = base + (int64_t)(k + u) * C + r;
+                        cc[u] = __ldg(col + e);
+                        w[u] = __ldg(ab + e);
+                    }
+                    CV<float, VC> p[UNR];
+#pragma unroll
+                    for (int u = 0; u < UNR; ++u) p[u] = ldcv(Pc + (int64_t)cc[u] * W);
+#pragma unroll
+                    for (int u = 0; u < UNR; ++u)
+#pragma unroll
+                        for (int v = 0; v < VC; ++v) {
+                            ffma2(sa[v], make_float2(w[u].x, w[u].x), p[u].v[v]);
+                            ffma2(sb[v], make_float2(w[u].y, w[u].y), p[u].v[v]);
+                        }
+                }
+                for (; k < len; ++k) {
+                    const int64_t e = base + (int64_t)k * C + r;
+                    const float2 w = __ldg(ab + e);
+                    const CV<float, VC> p = ldcv(Pc + (int64_t)__ldg(col + e) * W);
+#pragma unroll
+                    for (int v = 0; v < VC; ++v) {
+                        ffma2(sa[v], make_float2(w.x, w.x), p.v[v]);
+                        ffma2(sb[v], make_float2(w.y, w.y), p.v[v]);
+                    }
+                }
+                CV<float, VC> q;
+#pragma unroll
+                for (int v = 0; v < VC; ++v) q.v[v] = csub(sa[v], cmul(s, sb[v]));
+                stcv(Q + (int64_t)row * W + c0, q);
+                const CV<float, VC> pr = ldcv(P + (int64_t)row * W + c0);
+#pragma unroll
+                for (int v = 0; v < VC; ++v) mu[v] = cfma(pr.v[v], q.v[v], mu[v]);
+            }
+        }
+    }
+    __shared__ float red[TY][32][VC * 2];
+#pragma unroll
+    for (int v = 0; v < VC; ++v) {
+        red[ty][tx][2 * v] = mu[v].x;
+        red[ty][tx][2 * v + 1] = mu[v].y;
+    }
+    __syncthreads();
+    if (ty == 0 && cg < ng) {
+#pragma unroll
+        for (int v = 0; v < VC; ++v) {
+            float s0 = 0.f, s1 = 0.f;
+            for (int y = 0; y < TY; ++y) {
+                s0 += red[y][tx][2 * v];
+                s1 += red[y][tx][2 * v + 1];
+            }
+            float *o = part + ((int64_t)blockIdx.y * W + c0 + v) * 4;
+            o[0] = s0;
+            o[1] = s1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Staged (warp-specialized) variant of the FP32 row-group product.
 //
 // The row-group kernel above is latency-bound: every warp waits on its own
@@ -1121,6 +1225,14 @@ void krylov_spmm(Ctx &ctx, const KrylovDims &d, const DevPencil &A, const cplx<T
             k_spmm_shifted_nb<1><<<grid, block, 0, ctx.stream>>>(d.n, W, d.Lp, A.rg_ngroups, gpb, A.nb_ptr, A.nb_node,
                                                                  A.nb_coef, reinterpret_cast<const float2 *>(sig), P,
                                                                  Q, flag, part);
+            ctx.after();
+            return;
+        }
+        if (A.spmm_kind == SPMM_SELL && A.sell_ab) {
+            const int cpb = (A.sell_nchunks + gy - 1) / gy;
+            k_spmm_shifted_sell<4><<<grid, block, 0, ctx.stream>>>(
+                d.n, W, d.Lp, A.sell_c, A.sell_nchunks, cpb, A.sell_cptr, A.sell_col, A.sell_ab, A.sell_perm,
+                A.sell_rlen, reinterpret_cast<const float2 *>(sig), P, Q, flag, part);
             ctx.after();
             return;
         }

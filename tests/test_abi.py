@@ -55,6 +55,22 @@ def test_create_rejects_bad_input_without_gpu(lib):
     assert lib.slrf_create(C.byref(h), C.byref(p), None, None) == api.EINVAL
 
 
+@pytest.mark.parametrize("kw", [dict(sell_c=5), dict(sell_c=128), dict(sell_sigma=-1), dict(spmm_kernel=5),
+                                dict(spmm_kernel=-1)])
+def test_create_rejects_bad_spmm_options_without_gpu(lib, kw):
+    # the options are checked before the pencil is read or any device call
+    import ctypes as C
+    from paper_2503_21618_gb300 import api
+    from workloads import pencil_1d
+    pen = pencil_1d(50)
+    keep = [np.ascontiguousarray(pen.row_ptr, dtype=np.int32), np.ascontiguousarray(pen.col_idx, dtype=np.int32),
+            np.ascontiguousarray(pen.a_val), np.ascontiguousarray(pen.b_val)]
+    p = api.slrf_pencil(pen.n, int(keep[1].size), *[a.ctypes.data for a in keep], 0)
+    o = api.default_opts(**kw)
+    h = C.c_void_p()
+    assert lib.slrf_create(C.byref(h), C.byref(p), C.byref(o), None) == api.EINVAL
+
+
 @pytest.mark.parametrize("rule", ["midpoint", "gauss_legendre", "gauss_chebyshev"])
 @pytest.mark.parametrize("N", [1, 3, 4, 8])
 def test_quadrature_poles_match_oracle(lib, rule, N):

@@ -110,9 +110,9 @@ def test_subspace_1d_config(api, prec):
     np.testing.assert_allclose(Xh[:, :20].T @ (p.B() @ Xh[:, :20]), np.eye(20), atol=1e-10)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 4])
 def test_subspace_2d_small_matches_dense(api, kernel):
-    # shifted product kernel 0 = autotuned, 1 = row groups, 2 = staged
+    # shifted product kernel 0 = autotuned, 1 = row groups, 2 = staged, 4 = SELL-C-sigma
     p = pencil_2d_q1(40, seed=21)          # n = 1521
     lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
     nev = 30

@@ -28,14 +28,14 @@ def _cplx_block(n, N, m, ldp, seed):
     return P
 
 
-@pytest.mark.parametrize("prec,kernel", [("fp32", 1), ("fp32", 2), ("fp32", 3), ("fp64", 1)])
+@pytest.mark.parametrize("prec,kernel", [("fp32", 1), ("fp32", 2), ("fp32", 3), ("fp32", 4), ("fp64", 1)])
 @pytest.mark.parametrize("pencil,N,m,rows", [("2d", 3, 37, 0), ("3d", 2, 10, 0), ("1d", 1, 1, 0), ("2d", 9, 5, 0),
                                              ("2d", 2, 12, 1), ("2d", 2, 12, 3), ("2d", 4, 6, 4), ("3d", 1, 4, 2),
                                              ("2d", 4, 150, 0), ("3d", 3, 33, 0)])
 def test_shifted_spmm_matches_oracle(api, prec, kernel, pencil, N, m, rows):
     # kernel 1: row groups gathered by every warp; 2: staged (bulk copies into
     # shared memory by a producer warp); 3: node blocks (3-dof pencils; others
-    # run kernel 1); each against the oracle's product
+    # run kernel 1); 4: SELL-C-sigma; each against the oracle's product
     p = {"2d": lambda: pencil_2d_q1(23, seed=4), "3d": lambda: pencil_3d_elasticity(5, seed=2),
          "1d": lambda: pencil_1d(77)}[pencil]()
     s, w = poles.quadrature_poles("gauss_legendre", N, 300.0)
@@ -98,6 +98,37 @@ def test_node_block_kernel_on_graded_3d_pencil(api):
         scale = np.abs(A).sum(axis=1).max() * np.abs(Pq).max() * (1 + abs(s[j]))
         for kernel in (1, 3):
             assert np.abs(out[kernel][:, j] - ref).max() <= 2e-6 * scale
+
+
+@pytest.mark.parametrize("C,sigma", [(4, 1), (8, 7), (16, 256), (32, 1), (64, 10 ** 6)])
+@pytest.mark.parametrize("pencil", ["2d", "3d", "1d"])
+def test_sell_spmm_chunk_and_sorting_window(api, C, sigma, pencil):
+    # SELL-C-sigma with chunk sizes that leave a ragged last chunk, sorting
+    # windows from none (1) to the whole matrix; rows of unequal length (the
+    # boundary rows of the 2D/3D pencils) make padded chunks
+    p = {"2d": lambda: pencil_2d_q1(19, seed=6), "3d": lambda: pencil_3d_elasticity(4, seed=3),
+         "1d": lambda: pencil_1d(131)}[pencil]()
+    s, w = poles.quadrature_poles("gauss_legendre", 3, 200.0)
+    N, m = len(s), 11
+    ldp = m + 1
+    P = _cplx_block(p.n, N, m, ldp, 4)
+    h = api.Handle(p, api.default_opts(spmm_kernel=4, sell_c=C, sell_sigma=sigma))
+    Pd = torch.from_numpy(P.astype(np.complex64).view(np.float32).copy()).cuda()
+    Q = torch.zeros_like(Pd)
+    mu = torch.zeros(2 * N * m, dtype=Pd.dtype, device="cuda")
+    h.shifted_spmm(api.Filter(s, w), Pd, m, ldp, prec=api.PREC_MIXED, Q=Q, mu=mu)
+    torch.cuda.synchronize()
+    Qh = Q.cpu().numpy().view(np.complex64).reshape(p.n, N, ldp).astype(complex)
+    muh = mu.cpu().numpy().view(np.complex64).reshape(N, m).astype(complex)
+    A, B = p.A(), p.B()
+    Pq = P.astype(np.complex64).astype(complex)
+    for j in range(N):
+        ref = ofilt.shifted_product(A, B, s[j], Pq[:, j, :m])
+        scale = np.abs(A).sum(axis=1).max() * np.abs(Pq).max() * (1 + abs(s[j]))
+        assert np.abs(Qh[:, j, :m] - ref).max() <= 2e-6 * scale
+        assert np.all(Qh[:, j, m:] == 0)          # padding columns (zero in P) stay zero
+        muref = np.sum(Pq[:, j, :m] * ref, axis=0)
+        assert np.abs(muh[j] - muref).max() <= 2e-6 * scale * np.abs(Pq).max() * p.n
 
 
 @pytest.mark.parametrize("m", [1, 30, 65])
