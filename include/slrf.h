@@ -119,8 +119,14 @@ typedef struct {
                                (their correction is below the outer tolerance) (1e-9) */
     int32_t check_every;    /* Krylov iterations between host polls of the
                                active-column count                               (4) */
-    int32_t eig_refine;     /* small eigensolver: 1 = FP32 Jacobi + FP64 refinement,
-                               0 = FP64 Jacobi                                     (1) */
+    int32_t eig_refine;     /* small eigensolver of the projected problem (m <= 160;
+                               larger m always take 0): 2 = FP32 Jacobi, then
+                               three FP64 refinement steps X <- X (I + E) built
+                               from the products X^T X and X^T S X (Ogita-Aishima),
+                               and FP64 Jacobi inside groups of nearly equal
+                               eigenvalues; 1 = FP32 Jacobi, FP64 re-orthonormal-
+                               isation and an FP64 Jacobi polish of the whole
+                               matrix; 0 = FP64 Jacobi                          (2) */
     int64_t mem_budget;     /* workspace byte cap, 0 = none                       (0) */
     int32_t profile;        /* 1: time kernel classes with CUDA events around
                                each launch (those selected by profile_mask)      (0) */

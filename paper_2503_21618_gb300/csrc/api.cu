@@ -1746,7 +1746,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->inner_tol = 1e-5;
     o->lock_tol = 1e-9;
     o->check_every = 4;
-    o->eig_refine = 1;
+    o->eig_refine = 2;
     o->mem_budget = 0;
     o->profile = 0;
     o->spmm_rows = 0;
@@ -1780,6 +1780,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->inner_maxit < 1 || !(o->inner_tol > 0) || o->check_every < 1 || o->mem_budget < 0) return SLRF_EINVAL;
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
     if (o->spmm_kernel < 0 || o->spmm_kernel > 4) return SLRF_EINVAL;
+    if (o->eig_refine < 0 || o->eig_refine > 2) return SLRF_EINVAL;
     if (o->sell_c != 0 && o->sell_c != 4 && o->sell_c != 8 && o->sell_c != 16 && o->sell_c != 32 && o->sell_c != 64)
         return SLRF_EINVAL;
     if (o->sell_sigma < 0) return SLRF_EINVAL;

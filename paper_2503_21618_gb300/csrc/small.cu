@@ -472,8 +472,238 @@ __global__ void k_fro(int m, const double *__restrict__ S, double *__restrict__ 
 size_t small_syev_work_bytes(int m) {
     const size_t mp = (size_t)(m + (m & 1));
     const size_t m2 = (size_t)m * m;
-    // A32/V32 global fallback (2 mp^2 doubles) + S0, S1, G, Y, T, V (6 m^2) + lam0, normA, counters
-    return 2 * mp * mp * sizeof(double) + 6 * m2 * sizeof(double) + 2 * (size_t)m * sizeof(double) + 4096;
+    // A32/V32 global fallback (2 mp^2 doubles) + S0, S1, G, Y, T, V (6 m^2) + lam0, normA, counters,
+    // component labels and sizes (2 m ints)
+    return 2 * mp * mp * sizeof(double) + 6 * m2 * sizeof(double) + 2 * (size_t)m * sizeof(double) +
+           2 * (size_t)m * sizeof(int) + 4096;
+}
+
+// ---------------------------------------------------------------------------
+// Iterative refinement of an approximate eigendecomposition (Ogita and
+// Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
+// Japan J. Indust. Appl. Math. 35, 2018).  With Xh the current eigenvector
+// matrix, G = Xh^T Xh, T = Xh^T S Xh and R = I - G, the exact eigenvectors
+// are X = Xh (I + E) with, to first order in the error,
+//   E + E^T = R                         (orthonormality)
+//   T + E^T D + D E = D                 (diagonalisation, D = eigenvalues)
+// so lam_i = t_ii / g_ii, e_ii = r_ii / 2 and, for i != j,
+//   e_ij = (t_ij + lam_j r_ij) / (lam_j - lam_i).
+// A pair is refined this way only while the step is small: its eigenvalues
+// more than delta = 2 ||T - D||_F apart and |e_ij| <= 1/8; other pairs get
+// e_ij = r_ij / 2 (orthonormality only) and are left to k_oa_components.
+// (The paper's delta also carries ||S|| ||R||; here every step is preceded
+// by a Newton-Schulz orthonormalisation X <- X (3 I - X^T X) / 2, which
+// keeps R at rounding level, so that term is dropped: with the FP32
+// Jacobi's ||R|| ~ 1e-4 it would group most of a graded spectrum.)  The
+// products are FP64 GEMMs; three steps reach FP64 accuracy from the FP32
+// Jacobi's vectors wherever the pairs are separated.
+// ---------------------------------------------------------------------------
+__device__ double block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];
+    return t;
+}
+
+// Ep = I + E (row-major), lam_t = t_ii / g_ii
+__global__ void __launch_bounds__(1024) k_oa_update(int m, const double *__restrict__ G, const double *__restrict__ T,
+                                                   const double *__restrict__ normS, double *__restrict__ Ep,
+                                                   double *__restrict__ lam_t) {
+    __shared__ double red[32];
+    const int tid = threadIdx.x, bs = blockDim.x;
+    for (int i = tid; i < m; i += bs) lam_t[i] = T[(int64_t)i * m + i] / G[(int64_t)i * m + i];
+    __syncthreads();
+    double off = 0.0;
+    for (int e = tid; e < m * m; e += bs) {
+        const int i = e / m, j = e % m;
+        const double d = T[e] - (i == j ? lam_t[i] : 0.0);
+        off += d * d;
+    }
+    off = block_sum(off, red);
+    const double delta = 2.0 * sqrt(off);
+    for (int e = tid; e < m * m; e += bs) {
+        const int i = e / m, j = e % m;
+        const double r = (i == j ? 1.0 : 0.0) - G[e];
+        double v;
+        if (i == j) {
+            v = 1.0 + 0.5 * r;
+        } else {
+            const double li = lam_t[i], lj = lam_t[j], num = T[e] + lj * r;
+            const bool sep = fabs(li - lj) > delta && 8.0 * fabs(num) <= fabs(lj - li);
+            v = sep ? num / (lj - li) : 0.5 * r;
+        }
+        Ep[e] = v;
+    }
+}
+
+// Newton-Schulz orthonormalisation factor: Ep = (3 I - G) / 2
+__global__ void k_ns_factor(int m, const double *__restrict__ G, double *__restrict__ Ep) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    Ep[e] = (e / m == e % m ? 1.5 : 0.0) - 0.5 * G[e];
+}
+
+// After the refinement T = Q^T S Q is diagonal up to rounding except inside
+// groups of (nearly) equal eigenvalues.  Indices joined by an off-diagonal
+// entry above tau = 4 m u ||S||_F (about ten times the rounding of the FP64
+// products) form components (label propagation); each
+// component of two or more is diagonalised by cyclic FP64 Jacobi and its
+// columns of Q rotated; lam receives the diagonal (unsorted).  Workspace:
+// label, size (m ints each), blk, W (m^2 doubles each), Qc (m^2 doubles).
+__global__ void __launch_bounds__(1024) k_oa_components(int m, const double *__restrict__ T,
+                                                       const double *__restrict__ normS, double *__restrict__ Q,
+                                                       double *__restrict__ lam, int *__restrict__ label,
+                                                       int *__restrict__ size, double *__restrict__ blk,
+                                                       double *__restrict__ Wm, double *__restrict__ Qc) {
+    const int tid = threadIdx.x, bs = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
+    __shared__ int changed, k, nrot;
+    __shared__ int members[1024];
+    __shared__ double cs[512], sn[512];
+    __shared__ int pp[512], qq[512];
+    const double tau = 4.0 * m * 1.1102230246251565e-16 * (*normS);
+    auto joined = [&](int i, int j) {
+        return fabs(T[(int64_t)i * m + j]) > tau || fabs(T[(int64_t)j * m + i]) > tau;
+    };
+    for (int i = tid; i < m; i += bs) {
+        label[i] = i;
+        size[i] = 0;
+    }
+    __syncthreads();
+    // labels only decrease and label[i] <= i, so the jumps end; a chain of
+    // m indices needs at most m passes
+    for (int pass = 0; pass <= m; ++pass) {
+        if (tid == 0) changed = 0;
+        __syncthreads();
+        for (int e = tid; e < m * m; e += bs) {
+            const int i = e / m, j = e % m;
+            if (j <= i || !joined(i, j)) continue;
+            const int li = label[i], lj = label[j];
+            if (li != lj) {
+                const int l = min(li, lj);
+                atomicMin(&label[i], l);
+                atomicMin(&label[j], l);
+                changed = 1;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < m; i += bs) {
+            int l = label[i];
+            while (label[l] != l) l = label[l];
+            atomicMin(&label[i], l);
+        }
+        __syncthreads();
+        const int c = changed;
+        __syncthreads();
+        if (!c) break;
+    }
+    for (int i = tid; i < m; i += bs) atomicAdd(&size[label[i]], 1);
+    __syncthreads();
+    for (int i = tid; i < m; i += bs)
+        if (size[label[i]] == 1) lam[i] = T[(int64_t)i * m + i];
+    for (int r = 0; r < m; ++r) {
+        if (size[r] < 2) continue;   // uniform: every thread reads the same entry
+        if (tid == 0) {
+            int c = 0;
+            for (int i = r; i < m && c < 1024; ++i)
+                if (label[i] == r) members[c++] = i;
+            k = c;
+        }
+        __syncthreads();
+        const int kk = k;
+        for (int e = tid; e < kk * kk; e += bs) {
+            const int a = e / kk, b = e % kk;
+            const int ia = members[a], ib = members[b];
+            blk[e] = 0.5 * (T[(int64_t)ia * m + ib] + T[(int64_t)ib * m + ia]);
+            Wm[e] = a == b ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        const int kp = kk + (kk & 1), npair = kp / 2;
+        for (int sweep = 0; sweep < 40; ++sweep) {
+            if (tid == 0) nrot = 0;
+            __syncthreads();
+            for (int rd = 0; rd < kp - 1; ++rd) {
+                for (int t = tid; t < npair; t += bs) {
+                    int a, b;
+                    rr_pair(t, rd, kp, a, b);
+                    const int p = min(a, b), q = max(a, b);
+                    double c = 1.0, s = 0.0;
+                    if (q < kk) {
+                        const double apq = blk[p * kk + q];
+                        if (fabs(apq) > tau) {
+                            const double app = blk[p * kk + p], aqq = blk[q * kk + q];
+                            const double th = (aqq - app) / (2.0 * apq);
+                            const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                            c = 1.0 / sqrt(1.0 + tt * tt);
+                            s = tt * c;
+                            atomicAdd(&nrot, 1);
+                        }
+                    }
+                    cs[t] = c;
+                    sn[t] = s;
+                    pp[t] = p;
+                    qq[t] = (q < kk && s != 0.0) ? q : -1;
+                }
+                __syncthreads();
+                for (int t = warp; t < npair; t += nwarp) {
+                    const int q = qq[t];
+                    if (q < 0) continue;
+                    const int p = pp[t];
+                    const double c = cs[t], s = sn[t];
+                    for (int col = lane; col < kk; col += 32) {
+                        const double apk = blk[p * kk + col], aqk = blk[q * kk + col];
+                        blk[p * kk + col] = c * apk - s * aqk;
+                        blk[q * kk + col] = s * apk + c * aqk;
+                    }
+                }
+                __syncthreads();
+                for (int t = warp; t < npair; t += nwarp) {
+                    const int q = qq[t];
+                    if (q < 0) continue;
+                    const int p = pp[t];
+                    const double c = cs[t], s = sn[t];
+                    for (int row = lane; row < kk; row += 32) {
+                        const double akp = blk[row * kk + p], akq = blk[row * kk + q];
+                        blk[row * kk + p] = c * akp - s * akq;
+                        blk[row * kk + q] = s * akp + c * akq;
+                        const double wkp = Wm[row * kk + p], wkq = Wm[row * kk + q];
+                        Wm[row * kk + p] = c * wkp - s * wkq;
+                        Wm[row * kk + q] = s * wkp + c * wkq;
+                    }
+                }
+                __syncthreads();
+                for (int t = tid; t < npair; t += bs) {
+                    const int q = qq[t];
+                    if (q < 0) continue;
+                    const int p = pp[t];
+                    blk[p * kk + q] = 0.0;
+                    blk[q * kk + p] = 0.0;
+                }
+                __syncthreads();
+            }
+            const int nr = nrot;
+            __syncthreads();
+            if (nr == 0) break;
+        }
+        for (int a = tid; a < kk; a += bs) lam[members[a]] = blk[a * kk + a];
+        for (int e = tid; e < m * kk; e += bs) {
+            const int row = e / kk, b = e % kk;
+            Qc[e] = Q[(int64_t)row * m + members[b]];
+        }
+        __syncthreads();
+        for (int e = tid; e < m * kk; e += bs) {
+            const int row = e / kk, a = e % kk;
+            double v = 0.0;
+            for (int b = 0; b < kk; ++b) v = fma(Qc[row * kk + b], Wm[b * kk + a], v);
+            Q[(int64_t)row * m + members[a]] = v;
+        }
+        __syncthreads();
+    }
 }
 
 // At most one cooperative (grid-barrier) kernel of this process is in flight
@@ -557,6 +787,52 @@ cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q,
     k_jacobi<float><<<1, 1024, smem, ctx.stream>>>(m, S, (float *)Ag, (float *)Vg, lam0, S0, 40, 1, nullptr,
                                                       1e-6f);
     ctx.after();
+    if (mode == 2) {
+        // stage 2: three rounds of an orthonormalisation step and a
+        // refinement step X <- X (I + E) from the FP64 products G = X^T X and
+        // T = X^T (S X); then the groups of nearly equal eigenvalues are
+        // diagonalised and the pairs sorted
+        double *X0 = S0, *X1 = S1;
+        const unsigned eg = (unsigned)((m2 + 255) / 256);
+        for (int it = 0; it < 3; ++it) {
+            dgemm(ctx, 1, 0, m, m, m, X0, m, X0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
+            ctx.before(KC_SMALL_DENSE, 16.0 * m2, 2.0 * m2);
+            k_ns_factor<<<eg, 256, 0, ctx.stream>>>(m, G, Vm);
+            ctx.after();
+            dgemm(ctx, 0, 0, m, m, m, X0, m, Vm, m, 0.0, X1, m, 1, nullptr, KC_SMALL_DENSE);
+            std::swap(X0, X1);
+            dgemm(ctx, 1, 0, m, m, m, X0, m, X0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
+            dgemm(ctx, 0, 0, m, m, m, S, m, X0, m, 0.0, Ym, m, 1, nullptr, KC_SMALL_DENSE);
+            dgemm(ctx, 1, 0, m, m, m, X0, m, Ym, m, 0.0, Tm, m, 1, nullptr, KC_SMALL_DENSE);
+            ctx.before(KC_SMALL_DENSE, 24.0 * m2, 8.0 * m2);
+            k_oa_update<<<1, 1024, 0, ctx.stream>>>(m, G, Tm, normA, Vm, lam0);
+            ctx.after();
+            dgemm(ctx, 0, 0, m, m, m, X0, m, Vm, m, 0.0, X1, m, 1, nullptr, KC_SMALL_DENSE);
+            std::swap(X0, X1);
+        }
+        // the last refinement step leaves R at the square of its largest
+        // accepted steps: three orthonormalisation steps bring it back to
+        // rounding level before the groups are rotated
+        for (int it = 0; it < 3; ++it) {
+            dgemm(ctx, 1, 0, m, m, m, X0, m, X0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
+            ctx.before(KC_SMALL_DENSE, 16.0 * m2, 2.0 * m2);
+            k_ns_factor<<<eg, 256, 0, ctx.stream>>>(m, G, Vm);
+            ctx.after();
+            dgemm(ctx, 0, 0, m, m, m, X0, m, Vm, m, 0.0, X1, m, 1, nullptr, KC_SMALL_DENSE);
+            std::swap(X0, X1);
+        }
+        dgemm(ctx, 0, 0, m, m, m, S, m, X0, m, 0.0, Ym, m, 1, nullptr, KC_SMALL_DENSE);
+        dgemm(ctx, 1, 0, m, m, m, X0, m, Ym, m, 0.0, Tm, m, 1, nullptr, KC_SMALL_DENSE);
+        int *label = cst + 4, *csize = label + m;
+        ctx.before(KC_SMALL_DENSE, 24.0 * m2, 4.0 * m2);
+        k_oa_components<<<1, 1024, 0, ctx.stream>>>(m, Tm, normA, X0, lam0, label, csize, (double *)Ag,
+                                                     (double *)Vg, X1);
+        ctx.after();
+        ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
+        k_sort_eig<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, lam0, X0, lam, Q);
+        ctx.after();
+        return cudaGetLastError();
+    }
     // stage 2: FP64 re-orthonormalisation S1 = S0 R^{-1}, G = S0^T S0 = R^T R
     dgemm(ctx, 1, 0, m, m, m, S0, m, S0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
     small_chol_upper(ctx, m, G, G, cst, 0.0);

@@ -175,8 +175,8 @@ def _sym_with_spectrum(m, lam, seed):
     return (Qr * lam[None, :]) @ Qr.T
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("case", ["random", "graded", "clusters", "tiny", "odd"])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("case", ["random", "graded", "clusters", "tiny", "odd", "pairs", "wide"])
 def test_syev_matches_lapack(api, mode, case):
     rng = np.random.default_rng(5)
     if case == "random":
@@ -194,6 +194,19 @@ def test_syev_matches_lapack(api, mode, case):
     elif case == "tiny":
         m = 1
         S = np.array([[3.5]])
+    elif case == "wide":
+        # six decades, like the first projection of a random start block:
+        # the FP32 stage leaves the low end unresolved, so large groups reach
+        # the final FP64 Jacobi
+        m = 150
+        S = _sym_with_spectrum(m, np.geomspace(1.0, 1e6, m), 4)
+    elif case == "pairs":
+        # a spectrum like the projected problems': near-degenerate pairs at
+        # relative gaps from 1e-3 down to 1e-12, graded magnitudes
+        m = 150
+        base = np.geomspace(1.0, 1e3, 75)
+        gaps = np.geomspace(1e-3, 1e-12, 75)
+        S = _sym_with_spectrum(m, np.sort(np.concatenate([base, base * (1 + gaps)])), 3)
     else:
         m = 33
         S = rng.standard_normal((m, m))
