@@ -333,6 +333,14 @@ slrf_status slrf_spmm_ab(slrf_handle *h, int32_t m, const double *X, int64_t ldx
 slrf_status slrf_gram(slrf_handle *h, int32_t m, const double *X, int64_t ldx, const double *Y,
                       int64_t ldy, double *G);
 
+/* C = A B (device, row-major): A n x k with n = the handle's pencil size, B
+ * k x m, C n x m; FP64-accurate (the Ozaki digit products of opts.gram_ozaki:
+ * 2 = tcgen05 for k <= 512, else int8 mma.sync; 0 = FP64 GEMM).  The tall
+ * products Q1 = U T1 and X = Q1 M of Algorithm 1's orthonormalisation and
+ * Ritz vectors.  SLRF_ETIMEOUT if a bounded device wait gave up. */
+slrf_status slrf_tall_product(slrf_handle *h, int32_t k, int32_t m, const double *A, int64_t lda, const double *B,
+                              int64_t ldb, double *C, int64_t ldc);
+
 /* Symmetric eigendecomposition of the m x m row-major device matrix S:
  * S = Q diag(lam) Q^T, lam ascending (device), Q device row-major (columns are
  * eigenvectors).  The small eigenproblem of Algorithm 1 after

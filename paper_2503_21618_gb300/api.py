@@ -121,6 +121,7 @@ _SIGNATURES = {
     "slrf_noalloc_last_error": (C.c_char_p, []),
     "slrf_fma_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double), _P]),
     "slrf_release_cached_memory": (C.c_int, [C.c_int32]),
+    "slrf_tall_product": (C.c_int, [_P, C.c_int32, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64]),
     "slrf_mg_describe": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double), _P, _P, _P]),
     "slrf_mg_transfer": (C.c_int, [C.POINTER(slrf_pencil), C.POINTER(slrf_opts), C.c_int32, C.POINTER(C.c_int32),
@@ -409,6 +410,14 @@ class Handle:
         G = torch.empty((m, m), dtype=torch.float64, device=X.device)
         _check(self.lib.slrf_gram(self.h, m, _dptr(X), X.stride(0), _dptr(Y), Y.stride(0), _dptr(G)), "slrf_gram")
         return G
+
+    def tall_product(self, A, B):
+        """C = A B for A (n x k, n = the pencil's size) and B (k x m), device FP64."""
+        import torch
+        C = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=A.device)
+        _check(self.lib.slrf_tall_product(self.h, A.shape[1], B.shape[1], _dptr(A), A.stride(0), _dptr(B),
+                                          B.stride(0), _dptr(C), C.stride(0)), "slrf_tall_product")
+        return C
 
     def syev(self, S):
         import torch

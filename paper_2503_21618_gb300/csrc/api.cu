@@ -156,6 +156,7 @@ struct slrf_handle {
     Buf kP, kQ, kR, kDinv, kU, kPart, kSig, kScal, kFlags;
     Buf rOz;   // Ozaki Gram digits and partials
     Buf rOzT;  // Ozaki tall-product digits
+    Buf rTallB;   // slrf_tall_product: copy of B
     Buf rW1, rQ1, rQ2, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
     int64_t shifted_cholqr = 0;   // Rayleigh-Ritz steps that needed the shifted fallback
     Buf hostV, hostX;   // device staging for the host-buffer entry points
@@ -1309,7 +1310,8 @@ slrf_status tall_product(slrf_handle *h, int64_t n, int k, int m, const double *
     Ctx &ctx = h->ctx;
     if (h->opts.gram_ozaki && ozaki_tall_fits(k)) {
         CKS(ensure(h, h->rOzT, ozaki_tall_work_bytes(n, k, m)));
-        ozaki_tall(ctx, n, k, m, A, lda, cs, B, ldb, C, ldc, h->rOzT.p, KC_TALL_GEMM);
+        ozaki_tall(ctx, n, k, m, A, lda, cs, B, ldb, C, ldc, h->rOzT.p, KC_TALL_GEMM,
+                   h->opts.gram_ozaki == 2 ? h->d_pin + 1 : nullptr);
         return SLRF_OK;
     }
     if (cs) small_scale_rows(ctx, k, cs, B);
@@ -1325,6 +1327,7 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
                     double *AX, double *BX, int32_t *chol_status) {
     Ctx &ctx = h->ctx;
     *(volatile int32_t *)(h->h_pin + 1) = 0;   // device-side wait timeouts of this step
+    *(volatile int32_t *)(h->h_pin + 2) = 0;   // pass 1's Cholesky status
     const int64_t n = h->A.n;
     const size_t m2 = (size_t)m * m;
     const int split = gram_split(ctx, m, n);
@@ -1345,7 +1348,10 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     // ||U S||^2 (Fukaya et al., SIAM J. Sci. Comput. 2020; ||U S||^2 <= m after
     // the column scaling) and a third pass follows (shifted Cholesky-QR3).
     const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * m;
-    int32_t *pin_status = h->d_pin + 1;   // mapped: the host reads it after pass 1
+    // mapped (third word of the handle's poll slot; the second one collects
+    // the bounded-wait timeouts of the tensor-core kernels): the host reads
+    // it after pass 1
+    int32_t *pin_status = h->d_pin + 2;
     spmm_real(ctx, h->A, m, U, ldu, nullptr, 0, W1, m);
     CKS(gram(h, n, m, U, ldu, W1, m, G, true));
     small_colscale(ctx, m, G, s);
@@ -1355,7 +1361,11 @@ slrf_status rr_step(slrf_handle *h, int m, const double *U, int64_t ldu, double 
     CKS(tall_product(h, n, m, m, U, ldu, s, T1, m, Q1, m));
     CK(cudaEventRecord(h->ev_poll, ctx.stream));
     CK(cudaEventSynchronize(h->ev_poll));
-    const int32_t st1 = *(volatile int32_t *)(h->h_pin + 1);
+    if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
+        g_last_error = "projection step: a bounded device wait gave up";
+        return SLRF_ETIMEOUT;
+    }
+    const int32_t st1 = *(volatile int32_t *)(h->h_pin + 2);
     if (st1 > 0) {
         if (chol_status) {
             chol_status[0] = st1;
@@ -1885,7 +1895,7 @@ void slrf_destroy(slrf_handle *h) {
     if (!h) return;
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
-                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT, &h->kBcg,
+                   &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT, &h->kBcg, &h->rTallB,
                    &h->mg_eig[0].dev, &h->mg_eig[1].dev, &h->mg_eig[2].dev, &h->mg_eig[3].dev,
                    &h->mg_eig[4].dev, &h->mg_eig[5].dev, &h->mg_eig[6].dev, &h->mg_eig[7].dev,
                    &h->mg_eig[8].dev, &h->mg_eig[9].dev, &h->mg_eig[10].dev, &h->mg_eig[11].dev,
@@ -2360,6 +2370,25 @@ slrf_status slrf_gram(slrf_handle *h, int32_t m, const double *X, int64_t ldx, c
     CK(cudaGetLastError());
     if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
         g_last_error = "Gram: a bounded device wait gave up";
+        return SLRF_ETIMEOUT;
+    }
+    return SLRF_OK;
+}
+
+slrf_status slrf_tall_product(slrf_handle *h, int32_t k, int32_t m, const double *A, int64_t lda, const double *B,
+                              int64_t ldb, double *C, int64_t ldc) {
+    if (!h || !A || !B || !C || k < 1 || m < 1 || lda < k || ldb < m || ldc < m) return SLRF_EINVAL;
+    CK(cudaStreamSynchronize(h->ctx.stream));
+    *(volatile int32_t *)(h->h_pin + 1) = 0;
+    CKS(ensure(h, h->rTallB, (size_t)k * m * sizeof(double)));
+    // tall_product may scale B in place (FP64 path with column scaling): a copy
+    CK(cudaMemcpy2DAsync(h->rTallB.p, (size_t)m * 8, B, (size_t)ldb * 8, (size_t)m * 8, (size_t)k,
+                         cudaMemcpyDeviceToDevice, h->ctx.stream));
+    CKS(tall_product(h, h->A.n, k, m, A, lda, nullptr, as<double>(h->rTallB), m, C, ldc));
+    CK(cudaStreamSynchronize(h->ctx.stream));
+    CK(cudaGetLastError());
+    if (*(volatile int32_t *)(h->h_pin + 1) != 0) {
+        g_last_error = "tall product: a bounded device wait gave up";
         return SLRF_ETIMEOUT;
     }
     return SLRF_OK;

@@ -315,11 +315,14 @@ size_t ozaki_gram_work_bytes(int64_t n, int m, int sm_count);
 void ozaki_gram(Ctx &ctx, int64_t n, int m, const double *X, int64_t ldx, const double *Y, int64_t ldy, double *G,
                 void *work, bool symmetric = false, int32_t *tc_err = nullptr);
 // C = (A diag(cs)) B, A n x k, B k x m, C n x m (row-major, leading dims),
-// cs = nullptr for no column scaling; FP64-accurate from int8 digit products.
+// cs = nullptr for no column scaling; FP64-accurate from exact digit
+// products.  tc_err != nullptr (and k <= 512) selects the tcgen05 form (bf16
+// digits, FP32 tensor-memory sums); it receives a nonzero code if one of that
+// kernel's bounded waits gives up.  Otherwise int8 mma.sync.
 size_t ozaki_tall_work_bytes(int64_t n, int k, int m);
 bool ozaki_tall_fits(int k);
 void ozaki_tall(Ctx &ctx, int64_t n, int k, int m, const double *A, int64_t lda, const double *cs, const double *B,
-                int64_t ldb, double *C, int64_t ldc, void *work, int kc);
+                int64_t ldb, double *C, int64_t ldc, void *work, int kc, int32_t *tc_err = nullptr);
 
 // ---------------------------------------------------------------- small.cu
 // All m x m matrices row-major, device.  status: device int, set nonzero on

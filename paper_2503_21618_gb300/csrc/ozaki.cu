@@ -323,17 +323,41 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// sum_d v_d 2^(-7(d+2)) of the seven FP32 accumulators (exact integers,
+// |v_d| <= (d+1) 2^12 K with K <= 512 rows per slice) with two FP64
+// operations instead of seven: T = sum_{d>=1} v_d 2^(7(6-d)) is exact in
+// int64 (|T| < K 2^49), and the result is 2^-14 (v_0 + 2^-42 T), whose one
+// rounding is that of an FP64 sum.  FP64 runs at a small fraction of the
+// integer rate here, and these epilogues make one such sum per output.
+__device__ __forceinline__ double oz_combine(const float v[OZ_S]) {
+    long long t = 0;
+#pragma unroll
+    for (int d = 1; d < OZ_S; ++d) t += (long long)__float2int_rn(v[d]) * (1ll << (7 * (OZ_S - 1 - d)));
+    return fma((double)t, 0x1p-56, (double)__float2int_rn(v[0]) * 0x1p-14);
+}
+
+// x 2^e for the exponents of these products (power of two built from its
+// bits while 2^e is a normal number, else ldexp)
+__device__ __forceinline__ double oz_scale(double x, int e) {
+    return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(x, e);
+}
+
 // One CTA: output block a in [128 ta, +128), b in [64 tb, +64) of K-slice z
 // (rows [512 z, 512 z + 512)).  Warp 0: TMEM allocation and the bulk copies
 // of the digit panels; warp 1 lane 0: the MMAs; all four warps: epilogue
-// (thread = TMEM lane = row a).  work[z][a][b] (m x m per slice) receives
-// sum_d 2^(-7(d+2)) sum_{s+t=d} D_s^T E_t for a, b < m.
+// (thread = TMEM lane = row a).  Gram (TALL = false): work[z][a][b] (m x m
+// per slice) receives sum_d 2^(-7(d+2)) sum_{s+t=d} D_s^T E_t for a, b < m.
+// Tall product (TALL = true, one slice: K <= 512): C[a][b] receives that sum
+// times 2^(ea[a] + eb[b]) for a < nrows, b < m.
+template <bool TALL>
 __global__ void __launch_bounds__(128, 1)
 k_oz_gram_tc(int m, int nta, int ntb, int64_t nks, int ntrx, int ntry, const __nv_bfloat16 *__restrict__ PX,
-             const __nv_bfloat16 *__restrict__ PY, double *__restrict__ work, int symmetric, int32_t *__restrict__ err) {
+             const __nv_bfloat16 *__restrict__ PY, double *__restrict__ work, int symmetric, int32_t *__restrict__ err,
+             int64_t nrows, double *__restrict__ C, int64_t ldc, const int *__restrict__ ea,
+             const int *__restrict__ eb) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int ta = blockIdx.x / ntb, tb = blockIdx.x % ntb;
-    if (symmetric && tb < 2 * ta) return;   // block entirely below the diagonal
+    if (!TALL && symmetric && tb < 2 * ta) return;   // block entirely below the diagonal
     const int z = blockIdx.y;
     const int64_t ks0 = (int64_t)z * (TC_KSLICE / TC_KSTEP);
     const int nsteps = (int)min((int64_t)(TC_KSLICE / TC_KSTEP), nks - ks0);
@@ -406,27 +430,45 @@ k_oz_gram_tc(int m, int nta, int ntb, int64_t nks, int ntrx, int ntry, const __n
     // ---- epilogue: thread = row a of the block (TMEM lane 32 warp + lane)
     const bool ok = mbar_wait_bounded(done, 0, LIMIT_NS);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int a = ta * TC_TM + warp * 32 + lane;
-    double *W = work + (int64_t)z * m * m;
+    const int64_t a = (int64_t)ta * TC_TM + warp * 32 + lane;
+    double *W = TALL ? nullptr : work + (int64_t)z * m * m;
     if (__any_sync(0xffffffffu, !ok)) {
         if (lane == 0) atomicExch(err, 5);
+    } else if (TALL) {
+        const int e_a = a < nrows ? ea[a] : 0;
+        for (int c16 = 0; c16 < TC_TN / 16; ++c16) {
+            float v[OZ_S][16];
+#pragma unroll
+            for (int d = 0; d < OZ_S; ++d)
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TC_TN + c16 * 16), v[d]);
+            if (a < nrows)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int b = tb * TC_TN + c16 * 16 + j;
+                    if (b < m) {
+                        float u[OZ_S];
+#pragma unroll
+                        for (int d = 0; d < OZ_S; ++d) u[d] = v[d][j];
+                        C[a * ldc + b] = oz_scale(oz_combine(u), e_a + eb[b]);
+                    }
+                }
+        }
     } else {
         for (int c16 = 0; c16 < TC_TN / 16; ++c16) {
-            double acc[16];
+            float v[OZ_S][16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-            for (int d = 0; d < OZ_S; ++d) {
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TC_TN + c16 * 16), v);
-                const double scale = ldexp(1.0, -7 * (d + 2));
-#pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] = fma((double)v[j], scale, acc[j]);
-            }
+            for (int d = 0; d < OZ_S; ++d)
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * TC_TN + c16 * 16), v[d]);
             if (a < m)
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int b = tb * TC_TN + c16 * 16 + j;
-                    if (b < m) W[(int64_t)a * m + b] = acc[j];
+                    if (b < m) {
+                        float u[OZ_S];
+#pragma unroll
+                        for (int d = 0; d < OZ_S; ++d) u[d] = v[d][j];
+                        W[a * m + b] = oz_combine(u);
+                    }
                 }
         }
     }
@@ -435,6 +477,19 @@ k_oz_gram_tc(int m, int nta, int ntb, int64_t nks, int ntrx, int ntry, const __n
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// The kernels' shared-memory limit, raised once per device (attributes are
+// process-wide and every launch uses the same size).
+static void raise_tc_smem() {
+    static bool raised[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !raised[dev]) {
+        cudaFuncSetAttribute(k_oz_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        cudaFuncSetAttribute(k_oz_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        raised[dev] = true;
     }
 }
 
@@ -452,13 +507,7 @@ static void ozaki_gram_tc(Ctx &ctx, int64_t n, int m, const double *X, int64_t l
     int *ex = reinterpret_cast<int *>(mb + 2 * m);
     int *ey = ex + m;
     double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(ey + m) + 16 - ((uintptr_t)(ey + m) & 15));
-    static bool raised[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !raised[dev]) {
-        cudaFuncSetAttribute(k_oz_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        raised[dev] = true;
-    }
+    raise_tc_smem();
     cudaMemsetAsync(mb, 0, 2 * (size_t)m * sizeof(unsigned long long), ctx.stream);
     const dim3 cgrid((m + 31) / 32, 64), cblock(32, 8);
     ctx.before(KC_GRAM, 8.0 * (double)n * m * 2, 0);
@@ -480,8 +529,8 @@ static void ozaki_gram_tc(Ctx &ctx, int64_t n, int m, const double *X, int64_t l
     const double pairs = OZ_S * (OZ_S + 1) / 2.0;
     ctx.before(KC_GRAM, 2.0 * OZ_S * (double)nks * TC_KSTEP * 64.0 * (2.0 * live + live) + 8.0 * nz * m * m,
                2.0 * pairs * (double)live * TC_TM * TC_TN * nks * TC_KSTEP);
-    k_oz_gram_tc<<<dim3(nta * ntb, nz), 128, TC_SMEM, ctx.stream>>>(m, nta, ntb, nks, ntrx, ntry, PX, PY, part,
-                                                                    symmetric ? 1 : 0, err);
+    k_oz_gram_tc<false><<<dim3(nta * ntb, nz), 128, TC_SMEM, ctx.stream>>>(
+        m, nta, ntb, nks, ntrx, ntry, PX, PY, part, symmetric ? 1 : 0, err, 0, nullptr, 0, nullptr, nullptr);
     ctx.after();
     ctx.before(KC_GRAM, 8.0 * (double)nz * m * m, 0);
     k_oz_reduce<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, ctx.stream>>>(m, nz, part, ex, ey, G, m,
@@ -662,17 +711,106 @@ k_oz_tall(int64_t n, int m, int kpad, int64_t npad, int mpad, const int8_t *__re
             }
 }
 
+// Tall product on tcgen05: row exponents and digits of A diag(cs) into the
+// K-major panel layout of k_oz_gram_tc's A operand (panel rows = rows a of
+// A, K = its columns i, zero beyond k and beyond n).  One warp per row: the
+// row maximum, then each lane the digits of 8 consecutive columns.
+__global__ void __launch_bounds__(256)
+k_oz_rowsplit_panel(int64_t n, int k, const double *__restrict__ A, int64_t lda, const double *__restrict__ cs,
+                    int64_t nks, int ntr, int *__restrict__ e, __nv_bfloat16 *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (a >= (int64_t)ntr * 64) return;
+    const bool live = a < n;
+    double mx = 0.0;
+    if (live)
+        for (int i = lane; i < k; i += 32) mx = fmax(mx, fabs(A[a * lda + i] * (cs ? cs[i] : 1.0)));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    const int ea = mx > 0.0 ? ilogb(mx) + 2 : 0;
+    if (lane == 0 && live) e[a] = ea;
+    const int panel = (int)(a >> 6), mg = (int)((a & 63) >> 3), r = (int)(a & 7);
+    for (int64_t i8 = lane; i8 < nks * 4; i8 += 32) {
+        int8_t d[8][OZ_S];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int64_t i = i8 * 8 + t;
+            const double x = (live && i < k) ? A[a * lda + i] * (cs ? cs[i] : 1.0) : 0.0;
+            oz_digits(x, ea, d[t]);
+        }
+        const int64_t ks = i8 >> 2;
+        const int kc = (int)(i8 & 3);
+#pragma unroll
+        for (int s = 0; s < OZ_S; ++s) {
+            const int64_t core = (((int64_t)s * nks + ks) * ntr + panel) * 32 + mg * 4 + kc;
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = __int2bfloat16_rn((int)d[t][s]);
+            *reinterpret_cast<uint4 *>(out + core * 64 + r * 8) = *reinterpret_cast<const uint4 *>(v);
+        }
+    }
+}
+
+// C = (A diag(cs)) B with A n x k, B k x m, k <= 512 (one K-slice: the FP32
+// tensor-memory sums of digit products stay exact), on tcgen05.  *err (a
+// mapped host word) records a bounded wait that gave up.
+static void ozaki_tall_tc(Ctx &ctx, int64_t n, int k, int m, const double *A, int64_t lda, const double *cs,
+                          const double *B, int64_t ldb, double *C, int64_t ldc, void *work, int kc, int32_t *err) {
+    const int64_t nks = (k + TC_KSTEP - 1) / TC_KSTEP;
+    const int nta = (int)((n + TC_TM - 1) / TC_TM), ntb = (m + TC_TN - 1) / TC_TN;
+    const int ntra = 2 * nta, ntrb = ntb;
+    char *w = reinterpret_cast<char *>(work);
+    __nv_bfloat16 *PA = reinterpret_cast<__nv_bfloat16 *>(w);
+    __nv_bfloat16 *PB = PA + (size_t)OZ_S * nks * ntra * 2048;
+    char *tail = reinterpret_cast<char *>(PB + (size_t)OZ_S * nks * ntrb * 2048);
+    unsigned long long *mb = reinterpret_cast<unsigned long long *>(tail);
+    int *eb = reinterpret_cast<int *>(mb + m);
+    int *ea = eb + m;
+    raise_tc_smem();
+    // B: column exponents and digit panels (panel rows = columns b, K = rows of B)
+    cudaMemsetAsync(mb, 0, (size_t)m * sizeof(unsigned long long), ctx.stream);
+    const dim3 cgrid((m + 31) / 32, (unsigned)std::min<int64_t>((k + 7) / 8, 64)), cblock(32, 8);
+    ctx.before(kc, 8.0 * (double)k * m * 2 + 2.0 * OZ_S * nks * TC_KSTEP * 64.0 * ntrb, 0);
+    k_oz_colmax<<<cgrid, cblock, 0, ctx.stream>>>(k, m, B, ldb, mb);
+    k_oz_exponent<<<(m + 127) / 128, 128, 0, ctx.stream>>>(m, mb, eb);
+    const unsigned gy = (unsigned)std::min<int64_t>((nks * 4 + 7) / 8, 8192);
+    k_oz_split_panel<<<dim3(ntrb * 2, gy), 256, 0, ctx.stream>>>(k, m, B, ldb, eb, nks, ntrb, PB);
+    ctx.after();
+    // A: row exponents and digit panels
+    ctx.before(kc, 8.0 * (double)n * k + 2.0 * OZ_S * nks * TC_KSTEP * 64.0 * ntra, 0);
+    k_oz_rowsplit_panel<<<(unsigned)((int64_t)ntra * 64 / 8), 256, 0, ctx.stream>>>(n, k, A, lda, cs, nks, ntra,
+                                                                                   ea, PA);
+    ctx.after();
+    const double pairs = OZ_S * (OZ_S + 1) / 2.0;
+    ctx.before(kc, 2.0 * OZ_S * (double)nks * TC_KSTEP * 64.0 * (2.0 * nta * ntb + (double)nta * ntb) +
+                       8.0 * (double)n * m,
+               2.0 * pairs * (double)nta * ntb * TC_TM * TC_TN * nks * TC_KSTEP);
+    k_oz_gram_tc<true><<<dim3(nta * ntb, 1), 128, TC_SMEM, ctx.stream>>>(m, nta, ntb, nks, ntra, ntrb, PA, PB,
+                                                                        nullptr, 0, err, n, C, ldc, ea, eb);
+    ctx.after();
+}
+
 size_t ozaki_tall_work_bytes(int64_t n, int k, int m) {
     const int64_t npad = (n + OZ_TA - 1) / OZ_TA * OZ_TA;
     const int kpad = (k + 31) / 32 * 32, mpad = (m + OZ_TB - 1) / OZ_TB * OZ_TB;
-    return (size_t)OZ_S * npad * kpad + (size_t)OZ_S * mpad * kpad + 256 + (size_t)npad * sizeof(int) +
-           (size_t)m * (sizeof(int) + 8) + 1024;
+    const size_t mma_sync = (size_t)OZ_S * npad * kpad + (size_t)OZ_S * mpad * kpad + 256 +
+                            (size_t)npad * sizeof(int) + (size_t)m * (sizeof(int) + 8) + 1024;
+    // tensor-core form: bf16 digit panels of A (rows) and B (columns), exponents
+    const int64_t nks = (k + TC_KSTEP - 1) / TC_KSTEP;
+    const int64_t nta = (n + TC_TM - 1) / TC_TM, ntb = (m + TC_TN - 1) / TC_TN;
+    const size_t tc = (size_t)OZ_S * nks * (2 * nta + ntb) * 2048 * sizeof(__nv_bfloat16) + (size_t)m * 12 +
+                      (size_t)nta * TC_TM * sizeof(int) + 1024;
+    return std::max(mma_sync, tc);
 }
 
 bool ozaki_tall_fits(int k) { return (k + 31) / 32 * 32 <= 65536; }
 
 void ozaki_tall(Ctx &ctx, int64_t n, int k, int m, const double *A, int64_t lda, const double *cs, const double *B,
-                int64_t ldb, double *C, int64_t ldc, void *work, int kc) {
+                int64_t ldb, double *C, int64_t ldc, void *work, int kc, int32_t *tc_err) {
+    if (tc_err && k <= TC_KSLICE) {
+        ozaki_tall_tc(ctx, n, k, m, A, lda, cs, B, ldb, C, ldc, work, kc, tc_err);
+        return;
+    }
     const int64_t npad = (n + OZ_TA - 1) / OZ_TA * OZ_TA;
     const int kpad = (k + 31) / 32 * 32, mpad = (m + OZ_TB - 1) / OZ_TB * OZ_TB;
     char *w = reinterpret_cast<char *>(work);

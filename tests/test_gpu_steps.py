@@ -154,6 +154,23 @@ def test_gram_matches_numpy(api, n, m, ozaki):
     assert np.abs(G - ref).max() <= 1e-13 * np.abs(X).max() * np.abs(Y).max() * n
 
 
+@pytest.mark.parametrize("ozaki", [2, 1, 0])
+@pytest.mark.parametrize("n,k,m", [(1000, 1, 1), (5001, 150, 150), (20011, 31, 77), (3001, 300, 65), (777, 512, 40),
+                                   (2049, 513, 33), (70000, 96, 150)])
+def test_tall_product_matches_numpy(api, n, k, m, ozaki):
+    # C = A B: rows of A graded over 20 decades (each row takes its own
+    # exponent), columns of B over 10; k = 513 leaves the tensor-core form's
+    # single 512-row K-slice and runs mma.sync
+    rng = np.random.default_rng(n + k)
+    A = rng.standard_normal((n, k)) * np.exp2(rng.integers(-33, 33, n))[:, None]
+    B = rng.standard_normal((k, m)) * np.exp2(rng.integers(-16, 16, m))[None, :]
+    h = api.Handle(pencil_1d(n), api.default_opts(gram_ozaki=ozaki))
+    C = h.tall_product(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()).cpu().numpy()
+    ref = A @ B
+    bound = np.abs(A) @ np.abs(B)
+    assert np.all(np.abs(C - ref) <= 1e-13 * bound + 1e-300)
+
+
 @pytest.mark.parametrize("ozaki", [2, 1])
 def test_ozaki_gram_graded_columns(api, ozaki):
     # columns spanning 16 orders of magnitude, zero and subnormal-free tiny columns
