@@ -72,27 +72,37 @@ void small_scale_rows(Ctx &ctx, int m, const double *s, double *T) {
 // ---------------------------------------------------------------------------
 // Cholesky G + shift I = R^T R (R upper), one block, right-looking.  G is read
 // and left untouched; R is written to Rg.  If the factorisation of G breaks
-// down (pivot <= 0 or non-finite) and shift_on_fail > 0, it is redone on
-// G + shift_on_fail I (shifted Cholesky-QR) and *status = -1; an
-// unrecoverable breakdown sets *status = k + 1 (k = failing pivot).
+// down (a pivot <= shift_on_fail, or non-finite) and shift_on_fail > 0, it is
+// redone on G + shift_on_fail I (shifted Cholesky-QR) and *status = -1; an
+// unrecoverable breakdown (pivot <= 0 with no shift) sets *status = k + 1
+// (k = failing pivot).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *__restrict__ G, double *__restrict__ Rg,
                                                       int32_t *__restrict__ status, int use_smem,
-                                                      double shift_on_fail) {
+                                                      double shift_on_fail, int only_if_failed) {
     extern __shared__ double sm[];
     double *A = use_smem ? sm : Rg;
     const int tid = threadIdx.x, bs = blockDim.x;
     __shared__ int bad;
     __shared__ double dinv;
     double shift = 0.0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    int first = 0;
+    if (only_if_failed) {   // the blocked form's breakdown fallback: shifted factor only
+        if (*(volatile int32_t *)status <= 0) return;
+        first = 1;
+        shift = shift_on_fail;
+    }
+    for (int attempt = first; attempt < 2; ++attempt) {
         for (int e = tid; e < m * m; e += bs) A[e] = G[e] + ((e / m == e % m) ? shift : 0.0);
         if (tid == 0) bad = 0;
         __syncthreads();
+        // unshifted: a pivot at or below the shift (a numerically dependent
+        // column of the column-scaled Gram) counts as a breakdown too
+        const double pmin = attempt == 0 ? shift_on_fail : 0.0;
         for (int k = 0; k < m; ++k) {
             if (tid == 0) {
                 const double d = A[k * m + k];
-                if (!(d > 0.0) || !isfinite(d)) {
+                if (!(d > pmin) || !isfinite(d)) {
                     bad = k + 1;
                 } else {
                     const double r = sqrt(d);
@@ -128,13 +138,156 @@ __global__ void __launch_bounds__(1024) k_chol_upper(int m, const double *__rest
 
 void raise_smem_limits();   // defined after the kernels it configures
 
+// ---------------------------------------------------------------------------
+// Blocked form for m >= 64: the CHB x CHB diagonal blocks on one CTA, the
+// panel solves and the symmetric trailing updates spread over the GPU (FP64
+// runs at a small fraction of the FP32 rate here, and one CTA would do all
+// m^3/6 FMAs of the update alone).  Right-looking, in place in R (upper).
+// A breakdown at pivot k (a pivot at or below shift_on_fail) sets *status =
+// k + 1 and stops the later steps; with shift_on_fail > 0 the one-block
+// kernel then refactors G + shift I.
+// ---------------------------------------------------------------------------
+constexpr int CHB = 32;
+
+__global__ void k_chol_init(int m, const double *__restrict__ G, double *__restrict__ A, int32_t *__restrict__ status) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e == 0) *status = 0;
+    if (e < (int64_t)m * m && G != A) A[e] = G[e];
+}
+
+__global__ void __launch_bounds__(256) k_chol_diag(int m, int k0, int kb, double *__restrict__ A,
+                                                  int32_t *__restrict__ status, double pmin) {
+    __shared__ double S[CHB][CHB + 1];
+    __shared__ int bad;
+    __shared__ double dinv;
+    if (*(volatile int32_t *)status != 0) return;
+    const int tid = threadIdx.x, bs = blockDim.x;
+    for (int e = tid; e < kb * kb; e += bs) S[e / kb][e % kb] = A[(int64_t)(k0 + e / kb) * m + k0 + e % kb];
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int k = 0; k < kb; ++k) {
+        if (tid == 0) {
+            const double d = S[k][k];
+            if (!(d > pmin) || !isfinite(d)) {
+                bad = k0 + k + 1;
+            } else {
+                const double r = sqrt(d);
+                S[k][k] = r;
+                dinv = 1.0 / r;
+            }
+        }
+        __syncthreads();
+        if (bad) break;
+        for (int j = k + 1 + tid; j < kb; j += bs) S[k][j] *= dinv;
+        __syncthreads();
+        const int r = kb - k - 1;
+        for (int e = tid; e < r * r; e += bs) {
+            const int i = k + 1 + e / r, j = k + 1 + e % r;
+            if (j >= i) S[i][j] -= S[k][i] * S[k][j];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) *status = bad;
+        return;
+    }
+    for (int e = tid; e < kb * kb; e += bs) {
+        const int i = e / kb, j = e % kb;
+        A[(int64_t)(k0 + i) * m + k0 + j] = j >= i ? S[i][j] : 0.0;
+    }
+}
+
+// rows k0 .. k0+kb of the columns right of the block: x = R_kk^{-T} a
+__global__ void __launch_bounds__(128) k_chol_panel(int m, int k0, int kb, double *__restrict__ A,
+                                                   const int32_t *__restrict__ status) {
+    __shared__ double Rk[CHB][CHB + 1];
+    __shared__ double rinv[CHB];
+    if (*(volatile int32_t *)status != 0) return;
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x)
+        Rk[e / kb][e % kb] = A[(int64_t)(k0 + e / kb) * m + k0 + e % kb];
+    __syncthreads();
+    for (int i = threadIdx.x; i < kb; i += blockDim.x) rinv[i] = 1.0 / Rk[i][i];
+    __syncthreads();
+    const int c = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    double x[CHB];
+#pragma unroll
+    for (int i = 0; i < CHB; ++i) {
+        if (i < kb) {
+            double v = A[(int64_t)(k0 + i) * m + c];
+            for (int p = 0; p < i; ++p) v = fma(-Rk[p][i], x[p], v);
+            x[i] = v * rinv[i];
+            A[(int64_t)(k0 + i) * m + c] = x[i];
+        }
+    }
+}
+
+// A[i][j] -= sum_p A[k0+p][i] A[k0+p][j] for k0+kb <= i <= j < m, 16 x 16
+// output tiles (the tiles below the diagonal return at once)
+__global__ void __launch_bounds__(256) k_chol_update(int m, int k0, int kb, double *__restrict__ A,
+                                                    const int32_t *__restrict__ status) {
+    __shared__ double Pi[CHB][17], Pj[CHB][17];
+    if (*(volatile int32_t *)status != 0) return;
+    const int r0 = k0 + kb;
+    if (blockIdx.x < blockIdx.y) return;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = r0 + blockIdx.y * 16, j0 = r0 + blockIdx.x * 16;
+    for (int e = threadIdx.x; e < kb * 16; e += 256) {
+        const int p = e / 16, q = e % 16;
+        Pi[p][q] = (i0 + q < m) ? A[(int64_t)(k0 + p) * m + i0 + q] : 0.0;
+        Pj[p][q] = (j0 + q < m) ? A[(int64_t)(k0 + p) * m + j0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int i = i0 + ty, j = j0 + tx;
+    if (i >= m || j >= m || j < i) return;
+    double s = 0.0;
+    for (int p = 0; p < kb; ++p) s = fma(Pi[p][ty], Pj[p][tx], s);
+    A[(int64_t)i * m + j] -= s;
+}
+
+__global__ void k_chol_finish(int m, double *__restrict__ A, const int32_t *__restrict__ status) {
+    if (*(volatile int32_t *)status != 0) return;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < (int64_t)m * m && e % m < e / m) A[e] = 0.0;
+}
+
 void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *status, double shift_on_fail) {
     const size_t smem = (size_t)m * m * sizeof(double);
     const int use_smem = smem <= 200 * 1024;
     raise_smem_limits();
-    ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
-    k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, R, status, use_smem, shift_on_fail);
+    if (m < 64) {
+        ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
+        k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, R, status, use_smem, shift_on_fail, 0);
+        ctx.after();
+        return;
+    }
+    const int64_t m2 = (int64_t)m * m;
+    const unsigned eg = (unsigned)((m2 + 255) / 256);
+    ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
+    k_chol_init<<<eg, 256, 0, ctx.stream>>>(m, G, R, status);
     ctx.after();
+    for (int k0 = 0; k0 < m; k0 += CHB) {
+        const int kb = std::min(CHB, m - k0), rest = m - k0 - kb;
+        ctx.before(KC_SMALL_DENSE, 16.0 * kb * kb, (double)kb * kb * kb / 3.0);
+        k_chol_diag<<<1, 256, 0, ctx.stream>>>(m, k0, kb, R, status, shift_on_fail);
+        ctx.after();
+        if (rest == 0) break;
+        ctx.before(KC_SMALL_DENSE, 16.0 * kb * rest, 0.5 * kb * kb * rest);
+        k_chol_panel<<<(rest + 127) / 128, 128, 0, ctx.stream>>>(m, k0, kb, R, status);
+        ctx.after();
+        const int tiles = (rest + 15) / 16;
+        ctx.before(KC_SMALL_DENSE, 8.0 * rest * rest, 0.5 * (double)rest * rest * kb);
+        k_chol_update<<<dim3(tiles, tiles), 256, 0, ctx.stream>>>(m, k0, kb, R, status);
+        ctx.after();
+    }
+    ctx.before(KC_SMALL_DENSE, 8.0 * m2, 0);
+    k_chol_finish<<<eg, 256, 0, ctx.stream>>>(m, R, status);
+    ctx.after();
+    if (shift_on_fail > 0.0 && G != R) {
+        ctx.before(KC_SMALL_DENSE, 16.0 * m2, 0);
+        k_chol_upper<<<1, 1024, use_smem ? smem : 0, ctx.stream>>>(m, G, R, status, use_smem, shift_on_fail, 1);
+        ctx.after();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -143,10 +296,16 @@ void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *stat
 // column in shared memory and each sum split over the lanes (R rows are read
 // coalesced; R stays in L1/L2).  Entries below the diagonal are set to zero.
 // ---------------------------------------------------------------------------
+// The reciprocals of the diagonal are formed once per column block up front
+// (FP64 division is slow here), so each step of the chain is FMAs and one
+// warp reduction.
 __global__ void __launch_bounds__(32) k_triinv_upper(int m, const double *__restrict__ R, double *__restrict__ X) {
     extern __shared__ double xcol[];
+    double *rinv = xcol + m;
     const int j = blockIdx.x, lane = threadIdx.x;
+    for (int i = lane; i <= j; i += 32) rinv[i] = 1.0 / R[(int64_t)i * m + i];
     for (int i = j + 1 + lane; i < m; i += 32) X[(int64_t)i * m + j] = 0.0;
+    __syncwarp();
     for (int i = j; i >= 0; --i) {
         const double *Ri = R + (int64_t)i * m;
         double s = 0.0;
@@ -154,7 +313,7 @@ __global__ void __launch_bounds__(32) k_triinv_upper(int m, const double *__rest
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) {
-            const double x = ((i == j ? 1.0 : 0.0) - s) / Ri[i];
+            const double x = ((i == j ? 1.0 : 0.0) - s) * rinv[i];
             xcol[i] = x;
             X[(int64_t)i * m + j] = x;
         }
@@ -163,7 +322,7 @@ __global__ void __launch_bounds__(32) k_triinv_upper(int m, const double *__rest
 }
 
 void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv) {
-    const size_t smem = (size_t)m * sizeof(double);
+    const size_t smem = 2 * (size_t)m * sizeof(double);
     ctx.before(KC_SMALL_DENSE, 16.0 * m * m, (double)m * m * m / 3.0);
     raise_smem_limits();
     k_triinv_upper<<<m, 32, smem, ctx.stream>>>(m, R, Rinv);
@@ -474,7 +633,7 @@ size_t small_syev_work_bytes(int m) {
     const size_t m2 = (size_t)m * m;
     // A32/V32 global fallback (2 mp^2 doubles) + S0, S1, G, Y, T, V (6 m^2) + lam0, normA, counters,
     // component labels and sizes (2 m ints)
-    return 2 * mp * mp * sizeof(double) + 6 * m2 * sizeof(double) + 2 * (size_t)m * sizeof(double) +
+    return 2 * mp * mp * sizeof(double) + 6 * m2 * sizeof(double) + (2 * (size_t)m + 2) * sizeof(double) +
            2 * (size_t)m * sizeof(int) + 4096;
 }
 
@@ -510,35 +669,40 @@ __device__ double block_sum(double v, double *red) {
     return t;
 }
 
-// Ep = I + E (row-major), lam_t = t_ii / g_ii
-__global__ void __launch_bounds__(1024) k_oa_update(int m, const double *__restrict__ G, const double *__restrict__ T,
-                                                   const double *__restrict__ normS, double *__restrict__ Ep,
-                                                   double *__restrict__ lam_t) {
+// lam_t = t_ii / g_ii and the pair threshold delta = 2 ||T - D||_F (one
+// block: the norm is one fixed-order reduction)
+__global__ void __launch_bounds__(1024) k_oa_norms(int m, const double *__restrict__ G, const double *__restrict__ T,
+                                                  double *__restrict__ lam_t, double *__restrict__ delta) {
     __shared__ double red[32];
     const int tid = threadIdx.x, bs = blockDim.x;
-    for (int i = tid; i < m; i += bs) lam_t[i] = T[(int64_t)i * m + i] / G[(int64_t)i * m + i];
-    __syncthreads();
     double off = 0.0;
     for (int e = tid; e < m * m; e += bs) {
         const int i = e / m, j = e % m;
-        const double d = T[e] - (i == j ? lam_t[i] : 0.0);
+        const double d = i == j ? T[e] - T[e] / G[e] : T[e];
         off += d * d;
     }
     off = block_sum(off, red);
-    const double delta = 2.0 * sqrt(off);
-    for (int e = tid; e < m * m; e += bs) {
-        const int i = e / m, j = e % m;
-        const double r = (i == j ? 1.0 : 0.0) - G[e];
-        double v;
-        if (i == j) {
-            v = 1.0 + 0.5 * r;
-        } else {
-            const double li = lam_t[i], lj = lam_t[j], num = T[e] + lj * r;
-            const bool sep = fabs(li - lj) > delta && 8.0 * fabs(num) <= fabs(lj - li);
-            v = sep ? num / (lj - li) : 0.5 * r;
-        }
-        Ep[e] = v;
+    for (int i = tid; i < m; i += bs) lam_t[i] = T[(int64_t)i * m + i] / G[(int64_t)i * m + i];
+    if (tid == 0) *delta = 2.0 * sqrt(off);
+}
+
+// Ep = I + E (row-major), one thread per entry over many blocks (the FP64
+// divisions spread over the GPU)
+__global__ void k_oa_step(int m, const double *__restrict__ G, const double *__restrict__ T,
+                          const double *__restrict__ lam_t, const double *__restrict__ delta, double *__restrict__ Ep) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)m * m) return;
+    const int i = (int)(e / m), j = (int)(e % m);
+    const double r = (i == j ? 1.0 : 0.0) - G[e];
+    double v;
+    if (i == j) {
+        v = 1.0 + 0.5 * r;
+    } else {
+        const double li = lam_t[i], lj = lam_t[j], num = T[e] + lj * r;
+        const bool sep = fabs(li - lj) > *delta && 8.0 * fabs(num) <= fabs(lj - li);
+        v = sep ? num / (lj - li) : 0.5 * r;
     }
+    Ep[e] = v;
 }
 
 // Newton-Schulz orthonormalisation factor: Ep = (3 I - G) / 2
@@ -758,8 +922,8 @@ cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q,
     double *Tm = Ym + m2;
     double *Vm = Tm + m2;
     double *lam0 = Vm + m2;
-    double *normA = lam0 + m;
-    int *cnt = reinterpret_cast<int *>(normA + m);
+    double *normA = lam0 + m;   // [0] = ||S||_F, [1] = the refinement's pair threshold
+    int *cnt = reinterpret_cast<int *>(normA + m + 2);
     int32_t *cst = cnt + 4;
 
     ctx.before(KC_SMALL_DENSE, 8.0 * m2, 2.0 * m2);
@@ -804,8 +968,11 @@ cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q,
             dgemm(ctx, 1, 0, m, m, m, X0, m, X0, m, 0.0, G, m, 1, nullptr, KC_SMALL_DENSE);
             dgemm(ctx, 0, 0, m, m, m, S, m, X0, m, 0.0, Ym, m, 1, nullptr, KC_SMALL_DENSE);
             dgemm(ctx, 1, 0, m, m, m, X0, m, Ym, m, 0.0, Tm, m, 1, nullptr, KC_SMALL_DENSE);
+            ctx.before(KC_SMALL_DENSE, 16.0 * m2, 4.0 * m2);
+            k_oa_norms<<<1, 1024, 0, ctx.stream>>>(m, G, Tm, lam0, normA + 1);
+            ctx.after();
             ctx.before(KC_SMALL_DENSE, 24.0 * m2, 8.0 * m2);
-            k_oa_update<<<1, 1024, 0, ctx.stream>>>(m, G, Tm, normA, Vm, lam0);
+            k_oa_step<<<eg, 256, 0, ctx.stream>>>(m, G, Tm, lam0, normA + 1, Vm);
             ctx.after();
             dgemm(ctx, 0, 0, m, m, m, X0, m, Vm, m, 0.0, X1, m, 1, nullptr, KC_SMALL_DENSE);
             std::swap(X0, X1);

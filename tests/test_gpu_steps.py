@@ -278,6 +278,26 @@ def test_rayleigh_ritz_survives_dependent_columns(api):
     assert max(hits) < 1e-9
 
 
+@pytest.mark.parametrize("m,dup", [(80, 0), (150, 37), (97, 95), (40, 3)])
+def test_rayleigh_ritz_cholesky_pivot_below_shift(api, m, dup):
+    # a column repeated up to 1e-9 leaves a positive pivot far below the
+    # shifted Cholesky-QR shift (column-scaled Gram: ~1e-18 against ~1e-8);
+    # the first pass must treat it as a breakdown and refactor with the shift,
+    # in the blocked form (m >= 64: first, middle or last block) and the
+    # one-block form, and the Ritz values of the well-determined part stay
+    # accurate
+    p = pencil_2d_q1(20, seed=3)
+    A, B = p.A(), p.B()
+    lam, Xe = la.eigh(A.toarray(), B.toarray())
+    U = Xe[:, :m - 1] @ start_block(m - 1, m - 1, 4)
+    U = np.concatenate([U[:, :dup + 1], U[:, dup:dup + 1] + 1e-9 * start_block(p.n, 1, 5), U[:, dup + 1:]], axis=1)
+    h = api.Handle(p)
+    theta, X, resid = h.rayleigh_ritz(torch.from_numpy(np.ascontiguousarray(U)).cuda())
+    th = np.sort(theta.cpu().numpy())
+    hits = [np.min(np.abs(th - l)) / l for l in lam[:m - 1]]
+    assert max(hits) < 1e-9
+
+
 def test_fma_peak_is_plausible(api):
     # 152 SMs x 128 FP32 lanes x 2 flops x ~2 GHz ~ 80 TFLOP/s nominal; FP64
     # runs far slower on this part.  A broken timer or a dead-code-eliminated
