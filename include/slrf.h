@@ -192,6 +192,11 @@ typedef struct {
     int32_t sell_sigma;     /* SELL-C-sigma: rows are sorted by length within
                                windows of this many rows (1 = natural order);
                                0 = 256                                         */
+    int32_t mg_exact_tc;    /* mg_exact level: 1 = apply the inverses on the
+                               tcgen05 tensor cores (three-way bf16 split of both
+                               operands, FP32 accumulation: FP32-accurate; needs
+                               subspace size <= 256), 0 = cuBLAS FP32 complex
+                               GEMM                                           (1) */
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the

@@ -48,7 +48,7 @@ class slrf_opts(C.Structure):
                 ("stagnation_window", C.c_int32),
                 ("profile_mask", C.c_uint32), ("spmm_kernel", C.c_int32), ("mg_exact", C.c_int32),
                 ("ilu_sweeps", C.c_int32), ("ilu_tri_sweeps", C.c_int32), ("sell_c", C.c_int32),
-                ("sell_sigma", C.c_int32)]
+                ("sell_sigma", C.c_int32), ("mg_exact_tc", C.c_int32)]
 
 
 class slrf_report(C.Structure):

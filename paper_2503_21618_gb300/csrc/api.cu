@@ -157,6 +157,9 @@ struct slrf_handle {
     Buf rOz;   // Ozaki Gram digits and partials
     Buf rOzT;  // Ozaki tall-product digits
     Buf rTallB;   // slrf_tall_product: copy of B
+    Buf mgInvPan, mgCtWork;   // exact level on the tensor cores: split inverses, per-apply work
+    bool inv_pan_ok = false;
+    void *inv_pan_buf = nullptr;
     Buf rW1, rQ1, rQ2, rX, rAX, rBX, rRes, rSmall, rSplit, rV, rTheta, rRho;
     int64_t shifted_cholqr = 0;   // Rayleigh-Ritz steps that needed the shifted fallback
     Buf hostV, hostX;   // device staging for the host-buffer entry points
@@ -949,9 +952,23 @@ slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d
                 }
                 h->inv_key = key;
                 h->inv_buf = h->mgInv.p;
+                h->inv_pan_ok = false;
             }
             mg.Minv = reinterpret_cast<const cplx<T> *>(Minv);
             mg.cublas = h->cublas;
+            mg.Mpan = nullptr;
+            if (h->opts.mg_exact_tc && coarse_tc_fits(d.Lp)) {
+                CKS(ensure(h, h->mgInvPan, coarse_tc_panel_bytes(nc, N)));
+                CKS(ensure(h, h->mgCtWork, coarse_tc_work_bytes(nc, N, d.Lp)));
+                if (!h->inv_pan_ok || h->inv_pan_buf != h->mgInvPan.p) {
+                    coarse_tc_panels(h->ctx, nc, N, Minv, h->mgInvPan.p);
+                    h->inv_pan_ok = true;
+                    h->inv_pan_buf = h->mgInvPan.p;
+                }
+                mg.Mpan = h->mgInvPan.p;
+                mg.ct_work = h->mgCtWork.p;
+                mg.ct_err = h->d_pin + 1;
+            }
         }
         mg_dinv<T>(h->ctx, mg, make_poleset<T>(f));
         return SLRF_OK;
@@ -1772,6 +1789,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->mg_exact = 1536;
     o->ilu_sweeps = 3;
     o->ilu_tri_sweeps = 3;
+    o->mg_exact_tc = 1;
     return SLRF_OK;
 }
 
@@ -1791,6 +1809,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->spmm_rows < 0 || o->spmm_rows > 4) return SLRF_EINVAL;
     if (o->spmm_kernel < 0 || o->spmm_kernel > 4) return SLRF_EINVAL;
     if (o->eig_refine < 0 || o->eig_refine > 2) return SLRF_EINVAL;
+    if (o->mg_exact_tc < 0 || o->mg_exact_tc > 1) return SLRF_EINVAL;
     if (o->sell_c != 0 && o->sell_c != 4 && o->sell_c != 8 && o->sell_c != 16 && o->sell_c != 32 && o->sell_c != 64)
         return SLRF_EINVAL;
     if (o->sell_sigma < 0) return SLRF_EINVAL;
@@ -1896,6 +1915,7 @@ void slrf_destroy(slrf_handle *h) {
     Buf *bufs[] = {&h->kP, &h->kQ, &h->kR, &h->kDinv, &h->kU, &h->kPart, &h->kSig, &h->kScal, &h->kFlags,
                    &h->rOz, &h->rW1, &h->rQ1, &h->rQ2, &h->rX, &h->rAX, &h->rBX, &h->rRes, &h->rSmall, &h->rSplit, &h->rV,
                    &h->rTheta, &h->rRho, &h->hostV, &h->hostX, &h->mgStatic, &h->mgState, &h->kZ, &h->rOzT, &h->kBcg, &h->rTallB,
+                   &h->mgInvPan, &h->mgCtWork,
                    &h->mg_eig[0].dev, &h->mg_eig[1].dev, &h->mg_eig[2].dev, &h->mg_eig[3].dev,
                    &h->mg_eig[4].dev, &h->mg_eig[5].dev, &h->mg_eig[6].dev, &h->mg_eig[7].dev,
                    &h->mg_eig[8].dev, &h->mg_eig[9].dev, &h->mg_eig[10].dev, &h->mg_eig[11].dev,

@@ -215,6 +215,12 @@ template <typename T> struct MgSolve {
     // cublas is the handle's cuBLAS handle for their GEMMs
     const cplx<T> *Minv = nullptr;
     void *cublas = nullptr;
+    // tensor-core application of those inverses (coarse_tc.cu): the split
+    // panels of the inverses, the per-apply workspace and the mapped word
+    // that records a bounded wait that gave up; Mpan == nullptr: cuBLAS
+    const void *Mpan = nullptr;
+    void *ct_work = nullptr;
+    int32_t *ct_err = nullptr;
 };
 template <typename T>
 void mg_dinv(Ctx &ctx, MgSolve<T> &mg, const PoleSet<T> &ps);
@@ -229,6 +235,19 @@ int coarse_inverse(Ctx &ctx, void *cublas, int n, const PoleSet<float> &ps, cons
 // Z_j = Minv_j R_j for every pole's columns of the level block (layout of the state)
 int coarse_inverse_apply(Ctx &ctx, void *cublas, const KrylovDims &d, int n, const float2 *Minv, const float2 *R,
                          float2 *Z);
+
+// ---------------------------------------------------------------- coarse_tc.cu
+// The same application on the tcgen05 tensor cores (three-way bf16 split of
+// both operands, six part products into one FP32 accumulator): the panels of
+// the inverses are formed once per solve (coarse_tc_panels, coarse_tc_panel_bytes
+// bytes), each application splits the level block into work
+// (coarse_tc_work_bytes) and writes Z; Lp <= 256 (coarse_tc_fits).
+bool coarse_tc_fits(int Lp);
+size_t coarse_tc_panel_bytes(int n, int N);
+size_t coarse_tc_work_bytes(int n, int N, int Lp);
+void coarse_tc_panels(Ctx &ctx, int n, int N, const float2 *Minv, void *Mpan);
+void coarse_tc_apply(Ctx &ctx, const KrylovDims &d, int n, const void *Mpan, const float2 *R, float2 *Z, void *work,
+                     int32_t *err);
 // Z0 = cycle(R0) for all active columns of the state; part receives the
 // partial sums r^T z (slots 0, 1).  Y0 = D R0 with the finest level's
 // damped Jacobi diagonal (mg.lv[0].dinv), if the caller has it (the COCG

@@ -549,6 +549,10 @@ template <typename T>
 void coarse_solve(Ctx &ctx, const KrylovDims &d, const MgSolve<T> &mg, const cplx<T> *Rv, cplx<T> *Y, cplx<T> *Z,
                   const int32_t *flag) {
     if constexpr (sizeof(T) == 4) {
+        if (mg.Mpan) {   // dense shifted inverses of this level on the tensor cores
+            coarse_tc_apply(ctx, d, mg.nc, mg.Mpan, Rv, Z, mg.ct_work, mg.ct_err);
+            return;
+        }
         if (mg.Minv) {   // dense shifted inverses of this level (FP32 cycles)
             coarse_inverse_apply(ctx, mg.cublas, d, mg.nc, mg.Minv, Rv, Z);
             return;

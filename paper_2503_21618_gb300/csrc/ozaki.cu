@@ -285,43 +285,8 @@ k_oz_split_panel(int64_t n, int m, const double *__restrict__ X, int64_t ldx, co
     }
 }
 
-__device__ __forceinline__ uint64_t umma_desc(unsigned smem_byte_addr) {
-    // K-major, no swizzle: leading offset 128 B (next K core), stride offset
-    // 512 B (next 8-row group), descriptor version 1 (bits 46-47)
-    uint64_t d = 0;
-    d |= (uint64_t)((smem_byte_addr >> 4) & 0x3fff);
-    d |= (uint64_t)((128u >> 4) & 0x3fff) << 16;
-    d |= (uint64_t)((512u >> 4) & 0x3fff) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
 // M = 128, N = 64, bf16 x bf16 -> FP32, both operands K-major
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_TN >> 3) << 17) |
-                              ((uint32_t)(TC_TM >> 4) << 24);
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
-    asm volatile(
-        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accum)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(void *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
+constexpr uint32_t TC_IDESC = umma_idesc_bf16(TC_TM, TC_TN);
 
 // sum_d v_d 2^(-7(d+2)) of the seven FP32 accumulators (exact integers,
 // |v_d| <= (d+1) 2^12 K with K <= 512 rows per slice) with two FP64
@@ -419,7 +384,7 @@ k_oz_gram_tc(int m, int nta, int ntb, int64_t nks, int ntrx, int ntry, const __n
                     for (int k16 = 0; k16 < 2; ++k16) {
                         const uint64_t ad = umma_desc(a0 + sd * 8192u + k16 * 256u);
                         const uint64_t bd = umma_desc(b0 + (d - sd) * 4096u + k16 * 256u);
-                        umma_bf16(tmem + (uint32_t)(d * TC_TN), ad, bd, (first && sd == 0 && k16 == 0) ? 0u : 1u);
+                        umma_bf16(tmem + (uint32_t)(d * TC_TN), ad, bd, TC_IDESC, (first && sd == 0 && k16 == 0) ? 0u : 1u);
                     }
             first = false;
             umma_commit(empty + st);   // stage free once these MMAs have read it

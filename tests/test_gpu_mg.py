@@ -338,40 +338,44 @@ def test_profile_mask_times_only_the_selected_classes(api):
     assert all(v["ms"] > 0 for v in rep.as_dict()["kernels"].values())
 
 
-@pytest.mark.parametrize("mg_exact,level", [(1536, 2), (2000, 1)])
-def test_precond_apply_mixed_exact_inverse_level(api, mg_exact, level):
+@pytest.mark.parametrize("tc", [1, 0])
+@pytest.mark.parametrize("mg_exact,level,m,ldp", [(1536, 2, 3, 4), (2000, 1, 3, 4), (1536, 2, 70, 70),
+                                                  (1536, 2, 150, 150)])
+def test_precond_apply_mixed_exact_inverse_level(api, mg_exact, level, m, ldp, tc):
     # FP32 cycle ending at a level solved by its dense shifted inverses,
-    # formed on the GPU by blocked Gauss-Jordan: levels 16641 -> 1899 -> 260 -> 41
+    # formed on the GPU by blocked Gauss-Jordan: levels 16641 -> 1899 -> 260 -> 41;
+    # the inverses applied on the tensor cores (tc = 1: three-way bf16 split,
+    # one N tile of 16 / 80 / 160 columns) or by cuBLAS (tc = 0)
     from workloads import weyl_gamma
     p = pencil_2d_q1(130, seed=5)
     # poles for an interval of ~40 eigenvalues (the apply needs no exact gap)
     s, w = poles.slrf_poles(4, 1.0, 0.01, weyl_gamma("2d", 40))
-    o = api.default_opts(precond=api.PRECOND_MG, mg_exact=mg_exact)
+    o = api.default_opts(precond=api.PRECOND_MG, mg_exact=mg_exact, mg_exact_tc=tc)
     H = _hierarchy_model(api, p, o)
     assert [A.shape[0] for A in H[0]] == [16641, 1899, 260, 41]
-    R, Z, mu, lv = _apply_case(api, p, o, s, w, api.PREC_MIXED, m=3, ldp=4, seed=6)
+    R, Z, mu, lv = _apply_case(api, p, o, s, w, api.PREC_MIXED, m=m, ldp=ldp, seed=6)
     assert lv == level + 1
     for j, sig in enumerate(s):
-        for c in range(3):
-            col = j * 4 + c
+        for c in sorted({0, 1, m // 2, m - 1}):
+            col = j * ldp + c
             ref = _cycle_model(H, o, sig, R[:, col], 0, level)
             assert np.linalg.norm(Z[:, col] - ref) <= 5e-4 * np.linalg.norm(ref)
     # complex symmetric up to FP32 rounding: x^T C y = y^T C x
     for j in range(len(s)):
-        x, y = R[:, 4 * j], R[:, 4 * j + 1]
-        Cx, Cy = Z[:, 4 * j], Z[:, 4 * j + 1]
+        x, y = R[:, ldp * j], R[:, ldp * j + 1]
+        Cx, Cy = Z[:, ldp * j], Z[:, ldp * j + 1]
         assert abs(x @ Cy - y @ Cx) <= 1e-4 * abs(x @ Cy)
 
 
-@pytest.mark.parametrize("mg_exact", [1536, 0])
-def test_subspace_2d_with_and_without_the_exact_inverse_level(api, mg_exact):
+@pytest.mark.parametrize("mg_exact,tc", [(1536, 1), (1536, 0), (0, 1)])
+def test_subspace_2d_with_and_without_the_exact_inverse_level(api, mg_exact, tc):
     p = pencil_2d_q1(60, seed=12)                     # levels 3481 -> 402 -> 66
     lam = la.eigvalsh(p.A().toarray(), p.B().toarray())
     nev = 30
     gamma = 0.5 * (lam[nev - 1] + lam[nev])
     s, w = poles.slrf_poles(4, 1.0, 0.01, gamma)
     V0 = start_block(p.n, 45, 13)
-    h = api.Handle(p, api.default_opts(precond=api.PRECOND_MG, mg_exact=mg_exact))
+    h = api.Handle(p, api.default_opts(precond=api.PRECOND_MG, mg_exact=mg_exact, mg_exact_tc=tc))
     theta, X, resid, nconv, st, rep = h.subspace_iterate(api.Filter(s, w), gamma, torch.from_numpy(V0).cuda())
     assert st == api.OK and nconv == nev
     assert rep.mg_levels == (2 if mg_exact else 3)
