@@ -641,7 +641,7 @@ def main():
             "time_split": {"setup_ms": t_setup * 1e3,
                            "krylov_ms_per_step": sum(r["ms_krylov"] for r in reps) / len(reps),
                            "rr_ms_per_step": sum(r["ms_rr"] for r in reps) / len(reps),
-                           "setup": "handle creation: pencil upload, row groups, multigrid hierarchy (host)"},
+                           "setup": "handle creation: pencil upload, row groups and the other SpMM forms; the multigrid hierarchy is built on a host thread that the first solve waits for after its first projection"},
             "e2e": e2e,
         }
         if plain is not None:

@@ -9,12 +9,14 @@
 #include <algorithm>
 #include <array>
 #include <complex>
+#include <functional>
 #include <future>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <type_traits>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -168,6 +170,9 @@ struct slrf_handle {
     Buf kBcg;   // BiCGStab: r^, v, y, z, t blocks and omega scalars
     bool node_blocks = false;             // 3-dof node-block pattern (elasticity)
     bool mg_ready = false;
+    // a hierarchy still being built on a host thread when slrf_create
+    // returned: waits for it and uploads it (run by the first mg_ensure)
+    std::function<slrf_status(slrf_handle *)> mg_finish;
     int mg_block = 0, mg_coarse = 0;      // parameters the hierarchy was built with
     double mg_theta = 0.0;
     std::vector<double> mg_lam;           // coarsest eigenvalues
@@ -398,33 +403,65 @@ void build_rowgroups(int R, int64_t n, const std::vector<int32_t> &rp, const std
                      const std::vector<double> &av, const std::vector<double> &bv, std::vector<int32_t> &gptr,
                      std::vector<int32_t> &ucol, std::vector<double2> &uab) {
     const int64_t ng = (n + R - 1) / R;
+    // group ranges on up to 8 host threads (the multigrid setup runs beside
+    // this on its own threads); each range's lists are concatenated in group
+    // order, so the result does not depend on the thread count
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(8, (int64_t)rp[n] / 100000));
+    struct Part {
+        std::vector<int32_t> len, col;
+        std::vector<double2> ab;
+    };
+    std::vector<Part> parts(nt);
+    auto work = [&](int t) {
+        const int64_t g0 = ng * t / nt, g1 = ng * (t + 1) / nt;
+        Part &P = parts[t];
+        std::vector<int32_t> u;
+        for (int64_t g = g0; g < g1; ++g) {
+            u.clear();
+            const int64_t r0 = g * R, r1 = std::min<int64_t>(n, r0 + R);
+            for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), ci.begin() + rp[r], ci.begin() + rp[r + 1]);
+            std::sort(u.begin(), u.end());
+            u.erase(std::unique(u.begin(), u.end()), u.end());
+            for (int32_t c : u) {
+                P.col.push_back(c);
+                for (int r = 0; r < R; ++r) {
+                    const int64_t row = r0 + r;
+                    double2 v = make_double2(0.0, 0.0);
+                    if (row < n) {
+                        const auto b = ci.begin() + rp[row], e = ci.begin() + rp[row + 1];
+                        const auto it = std::lower_bound(b, e, c);
+                        if (it != e && *it == c) {
+                            const int64_t k = it - ci.begin();
+                            v = make_double2(av[k], bv[k]);
+                        }
+                    }
+                    P.ab.push_back(v);
+                }
+            }
+            P.len.push_back((int32_t)u.size());
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) {
+        try {
+            th.emplace_back(work, t);
+        } catch (...) {   // no thread: in line
+            work(t);
+        }
+    }
+    work(0);
+    for (auto &x : th) x.join();
     gptr.assign(ng + 1, 0);
     ucol.clear();
     uab.clear();
-    std::vector<int32_t> u;
-    for (int64_t g = 0; g < ng; ++g) {
-        u.clear();
-        const int64_t r0 = g * R, r1 = std::min<int64_t>(n, r0 + R);
-        for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), ci.begin() + rp[r], ci.begin() + rp[r + 1]);
-        std::sort(u.begin(), u.end());
-        u.erase(std::unique(u.begin(), u.end()), u.end());
-        for (int32_t c : u) {
-            ucol.push_back(c);
-            for (int r = 0; r < R; ++r) {
-                const int64_t row = r0 + r;
-                double2 v = make_double2(0.0, 0.0);
-                if (row < n) {
-                    const auto b = ci.begin() + rp[row], e = ci.begin() + rp[row + 1];
-                    const auto it = std::lower_bound(b, e, c);
-                    if (it != e && *it == c) {
-                        const int64_t k = it - ci.begin();
-                        v = make_double2(av[k], bv[k]);
-                    }
-                }
-                uab.push_back(v);
-            }
+    int64_t g = 0;
+    for (const Part &P : parts) {
+        for (int32_t l : P.len) {
+            gptr[g + 1] = gptr[g] + l;
+            ++g;
         }
-        gptr[g + 1] = (int32_t)ucol.size();
+        ucol.insert(ucol.end(), P.col.begin(), P.col.end());
+        uab.insert(uab.end(), P.ab.begin(), P.ab.end());
     }
 }
 
@@ -795,6 +832,11 @@ slrf_status mg_build_upload(slrf_handle *h, const std::vector<int32_t> &rp, cons
 // Build the hierarchy if the options ask for one it does not have yet (from
 // the device copy of the pencil).
 slrf_status mg_ensure(slrf_handle *h) {
+    if (h->mg_finish) {   // the setup thread of slrf_create
+        auto fin = std::move(h->mg_finish);
+        h->mg_finish = nullptr;
+        CKS(fin(h));
+    }
     if (h->mg_ready && h->mg_coarse == h->opts.mg_coarse && h->mg_theta == h->opts.mg_theta &&
         (h->opts.mg_block == 0 || h->opts.mg_block == h->mg_block))
         return SLRF_OK;
@@ -1960,9 +2002,19 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     if (!o) o = &def;
     CKS(check_opts(o));
     const int64_t n = p->n, nnz = p->nnz;
-    // host copies for validation
-    std::vector<int32_t> rp(n + 1), ci(nnz);
-    std::vector<double> av(nnz), bv(nnz);
+    // host copies for validation (shared with the multigrid setup thread,
+    // which may outlive this call)
+    struct HostCopy {
+        std::vector<int32_t> rp, ci;
+        std::vector<double> av, bv;
+    };
+    auto hc = std::make_shared<HostCopy>();
+    hc->rp.resize(n + 1);
+    hc->ci.resize(nnz);
+    hc->av.resize(nnz);
+    hc->bv.resize(nnz);
+    std::vector<int32_t> &rp = hc->rp, &ci = hc->ci;
+    std::vector<double> &av = hc->av, &bv = hc->bv;
     const cudaMemcpyKind kind = p->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
     CK(cudaMemcpy(rp.data(), p->row_ptr, (n + 1) * sizeof(int32_t), kind));
     CK(cudaMemcpy(ci.data(), p->col_idx, nnz * sizeof(int32_t), kind));
@@ -1976,8 +2028,9 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     if (R == 0) R = blocks ? 3 : 2;
     // The multigrid hierarchy (host) is built, and its device image laid out,
     // on its own thread while the row groups are formed and the pencil is
-    // uploaded; the guard waits for it on every return, before the host
-    // copies it reads go out of scope.
+    // uploaded; the handle keeps the pending result, and the first solve
+    // that needs the hierarchy waits for it (after the work it can do
+    // without it, such as the first projection of the start block).
     const slrf_opts opts_copy = *o;
     const bool want_mg = o->precond == SLRF_PRECOND_MG || (o->precond == SLRF_PRECOND_AUTO && !blocks);
     const int mg_blk = want_mg ? mg_block_for(opts_copy, n, rp, ci) : 0;
@@ -1987,17 +2040,11 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         MgStaged S;
     };
     std::future<MgBuilt> mg_fut;
-    struct Join {
-        std::future<MgBuilt> &f;
-        ~Join() {
-            if (f.valid()) f.wait();
-        }
-    } mg_join{mg_fut};
-    auto build_mg = [&rp, &ci, &av, &bv, &opts_copy, n, mg_blk, R] {
+    auto build_mg = [hc, opts_copy, n, mg_blk, R] {
         MgBuilt r;
         MgParams prm = mg_params(opts_copy, mg_blk);
         prm.defer_coarse_eig = true;
-        r.err = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), prm, r.H);
+        r.err = mg_build((int)n, hc->rp.data(), hc->ci.data(), hc->av.data(), hc->bv.data(), prm, r.H);
         if (!r.err.empty()) return r;
         // the coarsest level's eigenvectors on a second thread while the
         // image of the other levels is laid out and filled
@@ -2166,20 +2213,30 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         return SLRF_ECUDA;
     }
     if (want_mg) {
-        MgBuilt built;
-        try {
-            built = mg_fut.valid() ? mg_fut.get() : build_mg();
-        } catch (const std::exception &ex) {
-            built.err = std::string("multigrid setup: ") + ex.what();
-        }
-        slrf_status st = SLRF_BREAKDOWN;
-        if (built.err.empty())
-            st = mg_upload(h, built.H, built.S, mg_blk);
-        else
-            g_last_error = built.err;
-        if (st != SLRF_OK) {
-            slrf_destroy(h);
-            return st;
+        auto finish = [mg_blk](slrf_handle *hh, MgBuilt built) -> slrf_status {
+            if (!built.err.empty()) {
+                g_last_error = built.err;
+                return SLRF_BREAKDOWN;
+            }
+            return mg_upload(hh, built.H, built.S, mg_blk);
+        };
+        if (mg_fut.valid()) {
+            auto fut = std::make_shared<std::future<MgBuilt>>(std::move(mg_fut));
+            h->mg_finish = [fut, finish](slrf_handle *hh) -> slrf_status {
+                MgBuilt built;
+                try {
+                    built = fut->get();
+                } catch (const std::exception &ex) {
+                    built.err = std::string("multigrid setup: ") + ex.what();
+                }
+                return finish(hh, std::move(built));
+            };
+        } else {   // no setup thread: built here
+            const slrf_status st = finish(h, build_mg());
+            if (st != SLRF_OK) {
+                slrf_destroy(h);
+                return st;
+            }
         }
     }
     *out = h;
