@@ -330,8 +330,7 @@ void small_triinv_upper(Ctx &ctx, int m, const double *R, double *Rinv) {
 }
 
 // ---------------------------------------------------------------------------
-// cyclic parallel Jacobi (one block).  A, V in shared memory when they fit.
-// Output: lam ascending (FP64), Q (FP64, columns = eigenvectors).
+// cyclic parallel Jacobi: round-robin pair ordering (circle method)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void rr_pair(int k, int r, int mp, int &a, int &b) {
     // circle method: position 0 fixed, positions 1..mp-1 rotate by r
@@ -339,73 +338,82 @@ __device__ __forceinline__ void rr_pair(int k, int r, int mp, int &a, int &b) {
     b = ((mp - 2 - k + r) % (mp - 1)) + 1;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024)
-k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict__ Vg, double *__restrict__ lam,
-         double *__restrict__ Q, int max_sweeps, int use_smem, int32_t *__restrict__ info, float rel_tol) {
-    extern __shared__ unsigned char smraw[];
-    T *A = use_smem ? reinterpret_cast<T *>(smraw) : Ag;
-    T *V = use_smem ? A + (size_t)m * m : Vg;
+// ---------------------------------------------------------------------------
+// FP32 cyclic Jacobi for m <= JMAX in one block: all m/2 rotations of a
+// round applied at once (rows, then columns), A and V in shared memory with
+// an odd row pitch (the column phase's lanes walk a column without bank
+// conflicts), every row and column loop unrolled to its fixed trip count
+// (predicated on m), and the pivot pair's zeroing folded into the column
+// phase (three block barriers per round).  A rotation is skipped below
+// rel_tol of sqrt(|a_pp a_qq|); the sweeps stop once every rotation of a
+// sweep was below sqrt(rel_tol) (quadratic convergence: the next sweep would
+// find nothing).  Output: lam ascending (FP64), Q (FP64, columns =
+// eigenvectors).
+// ---------------------------------------------------------------------------
+constexpr int JMAX = 160;
+
+__global__ void __launch_bounds__(1024) k_jacobi32(int m, const double *__restrict__ S, double *__restrict__ lam,
+                                                  double *__restrict__ Q, int max_sweeps, float rel_tol) {
+    extern __shared__ float jsm[];
+    const int ld = m | 1;
+    float *A = jsm, *V = jsm + (size_t)m * ld;
     const int tid = threadIdx.x, bs = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarp = bs >> 5;
     const int mp = m + (m & 1);
     const int npair = mp / 2;
-    __shared__ T cs[512], sn[512];
-    __shared__ int pp[512], qq[512];
+    constexpr int NIT = (JMAX + 31) / 32;
+    __shared__ float cs[JMAX / 2], sn[JMAX / 2];
+    __shared__ int pp[JMAX / 2], qq[JMAX / 2];
     __shared__ int nrot;
     __shared__ float maxrel;
     __shared__ double red[32];
-    __shared__ T absmin;
-
+    __shared__ float absmin;
     double fro = 0.0;
     for (int e = tid; e < m * m; e += bs) {
         const double v = S[e];
-        A[e] = (T)v;
+        A[(e / m) * ld + e % m] = (float)v;
         fro += v * v;
     }
-    for (int i = warp; i < m; i += nwarp)
-        for (int j = lane; j < m; j += 32) V[i * m + j] = (T)(i == j ? 1 : 0);
+    for (int e = tid; e < m * m; e += bs) V[(e / m) * ld + e % m] = (e / m == e % m) ? 1.f : 0.f;
     for (int off = 16; off > 0; off >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, off);
     if (lane == 0) red[warp] = fro;
     __syncthreads();
     if (tid == 0) {
         double t = 0;
         for (int w = 0; w < nwarp; ++w) t += red[w];
-        absmin = (T)(sqrt(t) * (double)rel_tol * (sizeof(T) == 4 ? 1.0 / sqrt((double)m) : 0.5 / (double)m));
+        absmin = (float)(sqrt(t) * (double)rel_tol / sqrt((double)m));
     }
     __syncthreads();
-
-    int sweep = 0;
-    for (; sweep < max_sweeps; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (tid == 0) {
             nrot = 0;
             maxrel = 0.f;
         }
         __syncthreads();
         for (int r = 0; r < mp - 1; ++r) {
-            for (int k = tid; k < npair; k += bs) {
+            if (tid < npair) {
                 int a, b;
-                rr_pair(k, r, mp, a, b);
+                rr_pair(tid, r, mp, a, b);
                 const int p = min(a, b), q = max(a, b);
-                T c = 1, s = 0;
+                float c = 1.f, sv = 0.f;
                 if (q < m) {
-                    const T apq = A[p * m + q];
-                    const T app = A[p * m + p], aqq = A[q * m + q];
-                    const T scale = sqrt(fabs(app * aqq));
-                    if (fabs(apq) > (T)rel_tol * scale && fabs(apq) > absmin) {
-                        const T th = (aqq - app) / (2 * apq);
-                        const T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt((T)1 + th * th));
-                        c = (T)1 / sqrt((T)1 + t * t);
-                        s = t * c;
+                    const float apq = A[p * ld + q];
+                    const float app = A[p * ld + p], aqq = A[q * ld + q];
+                    const float scale = sqrtf(fabsf(app * aqq));
+                    if (fabsf(apq) > rel_tol * scale && fabsf(apq) > absmin) {
+                        const float th = (aqq - app) / (2.f * apq);
+                        const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(1.f + th * th));
+                        c = 1.f / sqrtf(1.f + t * t);
+                        sv = t * c;
                         atomicAdd(&nrot, 1);
-                        const float rel = (float)(fabs(apq) / (scale > 0 ? scale : (T)1));
+                        const float rel = fabsf(apq) / (scale > 0.f ? scale : 1.f);
                         atomicMax(reinterpret_cast<int *>(&maxrel), __float_as_int(rel));
                     }
                 }
-                cs[k] = c;
-                sn[k] = s;
-                pp[k] = p;
-                qq[k] = (q < m && s != (T)0) ? q : -1;
+                cs[tid] = c;
+                sn[tid] = sv;
+                pp[tid] = p;
+                qq[tid] = (q < m && sv != 0.f) ? q : -1;
             }
             __syncthreads();
             // rows: A <- J^T A (warp per pair, lanes over columns)
@@ -413,59 +421,55 @@ k_jacobi(int m, const double *__restrict__ S, T *__restrict__ Ag, T *__restrict_
                 const int q = qq[k];
                 if (q < 0) continue;
                 const int p = pp[k];
-                const T c = cs[k], s = sn[k];
-                for (int col = lane; col < m; col += 32) {
-                    const T apk = A[p * m + col], aqk = A[q * m + col];
-                    A[p * m + col] = c * apk - s * aqk;
-                    A[q * m + col] = s * apk + c * aqk;
+                const float c = cs[k], sv = sn[k];
+                float *Ap = A + p * ld, *Aq = A + q * ld;
+#pragma unroll
+                for (int it = 0; it < NIT; ++it) {
+                    const int col = lane + 32 * it;
+                    if (col < m) {
+                        const float x = Ap[col], y = Aq[col];
+                        Ap[col] = c * x - sv * y;
+                        Aq[col] = sv * x + c * y;
+                    }
                 }
             }
             __syncthreads();
-            // columns: A <- A J, V <- V J
+            // columns: A <- A J, V <- V J; the pivot pair (p, q) / (q, p) becomes 0
             for (int k = warp; k < npair; k += nwarp) {
                 const int q = qq[k];
                 if (q < 0) continue;
                 const int p = pp[k];
-                const T c = cs[k], s = sn[k];
-                for (int row = lane; row < m; row += 32) {
-                    const T akp = A[row * m + p], akq = A[row * m + q];
-                    A[row * m + p] = c * akp - s * akq;
-                    A[row * m + q] = s * akp + c * akq;
-                    const T vkp = V[row * m + p], vkq = V[row * m + q];
-                    V[row * m + p] = c * vkp - s * vkq;
-                    V[row * m + q] = s * vkp + c * vkq;
+                const float c = cs[k], sv = sn[k];
+#pragma unroll
+                for (int it = 0; it < NIT; ++it) {
+                    const int row = lane + 32 * it;
+                    if (row < m) {
+                        float *Ar = A + row * ld, *Vr = V + row * ld;
+                        const float x = Ar[p], y = Ar[q];
+                        Ar[p] = row == q ? 0.f : c * x - sv * y;
+                        Ar[q] = row == p ? 0.f : sv * x + c * y;
+                        const float vx = Vr[p], vy = Vr[q];
+                        Vr[p] = c * vx - sv * vy;
+                        Vr[q] = sv * vx + c * vy;
+                    }
                 }
             }
             __syncthreads();
-            for (int k = tid; k < npair; k += bs) {
-                const int q = qq[k];
-                if (q < 0) continue;
-                const int p = pp[k];
-                A[p * m + q] = 0;
-                A[q * m + p] = 0;
-            }
-            __syncthreads();
         }
-        // Jacobi converges quadratically: once every rotation of a sweep was
-        // below sqrt(rel_tol) (relative), the next sweep would find nothing.
-        if (nrot == 0 || maxrel < sqrtf(rel_tol)) {
-            ++sweep;
-            break;
-        }
+        if (nrot == 0 || maxrel < sqrtf(rel_tol)) break;
         __syncthreads();
     }
     // sort eigenvalues ascending (rank sort), permute columns into Q (FP64)
     for (int i = tid; i < m; i += bs) {
-        const T di = A[i * m + i];
+        const float di = A[i * ld + i];
         int rank = 0;
         for (int j = 0; j < m; ++j) {
-            const T dj = A[j * m + j];
+            const float dj = A[j * ld + j];
             rank += (dj < di) || (dj == di && j < i);
         }
         lam[rank] = (double)di;
-        for (int row = 0; row < m; ++row) Q[(int64_t)row * m + rank] = (double)V[row * m + i];
+        for (int row = 0; row < m; ++row) Q[(int64_t)row * m + rank] = (double)V[row * ld + i];
     }
-    if (tid == 0 && info) *info = sweep;
 }
 
 // ---------------------------------------------------------------------------
@@ -932,11 +936,10 @@ cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q,
     ctx.before(KC_SMALL_DENSE, 8.0 * m2, 0);
     k_identity<<<(unsigned)((m2 + 255) / 256), 256, 0, ctx.stream>>>(m, Vm);
     ctx.after();
-    // The FP32 stage needs A and V in one block's shared memory (m <= 160);
-    // larger problems go straight to the cooperative FP64 Jacobi.
-    const size_t smem = 2 * m2 * sizeof(float);
-    const int use_smem = smem <= 200 * 1024;
-    if (mode == 0 || !use_smem) {
+    // The FP32 stage needs A and V in one block's shared memory (m <= 160:
+    // 206 KB with the odd row pitch); larger problems go straight to the
+    // cooperative FP64 Jacobi.
+    if (mode == 0 || m > JMAX) {
         cudaMemcpyAsync(Tm, S, m2 * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream);
         const cudaError_t e = coop_jacobi(ctx, m, Tm, Vm, lam0, 60, normA, cnt);
         if (e != cudaSuccess) return e;
@@ -948,8 +951,8 @@ cudaError_t small_syev(Ctx &ctx, int m, const double *S, double *lam, double *Q,
     // stage 1: FP32 Jacobi in shared memory
     raise_smem_limits();
     ctx.before(KC_SMALL_DENSE, 24.0 * m2, 9.0 * (double)m * m2 * 8);
-    k_jacobi<float><<<1, 1024, smem, ctx.stream>>>(m, S, (float *)Ag, (float *)Vg, lam0, S0, 40, 1, nullptr,
-                                                      1e-6f);
+    const size_t smem32 = 2 * (size_t)m * (m | 1) * sizeof(float);
+    k_jacobi32<<<1, 1024, smem32, ctx.stream>>>(m, S, lam0, S0, 40, 1e-6f);
     ctx.after();
     if (mode == 2) {
         // stage 2: three rounds of an orthonormalisation step and a
@@ -1030,7 +1033,7 @@ void raise_smem_limits() {
         const int lim = 200 * 1024;
         cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_triinv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     });
 }
 

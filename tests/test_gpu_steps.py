@@ -193,7 +193,7 @@ def _sym_with_spectrum(m, lam, seed):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
-@pytest.mark.parametrize("case", ["random", "graded", "clusters", "tiny", "odd", "pairs", "wide"])
+@pytest.mark.parametrize("case", ["random", "graded", "clusters", "tiny", "odd", "pairs", "wide", "m160"])
 def test_syev_matches_lapack(api, mode, case):
     rng = np.random.default_rng(5)
     if case == "random":
@@ -211,6 +211,11 @@ def test_syev_matches_lapack(api, mode, case):
     elif case == "tiny":
         m = 1
         S = np.array([[3.5]])
+    elif case == "m160":
+        # the largest size of the one-block FP32 stage (odd-pitch shared copy)
+        m = 160
+        S = rng.standard_normal((m, m))
+        S = S + S.T
     elif case == "wide":
         # six decades, like the first projection of a random start block:
         # the FP32 stage leaves the low end unresolved, so large groups reach
