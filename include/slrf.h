@@ -139,7 +139,9 @@ typedef struct {
                                accumulators), tall products as with 1; 1 = int8
                                mma.sync digits for both; 0 = FP64 CUDA cores    (2) */
     int32_t mg_nu;          /* MG: Jacobi sweeps per side on the levels below the
-                               finest (the finest always takes one)                (2) */
+                               finest (the finest always takes one); 0 = one when
+                               the FP32 cycle ends at the mg_exact level, else
+                               two                                                 (0) */
     int32_t mg_cycle;       /* MG: coarse visits per level, 1 = V-, 2 = W-cycle    (1) */
     int32_t mg_coarse;      /* MG: coarsening stops at or below this size         (256) */
     int32_t mg_block;       /* MG: dofs per node for aggregation, 0 = auto (3 for

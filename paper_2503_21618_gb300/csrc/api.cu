@@ -934,7 +934,10 @@ slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d
     mg.nlev = c + 1;
     mg.nc = h->mg_host_lv[c].n;
     mg.V = V;
-    mg.nu = std::max(1, h->opts.mg_nu);
+    // auto (0): one sweep per side when the cycle ends at the exact level
+    // (measured on the 2D workload: 224 against 230 ms per solve with two,
+    // 10.4 against 10.2 iterations per pole), else two
+    mg.nu = h->opts.mg_nu > 0 ? h->opts.mg_nu : (e_inv >= 0 ? 1 : 2);
     mg.gamma = std::max(1, h->opts.mg_cycle);
     mg.omega = h->opts.mg_omega;
     const int W = d.W(), N = d.N, nc = mg.nc;
@@ -1820,7 +1823,7 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->profile = 0;
     o->spmm_rows = 0;
     o->gram_ozaki = 2;
-    o->mg_nu = 2;
+    o->mg_nu = 0;
     o->mg_cycle = 1;
     o->mg_coarse = 256;
     o->mg_block = 0;
@@ -1842,7 +1845,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->precond < SLRF_PRECOND_NONE || o->precond > SLRF_PRECOND_ILU) return SLRF_EINVAL;
     if (o->ilu_sweeps < 0 || o->ilu_sweeps > 32 || o->ilu_tri_sweeps < 1 || o->ilu_tri_sweeps > 32)
         return SLRF_EINVAL;
-    if (o->mg_nu < 1 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
+    if (o->mg_nu < 0 || o->mg_nu > 8 || o->mg_cycle < 1 || o->mg_cycle > 2 || o->mg_coarse < 1 ||
         o->mg_coarse > 4096 || o->mg_block < 0 || o->mg_block > 8 || !(o->mg_omega > 0.0) ||
         !(o->mg_omega < 2.0) || !(o->mg_theta >= 0.0) || !(o->mg_theta < 1.0) || o->stagnation_window < 0 ||
         !(o->mg_shift_limit > 0.0))

@@ -199,10 +199,14 @@ def _hierarchy_model(api, p, o):
     return As, Bs, Ps, rhos
 
 
-def _cycle_model(H, o, sig, r, l, c):
+def _cycle_model(H, o, sig, r, l, c, nu=None):
     """The cycle as written in the textbook: damped Jacobi D = (omega/rho_l) /
     diag(A_l - sigma B_l), nu sweeps per side below the finest level (one
-    there), gamma coarse visits, exact solve on level c."""
+    there), gamma coarse visits, exact solve on level c.  nu: o.mg_nu, whose
+    0 (auto) means two unless the caller says otherwise (one when an FP32
+    cycle ends at its dense-inverse level)."""
+    if nu is None:
+        nu = o.mg_nu if o.mg_nu > 0 else 2
     As, Bs, Ps, rhos = H
     M = (As[l] - sig * Bs[l]).tocsr()
     if l == c:
@@ -211,15 +215,15 @@ def _cycle_model(H, o, sig, r, l, c):
     P = Ps[l]
     if l == 0:
         x = D * r
-        e = _cycle_model(H, o, sig, P.T @ (r - M @ x), 1, c)
+        e = _cycle_model(H, o, sig, P.T @ (r - M @ x), 1, c, nu)
         z1 = x + P @ e
         return z1 + D * (r - M @ z1)
     z = D * r
-    for _ in range(o.mg_nu - 1):
+    for _ in range(nu - 1):
         z = z + D * (r - M @ z)
     for _ in range(o.mg_cycle):
-        z = z + P @ _cycle_model(H, o, sig, P.T @ (r - M @ z), l + 1, c)
-    for _ in range(o.mg_nu):
+        z = z + P @ _cycle_model(H, o, sig, P.T @ (r - M @ z), l + 1, c, nu)
+    for _ in range(nu):
         z = z + D * (r - M @ z)
     return z
 
@@ -358,7 +362,7 @@ def test_precond_apply_mixed_exact_inverse_level(api, mg_exact, level, m, ldp, t
     for j, sig in enumerate(s):
         for c in sorted({0, 1, m // 2, m - 1}):
             col = j * ldp + c
-            ref = _cycle_model(H, o, sig, R[:, col], 0, level)
+            ref = _cycle_model(H, o, sig, R[:, col], 0, level, nu=o.mg_nu or 1)
             assert np.linalg.norm(Z[:, col] - ref) <= 5e-4 * np.linalg.norm(ref)
     # complex symmetric up to FP32 rounding: x^T C y = y^T C x
     for j in range(len(s)):
