@@ -51,49 +51,50 @@ __global__ void k_dense_shift(int n, int N, const int32_t *__restrict__ ptr, con
 // In-place inverse of the b x b diagonal block at (k0, k0) of each of the
 // N matrices (column-major, leading dimension n), copied out to P (b x b,
 // column-major, ld CB) -- Gauss-Jordan without pivoting in shared memory.
-__global__ void __launch_bounds__(256) k_block_inverse(int n, int b, int k0, const float2 *__restrict__ M,
-                                                      float2 *__restrict__ P) {
+// 1024 threads, thread (r, c0) owns rows r and columns c0, c0 + 16, ...: no
+// index division in the elimination loop, four entries per thread.
+__global__ void __launch_bounds__(1024) k_block_inverse(int n, int b, int k0, const float2 *__restrict__ M,
+                                                       float2 *__restrict__ P) {
     __shared__ float2 S[CB][CB + 1];   // S[r][c]
     __shared__ float2 rowk[CB], colk[CB];
     const int j = blockIdx.x;
     const float2 *Mj = M + (int64_t)j * n * n;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-        const int r = e % b, c = e / b;
-        S[r][c] = Mj[(int64_t)(k0 + c) * n + k0 + r];
-    }
+    const int r = threadIdx.x & (CB - 1), c0 = threadIdx.x >> 6;   // c0 in [0, 16)
+    for (int c = c0; c < b; c += 16)
+        if (r < b) S[r][c] = Mj[(int64_t)(k0 + c) * n + k0 + r];
     __syncthreads();
     for (int k = 0; k < b; ++k) {
-        for (int e = threadIdx.x; e < b; e += blockDim.x) {
-            rowk[e] = S[k][e];
-            colk[e] = S[e][k];
+        if (threadIdx.x < b) {
+            rowk[threadIdx.x] = S[k][threadIdx.x];
+            colk[threadIdx.x] = S[threadIdx.x][k];
         }
         __syncthreads();
         const float2 p = rowk[k];
         const float den = p.x * p.x + p.y * p.y;
         const float2 pinv = make_float2(p.x / den, -p.y / den);
-        for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-            const int r = e % b, c = e / b;
-            float2 v;
-            if (r == k && c == k) {
-                v = pinv;
-            } else if (r == k) {
-                v = cmul(rowk[c], pinv);
-            } else if (c == k) {
-                v = cmul(colk[r], pinv);
-                v.x = -v.x;
-                v.y = -v.y;
-            } else {
-                v = csub(S[r][c], cmul(colk[r], cmul(rowk[c], pinv)));
+        if (r < b) {
+            const float2 cr = colk[r];
+            for (int c = c0; c < b; c += 16) {
+                float2 v;
+                if (r == k && c == k) {
+                    v = pinv;
+                } else if (r == k) {
+                    v = cmul(rowk[c], pinv);
+                } else if (c == k) {
+                    v = cmul(cr, pinv);
+                    v.x = -v.x;
+                    v.y = -v.y;
+                } else {
+                    v = csub(S[r][c], cmul(cr, cmul(rowk[c], pinv)));
+                }
+                S[r][c] = v;
             }
-            S[r][c] = v;
         }
         __syncthreads();
     }
     float2 *Pj = P + (int64_t)j * CB * CB;
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-        const int r = e % b, c = e / b;
-        Pj[c * CB + r] = S[r][c];
-    }
+    for (int c = c0; c < b; c += 16)
+        if (r < b) Pj[c * CB + r] = S[r][c];
 }
 
 // dst(r, c) = scale * src(r, c) for an rows x cols column-major block of
@@ -149,7 +150,7 @@ int coarse_inverse(Ctx &ctx, void *cublas, int n, const PoleSet<float> &ps, cons
     for (int k0 = 0; k0 < n; k0 += CB) {
         const int b = std::min(CB, n - k0);
         ctx.before(KC_MG_COARSE, (double)N * b * b * 16, 8.0 * N * b * b * b);
-        k_block_inverse<<<N, 256, 0, ctx.stream>>>(n, b, k0, Minv, P);
+        k_block_inverse<<<N, 1024, 0, ctx.stream>>>(n, b, k0, Minv, P);
         ctx.after();
         // T = P M_K*  (b x n)
         ctx.before(KC_MG_COARSE, (double)N * b * n * 16, 8.0 * N * b * b * n);
