@@ -155,71 +155,64 @@ __global__ void k_chol_init(int m, const double *__restrict__ G, double *__restr
     if (e < (int64_t)m * m && G != A) A[e] = G[e];
 }
 
-__global__ void __launch_bounds__(256) k_chol_diag(int m, int k0, int kb, double *__restrict__ A,
-                                                  int32_t *__restrict__ status, double pmin) {
+// One warp factors the kb x kb diagonal block (lane j owns column j of its
+// upper triangle; warp barriers only).
+__global__ void __launch_bounds__(32) k_chol_diag(int m, int k0, int kb, double *__restrict__ A,
+                                                 int32_t *__restrict__ status, double pmin) {
     __shared__ double S[CHB][CHB + 1];
-    __shared__ int bad;
-    __shared__ double dinv;
     if (*(volatile int32_t *)status != 0) return;
-    const int tid = threadIdx.x, bs = blockDim.x;
-    for (int e = tid; e < kb * kb; e += bs) S[e / kb][e % kb] = A[(int64_t)(k0 + e / kb) * m + k0 + e % kb];
-    if (tid == 0) bad = 0;
-    __syncthreads();
+    const int lane = threadIdx.x;
+    for (int i = 0; i < kb; ++i)
+        if (lane < kb) S[i][lane] = A[(int64_t)(k0 + i) * m + k0 + lane];
+    __syncwarp();
+    int bad = 0;
     for (int k = 0; k < kb; ++k) {
-        if (tid == 0) {
-            const double d = S[k][k];
-            if (!(d > pmin) || !isfinite(d)) {
-                bad = k0 + k + 1;
-            } else {
-                const double r = sqrt(d);
-                S[k][k] = r;
-                dinv = 1.0 / r;
-            }
+        const double d = S[k][k];
+        if (!(d > pmin) || !isfinite(d)) {
+            bad = k0 + k + 1;
+            break;   // uniform: every lane read the same pivot
         }
-        __syncthreads();
-        if (bad) break;
-        for (int j = k + 1 + tid; j < kb; j += bs) S[k][j] *= dinv;
-        __syncthreads();
-        const int r = kb - k - 1;
-        for (int e = tid; e < r * r; e += bs) {
-            const int i = k + 1 + e / r, j = k + 1 + e % r;
-            if (j >= i) S[i][j] -= S[k][i] * S[k][j];
+        const double r = sqrt(d), dinv = 1.0 / r;
+        __syncwarp();
+        if (lane == k) S[k][k] = r;
+        if (lane > k && lane < kb) S[k][lane] *= dinv;
+        __syncwarp();
+        if (lane > k && lane < kb) {
+            const double skj = S[k][lane];
+            for (int i = k + 1; i <= lane; ++i) S[i][lane] -= S[k][i] * skj;
         }
-        __syncthreads();
+        __syncwarp();
     }
     if (bad) {
-        if (tid == 0) *status = bad;
+        if (lane == 0) *status = bad;
         return;
     }
-    for (int e = tid; e < kb * kb; e += bs) {
-        const int i = e / kb, j = e % kb;
-        A[(int64_t)(k0 + i) * m + k0 + j] = j >= i ? S[i][j] : 0.0;
-    }
+    for (int i = 0; i < kb; ++i)
+        if (lane < kb) A[(int64_t)(k0 + i) * m + k0 + lane] = lane >= i ? S[i][lane] : 0.0;
 }
 
-// rows k0 .. k0+kb of the columns right of the block: x = R_kk^{-T} a
+// rows k0 .. k0+kb of the columns right of the block: x = R_kk^{-T} a, one
+// warp per column (lane i = row i; the forward substitution broadcasts
+// x_p from lane p), four columns per block
 __global__ void __launch_bounds__(128) k_chol_panel(int m, int k0, int kb, double *__restrict__ A,
                                                    const int32_t *__restrict__ status) {
     __shared__ double Rk[CHB][CHB + 1];
-    __shared__ double rinv[CHB];
     if (*(volatile int32_t *)status != 0) return;
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x)
         Rk[e / kb][e % kb] = A[(int64_t)(k0 + e / kb) * m + k0 + e % kb];
     __syncthreads();
-    for (int i = threadIdx.x; i < kb; i += blockDim.x) rinv[i] = 1.0 / Rk[i][i];
-    __syncthreads();
-    const int c = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int c = k0 + kb + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (c >= m) return;
-    double x[CHB];
-#pragma unroll
-    for (int i = 0; i < CHB; ++i) {
-        if (i < kb) {
-            double v = A[(int64_t)(k0 + i) * m + c];
-            for (int p = 0; p < i; ++p) v = fma(-Rk[p][i], x[p], v);
-            x[i] = v * rinv[i];
-            A[(int64_t)(k0 + i) * m + c] = x[i];
-        }
+    double v = lane < kb ? A[(int64_t)(k0 + lane) * m + c] : 0.0;
+    const double ri = lane < kb ? 1.0 / Rk[lane][lane] : 0.0;
+    double x = 0.0;
+    for (int p = 0; p < kb; ++p) {
+        const double xp = __shfl_sync(0xffffffffu, v * ri, p);
+        if (lane == p) x = xp;
+        if (lane > p && lane < kb) v = fma(-Rk[p][lane], xp, v);
     }
+    if (lane < kb) A[(int64_t)(k0 + lane) * m + c] = x;
 }
 
 // A[i][j] -= sum_p A[k0+p][i] A[k0+p][j] for k0+kb <= i <= j < m, 16 x 16
@@ -269,11 +262,11 @@ void small_chol_upper(Ctx &ctx, int m, const double *G, double *R, int32_t *stat
     for (int k0 = 0; k0 < m; k0 += CHB) {
         const int kb = std::min(CHB, m - k0), rest = m - k0 - kb;
         ctx.before(KC_SMALL_DENSE, 16.0 * kb * kb, (double)kb * kb * kb / 3.0);
-        k_chol_diag<<<1, 256, 0, ctx.stream>>>(m, k0, kb, R, status, shift_on_fail);
+        k_chol_diag<<<1, 32, 0, ctx.stream>>>(m, k0, kb, R, status, shift_on_fail);
         ctx.after();
         if (rest == 0) break;
         ctx.before(KC_SMALL_DENSE, 16.0 * kb * rest, 0.5 * kb * kb * rest);
-        k_chol_panel<<<(rest + 127) / 128, 128, 0, ctx.stream>>>(m, k0, kb, R, status);
+        k_chol_panel<<<(rest + 3) / 4, 128, 0, ctx.stream>>>(m, k0, kb, R, status);
         ctx.after();
         const int tiles = (rest + 15) / 16;
         ctx.before(KC_SMALL_DENSE, 8.0 * rest * rest, 0.5 * (double)rest * rest * kb);
