@@ -1073,6 +1073,58 @@ slrf_status ilu_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &
     return SLRF_OK;
 }
 
+// SELL-C-sigma form of the handle's pencil (shape from the options); no-op
+// if built.  An allocation failure leaves the handle without the form (the
+// row-group kernel runs instead).
+slrf_status sell_upload(slrf_handle *h, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
+                        const std::vector<double> &av, const std::vector<double> &bv) {
+    DevPencil &A = h->A;
+    if (A.sell_ab) return SLRF_OK;
+    const int C = h->opts.sell_c ? h->opts.sell_c : 32, sg = h->opts.sell_sigma ? h->opts.sell_sigma : 256;
+    std::vector<int32_t> cptr, scol, perm, rlen;
+    std::vector<float2> sab;
+    if (!build_sell(A.n, rp, ci, av, bv, C, sg, cptr, scol, sab, perm, rlen)) return SLRF_OK;
+    cudaStream_t s = h->ctx.stream;
+    void **bufs[] = {(void **)&A.sell_cptr, (void **)&A.sell_col, (void **)&A.sell_ab, (void **)&A.sell_perm,
+                     (void **)&A.sell_rlen};
+    const size_t bytes[] = {cptr.size() * 4, scol.size() * 4, sab.size() * 8, perm.size() * 4, rlen.size() * 4};
+    const void *src[] = {cptr.data(), scol.data(), sab.data(), perm.data(), rlen.data()};
+    for (int i = 0; i < 5; ++i) {
+        if (dev_alloc(h, bufs[i], bytes[i]) != cudaSuccess) {
+            cudaGetLastError();
+            *bufs[i] = nullptr;
+            for (int k = 0; k < i; ++k) {
+                cudaFreeAsync(*bufs[k], s);
+                *bufs[k] = nullptr;
+            }
+            return SLRF_OK;
+        }
+        h->pencil_bytes += bytes[i];
+    }
+    for (int i = 0; i < 5; ++i) CK(cudaMemcpyAsync(*bufs[i], src[i], bytes[i], cudaMemcpyHostToDevice, s));
+    A.sell_c = C;
+    A.sell_sigma = sg;
+    A.sell_nchunks = (int)(cptr.size() - 1);
+    A.sell_slots = cptr.back();
+    CK(cudaStreamSynchronize(s));   // pageable sources
+    return SLRF_OK;
+}
+
+// the same from the device copy of the pencil
+slrf_status ensure_sell(slrf_handle *h) {
+    if (h->A.sell_ab) return SLRF_OK;
+    const int64_t n = h->A.n, nnz = h->A.nnz;
+    std::vector<int32_t> rp(n + 1), ci(nnz);
+    std::vector<double> av(nnz), bv(nnz);
+    cudaStream_t s = h->ctx.stream;
+    CK(cudaMemcpyAsync(rp.data(), h->A.rowptr, (n + 1) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ci.data(), h->A.col, nnz * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(av.data(), h->A.a, nnz * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(bv.data(), h->A.b, nnz * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return sell_upload(h, rp, ci, av, bv);
+}
+
 // Kernel choice of the FP32 shifted product (slrf_opts.spmm_kernel = 0):
 // the candidate kernels are timed on this solve's blocks (one warm launch,
 // then three timed ones each) and the fastest is kept, per device, pattern
@@ -1084,13 +1136,29 @@ template <typename T>
 slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffers<T> &kb, const cplx<T> *sig) {
     DevPencil &A = h->A;
     if (sizeof(T) != 4) return SLRF_OK;
+    if (A.spmm_kind == SPMM_SELL) CKS(ensure_sell(h));
     // a requested form the pencil does not have runs as the row-group kernel
     if ((A.spmm_kind == SPMM_STAGED && spmm_staged_smem(A) == 0) || (A.spmm_kind == SPMM_NODEBLOCK && !A.nb_coef) ||
         (A.spmm_kind == SPMM_SELL && !A.sell_ab))
         A.spmm_kind = SPMM_ROWGROUP;
     if (A.spmm_kind != 0) return SLRF_OK;
-    // node pencils: row groups against node blocks (the staged kernel,
-    // bulk-copying 81-entry union lists, measured ~10x slower than either)
+    const int sell_c = h->opts.sell_c ? h->opts.sell_c : 32, sell_sigma = h->opts.sell_sigma ? h->opts.sell_sigma : 256;
+    const std::array<int64_t, 7> key = {h->device, A.n, A.nnz, A.rg_rows, A.rg_nnz, d.W(),
+                                        (int64_t)sell_c * 1000000 + sell_sigma};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            A.spmm_kind = it->second;
+            if (A.spmm_kind == SPMM_SELL) CKS(ensure_sell(h));
+            if (A.spmm_kind == SPMM_SELL && !A.sell_ab) A.spmm_kind = SPMM_ROWGROUP;
+            return SLRF_OK;
+        }
+    }
+    // first timing for this pattern: every form is a candidate; node pencils
+    // time row groups against node blocks (the staged kernel, bulk-copying
+    // 81-entry union lists, measured ~10x slower than either)
+    CKS(ensure_sell(h));
     std::vector<int> kinds = {SPMM_ROWGROUP};
     if (A.nb_coef) kinds.push_back(SPMM_NODEBLOCK);
     else if (spmm_staged_smem(A) > 0) kinds.push_back(SPMM_STAGED);
@@ -1098,16 +1166,6 @@ slrf_status resolve_spmm_kernel(slrf_handle *h, const KrylovDims &d, KrylovBuffe
     if (kinds.size() == 1) {
         A.spmm_kind = SPMM_ROWGROUP;
         return SLRF_OK;
-    }
-    const std::array<int64_t, 7> key = {h->device, A.n, A.nnz, A.rg_rows, A.rg_nnz, d.W(),
-                                        (int64_t)A.sell_c * 1000000 + A.sell_sigma};
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
-            A.spmm_kind = it->second;
-            return SLRF_OK;
-        }
     }
     Ctx &ctx = h->ctx;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -2181,32 +2239,13 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         cudaMemcpyAsync(h->A.rg_ab32, uab32.data(), uab32.size() * 8, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(h->A.rg_ab64, uab.data(), uab.size() * 16, cudaMemcpyHostToDevice, s);
     }
-    // SELL-C-sigma form (optional: without it the row-group kernel runs)
-    {
-        const int C = o->sell_c ? o->sell_c : 32, sg = o->sell_sigma ? o->sell_sigma : 256;
-        std::vector<int32_t> cptr, scol, perm, rlen;
-        std::vector<float2> sab;
-        if (build_sell(n, rp, ci, av, bv, C, sg, cptr, scol, sab, perm, rlen) &&
-            alloc((void **)&h->A.sell_cptr, cptr.size() * 4) && alloc((void **)&h->A.sell_col, scol.size() * 4) &&
-            alloc((void **)&h->A.sell_ab, sab.size() * 8) && alloc((void **)&h->A.sell_perm, perm.size() * 4) &&
-            alloc((void **)&h->A.sell_rlen, rlen.size() * 4)) {
-            cudaMemcpyAsync(h->A.sell_cptr, cptr.data(), cptr.size() * 4, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(h->A.sell_col, scol.data(), scol.size() * 4, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(h->A.sell_ab, sab.data(), sab.size() * 8, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(h->A.sell_perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(h->A.sell_rlen, rlen.data(), rlen.size() * 4, cudaMemcpyHostToDevice, s);
-            h->A.sell_c = C;
-            h->A.sell_sigma = sg;
-            h->A.sell_nchunks = (int)(cptr.size() - 1);
-            h->A.sell_slots = cptr.back();
-            cudaStreamSynchronize(s);
-        } else {
-            for (void **q : {(void **)&h->A.sell_cptr, (void **)&h->A.sell_col, (void **)&h->A.sell_ab,
-                             (void **)&h->A.sell_perm, (void **)&h->A.sell_rlen})
-                if (*q) {
-                    cudaFreeAsync(*q, s);
-                    *q = nullptr;
-                }
+    // SELL-C-sigma form: built here when asked for, else when the kernel
+    // autotuner first times it for this pattern (from the device copy)
+    if (o->spmm_kernel == SPMM_SELL) {
+        const slrf_status st = sell_upload(h, rp, ci, av, bv);
+        if (st != SLRF_OK) {
+            slrf_destroy(h);
+            return st;
         }
     }
     const cudaError_t e = cudaStreamSynchronize(s);

@@ -106,6 +106,26 @@ def test_switching_to_multigrid_builds_the_hierarchy_lazily(api):
     assert rel_err(U2.cpu().numpy(), U1.cpu().numpy()) < 1e-10
 
 
+def test_hierarchy_built_behind_handle_creation(api):
+    # slrf_create returns before the host hierarchy is ready: a handle
+    # destroyed at once waits for its setup thread; one whose options change
+    # before the first solve finishes the pending build first, then rebuilds
+    # with the new coarsening; results equal a handle that had it ready
+    p = pencil_2d_q1(60, seed=4)
+    for _ in range(3):
+        api.Handle(p, api.default_opts(precond=api.PRECOND_MG)).close()
+    _, _, s, w = _filter_case(p, 15)
+    V = torch.from_numpy(start_block(p.n, 8, 2)).cuda()
+    o = dict(precision=api.PREC_FP64, inner_tol=1e-13, precond=api.PRECOND_MG)
+    h1 = api.Handle(p, api.default_opts(**o))
+    h1.set_opts(mg_coarse=64)
+    U1, st1, rep1 = h1.filter_apply(api.Filter(s, w), V)
+    h2 = api.Handle(p, api.default_opts(mg_coarse=64, **o))
+    U2, st2, rep2 = h2.filter_apply(api.Filter(s, w), V)
+    assert st1 == st2 == api.OK and rep1.mg_levels == rep2.mg_levels
+    np.testing.assert_array_equal(U1.cpu().numpy(), U2.cpu().numpy())
+
+
 @pytest.mark.parametrize("precond", ["JACOBI", "MG"])
 def test_subspace_2d_each_preconditioner_matches_dense(api, precond):
     p = pencil_2d_q1(40, seed=5)
