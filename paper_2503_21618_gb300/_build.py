@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libslrf.so")
 STAMP = LIB + ".stamp"
 
 CU_SOURCES = ["krylov.cu", "bicgstab.cu", "mg.cu", "dense.cu", "small.cu", "ozaki.cu", "api.cu", "serve.cu", "noalloc.cu", "peak.cu", "coarse.cu", "coarse_tc.cu", "ilu.cu"]
-CPP_SOURCES = ["poles.cpp", "mg_setup.cpp"]
+CPP_SOURCES = ["poles.cpp", "mg_setup.cpp", "host_pool.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I" + INCLUDE]

@@ -362,12 +362,21 @@ class Handle:
         return theta, X, resid, nconv.value, st, rep
 
     def subspace_iterate_host(self, f: Filter, gamma: float, V0: np.ndarray, tol=1e-8, max_outer=50,
-                              allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, STAGNATION)):
+                              allowed=(OK, NOT_CONVERGED, SUBSPACE_TOO_SMALL, STAGNATION),
+                              theta=None, X=None, resid=None):
+        """Host-buffer solve.  theta (L), X (n x L) and resid (L) may be given
+        as C-contiguous float64 arrays (e.g. in pinned memory, which the
+        device-to-host copy of X reads fastest); else they are allocated."""
         V0 = np.ascontiguousarray(V0, dtype=np.float64)
         n, L = V0.shape
-        theta = np.zeros(L)
-        X = np.zeros((n, L))
-        resid = np.zeros(L)
+
+        def out(a, shape):
+            if a is None:
+                return np.zeros(shape)
+            if a.shape != shape or a.dtype != np.float64 or not a.flags.c_contiguous or not a.flags.writeable:
+                raise ValueError(f"output array must be a writable C-contiguous float64 array of shape {shape}")
+            return a
+        theta, X, resid = out(theta, (L,)), out(X, (n, L)), out(resid, (L,))
         nconv = C.c_int32(0)
         rep = slrf_report()
         st = self.lib.slrf_subspace_iterate_host(self.h, C.byref(f.c), gamma, L, V0.ctypes.data, L, tol, max_outer,

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <array>
 #include <complex>
 #include <functional>
@@ -19,6 +21,7 @@
 #include <thread>
 #include <vector>
 
+#include "host_pool.h"
 #include "internal.h"
 #include "mg.h"
 #include "slrf.h"
@@ -176,6 +179,10 @@ struct slrf_handle {
     int mg_block = 0, mg_coarse = 0;      // parameters the hierarchy was built with
     double mg_theta = 0.0;
     std::vector<double> mg_lam;           // coarsest eigenvalues
+    // the coarsest level's eigenpairs still being computed on a host thread
+    // when the hierarchy was uploaded: waits for them and uploads V (run by
+    // the first cycle that reaches the coarsest level)
+    std::function<slrf_status(slrf_handle *)> mg_coarse_pending;
     std::vector<int64_t> mg_level_n, mg_level_nnz;
     double mg_setup_ms = 0.0;
     std::vector<char> mg_cinv_host;       // staging of 1/(lambda_k - sigma_j)
@@ -373,6 +380,96 @@ __global__ void k_diag(int n, const int32_t *rowptr, const int32_t *col, const d
     da[i] = x;
     db[i] = y;
 }
+// Row-group form on the device, from the uploaded CSR (rows sorted by
+// column): group g holds rows gR .. gR+R-1; its entries are the union of
+// their columns, ascending, with R (a, b) pairs per entry (zeros where a row
+// has no entry, and for the rows past n of a ragged last group).  Each
+// thread merges the R rows of one group: once to count (into gptr[g + 1]),
+// and after the prefix sum to write.
+__device__ __forceinline__ int rg_next(int R, const int32_t *col, const int *p, const int *e) {
+    int c = INT_MAX;
+    for (int r = 0; r < R; ++r)
+        if (p[r] < e[r]) c = min(c, col[p[r]]);
+    return c;
+}
+__global__ void k_rg_count(int64_t n, int R, int64_t ng, const int32_t *rowptr, const int32_t *col, int32_t *gptr) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    int p[4], e[4];
+    for (int r = 0; r < R; ++r) {
+        const int64_t row = g * R + r;
+        p[r] = row < n ? rowptr[row] : 0;
+        e[r] = row < n ? rowptr[row + 1] : 0;
+    }
+    int cnt = 0;
+    for (int c = rg_next(R, col, p, e); c != INT_MAX; c = rg_next(R, col, p, e), ++cnt)
+        for (int r = 0; r < R; ++r)
+            if (p[r] < e[r] && col[p[r]] == c) ++p[r];
+    gptr[g + 1] = cnt;
+    if (g == 0) gptr[0] = 0;
+}
+// In-place inclusive prefix sum of gptr[1 .. ng] (one block of 1024 threads,
+// each over a contiguous chunk) and the largest group size in *emax.
+__global__ void __launch_bounds__(1024) k_rg_scan(int64_t ng, int32_t *gptr, int32_t *emax) {
+    __shared__ int64_t part[1024];
+    __shared__ int32_t mx[1024];
+    const int t = threadIdx.x;
+    const int64_t c0 = 1 + ng * t / 1024, c1 = 1 + ng * (t + 1) / 1024;
+    int64_t sum = 0;
+    int32_t m = 0;
+    for (int64_t i = c0; i < c1; ++i) {
+        sum += gptr[i];
+        m = max(m, gptr[i]);
+    }
+    part[t] = sum;
+    mx[t] = m;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {   // Hillis-Steele over the chunk sums
+        const int64_t v = t >= off ? part[t - off] : 0;
+        const int32_t w = t >= off ? mx[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        mx[t] = max(mx[t], w);
+        __syncthreads();
+    }
+    int64_t run = t ? part[t - 1] : 0;
+    for (int64_t i = c0; i < c1; ++i) {
+        run += gptr[i];
+        gptr[i] = (int32_t)run;
+    }
+    if (t == 1023) *emax = mx[1023];
+}
+__global__ void k_rg_fill(int64_t n, int R, int64_t ng, const int32_t *rowptr, const int32_t *col, const double *a,
+                          const double *b, const int32_t *gptr, int32_t *ucol, float2 *ab32, double2 *ab64,
+                          float4 *ab4, uint8_t *dpos) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= ng) return;
+    int p[4], e[4];
+    for (int r = 0; r < R; ++r) {
+        const int64_t row = g * R + r;
+        p[r] = row < n ? rowptr[row] : 0;
+        e[r] = row < n ? rowptr[row + 1] : 0;
+        if (dpos) dpos[g * R + r] = 0;
+    }
+    const int64_t o0 = gptr[g];
+    int64_t o = o0;
+    for (int c = rg_next(R, col, p, e); c != INT_MAX; c = rg_next(R, col, p, e), ++o) {
+        ucol[o] = c;
+        for (int r = 0; r < R; ++r) {
+            double x = 0.0, y = 0.0;
+            if (p[r] < e[r] && col[p[r]] == c) {
+                x = a[p[r]];
+                y = b[p[r]];
+                ++p[r];
+            }
+            const int64_t q = o * R + r;
+            ab64[q] = make_double2(x, y);
+            ab32[q] = make_float2((float)x, (float)y);
+            if (ab4) ab4[q] = make_float4((float)x, (float)x, (float)y, (float)y);
+            if (dpos && c == g * R + r) dpos[g * R + r] = (uint8_t)(o - o0);
+        }
+    }
+}
 __global__ void k_symmetrize(int m, double *S) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= (int64_t)m * m) return;
@@ -397,72 +494,6 @@ bool has_node_blocks(int64_t n, const std::vector<int32_t> &rp, const std::vecto
         }
     }
     return true;
-}
-
-void build_rowgroups(int R, int64_t n, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
-                     const std::vector<double> &av, const std::vector<double> &bv, std::vector<int32_t> &gptr,
-                     std::vector<int32_t> &ucol, std::vector<double2> &uab) {
-    const int64_t ng = (n + R - 1) / R;
-    // group ranges on up to 8 host threads (the multigrid setup runs beside
-    // this on its own threads); each range's lists are concatenated in group
-    // order, so the result does not depend on the thread count
-    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(8, (int64_t)rp[n] / 100000));
-    struct Part {
-        std::vector<int32_t> len, col;
-        std::vector<double2> ab;
-    };
-    std::vector<Part> parts(nt);
-    auto work = [&](int t) {
-        const int64_t g0 = ng * t / nt, g1 = ng * (t + 1) / nt;
-        Part &P = parts[t];
-        std::vector<int32_t> u;
-        for (int64_t g = g0; g < g1; ++g) {
-            u.clear();
-            const int64_t r0 = g * R, r1 = std::min<int64_t>(n, r0 + R);
-            for (int64_t r = r0; r < r1; ++r) u.insert(u.end(), ci.begin() + rp[r], ci.begin() + rp[r + 1]);
-            std::sort(u.begin(), u.end());
-            u.erase(std::unique(u.begin(), u.end()), u.end());
-            for (int32_t c : u) {
-                P.col.push_back(c);
-                for (int r = 0; r < R; ++r) {
-                    const int64_t row = r0 + r;
-                    double2 v = make_double2(0.0, 0.0);
-                    if (row < n) {
-                        const auto b = ci.begin() + rp[row], e = ci.begin() + rp[row + 1];
-                        const auto it = std::lower_bound(b, e, c);
-                        if (it != e && *it == c) {
-                            const int64_t k = it - ci.begin();
-                            v = make_double2(av[k], bv[k]);
-                        }
-                    }
-                    P.ab.push_back(v);
-                }
-            }
-            P.len.push_back((int32_t)u.size());
-        }
-    };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nt; ++t) {
-        try {
-            th.emplace_back(work, t);
-        } catch (...) {   // no thread: in line
-            work(t);
-        }
-    }
-    work(0);
-    for (auto &x : th) x.join();
-    gptr.assign(ng + 1, 0);
-    ucol.clear();
-    uab.clear();
-    int64_t g = 0;
-    for (const Part &P : parts) {
-        for (int32_t l : P.len) {
-            gptr[g + 1] = gptr[g] + l;
-            ++g;
-        }
-        ucol.insert(ucol.end(), P.col.begin(), P.col.end());
-        uab.insert(uab.end(), P.ab.begin(), P.ab.end());
-    }
 }
 
 // Node-block form of a 3-dof pencil (rows of a node share one pattern, made
@@ -556,18 +587,29 @@ bool build_sell(int64_t n, const std::vector<int32_t> &rp, const std::vector<int
 bool pencil_valid(int64_t n, int64_t nnz, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
                   const std::vector<double> &av, const std::vector<double> &bv) {
     if (rp[0] != 0 || rp[n] != nnz) return false;
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t i = 0; i < n; ++i)
         if (rp[i + 1] < rp[i]) return false;
-        bool diag = false;
-        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-            if (ci[k] < 0 || ci[k] >= n) return false;
-            if (k > rp[i] && ci[k] <= ci[k - 1]) return false;
-            if (!isfinite(av[k]) || !isfinite(bv[k])) return false;
-            if (ci[k] == i) diag = av[k] > 0 && bv[k] > 0;
+    // rows in parallel: columns in range and strictly increasing, values
+    // finite, a positive diagonal in A and B
+    std::atomic<bool> ok{true};
+    host_parallel_rows((int)n, host_threads(nnz), [&](int r0, int r1, int) {
+        for (int64_t i = r0; i < r1; ++i) {
+            bool diag = false;
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                if (ci[k] < 0 || ci[k] >= n || (k > rp[i] && ci[k] <= ci[k - 1]) || !isfinite(av[k]) ||
+                    !isfinite(bv[k])) {
+                    ok.store(false, std::memory_order_relaxed);
+                    return;
+                }
+                if (ci[k] == i) diag = av[k] > 0 && bv[k] > 0;
+            }
+            if (!diag) {
+                ok.store(false, std::memory_order_relaxed);
+                return;
+            }
         }
-        if (!diag) return false;
-    }
-    return true;
+    });
+    return ok.load();
 }
 
 // ---------------------------------------------------------------------------
@@ -711,7 +753,10 @@ void mg_stage_v(const HostHierarchy &H, MgStaged &S) {
     memcpy(S.stage.get() + S.v64, H.V.data(), nc * nc * 8);
 }
 
-slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, const MgStaged &S, int block) {
+// Hp / eig: the hierarchy (kept alive) whose coarsest eigenpairs a host
+// thread is still computing; H.lam and the staged V are then not read.
+slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, const MgStaged &S, int block,
+                      std::shared_ptr<HostHierarchy> Hp = nullptr, std::shared_future<std::string> eig = {}) {
     const int nlev = (int)H.lv.size();
     if (nlev > MG_MAX_LEVELS) {
         g_last_error = "multigrid setup: too many levels";
@@ -780,10 +825,37 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, const MgStaged &S,
     };
     fill(h->mg32, 0.0f);
     fill(h->mg64, 0.0);
-    h->mg_lam = H.lam;
     h->mg_nlev_full = nlev;
     h->mg_fullV32 = h->mg32.V;
     h->mg_fullV64 = h->mg64.V;
+    h->mg_coarse_pending = nullptr;
+    if (eig.valid() && Hp) {
+        h->mg_lam.clear();
+        float *v32 = const_cast<float *>(h->mg_fullV32);
+        double *v64 = const_cast<double *>(h->mg_fullV64);
+        h->mg_coarse_pending = [Hp, eig, v32, v64](slrf_handle *hh) -> slrf_status {
+            std::string err;
+            try {
+                err = eig.get();
+            } catch (const std::exception &ex) {
+                err = std::string("multigrid setup: ") + ex.what();
+            }
+            if (!err.empty()) {
+                g_last_error = err;
+                return SLRF_BREAKDOWN;
+            }
+            const size_t nn = Hp->V.size();
+            std::vector<float> V32(nn);
+            for (size_t k = 0; k < nn; ++k) V32[k] = (float)Hp->V[k];
+            CK(cudaMemcpyAsync(v32, V32.data(), nn * 4, cudaMemcpyHostToDevice, hh->ctx.stream));
+            CK(cudaMemcpyAsync(v64, Hp->V.data(), nn * 8, cudaMemcpyHostToDevice, hh->ctx.stream));
+            CK(cudaStreamSynchronize(hh->ctx.stream));   // pageable sources
+            hh->mg_lam = Hp->lam;
+            return SLRF_OK;
+        };
+    } else {
+        h->mg_lam = H.lam;
+    }
     h->mg_maxba.clear();
     h->mg_host_lv.clear();
     for (int l = 0; l < nlev; ++l) {
@@ -930,6 +1002,10 @@ slrf_status mg_prepare(slrf_handle *h, const slrf_filter *f, const KrylovDims &d
             V = reinterpret_cast<const T *>(reinterpret_cast<char *>(E.dev.p) + (sizeof(T) == 4 ? 0 : off64));
             lam = &E.lam;
         }
+    }
+    if (e_inv < 0 && c == nfull - 1 && h->mg_coarse_pending) {   // the cycle reaches the coarsest level
+        CKS(h->mg_coarse_pending(h));
+        h->mg_coarse_pending = nullptr;
     }
     mg.nlev = c + 1;
     mg.nc = h->mg_host_lv[c].n;
@@ -2070,17 +2146,25 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         std::vector<double> av, bv;
     };
     auto hc = std::make_shared<HostCopy>();
-    hc->rp.resize(n + 1);
-    hc->ci.resize(nnz);
-    hc->av.resize(nnz);
-    hc->bv.resize(nnz);
     std::vector<int32_t> &rp = hc->rp, &ci = hc->ci;
     std::vector<double> &av = hc->av, &bv = hc->bv;
-    const cudaMemcpyKind kind = p->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    CK(cudaMemcpy(rp.data(), p->row_ptr, (n + 1) * sizeof(int32_t), kind));
-    CK(cudaMemcpy(ci.data(), p->col_idx, nnz * sizeof(int32_t), kind));
-    CK(cudaMemcpy(av.data(), p->a_val, nnz * sizeof(double), kind));
-    CK(cudaMemcpy(bv.data(), p->b_val, nnz * sizeof(double), kind));
+    if (p->on_device) {
+        rp.resize(n + 1);
+        ci.resize(nnz);
+        av.resize(nnz);
+        bv.resize(nnz);
+        CK(cudaMemcpy(rp.data(), p->row_ptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(ci.data(), p->col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(av.data(), p->a_val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(bv.data(), p->b_val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {   // the four arrays copied side by side
+        host_team(4, [&](int t) {
+            if (t == 0) rp.assign(p->row_ptr, p->row_ptr + n + 1);
+            if (t == 1) ci.assign(p->col_idx, p->col_idx + nnz);
+            if (t == 2) av.assign(p->a_val, p->a_val + nnz);
+            if (t == 3) bv.assign(p->b_val, p->b_val + nnz);
+        });
+    }
     if (!pencil_valid(n, nnz, rp, ci, av, bv)) return SLRF_EINVAL;
     // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
     // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
@@ -2097,26 +2181,30 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     const int mg_blk = want_mg ? mg_block_for(opts_copy, n, rp, ci) : 0;
     struct MgBuilt {
         std::string err;
-        HostHierarchy H;
+        std::shared_ptr<HostHierarchy> H;
         MgStaged S;
+        std::shared_future<std::string> eig;   // coarsest eigenpairs, if still running
     };
     std::future<MgBuilt> mg_fut;
     auto build_mg = [hc, opts_copy, n, mg_blk, R] {
         MgBuilt r;
+        r.H = std::make_shared<HostHierarchy>();
         MgParams prm = mg_params(opts_copy, mg_blk);
         prm.defer_coarse_eig = true;
-        r.err = mg_build((int)n, hc->rp.data(), hc->ci.data(), hc->av.data(), hc->bv.data(), prm, r.H);
+        r.err = mg_build((int)n, hc->rp.data(), hc->ci.data(), hc->av.data(), hc->bv.data(), prm, *r.H);
         if (!r.err.empty()) return r;
-        // the coarsest level's eigenvectors on a second thread while the
-        // image of the other levels is laid out and filled
-        std::future<std::string> eig;
+        // the coarsest level's eigenpairs on a thread of their own: a cycle
+        // that ends at a level with dense shifted inverses never needs them,
+        // and the first one that does waits for them
         try {
-            eig = std::async(std::launch::async, [&r] { return mg_coarse_eig(r.H); });
+            r.eig = std::async(std::launch::async, [Hp = r.H] { return mg_coarse_eig(*Hp); }).share();
         } catch (...) {   // no thread: in line
         }
-        mg_stage(r.H, R > 1 ? R : 1, r.S);
-        r.err = eig.valid() ? eig.get() : mg_coarse_eig(r.H);
-        if (r.err.empty()) mg_stage_v(r.H, r.S);
+        mg_stage(*r.H, R > 1 ? R : 1, r.S);
+        if (!r.eig.valid()) {
+            r.err = mg_coarse_eig(*r.H);
+            if (r.err.empty()) mg_stage_v(*r.H, r.S);
+        }
         return r;
     };
     if (want_mg) {
@@ -2125,9 +2213,6 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         } catch (...) {   // no thread: built synchronously below
         }
     }
-    std::vector<int32_t> gptr, ucol;
-    std::vector<double2> uab;
-    if (R > 1) build_rowgroups(R, n, rp, ci, av, bv, gptr, ucol, uab);
     slrf_handle *h = new slrf_handle();
     h->opts = *o;
     h->node_blocks = blocks;
@@ -2168,53 +2253,57 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     cudaEventCreate(&h->ev_t0);
     cudaEventCreate(&h->ev_t1);
     cudaStream_t s = h->ctx.stream;
-    cudaMemcpyAsync(h->A.rowptr, rp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(h->A.col, ci.data(), nnz * 4, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(h->A.a, av.data(), nnz * 8, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(h->A.b, bv.data(), nnz * 8, cudaMemcpyHostToDevice, s);
+    // from the caller's arrays (pinned host memory or device memory is read
+    // directly); complete before this call returns
+    cudaMemcpyAsync(h->A.rowptr, p->row_ptr, (n + 1) * 4, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(h->A.col, p->col_idx, nnz * 4, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(h->A.a, p->a_val, nnz * 8, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(h->A.b, p->b_val, nnz * 8, cudaMemcpyDefault, s);
     k_pack_ab<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(nnz, h->A.a, h->A.b, h->A.ab32, h->A.ab64);
     k_diag<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((int)n, h->A.rowptr, h->A.col, h->A.a, h->A.b, h->A.diag_a,
                                                          h->A.diag_b);
     if (R > 1) {
-        const int64_t U = (int64_t)ucol.size();
-        std::vector<float2> uab32(uab.size());
-        for (size_t i = 0; i < uab.size(); ++i) uab32[i] = make_float2((float)uab[i].x, (float)uab[i].y);
-        if (!(alloc((void **)&h->A.rg_ptr, gptr.size() * 4) && alloc((void **)&h->A.rg_col, U * 4) &&
-              alloc((void **)&h->A.rg_ab32, uab.size() * 8) && alloc((void **)&h->A.rg_ab64, uab.size() * 16))) {
+        // row-group form, built on the device from the uploaded CSR: sizes
+        // (one merge per group), prefix sum and largest group, then the arrays
+        const int64_t ng = (n + R - 1) / R;
+        if (!alloc((void **)&h->A.rg_ptr, (ng + 2) * 4)) {
+            g_last_error = "device allocation of the row-group pencil failed";
+            slrf_destroy(h);
+            return SLRF_ENOMEM;
+        }
+        const unsigned gb = (unsigned)((ng + 255) / 256);
+        k_rg_count<<<gb, 256, 0, s>>>(n, R, ng, h->A.rowptr, h->A.col, h->A.rg_ptr);
+        k_rg_scan<<<1, 1024, 0, s>>>(ng, h->A.rg_ptr, h->A.rg_ptr + ng + 1);
+        int32_t tail[2] = {0, 0};   // union entries, largest group
+        cudaMemcpyAsync(tail, h->A.rg_ptr + ng, sizeof(tail), cudaMemcpyDeviceToHost, s);
+        const cudaError_t e0 = cudaStreamSynchronize(s);
+        if (e0 != cudaSuccess) {
+            g_last_error = std::string("pencil upload: ") + cudaGetErrorString(e0);
+            slrf_destroy(h);
+            return SLRF_ECUDA;
+        }
+        const int64_t U = tail[0];
+        if (!(alloc((void **)&h->A.rg_col, U * 4) && alloc((void **)&h->A.rg_ab32, U * R * 8) &&
+              alloc((void **)&h->A.rg_ab64, U * R * 16))) {
             g_last_error = "device allocation of the row-group pencil failed";
             slrf_destroy(h);
             return SLRF_ENOMEM;
         }
         h->A.rg_rows = R;
-        h->A.rg_ngroups = (int)(gptr.size() - 1);
+        h->A.rg_ngroups = (int)ng;
         h->A.rg_nnz = U;
-        // staged-kernel form: packed (a, a, b, b) pairs and own-column positions
-        int emax = 0;
-        for (size_t g = 0; g + 1 < gptr.size(); ++g) emax = std::max(emax, gptr[g + 1] - gptr[g]);
-        h->A.rg_emax = emax;
-        if (emax <= 255) {
-            const int64_t ng = (int64_t)gptr.size() - 1;
-            std::vector<float4> ab4(uab.size());
-            for (size_t i = 0; i < uab.size(); ++i) {
-                const float a = (float)uab[i].x, b = (float)uab[i].y;
-                ab4[i] = make_float4(a, a, b, b);
-            }
-            std::vector<uint8_t> dpos((size_t)ng * R, 0);
-            for (int64_t g = 0; g < ng; ++g)
-                for (int r = 0; r < R; ++r) {
-                    const int64_t row = g * R + r;
-                    if (row >= n) break;
-                    const auto b = ucol.begin() + gptr[g], e = ucol.begin() + gptr[g + 1];
-                    dpos[(size_t)g * R + r] = (uint8_t)(std::lower_bound(b, e, (int32_t)row) - b);
+        h->A.rg_emax = tail[1];
+        // staged-kernel form, optional (without it the row-group kernel
+        // runs): packed (a, a, b, b) pairs and own-column positions
+        if (tail[1] <= 255 && !(alloc((void **)&h->A.rg_ab4, U * R * 16) && alloc((void **)&h->A.rg_dpos, ng * R))) {
+            for (void **q : {(void **)&h->A.rg_ab4, (void **)&h->A.rg_dpos})
+                if (*q) {
+                    cudaFreeAsync(*q, s);
+                    *q = nullptr;
                 }
-            // optional: without these arrays the row-group kernel runs
-            if (alloc((void **)&h->A.rg_ab4, ab4.size() * 16) && alloc((void **)&h->A.rg_dpos, dpos.size())) {
-                cudaMemcpyAsync(h->A.rg_ab4, ab4.data(), ab4.size() * 16, cudaMemcpyHostToDevice, s);
-                cudaMemcpyAsync(h->A.rg_dpos, dpos.data(), dpos.size(), cudaMemcpyHostToDevice, s);
-                // pageable sources: complete before they go out of scope
-                cudaStreamSynchronize(s);
-            }
         }
+        k_rg_fill<<<gb, 256, 0, s>>>(n, R, ng, h->A.rowptr, h->A.col, h->A.a, h->A.b, h->A.rg_ptr, h->A.rg_col,
+                                     h->A.rg_ab32, h->A.rg_ab64, h->A.rg_ab4, h->A.rg_dpos);
         // node-block form (optional: without it the row-group kernel runs)
         std::vector<int32_t> nptr, nnode;
         std::vector<float4> ncoef;
@@ -2224,7 +2313,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
             cudaMemcpyAsync(h->A.nb_ptr, nptr.data(), nptr.size() * 4, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(h->A.nb_node, nnode.data(), nnode.size() * 4, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(h->A.nb_coef, ncoef.data(), ncoef.size() * 16, cudaMemcpyHostToDevice, s);
-            cudaStreamSynchronize(s);
+            cudaStreamSynchronize(s);   // pageable sources
         } else {
             for (void **q : {(void **)&h->A.nb_ptr, (void **)&h->A.nb_node, (void **)&h->A.nb_coef})
                 if (*q) {
@@ -2232,12 +2321,6 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
                     *q = nullptr;
                 }
         }
-        // stream-ordered after the allocations; pageable sources are staged
-        // before each call returns
-        cudaMemcpyAsync(h->A.rg_ptr, gptr.data(), gptr.size() * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(h->A.rg_col, ucol.data(), U * 4, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(h->A.rg_ab32, uab32.data(), uab32.size() * 8, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(h->A.rg_ab64, uab.data(), uab.size() * 16, cudaMemcpyHostToDevice, s);
     }
     // SELL-C-sigma form: built here when asked for, else when the kernel
     // autotuner first times it for this pattern (from the device copy)
@@ -2260,7 +2343,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
                 g_last_error = built.err;
                 return SLRF_BREAKDOWN;
             }
-            return mg_upload(hh, built.H, built.S, mg_blk);
+            return mg_upload(hh, *built.H, built.S, mg_blk, built.H, built.eig);
         };
         if (mg_fut.valid()) {
             auto fut = std::make_shared<std::future<MgBuilt>>(std::move(mg_fut));

@@ -11,12 +11,14 @@
 // deterministic: the row products are computed in parallel, but every row
 // is formed by one thread in a fixed order and sorted by column.
 #include "mg.h"
+#include "host_pool.h"
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstdlib>
+#include <atomic>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -24,34 +26,11 @@
 namespace slrf {
 namespace {
 
-// Host threads for a setup step: up to 16 (or SLRF_HOST_THREADS, read once),
-// one for small work.  No result depends on the count.
-int n_threads(int64_t work) {
-    static const int cap = [] {
-        unsigned hc = std::thread::hardware_concurrency();
-        int t = (int)std::min<unsigned>(hc ? hc : 1, 16u);
-        if (const char *env = std::getenv("SLRF_HOST_THREADS")) {
-            const int v = std::atoi(env);
-            if (v >= 1) t = std::min(v, 64);
-        }
-        return t;
-    }();
-    return work < 200000 ? 1 : cap;
-}
+int n_threads(int64_t work) { return host_threads(work); }
 
-// Run fn(r0, r1, tid) over contiguous row ranges in parallel.
 template <class Fn>
 void parallel_for_rows(int nrows, int nt, Fn fn) {
-    if (nt <= 1) {
-        fn(0, nrows, 0);
-        return;
-    }
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) {
-        const int r0 = (int)((int64_t)nrows * t / nt), r1 = (int)((int64_t)nrows * (t + 1) / nt);
-        th.emplace_back(fn, r0, r1, t);
-    }
-    for (auto &x : th) x.join();
+    host_parallel_rows(nrows, nt, fn);
 }
 
 // Sparse rows produced by a per-row accumulator (sparse accumulator with a
@@ -110,31 +89,63 @@ void build_rows(int nrows, int ncols, bool pair, int64_t work, RowFn row_fn, Row
     out.col.resize(tot);
     out.a.resize(tot);
     if (pair) out.b.resize(tot);
-    int64_t off = 0;
-    for (auto &p : parts) {
-        std::copy(p.col.begin(), p.col.end(), out.col.begin() + off);
-        std::copy(p.a.begin(), p.a.end(), out.a.begin() + off);
-        if (pair) std::copy(p.b.begin(), p.b.end(), out.b.begin() + off);
-        off += (int64_t)p.col.size();
+    std::vector<int64_t> off(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) off[t + 1] = off[t] + (int64_t)parts[t].col.size();
+    host_team(nt, [&](int t) {   // each part to its place
+        const Part &p = parts[t];
+        std::copy(p.col.begin(), p.col.end(), out.col.begin() + off[t]);
+        std::copy(p.a.begin(), p.a.end(), out.a.begin() + off[t]);
+        if (pair) std::copy(p.b.begin(), p.b.end(), out.b.begin() + off[t]);
+    });
+}
+
+// Transpose of an nrows x ncols CSR pattern: tptr (ncols + 1) and, per entry
+// of the transpose, its source row trow and source position tsrc; every row
+// of the transpose lists its source rows ascending.  Row ranges in parallel:
+// counts per (range, column), offsets in (column, range) order, then each
+// range writes its entries; the result is that of one serial pass.
+void transpose_pattern(int nrows, int ncols, const int32_t *ptr, const int32_t *col, std::vector<int32_t> &tptr,
+                       int32_t *trow, int32_t *tsrc) {
+    const int nt = n_threads(ptr[nrows]);
+    std::vector<int32_t> cnt((size_t)nt * ncols, 0);
+    parallel_for_rows(nrows, nt, [&](int r0, int r1, int t) {
+        int32_t *c = &cnt[(size_t)t * ncols];
+        for (int32_t k = ptr[r0]; k < ptr[r1]; ++k) c[col[k]]++;
+    });
+    tptr.assign(ncols + 1, 0);
+    int32_t run = 0;
+    for (int c = 0; c < ncols; ++c) {
+        tptr[c] = run;
+        for (int t = 0; t < nt; ++t) {
+            const int32_t v = cnt[(size_t)t * ncols + c];
+            cnt[(size_t)t * ncols + c] = run;
+            run += v;
+        }
     }
+    tptr[ncols] = run;
+    parallel_for_rows(nrows, nt, [&](int r0, int r1, int t) {
+        int32_t *o = &cnt[(size_t)t * ncols];
+        for (int i = r0; i < r1; ++i)
+            for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+                const int32_t d = o[col[k]]++;
+                trow[d] = i;
+                tsrc[d] = k;
+            }
+    });
 }
 
 HostCsr transpose(const HostCsr &M) {
     HostCsr T;
     T.n_rows = M.n_cols;
     T.n_cols = M.n_rows;
-    T.ptr.assign(T.n_rows + 1, 0);
-    for (int32_t c : M.col) T.ptr[c + 1]++;
-    for (int i = 0; i < T.n_rows; ++i) T.ptr[i + 1] += T.ptr[i];
-    T.col.resize(M.col.size());
-    T.val.resize(M.col.size());
-    std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
-    for (int i = 0; i < M.n_rows; ++i)   // ascending i keeps each row of T sorted
-        for (int32_t k = M.ptr[i]; k < M.ptr[i + 1]; ++k) {
-            const int32_t d = fill[M.col[k]]++;
-            T.col[d] = i;
-            T.val[d] = M.val[k];
-        }
+    const size_t nz = M.col.size();
+    T.col.resize(nz);
+    T.val.resize(nz);
+    std::vector<int32_t> src(nz);
+    transpose_pattern(M.n_rows, M.n_cols, M.ptr.data(), M.col.data(), T.ptr, T.col.data(), src.data());
+    parallel_for_rows((int)nz, n_threads((int64_t)nz), [&](int d0, int d1, int) {
+        for (int d = d0; d < d1; ++d) T.val[d] = M.val[src[d]];
+    });
     return T;
 }
 
@@ -144,10 +155,17 @@ void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, in
               std::vector<int32_t> &sptr, std::vector<int32_t> &scol) {
     const int nn = n / bs;
     std::vector<double> dnorm(nn, 0.0);   // ||A_II||_F^2
-    for (int i = 0; i < n; ++i)
-        for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k)
-            if (col[k] / bs == i / bs) dnorm[i / bs] += a[k] * a[k];
     const int nt = n_threads(ptr[n]);
+    parallel_for_rows(nn, nt, [&](int I0, int I1, int) {
+        for (int I = I0; I < I1; ++I) {
+            const int lo = I * bs, hi = lo + bs;
+            double t = 0.0;
+            for (int i = lo; i < hi; ++i)
+                for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k)
+                    if (col[k] >= lo && col[k] < hi) t += a[k] * a[k];
+            dnorm[I] = t;
+        }
+    });
     std::vector<std::vector<int32_t>> len(nt), out(nt);
     const double th2 = theta * theta;
     parallel_for_rows(nn, nt, [&](int I0, int I1, int t) {
@@ -157,7 +175,7 @@ void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, in
             nb.clear();
             for (int i = I * bs; i < I * bs + bs; ++i)
                 for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-                    const int J = col[k] / bs;
+                    const int J = bs == 1 ? col[k] : col[k] / bs;
                     if (J == I) continue;
                     if (mark[J] != I) {
                         mark[J] = I;
@@ -177,15 +195,17 @@ void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, in
         }
     });
     sptr.assign(nn + 1, 0);
-    scol.clear();
     int I = 0;
+    std::vector<int64_t> off(nt + 1, 0);
     for (int t = 0; t < nt; ++t) {
         for (int32_t l : len[t]) {
             sptr[I + 1] = sptr[I] + l;
             ++I;
         }
-        scol.insert(scol.end(), out[t].begin(), out[t].end());
+        off[t + 1] = off[t] + (int64_t)out[t].size();
     }
+    scol.resize(off[nt]);
+    host_team(nt, [&](int t) { std::copy(out[t].begin(), out[t].end(), scol.begin() + off[t]); });
 }
 
 // Greedy aggregation in node order: (1) a node whose strong neighbours are
@@ -227,24 +247,32 @@ int aggregate(int nn, const std::vector<int32_t> &sptr, const std::vector<int32_
 class Barrier {
   public:
     explicit Barrier(int n) : n_(n), left_(n) {}
+    // The last thread to arrive opens the next generation; the others spin
+    // briefly on it (the teams here pass one barrier every few microseconds)
+    // and then sleep on the condition variable.
     void wait() {
-        std::unique_lock<std::mutex> lk(m_);
-        const int64_t g = gen_;
-        if (--left_ == 0) {
-            ++gen_;
-            left_ = n_;
+        const int64_t g = gen_.load(std::memory_order_acquire);
+        if (left_.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+            left_.store(n_, std::memory_order_relaxed);
+            {
+                std::lock_guard<std::mutex> lk(m_);
+                gen_.store(g + 1, std::memory_order_release);
+            }
             cv_.notify_all();
-        } else {
-            cv_.wait(lk, [&] { return gen_ != g; });
+            return;
         }
+        for (int i = 0; i < 20000; ++i)
+            if (gen_.load(std::memory_order_acquire) != g) return;
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != g; });
     }
 
   private:
     std::mutex m_;
     std::condition_variable cv_;
     const int n_;
-    int left_;
-    int64_t gen_ = 0;
+    std::atomic<int> left_;
+    std::atomic<int64_t> gen_{0};
 };
 
 // Largest |eigenvalue| of D^{-1} A by power iteration (deterministic start).
@@ -264,7 +292,8 @@ double rho_dinv_a(int n, const int32_t *ptr, const int32_t *col, const double *a
     // squared norm sum (scale x_i)^2 over its rows
     std::vector<double> part[2] = {std::vector<double>(2 * NCH), std::vector<double>(2 * NCH)};
     auto chunk = [&](int c) { return (int)((int64_t)n * c / NCH); };
-    const int nt = n_threads(ptr[n]);
+    // 30 sweeps over the pattern: threads pay off from ~50 k stored entries
+    const int nt = n_threads((int64_t)ptr[n] * 4);
     Barrier bar(nt);
     double lam_out = 0.0;
     auto team = [&](int c0, int c1, int tid) {
@@ -297,13 +326,7 @@ double rho_dinv_a(int n, const int32_t *ptr, const int32_t *col, const double *a
         }
         if (tid == 0) lam_out = lam;
     };
-    if (nt <= 1) {
-        team(0, NCH, 0);
-    } else {
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t) th.emplace_back(team, NCH * t / nt, NCH * (t + 1) / nt, t);
-        for (auto &x : th) x.join();
-    }
+    host_team(nt, [&](int t) { team(NCH * t / nt, NCH * (t + 1) / nt, t); });
     return lam_out;
 }
 
@@ -484,7 +507,7 @@ void host_syev(int n, std::vector<double> &S, std::vector<double> &w, std::vecto
             bar.wait();
         }
     };
-    parallel_for_rows(nt, nt, [&](int t0, int, int) { reduce(0, 0, t0); });
+    host_team(nt, [&](int t) { reduce(0, 0, t); });
     // the QR phase rotates pairs of eigenvector columns: keep them as rows of Q^T
     std::vector<double> Qt((size_t)n * n);
     for (int r = 0; r < n; ++r)
@@ -592,25 +615,17 @@ void mg_fused_pattern(const HostLevel &L0, int n_coarse, int R, FusedLayout &out
     out.up_ptr.assign(ng + 1, 0);
     for (int64_t g = 0; g < ng; ++g) out.up_ptr[g + 1] = out.up_ptr[g] + glen[g];
     out.up_col.resize(out.up_ptr[ng]);
-    for (int t = 0, g0 = 0; t < nt; ++t) {
+    host_team(nt, [&](int t) {
+        const int64_t g0 = ng * t / nt;   // the first group of range t
         std::copy(ucat[t].begin(), ucat[t].end(), out.up_col.begin() + out.up_ptr[g0]);
-        g0 = (int)(ng * (t + 1) / nt);
-    }
+    });
     // down: F^T, coarse row c lists the fine rows i with an entry (i, c),
-    // ascending (counting sort)
+    // ascending, and their positions in the pattern of A P
     const int64_t nz = (int64_t)L0.fcol.size();
-    out.down_ptr.assign(n_coarse + 1, 0);
-    for (int32_t c : L0.fcol) out.down_ptr[c + 1]++;
-    for (int c = 0; c < n_coarse; ++c) out.down_ptr[c + 1] += out.down_ptr[c];
     out.down_col.resize(nz);
     out.down_src.resize(nz);
-    std::vector<int32_t> fill(out.down_ptr.begin(), out.down_ptr.end() - 1);
-    for (int64_t i = 0; i < n0; ++i)
-        for (int32_t k = L0.fptr[i]; k < L0.fptr[i + 1]; ++k) {
-            const int32_t d = fill[L0.fcol[k]]++;
-            out.down_col[d] = (int32_t)i;
-            out.down_src[d] = k;
-        }
+    transpose_pattern((int)n0, n_coarse, L0.fptr.data(), L0.fcol.data(), out.down_ptr, out.down_col.data(),
+                      out.down_src.data());
 }
 
 void mg_fused_values(const HostLevel &L0, const FusedLayout &FL, double *q_out) {
@@ -669,12 +684,14 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         HostLevel &L = H.lv.back();
         L.diag_a.assign(cn, 0.0);
         L.diag_b.assign(cn, 0.0);
-        for (int i = 0; i < cn; ++i)
-            for (int32_t k = cp[i]; k < cp[i + 1]; ++k)
-                if (cc[k] == i) {
-                    L.diag_a[i] += ca[k];
-                    L.diag_b[i] += cb[k];
-                }
+        parallel_for_rows(cn, n_threads(cp[cn]), [&](int r0, int r1, int) {
+            for (int i = r0; i < r1; ++i)
+                for (int32_t k = cp[i]; k < cp[i + 1]; ++k)
+                    if (cc[k] == i) {
+                        L.diag_a[i] += ca[k];
+                        L.diag_b[i] += cb[k];
+                    }
+        });
         for (int i = 0; i < cn; ++i)
             if (!(L.diag_a[i] > 0.0) || !(L.diag_b[i] > 0.0))
                 return "multigrid setup: non-positive diagonal entry in row " + std::to_string(i);
@@ -737,14 +754,18 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
             L.fap = std::move(APr.a);
             L.fbp = std::move(APr.b);
             L.fp.assign(L.fcol.size(), 0.0);
-            for (int i = 0; i < cn; ++i) {
-                int32_t k = L.fptr[i];
-                for (int32_t t = P.ptr[i]; t < P.ptr[i + 1]; ++t) {
-                    while (k < L.fptr[i + 1] && L.fcol[k] < P.col[t]) ++k;
-                    if (k < L.fptr[i + 1] && L.fcol[k] == P.col[t]) L.fp[k] = P.val[t];
-                    else return "multigrid setup: prolongator entry outside the pattern of A P";
+            std::atomic<bool> outside{false};
+            parallel_for_rows(cn, n_threads((int64_t)L.fcol.size()), [&](int r0, int r1, int) {
+                for (int i = r0; i < r1; ++i) {
+                    int32_t k = L.fptr[i];
+                    for (int32_t t = P.ptr[i]; t < P.ptr[i + 1]; ++t) {
+                        while (k < L.fptr[i + 1] && L.fcol[k] < P.col[t]) ++k;
+                        if (k < L.fptr[i + 1] && L.fcol[k] == P.col[t]) L.fp[k] = P.val[t];
+                        else outside.store(true, std::memory_order_relaxed);
+                    }
                 }
-            }
+            });
+            if (outside.load()) return "multigrid setup: prolongator entry outside the pattern of A P";
         }
         next.ptr = std::move(Cr.ptr);
         next.col = std::move(Cr.col);

@@ -37,7 +37,8 @@ def dump_tool(tmp_path_factory):
         pytest.skip("no C++ compiler")
     exe = str(tmp_path_factory.mktemp("mgh") / "mg_host_dump")
     subprocess.run([gxx, "-O2", "-std=c++17", "-I" + CSRC, os.path.join(ROOT, "tests", "mg_host_dump.cpp"),
-                    os.path.join(CSRC, "mg_setup.cpp"), "-lpthread", "-o", exe], check=True)
+                    os.path.join(CSRC, "mg_setup.cpp"), os.path.join(CSRC, "host_pool.cpp"), "-lpthread", "-o", exe],
+                   check=True)
     return exe
 
 
@@ -130,17 +131,19 @@ def test_level_eigendecomposition(dump_tool, tmp_path, case):
 
 def test_setup_does_not_depend_on_the_thread_count(dump_tool, tmp_path):
     # power iteration, strength graph, row products, level eigensolver and
-    # layouts on 1 and on 4 host threads: byte-identical outputs
-    p = pencil_2d_q1(80, seed=7)                      # levels 6241, 725, 107
+    # layouts on 1, 4 and 16 host threads (every step of the finest level
+    # above the size at which it takes threads): byte-identical outputs
+    p = pencil_2d_q1(160, seed=7)
     outs = {}
-    for nt in (1, 4):
+    for nt in (1, 4, 16):
         d = str(tmp_path / f"t{nt}")
         os.makedirs(d)
         _write_pencil(p, d)
         env = dict(os.environ, SLRF_HOST_THREADS=str(nt))
-        subprocess.run([dump_tool, d, "eig", "1", "1"], check=True, env=env)
+        subprocess.run([dump_tool, d, "eig", "1", "2"], check=True, env=env)
         subprocess.run([dump_tool, d, "layout", "1", "2"], check=True, env=env)
         outs[nt] = {f: open(os.path.join(d, f), "rb").read()
                     for f in ("lam.bin", "V.bin", "Ad.bin", "Bd.bin", "up_col.bin", "down_col.bin", "q.bin")}
-    for f in outs[1]:
-        assert outs[1][f] == outs[4][f], f
+    for nt in (4, 16):
+        for f in outs[1]:
+            assert outs[1][f] == outs[nt][f], (nt, f)
