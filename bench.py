@@ -426,6 +426,16 @@ def bench_3d(pkg, fp32_peak):
                          "avg_launch_us": (k["ms"] / k["launches"] * 1e3) if k["launches"] else None}}
 
 
+def status_counts(pkg, statuses):
+    names = {getattr(pkg.api, k): k for k in ("OK", "NOT_CONVERGED", "STAGNATION", "BREAKDOWN", "SUBSPACE_TOO_SMALL",
+                                               "CHOLQR_FAIL", "ETIMEOUT", "ENOMEM", "EBUDGET")}
+    out = {}
+    for st in statuses:
+        key = names.get(int(st), str(int(st)))
+        out[key] = out.get(key, 0) + 1
+    return out
+
+
 def bench_batch(pkg, count=64):
     """The batched config: 64 independent FE pencils (n log-uniform in
     [1k, 50k], kinds 1D/2D/3D), each on its own handle and stream, solved
@@ -455,8 +465,8 @@ def bench_batch(pkg, count=64):
             "kinds": {k: sum(1 for p in probs if p["kind"] == k) for k in ("1d", "2d", "3d")},
             "n_range": [min(int(p["pencil"].n) for p in probs), max(int(p["pencil"].n) for p in probs)],
             "value": conv / t, "unit": UNIT, "seconds": t, "converged_eigenpairs": int(conv),
-            "ok": sum(1 for r in res if r[4] == pkg.OK), "setup_s": t_setup,
-            "warmup": "one outer step per problem", "steps": 1,
+            "ok": sum(1 for r in res if r[4] == pkg.OK), "statuses": status_counts(pkg, [r[4] for r in res]),
+            "setup_s": t_setup, "warmup": "one outer step per problem", "steps": 1,
             "counting": "every eigenpair that passed both gates, also from problems that stopped short"}
 
 

@@ -325,13 +325,25 @@ def weyl_gamma(kind: str, nev: int) -> float:
     raise KeyError(kind)
 
 
+# Largest 1D pencil drawn for a batch.  On [0, 1] with n interior nodes an
+# eigenvector stored in FP64 carries rounding noise of relative size eps per
+# entry, which the stiffness stencil amplifies by ~sqrt(6)/h while A x itself
+# is ~lambda h |x|: the relative residual |A x - lambda B x| / |A x| cannot go
+# below ~sqrt(6) eps n^2 / lambda_1 (lambda_1 ~ pi^2), which is 1e-8 at
+# n ~ 13 000 and 1.5e-9 at n = 5 000.  1D batch members stay at or below
+# 5 000 so that the 1e-8 gate is reachable in FP64 with a margin.
+N_MAX_1D = 5000
+
+
 def random_problem(rng, kind: str, n_lo: int, n_hi: int, nev_lo: int, nev_hi: int, seed: int):
-    """One random pencil of the given kind with n log-uniform in [n_lo, n_hi].
+    """One random pencil of the given kind with n log-uniform in [n_lo, n_hi]
+    (for 1D in [n_lo, min(n_hi, N_MAX_1D)]).
 
     Returns dict(pencil, kind, nev_target, L, gamma, V0).  L = 1.5 NEV
     (rounded up to even).  The grid size is rounded to the nearest valid one.
     """
-    n_target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+    hi = min(n_hi, max(n_lo, N_MAX_1D)) if kind == "1d" else n_hi
+    n_target = math.exp(rng.uniform(math.log(n_lo), math.log(hi)))
     nev = int(rng.integers(nev_lo, nev_hi + 1))
     if kind == "1d":
         pencil = pencil_1d(max(50, int(round(n_target))))
