@@ -19,6 +19,7 @@
 #include <condition_variable>
 #include <cstdlib>
 #include <atomic>
+#include <iterator>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -169,6 +170,20 @@ void strength(int n, const int32_t *ptr, const int32_t *col, const double *a, in
     std::vector<std::vector<int32_t>> len(nt), out(nt);
     const double th2 = theta * theta;
     parallel_for_rows(nn, nt, [&](int I0, int I1, int t) {
+        if (bs == 1) {   // rows hold each column once, ascending: no accumulation
+            for (int I = I0; I < I1; ++I) {
+                int32_t cnt = 0;
+                for (int32_t k = ptr[I]; k < ptr[I + 1]; ++k) {
+                    const int J = col[k];
+                    if (J != I && a[k] * a[k] >= th2 * std::sqrt(dnorm[I] * dnorm[J])) {
+                        out[t].push_back(J);
+                        ++cnt;
+                    }
+                }
+                len[t].push_back(cnt);
+            }
+            return;
+        }
         std::vector<int32_t> mark(nn, -1), nb;
         std::vector<double> acc(nn, 0.0);
         for (int I = I0; I < I1; ++I) {
@@ -600,14 +615,16 @@ void mg_fused_pattern(const HostLevel &L0, int n_coarse, int R, FusedLayout &out
     std::vector<std::vector<int32_t>> ucat(nt);
     std::vector<int32_t> glen(ng);
     parallel_for_rows((int)ng, nt, [&](int g0, int g1, int t) {
-        std::vector<int32_t> u;
+        std::vector<int32_t> u, w;
         for (int64_t g = g0; g < g1; ++g) {
             const int64_t r0 = g * R, r1 = std::min<int64_t>(n0, r0 + R);
             u.clear();
-            for (int64_t r = r0; r < r1; ++r)
-                u.insert(u.end(), L0.fcol.begin() + L0.fptr[r], L0.fcol.begin() + L0.fptr[r + 1]);
-            std::sort(u.begin(), u.end());
-            u.erase(std::unique(u.begin(), u.end()), u.end());
+            for (int64_t r = r0; r < r1; ++r) {   // rows are ascending without repeats: set unions
+                w.clear();
+                std::set_union(u.begin(), u.end(), L0.fcol.begin() + L0.fptr[r], L0.fcol.begin() + L0.fptr[r + 1],
+                               std::back_inserter(w));
+                u.swap(w);
+            }
             glen[g] = (int32_t)u.size();
             ucat[t].insert(ucat[t].end(), u.begin(), u.end());
         }
@@ -648,18 +665,17 @@ void mg_fused_values(const HostLevel &L0, const FusedLayout &FL, double *q_out) 
     parallel_for_rows((int)ng, nt, [&](int g0, int g1, int) {
         for (int64_t g = g0; g < g1; ++g) {
             const int64_t r0 = g * R;
-            for (int32_t e = FL.up_ptr[g]; e < FL.up_ptr[g + 1]; ++e) {
-                const int32_t c = FL.up_col[e];
-                for (int r = 0; r < R; ++r) {
+            // the group's union list and each row's list are both ascending:
+            // one cursor per row walks its list along the union
+            for (int r = 0; r < R; ++r) {
+                const int64_t row = r0 + r;
+                int32_t k = row < n0 ? L0.fptr[row] : 0;
+                const int32_t k1 = row < n0 ? L0.fptr[row + 1] : 0;
+                for (int32_t e = FL.up_ptr[g]; e < FL.up_ptr[g + 1]; ++e) {
                     double *q = q_up + ((size_t)e * R + r) * 4;
-                    const int64_t row = r0 + r;
-                    if (row >= n0) {
-                        slot(q, 0, 0, false);
-                        continue;
-                    }
-                    const auto b = L0.fcol.begin() + L0.fptr[row], e1 = L0.fcol.begin() + L0.fptr[row + 1];
-                    const auto it = std::lower_bound(b, e1, c);
-                    slot(q, row, (int32_t)(it - L0.fcol.begin()), it != e1 && *it == c);
+                    const bool hit = k < k1 && L0.fcol[k] == FL.up_col[e];
+                    slot(q, hit ? row : 0, hit ? k : 0, hit);
+                    if (hit) ++k;
                 }
             }
         }
