@@ -2172,8 +2172,8 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     int R = o->spmm_rows;
     if (R == 0) R = blocks ? 3 : 2;
     // The multigrid hierarchy (host) is built, and its device image laid out,
-    // on its own thread while the row groups are formed and the pencil is
-    // uploaded; the handle keeps the pending result, and the first solve
+    // on its own thread while the pencil is uploaded and its row-group form
+    // built on the device; the handle keeps the pending result, and the first solve
     // that needs the hierarchy waits for it (after the work it can do
     // without it, such as the first projection of the start block).
     const slrf_opts opts_copy = *o;

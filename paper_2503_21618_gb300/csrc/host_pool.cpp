@@ -61,11 +61,10 @@ class Pool {
             gen_.fetch_add(1, std::memory_order_release);
         }
         cv_work_.notify_all();
-        std::exception_ptr ex;   // member 0 fails: the others still finish first
-        try {
+        try {   // a member that fails: the others still finish first
             fn(0);
         } catch (...) {
-            ex = std::current_exception();
+            keep(std::current_exception());
         }
         for (int i = 0; left_.load(std::memory_order_acquire) != 0; ++i)
             if (i >= kSpin) {
@@ -73,10 +72,21 @@ class Pool {
                 cv_done_.wait(lk, [&] { return left_.load(std::memory_order_acquire) == 0; });
                 break;
             }
+        std::exception_ptr ex;
+        {
+            std::lock_guard<std::mutex> lk(m_);
+            ex = ex_;
+            ex_ = nullptr;
+        }
         if (ex) std::rethrow_exception(ex);
     }
 
   private:
+    void keep(std::exception_ptr e) {   // the first failure of a job
+        std::lock_guard<std::mutex> lk(m_);
+        if (!ex_) ex_ = e;
+    }
+
     void loop(int id) {
         int64_t seen = 0;
         for (;;) {
@@ -92,7 +102,11 @@ class Pool {
                 nt = nt_;
             }
             if (id >= nt) continue;
-            (*f)(id);
+            try {
+                (*f)(id);
+            } catch (...) {
+                keep(std::current_exception());
+            }
             if (left_.fetch_sub(1, std::memory_order_acq_rel) == 1) {
                 std::lock_guard<std::mutex> lk(m_);
                 cv_done_.notify_all();
@@ -106,6 +120,7 @@ class Pool {
     std::atomic<int64_t> gen_{0};
     std::atomic<int> left_{0};
     const std::function<void(int)> *job_ = nullptr;
+    std::exception_ptr ex_;
     int nt_ = 0;
     int size_ = 1;
 };
@@ -150,10 +165,44 @@ void host_team(int nt, const std::function<void(int)> &fn) {
         p->run(nt, fn);
         return;
     }
+    // threads of the caller's own: they start the job together once all of
+    // them exist (a team whose members wait on one another must not start
+    // short of a member); a failure to start one, or of any member, is
+    // rethrown here after every started thread has returned
+    std::atomic<int> go{0};   // 0 wait, 1 run, 2 give up
+    std::mutex em;
+    std::exception_ptr ex;
+    auto keep = [&](std::exception_ptr e) {
+        std::lock_guard<std::mutex> lk(em);
+        if (!ex) ex = e;
+    };
     std::vector<std::thread> th;
-    for (int t = 1; t < nt; ++t) th.emplace_back(fn, t);
-    fn(0);
+    try {
+        for (int t = 1; t < nt; ++t)
+            th.emplace_back([&, t] {
+                int g;
+                while ((g = go.load(std::memory_order_acquire)) == 0) std::this_thread::yield();
+                if (g != 1) return;
+                try {
+                    fn(t);
+                } catch (...) {
+                    keep(std::current_exception());
+                }
+            });
+    } catch (...) {
+        keep(std::current_exception());
+    }
+    const bool all = (int)th.size() == nt - 1;
+    go.store(all ? 1 : 2, std::memory_order_release);
+    if (all) {
+        try {
+            fn(0);
+        } catch (...) {
+            keep(std::current_exception());
+        }
+    }
     for (auto &x : th) x.join();
+    if (ex) std::rethrow_exception(ex);
 }
 
 }  // namespace slrf

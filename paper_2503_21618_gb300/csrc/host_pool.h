@@ -19,8 +19,11 @@ int host_threads(int64_t work);
 // Runs fn(t) for t = 0 .. nt-1 at the same time on nt threads; the calling
 // thread is member 0, so members may wait on one another (a barrier).  The
 // other members come from one of two process-wide pools of waiting workers;
-// a caller that finds both pools busy (a third concurrent setup) starts
-// threads of its own.  Returns when every member has returned.
+// a caller that finds both pools busy (a third concurrent setup), or asks
+// for more members than a pool has, starts threads of its own.  Returns when
+// every member has returned; the first exception of any member is rethrown
+// then (a member that throws before a barrier the others wait at leaves them
+// waiting: members that wait on one another must not throw).
 void host_team(int nt, const std::function<void(int)> &fn);
 
 // fn(r0, r1, t) over nt contiguous row ranges of [0, nrows) on a team.
