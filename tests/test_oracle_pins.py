@@ -311,3 +311,43 @@ def test_sparse_count_on_elasticity_pencil_matches_dense():
         gamma = 0.5 * (lam[k - 1] + lam[k])
         assert inertia.count_below_dense(p.A(), p.B(), gamma) == k
         assert inertia.count_below_sparse(p.A(), p.B(), gamma) == k
+
+
+# --------------------------------------------------------------------------
+# filter derivative and the shifted operator
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 2, 4, 8])
+def test_separation_factor_of_the_midpoint_rule_closed_form(N):
+    # The midpoint rule's filter is 1/(1 + ((x - c)/r)^(2N)) with c = r = gamma/2
+    # (pinned above); its slope at x = gamma is -2N/(4r) = -N/gamma, so the
+    # separation factor |Phi'(gamma)| (Definition 3.1) is N/gamma.
+    for gamma in (1.0, 37.5):
+        s, w = poles.quadrature_poles("midpoint", N, gamma)
+        assert abs(poles.separation_factor(s, w, gamma) - N / gamma) < 1e-12 * N / gamma
+
+
+@pytest.mark.parametrize("rule", ["gauss_legendre", "slrf"])
+def test_filter_derivative_matches_central_differences(rule):
+    s, w = poles.slrf_poles(4, 1.0, 0.01) if rule == "slrf" else poles.quadrature_poles(rule, 5, 1.0)
+    x = np.linspace(-0.5, 3.0, 29)
+    h = 1e-5
+    fd = (poles.phi_real(x + h, s, w) - poles.phi_real(x - h, s, w)) / (2 * h)
+    d = np.real(poles.dphi(x, s, w))
+    np.testing.assert_allclose(d, fd, rtol=0, atol=1e-7 * max(1.0, np.abs(d).max()))
+
+
+def test_shifted_product_on_closed_form_eigenvectors():
+    # (A - sigma B) v_k = (lambda_k - sigma) B v_k for the 1D closed-form
+    # eigenpairs, for complex shifts in both half planes and complex blocks.
+    n = 64
+    p = pencil_1d(n)
+    ks = [1, 2, 9, 40]
+    V = np.stack([inertia.eigvec_1d(n, k) for k in ks], axis=1)
+    lam = inertia.lambda_1d(n, ks)
+    coef = np.array([1.0, 0.5 - 2.0j, -1.5j, 3.0 + 1.0j])
+    P = V * coef[None, :]
+    BV = p.B() @ V
+    for sigma in (120.0 + 35.0j, 3.0 - 80.0j, 0.0):
+        Q = ofilt.shifted_product(p.A(), p.B(), sigma, P)
+        expect = BV * ((lam - sigma) * coef)[None, :]
+        np.testing.assert_allclose(Q, expect, rtol=0, atol=1e-9 * np.abs(expect).max())
