@@ -43,6 +43,11 @@ struct HostLevel {
     // finest-level restriction and prolongation.
     std::vector<int32_t> fptr, fcol;
     std::vector<double> fp, fap, fbp;
+    // levels >= 1 of a hierarchy built from a near-null space: this level's
+    // near-null space (n x n_null, row-major; the stacked R factors), with
+    // n_null dofs per node
+    std::vector<double> nullspace;
+    int n_null = 0;
 };
 
 struct MgParams {
@@ -51,6 +56,16 @@ struct MgParams {
     int max_levels = 10;
     double theta = 0.08;     // strength-of-connection threshold
     bool defer_coarse_eig = false;   // leave V, lam to mg_coarse_eig (run concurrently)
+    // Optional near-null space of A on level 0: n x n_null, row-major (for
+    // 3-dof elasticity the six rigid-body modes, with block = 3).  Without it
+    // each aggregate's tentative prolongator block is the constant per dof
+    // component; with it, the orthonormal factor Q of the thin QR of the
+    // aggregate's rows of the near-null space (aggregates smaller than
+    // n_null / block nodes are first merged into a neighbour, and a rank
+    // deficient block is completed with unit vectors), and the R factors form
+    // the next level's near-null space, with n_null dofs per coarse node.
+    const double *near_null = nullptr;
+    int n_null = 0;
 };
 
 struct HostHierarchy {

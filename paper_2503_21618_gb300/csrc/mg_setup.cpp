@@ -290,6 +290,143 @@ class Barrier {
     std::atomic<int64_t> gen_{0};
 };
 
+// Aggregates of fewer than min_nodes nodes join the aggregate of a neighbour
+// node in the matrix graph: for each small aggregate in turn (ascending), the
+// first neighbour, in node then column order, that lies in another
+// aggregate.  The aggregates are then renumbered by their first node.
+// Returns the new count.
+int merge_small_aggregates(int nn, int bs, const int32_t *ptr, const int32_t *col, int min_nodes,
+                           std::vector<int32_t> &agg, int na) {
+    if (min_nodes <= 1) return na;
+    std::vector<int32_t> parent(na), size(na, 0), first(na, -1);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int a) {
+        while (parent[a] != a) a = parent[a] = parent[parent[a]];
+        return a;
+    };
+    for (int I = 0; I < nn; ++I) {
+        size[agg[I]]++;
+        if (first[agg[I]] < 0) first[agg[I]] = I;
+    }
+    // nodes of each aggregate, ascending (counting sort)
+    std::vector<int32_t> aptr(na + 1, 0), anode(nn);
+    for (int I = 0; I < nn; ++I) aptr[agg[I] + 1]++;
+    for (int a = 0; a < na; ++a) aptr[a + 1] += aptr[a];
+    {
+        std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
+        for (int I = 0; I < nn; ++I) anode[fill[agg[I]]++] = I;
+    }
+    for (int a = 0; a < na; ++a) {
+        const int ra = find(a);
+        if (ra != a || size[ra] >= min_nodes) continue;
+        int target = -1;
+        for (int32_t t = aptr[a]; t < aptr[a + 1] && target < 0; ++t)
+            for (int i = anode[t] * bs; i < anode[t] * bs + bs && target < 0; ++i)
+                for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+                    const int rb = find(agg[col[k] / bs]);
+                    if (rb != ra) {
+                        target = rb;
+                        break;
+                    }
+                }
+        if (target < 0) continue;   // isolated: left as it is
+        parent[ra] = target;
+        size[target] += size[ra];
+    }
+    std::vector<int32_t> id(na, -1);
+    int cnt = 0;
+    for (int I = 0; I < nn; ++I) {
+        const int r = find(agg[I]);
+        if (id[r] < 0) id[r] = cnt++;
+        agg[I] = id[r];
+    }
+    return cnt;
+}
+
+// Tentative prolongator from a near-null space Bn (cn x kn, row-major): per
+// aggregate the thin QR of its rows (dofs of its nodes in ascending order),
+// by modified Gram-Schmidt with a second pass; a column whose remainder is
+// below 1e-10 of its norm is replaced by the unit vector with the largest
+// component outside the columns so far (R keeps zero on its diagonal).
+// tval (cn x kn): row i of T holds Q's row of dof i in columns agg*kn ..
+// agg*kn + kn - 1; Bc (na*kn x kn): the R factors, stacked.  Returns false if
+// an aggregate has fewer dofs than kn.
+bool tentative_qr(int cn, int bs, int kn, const std::vector<int32_t> &agg, int na, const std::vector<double> &Bn,
+                  std::vector<double> &tval, std::vector<double> &Bc) {
+    const int nn = cn / bs;
+    std::vector<int32_t> aptr(na + 1, 0), anode(nn);
+    for (int I = 0; I < nn; ++I) aptr[agg[I] + 1]++;
+    for (int a = 0; a < na; ++a) aptr[a + 1] += aptr[a];
+    {
+        std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
+        for (int I = 0; I < nn; ++I) anode[fill[agg[I]]++] = I;
+    }
+    for (int a = 0; a < na; ++a)
+        if ((aptr[a + 1] - aptr[a]) * bs < kn) return false;
+    tval.assign((size_t)cn * kn, 0.0);
+    Bc.assign((size_t)na * kn * kn, 0.0);
+    parallel_for_rows(na, n_threads((int64_t)cn * kn * kn), [&](int a0, int a1, int) {
+        std::vector<double> Q, v;
+        for (int a = a0; a < a1; ++a) {
+            const int m = (aptr[a + 1] - aptr[a]) * bs;
+            auto dof = [&](int l) { return anode[aptr[a] + l / bs] * bs + l % bs; };
+            Q.assign((size_t)m * kn, 0.0);   // column-major m x kn
+            double *R = &Bc[(size_t)a * kn * kn];
+            for (int j = 0; j < kn; ++j) {
+                v.resize(m);
+                double n0 = 0.0;
+                for (int l = 0; l < m; ++l) {
+                    v[l] = Bn[(size_t)dof(l) * kn + j];
+                    n0 += v[l] * v[l];
+                }
+                n0 = std::sqrt(n0);
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int i = 0; i < j; ++i) {
+                        const double *qi = &Q[(size_t)i * m];
+                        double r = 0.0;
+                        for (int l = 0; l < m; ++l) r += qi[l] * v[l];
+                        for (int l = 0; l < m; ++l) v[l] -= r * qi[l];
+                        R[(size_t)i * kn + j] += r;
+                    }
+                double nv = 0.0;
+                for (int l = 0; l < m; ++l) nv += v[l] * v[l];
+                nv = std::sqrt(nv);
+                if (nv > 1e-10 * n0 && nv > 0.0) {
+                    R[(size_t)j * kn + j] = nv;
+                } else {   // deficient: complete with the unit vector least inside span(Q)
+                    int best = 0;
+                    double bestr = -1.0;
+                    for (int l = 0; l < m; ++l) {
+                        double in = 0.0;
+                        for (int i = 0; i < j; ++i) in += Q[(size_t)i * m + l] * Q[(size_t)i * m + l];
+                        if (1.0 - in > bestr) {
+                            bestr = 1.0 - in;
+                            best = l;
+                        }
+                    }
+                    std::fill(v.begin(), v.end(), 0.0);
+                    v[best] = 1.0;
+                    for (int pass = 0; pass < 2; ++pass)
+                        for (int i = 0; i < j; ++i) {
+                            const double *qi = &Q[(size_t)i * m];
+                            double r = 0.0;
+                            for (int l = 0; l < m; ++l) r += qi[l] * v[l];
+                            for (int l = 0; l < m; ++l) v[l] -= r * qi[l];
+                        }
+                    nv = 0.0;
+                    for (int l = 0; l < m; ++l) nv += v[l] * v[l];
+                    nv = std::sqrt(nv);
+                }
+                double *qj = &Q[(size_t)j * m];
+                for (int l = 0; l < m; ++l) qj[l] = v[l] / nv;
+            }
+            for (int l = 0; l < m; ++l)
+                for (int j = 0; j < kn; ++j) tval[(size_t)dof(l) * kn + j] = Q[(size_t)j * m + l];
+        }
+    });
+    return true;
+}
+
 // Largest |eigenvalue| of D^{-1} A by power iteration (deterministic start).
 // One team of threads runs all the steps on fixed row chunks; the squared
 // norms are summed per chunk and the chunks added in order by every thread,
@@ -689,7 +826,12 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
                      const MgParams &prm, HostHierarchy &H) {
     const auto t0 = std::chrono::steady_clock::now();
     H = HostHierarchy();
-    const int bs = (prm.block > 1 && n % prm.block == 0) ? prm.block : 1;
+    int bs = (prm.block > 1 && n % prm.block == 0) ? prm.block : 1;
+    // near-null space of the current level (cn x kn); kn = 0: the constant
+    // per dof component
+    int kn = prm.near_null && prm.n_null > 0 ? prm.n_null : 0;
+    std::vector<double> Bn;
+    if (kn) Bn.assign(prm.near_null, prm.near_null + (size_t)n * kn);
     // current level as raw arrays (level 0 borrows the caller's pencil)
     const int32_t *cp = ptr, *cc = col;
     const double *ca = a, *cb = b;
@@ -717,27 +859,47 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         std::vector<int32_t> sptr, scol, agg;
         strength(cn, cp, cc, ca, bs, prm.theta, sptr, scol);
         const int nn = cn / bs;
-        const int na = aggregate(nn, sptr, scol, agg);
-        const int nc = na * bs;
+        int na = aggregate(nn, sptr, scol, agg);
+        if (kn) na = merge_small_aggregates(nn, bs, cp, cc, (kn + bs - 1) / bs, agg, na);
+        const int nc = na * (kn ? kn : bs);
         if (nc >= cn || nc > 0.85 * cn) break;   // coarsening stalled
-        std::vector<int32_t> asz(na, 0);
-        for (int I = 0; I < nn; ++I) asz[agg[I]]++;
-        std::vector<int32_t> tcol(cn);
-        std::vector<double> tval(cn);
-        for (int i = 0; i < cn; ++i) {
-            const int I = i / bs, c = i % bs;
-            tcol[i] = agg[I] * bs + c;
-            tval[i] = 1.0 / std::sqrt((double)asz[agg[I]]);
+        std::vector<int32_t> tcol;
+        std::vector<double> tval, Bc;
+        if (kn) {   // T from the near-null space: kn entries per row
+            if (!tentative_qr(cn, bs, kn, agg, na, Bn, tval, Bc))
+                return "multigrid setup: an aggregate has fewer unknowns than the near-null space";
+        } else {   // T: the constant per dof component, one entry per row
+            std::vector<int32_t> asz(na, 0);
+            for (int I = 0; I < nn; ++I) asz[agg[I]]++;
+            tcol.resize(cn);
+            tval.resize(cn);
+            for (int i = 0; i < cn; ++i) {
+                const int I = i / bs, c = i % bs;
+                tcol[i] = agg[I] * bs + c;
+                tval[i] = 1.0 / std::sqrt((double)asz[agg[I]]);
+            }
         }
         // P = T - w D^{-1} A T
         L.rho = rho_dinv_a(cn, cp, cc, ca, L.diag_a);
         const double w = 4.0 / (3.0 * L.rho);
         RowsOut Pr;
-        build_rows(cn, nc, false, (int64_t)cp[cn], [&](int i, auto &add) {
-            const double f = -w / L.diag_a[i];
-            for (int32_t k = cp[i]; k < cp[i + 1]; ++k) add(tcol[cc[k]], f * ca[k] * tval[cc[k]], 0.0);
-            add(tcol[i], tval[i], 0.0);
-        }, Pr);
+        if (kn) {
+            build_rows(cn, nc, false, (int64_t)cp[cn] * kn, [&](int i, auto &add) {
+                const double f = -w / L.diag_a[i];
+                for (int32_t k = cp[i]; k < cp[i + 1]; ++k) {
+                    const int j = cc[k], c0 = agg[j / bs] * kn;
+                    for (int t = 0; t < kn; ++t) add(c0 + t, f * ca[k] * tval[(size_t)j * kn + t], 0.0);
+                }
+                const int c0 = agg[i / bs] * kn;
+                for (int t = 0; t < kn; ++t) add(c0 + t, tval[(size_t)i * kn + t], 0.0);
+            }, Pr);
+        } else {
+            build_rows(cn, nc, false, (int64_t)cp[cn], [&](int i, auto &add) {
+                const double f = -w / L.diag_a[i];
+                for (int32_t k = cp[i]; k < cp[i + 1]; ++k) add(tcol[cc[k]], f * ca[k] * tval[cc[k]], 0.0);
+                add(tcol[i], tval[i], 0.0);
+            }, Pr);
+        }
         L.P.n_rows = cn;
         L.P.n_cols = nc;
         L.P.ptr = std::move(Pr.ptr);
@@ -794,6 +956,12 @@ std::string mg_build(int n, const int32_t *ptr, const int32_t *col, const double
         ca = N2.a.data();
         cb = N2.b.data();
         cn = nc;
+        if (kn) {   // the next level: kn dofs per node, near-null space from the R factors
+            bs = kn;
+            Bn.swap(Bc);
+            N2.nullspace = Bn;
+            N2.n_null = kn;
+        }
     }
     HostLevel &Lc = H.lv.back();
     if (H.lv.size() == 1) {   // no coarsening: the coarsest level is the pencil itself

@@ -3,7 +3,11 @@
 //   mg_host_dump <dir> layout <block> <R>: the finest level's fused-transfer
 //       layouts (mg_fused_layout);
 //   mg_host_dump <dir> eig <block> <level>: that level's dense pencil and its
-//       eigendecomposition by mg_level_eig (V^T A V = diag(lam), V^T B V = I).
+//       eigendecomposition by mg_level_eig (V^T A V = diag(lam), V^T B V = I);
+//   mg_host_dump <dir> nullspace <block> <n_null>: the hierarchy built from
+//       the near-null space in <dir>/nul.bin (n x n_null float64; n_null = 0:
+//       without one): level 0's P, rho and diagonal, level 1's pencil and
+//       near-null space, every level's P (p<l>_*.bin) and the level sizes.
 // <dir>/hdr.bin: int64 n, nnz; rp.bin, ci.bin (int32); a.bin, b.bin (float64).
 #include <cstdio>
 #include <string>
@@ -43,6 +47,14 @@ int main(int argc, char **argv) {
         return 3;
     MgParams prm;
     prm.block = std::stoi(argv[3]);
+    std::vector<double> nul;
+    if (mode == "nullspace") {
+        prm.n_null = std::stoi(argv[4]);
+        if (prm.n_null > 0) {
+            if (!rd(dir + "/nul.bin", nul, (size_t)n * prm.n_null)) return 3;
+            prm.near_null = nul.data();
+        }
+    }
     HostHierarchy H;
     const std::string err = mg_build(n, rp.data(), ci.data(), a.data(), b.data(), prm, H);
     if (!err.empty() || H.lv.size() < 2) {
@@ -63,6 +75,25 @@ int main(int argc, char **argv) {
         const std::string e2 = mg_level_eig(Lv, V, lam);
         if (!e2.empty()) return 4;
         return wr(dir + "/Ad.bin", Ad) && wr(dir + "/Bd.bin", Bd) && wr(dir + "/V.bin", V) && wr(dir + "/lam.bin", lam)
+                   ? 0
+                   : 5;
+    }
+    if (mode == "nullspace") {
+        const HostLevel &L0 = H.lv[0], &L1 = H.lv[1];
+        std::vector<long long> sizes;
+        for (const HostLevel &L : H.lv) sizes.push_back(L.n);
+        const std::vector<double> r0 = {L0.rho};
+        for (size_t l = 0; l + 1 < H.lv.size(); ++l) {   // every level's transfer
+            const std::string s = dir + "/p" + std::to_string(l);
+            if (!(wr(s + "_ptr.bin", H.lv[l].P.ptr) && wr(s + "_col.bin", H.lv[l].P.col) &&
+                  wr(s + "_val.bin", H.lv[l].P.val)))
+                return 5;
+        }
+        return wr(dir + "/sizes.bin", sizes) && wr(dir + "/p_ptr.bin", L0.P.ptr) && wr(dir + "/p_col.bin", L0.P.col) &&
+                       wr(dir + "/p_val.bin", L0.P.val) && wr(dir + "/rho0.bin", r0) &&
+                       wr(dir + "/diag0.bin", L0.diag_a) && wr(dir + "/l1_ptr.bin", L1.ptr) &&
+                       wr(dir + "/l1_col.bin", L1.col) && wr(dir + "/l1_a.bin", L1.a) && wr(dir + "/l1_b.bin", L1.b) &&
+                       wr(dir + "/l1_nul.bin", L1.nullspace)
                    ? 0
                    : 5;
     }

@@ -53,3 +53,18 @@ def test_generators_are_seeded():
     np.testing.assert_array_equal(a.a_val, b.a_val)
     assert not np.array_equal(a.a_val, c.a_val)
     np.testing.assert_array_equal(fe.start_block(10, 3, 1), fe.start_block(10, 3, 1))
+
+
+def test_rigid_body_modes_are_annihilated_away_from_the_clamp():
+    # A B = 0 on every row whose element neighbourhood avoids the clamped face
+    # (x = 0): translations and rotations strain no element; B has rank 6.
+    from workloads import pencil_3d_elasticity, rigid_body_modes
+    p = pencil_3d_elasticity(6, seed=3)
+    B = rigid_body_modes(p)
+    assert B.shape == (p.n, 6)
+    assert np.linalg.matrix_rank(B) == 6
+    node = np.arange(p.n // 3)
+    far = np.repeat(node % (p.meta["p"] - 1) + 1 >= 2, 3)
+    r = p.A() @ B
+    assert np.abs(r[far]).max() < 1e-12 * np.abs(p.a_val).max()
+    assert np.abs(r[~far]).max() > 1e-3 * np.abs(p.a_val).max()   # the clamp breaks it

@@ -5,10 +5,10 @@ random start blocks that the rational-filter subspace iteration consumes.  It
 holds none of the eigensolver's arithmetic: no filter, no shifted solve, no
 Rayleigh-Ritz.  Everything is deterministic in its seed.
 """
-from .fe import (Pencil, pencil_1d, pencil_2d_q1, pencil_3d_elasticity,
+from .fe import (Pencil, pencil_1d, pencil_2d_q1, pencil_3d_elasticity, rigid_body_modes,
                  start_block, config_pencil, CONFIGS, interval_for, weyl_gamma,
                  random_problem, batch_workload, serving_stream)
 
-__all__ = ["Pencil", "pencil_1d", "pencil_2d_q1", "pencil_3d_elasticity",
+__all__ = ["Pencil", "pencil_1d", "pencil_2d_q1", "pencil_3d_elasticity", "rigid_body_modes",
            "start_block", "config_pencil", "CONFIGS", "interval_for", "weyl_gamma",
            "random_problem", "batch_workload", "serving_stream"]

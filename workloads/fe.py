@@ -248,6 +248,29 @@ def pencil_3d_elasticity(nodes_per_edge: int, seed: int | None = BASE_SEED + 3,
                      {"p": p, "h": h, "seed": seed, "sigma": sigma, "nu": nu, "rho": rho})
 
 
+def rigid_body_modes(pencil: Pencil) -> np.ndarray:
+    """The six rigid-body displacement fields of a ``pencil_3d_elasticity``
+    mesh restricted to its free dofs (n x 6, row-major float64): translations
+    along x, y, z and rotations about axes through the cube's centre
+    (x, y, z) -> (0, -z, y), (z, 0, -x), (-y, x, 0).  They are the near-null
+    space of the stiffness away from the clamped face."""
+    p = int(pencil.meta["p"])
+    h = float(pencil.meta["h"])
+    node = np.arange(pencil.n // 3)
+    ix = node % (p - 1) + 1
+    rest = node // (p - 1)
+    iy = rest % p
+    iz = rest // p
+    x, y, z = ix * h - 0.5, iy * h - 0.5, iz * h - 0.5
+    B = np.zeros((pencil.n, 6))
+    for c in range(3):
+        B[c::3, c] = 1.0
+    B[1::3, 3], B[2::3, 3] = -z, y
+    B[0::3, 4], B[2::3, 4] = z, -x
+    B[0::3, 5], B[1::3, 5] = -y, x
+    return np.ascontiguousarray(B)
+
+
 # --------------------------------------------------------------------------
 # start blocks and the named configurations
 # --------------------------------------------------------------------------
