@@ -205,3 +205,46 @@ def test_rigid_body_near_null_space(dump_tool, tmp_path):
     rho_trn = _two_grid_factor(A, out[0]["P"], 1.0 / r["rho"])
     # (measured 0.87 against 0.96: ~3.8 times the convergence rate per cycle)
     assert rho_trn < 1.0 and np.log(rho_rbm) < 2.0 * np.log(rho_trn), (rho_rbm, rho_trn)
+
+
+def test_near_null_space_with_a_rank_deficient_block(dump_tool, tmp_path):
+    # A chain of 3-dof nodes on the x axis: the rotation about x vanishes
+    # (a zero column) and the other modes leave every aggregate's block one
+    # short of rank 6, so each block of T is completed with a unit vector.
+    # The hierarchy still builds, reproduces the near-null space through the
+    # R factors (P B_c = B_n - w D^{-1} A B_n) and has a positive diagonal.
+    nn = 300
+    L1 = sp.diags([-np.ones(nn - 1), 2.0 * np.ones(nn), -np.ones(nn - 1)], [-1, 0, 1])
+    M1 = sp.diags([np.ones(nn - 1), 4.0 * np.ones(nn), np.ones(nn - 1)], [-1, 0, 1]) / 6.0
+    C = np.array([[2.0, 0.3, 0.1], [0.3, 1.5, 0.2], [0.1, 0.2, 1.0]])
+    A = sp.kron(L1, C).tocsr()
+    A.sort_indices()
+    rows = np.repeat(np.arange(3 * nn), np.diff(A.indptr))
+    b_val = sp.kron(M1, np.eye(3)).toarray()[rows, A.indices]    # B on A's (union) pattern
+    from workloads import Pencil
+    p = Pencil(n=3 * nn, row_ptr=A.indptr.astype(np.int32), col_idx=A.indices.astype(np.int32),
+               a_val=A.data.astype(np.float64), b_val=b_val.astype(np.float64))
+    x = np.arange(nn) / nn - 0.5
+    Bn = np.zeros((3 * nn, 6))
+    for c in range(3):
+        Bn[c::3, c] = 1.0
+    Bn[2::3, 4] = -x               # rotation about y on the x axis
+    Bn[1::3, 5] = x                # rotation about z; column 3 (about x) stays zero
+    d = str(tmp_path)
+    _write_pencil(p, d)
+    Bn.tofile(os.path.join(d, "nul.bin"))
+    subprocess.run([dump_tool, d, "nullspace", "3", "6"], check=True)
+    rd = lambda name, dt: np.fromfile(os.path.join(d, name), dtype=dt)  # noqa: E731
+    sizes = rd("sizes.bin", np.int64)
+    nc = int(sizes[1])
+    assert nc % 6 == 0 and nc < 3 * nn
+    P = sp.csr_matrix((rd("p_val.bin", np.float64), rd("p_col.bin", np.int32), rd("p_ptr.bin", np.int32)),
+                      shape=(3 * nn, nc))
+    Bc = rd("l1_nul.bin", np.float64).reshape(nc, 6)
+    w = 4.0 / (3.0 * float(rd("rho0.bin", np.float64)[0]))
+    rhs = Bn - w * (A @ Bn) / rd("diag0.bin", np.float64)[:, None]
+    np.testing.assert_allclose(P @ Bc, rhs, rtol=0, atol=1e-9 * np.abs(rhs).max())
+    assert np.abs(Bc[:, 3]).max() == 0.0          # the zero mode stays zero on the next level
+    A1 = sp.csr_matrix((rd("l1_a.bin", np.float64), rd("l1_col.bin", np.int32), rd("l1_ptr.bin", np.int32)),
+                       shape=(nc, nc))
+    assert (A1.diagonal() > 0).all()
