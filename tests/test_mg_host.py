@@ -248,3 +248,86 @@ def test_near_null_space_with_a_rank_deficient_block(dump_tool, tmp_path):
     A1 = sp.csr_matrix((rd("l1_a.bin", np.float64), rd("l1_col.bin", np.int32), rd("l1_ptr.bin", np.int32)),
                        shape=(nc, nc))
     assert (A1.diagonal() > 0).all()
+
+
+def _vcycle(As, Bs, Ps, s, omega=4.0 / 3.0, exact_max=400):
+    # V(1,1) cycle for A - s B: damped Jacobi (omega / rho(D_l^-1 A_l)) on each
+    # level down to the first with at most exact_max unknowns, solved exactly
+    import scipy.sparse.linalg as spla
+    c = next((l for l in range(1, len(As)) if As[l].shape[0] <= exact_max), len(As) - 1)
+    Ks = [(As[l] - s * Bs[l]).tocsr() for l in range(c + 1)]
+    Ds = []
+    for l in range(c):
+        Dinv = sp.diags(1.0 / As[l].diagonal())
+        rho = abs(spla.eigs(Dinv @ As[l], k=1, which="LM", return_eigenvectors=False)[0])
+        Ds.append((omega / rho) / Ks[l].diagonal())
+    lu = spla.splu(Ks[c].tocsc())
+
+    def cyc(l, r):
+        if l == c:
+            return lu.solve(r)
+        z = Ds[l] * r
+        z = z + Ps[l] @ cyc(l + 1, Ps[l].T @ (r - Ks[l] @ z))
+        return z + Ds[l] * (r - Ks[l] @ z)
+    return lambda r: cyc(0, r)
+
+
+def _cocg_iterations(K, b, prec, tol=1e-5, maxit=2000):
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = prec(r)
+    d = z.copy()
+    rho = r @ z
+    b0 = np.linalg.norm(b)
+    for it in range(1, maxit + 1):
+        q = K @ d
+        al = rho / (d @ q)
+        x += al * d
+        r -= al * q
+        if np.linalg.norm(r) <= tol * b0:
+            return it
+        z = prec(r)
+        rn = r @ z
+        d = z + (rn / rho) * d
+        rho = rn
+    return maxit
+
+
+def test_rigid_body_cycle_for_the_shifted_systems(dump_tool, tmp_path):
+    # COCG iterations for the complex-shifted systems (A - sigma_j B) y = B v
+    # of the four SLRF poles of an interval holding 12 modes of an elasticity
+    # cube, preconditioned by a V(1,1) cycle on each hierarchy: the rigid-body
+    # hierarchy needs fewer iterations than translations alone at every pole
+    # (both far fewer than Jacobi; measured 18-19 against 32-35 and 100-108).
+    import scipy.sparse.linalg as spla
+    from oracle import poles as opoles
+    from workloads import rigid_body_modes
+    p = pencil_3d_elasticity(9, seed=4)              # n = 1 944
+    A, M = p.A().tocsr(), p.B().tocsr()
+    lam = np.sort(spla.eigsh(A, k=14, M=M, sigma=0.0, return_eigenvectors=False))
+    gamma = 0.5 * (lam[11] + lam[12])
+    sig, _ = opoles.slrf_poles(4, 1.0, 0.01, gamma)
+    hier = {}
+    for k in (0, 6):
+        d = str(tmp_path / f"h{k}")
+        os.makedirs(d)
+        _write_pencil(p, d)
+        rigid_body_modes(p).tofile(os.path.join(d, "nul.bin"))
+        subprocess.run([dump_tool, d, "nullspace", "3", str(k)], check=True)
+        sizes = np.fromfile(os.path.join(d, "sizes.bin"), np.int64)
+        Ps = []
+        for l in range(len(sizes) - 1):
+            rd = lambda name, dt: np.fromfile(os.path.join(d, f"p{l}_{name}.bin"), dtype=dt)  # noqa: E731
+            Ps.append(sp.csr_matrix((rd("val", np.float64), rd("col", np.int32), rd("ptr", np.int32)),
+                                    shape=(int(sizes[l]), int(sizes[l + 1]))))
+        As, Bs = [A], [M]
+        for P in Ps:
+            As.append((P.T @ As[-1] @ P).tocsr())
+            Bs.append((P.T @ Bs[-1] @ P).tocsr())
+        hier[k] = (As, Bs, Ps)
+    b = (M @ np.random.default_rng(9).standard_normal(p.n)).astype(complex)
+    for s in sig:
+        K = (A - s * M).tocsr()
+        it = {k: _cocg_iterations(K, b, _vcycle(*hier[k], s)) for k in (0, 6)}
+        it_j = _cocg_iterations(K, b, lambda r, dk=1.0 / K.diagonal(): dk * r)
+        assert it[6] < it[0] < it_j, (s, it, it_j)
