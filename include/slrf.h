@@ -199,6 +199,19 @@ typedef struct {
                                operands, FP32 accumulation: FP32-accurate; needs
                                subspace size <= 256), 0 = cuBLAS FP32 complex
                                GEMM                                           (1) */
+    int32_t mg_n_null;      /* MG: columns of mg_near_null, 0..16; 0 = none  (0) */
+    const double *mg_near_null; /* MG: host n x mg_n_null row-major near-null
+                               space of A for the aggregation (e.g. the six
+                               rigid-body modes of a 3-dof elasticity pencil,
+                               with mg_block 3 or auto): each aggregate's block
+                               of the tentative prolongator is the Q factor of
+                               its rows, and the next level has mg_n_null dofs
+                               per node.  Read and copied by the call that takes
+                               the options (create, set_opts, server submit,
+                               mg_describe, mg_transfer): it need not outlive
+                               it.  Entries must be finite.  Used only where the
+                               preconditioner resolves to multigrid (AUTO keeps
+                               Jacobi on 3-dof node-block pencils).   (NULL) */
 } slrf_opts;
 
 /* Counters of one call.  Krylov iteration counts follow Table 4/5 of the
@@ -260,8 +273,8 @@ slrf_status slrf_opts_default(slrf_opts *o);
 slrf_status slrf_create(slrf_handle **h, const slrf_pencil *p, const slrf_opts *o,
                         void *cuda_stream);
 /* Replace the handle's options (workspace is resized lazily; switching to
- * SLRF_PRECOND_MG or changing mg_coarse / mg_block / mg_theta rebuilds the
- * multigrid hierarchy on the next solve). */
+ * SLRF_PRECOND_MG or changing mg_coarse / mg_block / mg_theta / the near-null
+ * space rebuilds the multigrid hierarchy on the next solve). */
 slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o);
 /* Release the handle and all its device memory.  NULL is ignored. */
 void slrf_destroy(slrf_handle *h);

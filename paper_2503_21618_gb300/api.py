@@ -48,7 +48,8 @@ class slrf_opts(C.Structure):
                 ("stagnation_window", C.c_int32),
                 ("profile_mask", C.c_uint32), ("spmm_kernel", C.c_int32), ("mg_exact", C.c_int32),
                 ("ilu_sweeps", C.c_int32), ("ilu_tri_sweeps", C.c_int32), ("sell_c", C.c_int32),
-                ("sell_sigma", C.c_int32), ("mg_exact_tc", C.c_int32)]
+                ("sell_sigma", C.c_int32), ("mg_exact_tc", C.c_int32), ("mg_n_null", C.c_int32),
+                ("mg_near_null", C.c_void_p)]
 
 
 class slrf_report(C.Structure):
@@ -171,13 +172,28 @@ def _check(status, where, allowed=(OK,)):
 
 
 def default_opts(**kw) -> slrf_opts:
+    """Library defaults with the given fields replaced.  ``mg_near_null`` takes
+    an (n, k) array (the near-null space of A for the multigrid aggregation);
+    the options object keeps it alive and sets ``mg_n_null`` = k."""
     o = slrf_opts()
     load().slrf_opts_default(C.byref(o))
     for k, v in kw.items():
-        if not hasattr(o, k):
-            raise KeyError(k)
-        setattr(o, k, v)
+        _set_opt(o, k, v)
     return o
+
+
+def _set_opt(o: slrf_opts, k: str, v):
+    if not hasattr(o, k):
+        raise KeyError(k)
+    if k == "mg_near_null" and v is not None and not isinstance(v, int):
+        arr = np.ascontiguousarray(v, dtype=np.float64)
+        if arr.ndim != 2:
+            raise ValueError("mg_near_null must be an (n, k) array")
+        o._near_null = arr
+        o.mg_near_null = arr.ctypes.data
+        o.mg_n_null = arr.shape[1]
+        return
+    setattr(o, k, v)
 
 
 class Filter:
@@ -330,7 +346,7 @@ class Handle:
 
     def set_opts(self, **kw):
         for k, v in kw.items():
-            setattr(self.opts, k, v)
+            _set_opt(self.opts, k, v)
         _check(self.lib.slrf_set_opts(self.h, C.byref(self.opts)), "slrf_set_opts")
 
     # ---- hot path ----------------------------------------------------------

@@ -178,6 +178,11 @@ struct slrf_handle {
     std::function<slrf_status(slrf_handle *)> mg_finish;
     int mg_block = 0, mg_coarse = 0;      // parameters the hierarchy was built with
     double mg_theta = 0.0;
+    // the options' near-null space (n x mg_null_k, copied from the options);
+    // mg_null_dirty: set since the hierarchy was built
+    std::vector<double> mg_null;
+    int mg_null_k = 0;
+    bool mg_null_dirty = false;
     std::vector<double> mg_lam;           // coarsest eigenvalues
     // the coarsest level's eigenpairs still being computed on a host thread
     // when the hierarchy was uploaded: waits for them and uploads V (run by
@@ -620,6 +625,17 @@ int mg_block_for(const slrf_opts &o, int64_t n, const std::vector<int32_t> &rp, 
     return has_node_blocks(n, rp, ci, 3) ? 3 : 1;
 }
 
+// The options' near-null space (n x mg_n_null, host), copied; false if an
+// entry is not finite.  Empty when mg_n_null is 0.
+bool copy_near_null(const slrf_opts &o, int64_t n, std::vector<double> &out) {
+    out.clear();
+    if (o.mg_n_null <= 0) return true;
+    out.assign(o.mg_near_null, o.mg_near_null + (size_t)n * o.mg_n_null);
+    for (double v : out)
+        if (!isfinite(v)) return false;
+    return true;
+}
+
 MgParams mg_params(const slrf_opts &o, int block) {
     MgParams prm;
     prm.block = block;
@@ -889,8 +905,11 @@ slrf_status mg_upload(slrf_handle *h, const HostHierarchy &H, const MgStaged &S,
 slrf_status mg_build_upload(slrf_handle *h, const std::vector<int32_t> &rp, const std::vector<int32_t> &ci,
                             const std::vector<double> &av, const std::vector<double> &bv) {
     const int block = mg_block_for(h->opts, h->A.n, rp, ci);
+    MgParams prm = mg_params(h->opts, block);
+    prm.near_null = h->mg_null_k ? h->mg_null.data() : nullptr;
+    prm.n_null = h->mg_null_k;
     HostHierarchy H;
-    const std::string err = mg_build(h->A.n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(h->opts, block), H);
+    const std::string err = mg_build(h->A.n, rp.data(), ci.data(), av.data(), bv.data(), prm, H);
     if (!err.empty()) {
         g_last_error = err;
         return SLRF_BREAKDOWN;
@@ -898,7 +917,9 @@ slrf_status mg_build_upload(slrf_handle *h, const std::vector<int32_t> &rp, cons
     MgStaged S;
     mg_stage(H, h->A.rg_rows > 1 ? h->A.rg_rows : 1, S);
     mg_stage_v(H, S);
-    return mg_upload(h, H, S, block);
+    CKS(mg_upload(h, H, S, block));
+    h->mg_null_dirty = false;
+    return SLRF_OK;
 }
 
 // Build the hierarchy if the options ask for one it does not have yet (from
@@ -910,7 +931,7 @@ slrf_status mg_ensure(slrf_handle *h) {
         CKS(fin(h));
     }
     if (h->mg_ready && h->mg_coarse == h->opts.mg_coarse && h->mg_theta == h->opts.mg_theta &&
-        (h->opts.mg_block == 0 || h->opts.mg_block == h->mg_block))
+        (h->opts.mg_block == 0 || h->opts.mg_block == h->mg_block) && !h->mg_null_dirty)
         return SLRF_OK;
     const int64_t n = h->A.n, nnz = h->A.nnz;
     std::vector<int32_t> rp(n + 1), ci(nnz);
@@ -1969,6 +1990,8 @@ slrf_status slrf_opts_default(slrf_opts *o) {
     o->ilu_sweeps = 3;
     o->ilu_tri_sweeps = 3;
     o->mg_exact_tc = 1;
+    o->mg_n_null = 0;
+    o->mg_near_null = nullptr;
     return SLRF_OK;
 }
 
@@ -1989,6 +2012,7 @@ static slrf_status check_opts(const slrf_opts *o) {
     if (o->spmm_kernel < 0 || o->spmm_kernel > 4) return SLRF_EINVAL;
     if (o->eig_refine < 0 || o->eig_refine > 2) return SLRF_EINVAL;
     if (o->mg_exact_tc < 0 || o->mg_exact_tc > 1) return SLRF_EINVAL;
+    if (o->mg_n_null < 0 || o->mg_n_null > 16 || (o->mg_n_null > 0 && !o->mg_near_null)) return SLRF_EINVAL;
     if (o->sell_c != 0 && o->sell_c != 4 && o->sell_c != 8 && o->sell_c != 16 && o->sell_c != 32 && o->sell_c != 64)
         return SLRF_EINVAL;
     if (o->sell_sigma < 0) return SLRF_EINVAL;
@@ -2012,9 +2036,14 @@ slrf_status slrf_mg_describe(const slrf_pencil *p, const slrf_opts *o, int32_t *
     std::vector<int32_t> rp(p->row_ptr, p->row_ptr + n + 1), ci(p->col_idx, p->col_idx + nnz);
     std::vector<double> av(p->a_val, p->a_val + nnz), bv(p->b_val, p->b_val + nnz);
     if (!pencil_valid(n, nnz, rp, ci, av, bv)) return SLRF_EINVAL;
+    std::vector<double> nul;
+    if (!copy_near_null(*o, n, nul)) return SLRF_EINVAL;
     const int block = mg_block_for(*o, n, rp, ci);
+    MgParams prm = mg_params(*o, block);
+    prm.near_null = nul.empty() ? nullptr : nul.data();
+    prm.n_null = nul.empty() ? 0 : o->mg_n_null;
     HostHierarchy H;
-    const std::string err = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(*o, block), H);
+    const std::string err = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), prm, H);
     if (!err.empty()) {
         g_last_error = err;
         return SLRF_BREAKDOWN;
@@ -2060,9 +2089,13 @@ slrf_status slrf_mg_transfer(const slrf_pencil *p, const slrf_opts *o, int32_t l
     std::vector<int32_t> rp(p->row_ptr, p->row_ptr + n + 1), ci(p->col_idx, p->col_idx + nnzA);
     std::vector<double> av(p->a_val, p->a_val + nnzA), bv(p->b_val, p->b_val + nnzA);
     if (!pencil_valid(n, nnzA, rp, ci, av, bv)) return SLRF_EINVAL;
+    std::vector<double> nul;
+    if (!copy_near_null(*o, n, nul)) return SLRF_EINVAL;
+    MgParams prm = mg_params(*o, mg_block_for(*o, n, rp, ci));
+    prm.near_null = nul.empty() ? nullptr : nul.data();
+    prm.n_null = nul.empty() ? 0 : o->mg_n_null;
     HostHierarchy H;
-    const std::string err =
-        mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), mg_params(*o, mg_block_for(*o, n, rp, ci)), H);
+    const std::string err = mg_build((int)n, rp.data(), ci.data(), av.data(), bv.data(), prm, H);
     if (!err.empty()) {
         g_last_error = err;
         return SLRF_BREAKDOWN;
@@ -2082,7 +2115,16 @@ slrf_status slrf_mg_transfer(const slrf_pencil *p, const slrf_opts *o, int32_t l
 slrf_status slrf_set_opts(slrf_handle *h, const slrf_opts *o) {
     if (!h) return SLRF_EINVAL;
     CKS(check_opts(o));
+    std::vector<double> nul;
+    if (!copy_near_null(*o, h->A.n, nul)) return SLRF_EINVAL;
+    const int k = nul.empty() ? 0 : o->mg_n_null;
+    if (k != h->mg_null_k || nul != h->mg_null) {
+        h->mg_null.swap(nul);
+        h->mg_null_k = k;
+        h->mg_null_dirty = true;
+    }
     h->opts = *o;
+    h->opts.mg_near_null = nullptr;   // the handle keeps its own copy
     h->ctx.profile = o->profile != 0;
     h->ctx.profile_mask = o->profile_mask ? o->profile_mask : ~0u;
     h->A.spmm_kind = o->spmm_kernel;
@@ -2144,6 +2186,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     struct HostCopy {
         std::vector<int32_t> rp, ci;
         std::vector<double> av, bv;
+        std::vector<double> nul;   // the options' near-null space
     };
     auto hc = std::make_shared<HostCopy>();
     std::vector<int32_t> &rp = hc->rp, &ci = hc->ci;
@@ -2166,6 +2209,7 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         });
     }
     if (!pencil_valid(n, nnz, rp, ci, av, bv)) return SLRF_EINVAL;
+    if (!copy_near_null(*o, n, hc->nul)) return SLRF_EINVAL;
     // Row grouping of the shifted SpMM (measured on the 2D Q1 pencil: 2 rows
     // per group beats 1 and 4; 3-dof elasticity groups the rows of a node).
     const bool blocks = has_node_blocks(n, rp, ci, 3);
@@ -2176,7 +2220,8 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     // built on the device; the handle keeps the pending result, and the first solve
     // that needs the hierarchy waits for it (after the work it can do
     // without it, such as the first projection of the start block).
-    const slrf_opts opts_copy = *o;
+    slrf_opts opts_copy = *o;
+    opts_copy.mg_near_null = nullptr;   // the setup thread reads hc->nul
     const bool want_mg = o->precond == SLRF_PRECOND_MG || (o->precond == SLRF_PRECOND_AUTO && !blocks);
     const int mg_blk = want_mg ? mg_block_for(opts_copy, n, rp, ci) : 0;
     struct MgBuilt {
@@ -2191,6 +2236,8 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
         r.H = std::make_shared<HostHierarchy>();
         MgParams prm = mg_params(opts_copy, mg_blk);
         prm.defer_coarse_eig = true;
+        prm.near_null = hc->nul.empty() ? nullptr : hc->nul.data();
+        prm.n_null = hc->nul.empty() ? 0 : opts_copy.mg_n_null;
         r.err = mg_build((int)n, hc->rp.data(), hc->ci.data(), hc->av.data(), hc->bv.data(), prm, *r.H);
         if (!r.err.empty()) return r;
         // the coarsest level's eigenpairs on a thread of their own: a cycle
@@ -2215,6 +2262,9 @@ slrf_status slrf_create(slrf_handle **out, const slrf_pencil *p, const slrf_opts
     }
     slrf_handle *h = new slrf_handle();
     h->opts = *o;
+    h->opts.mg_near_null = nullptr;   // the handle keeps its own copy
+    h->mg_null = hc->nul;
+    h->mg_null_k = hc->nul.empty() ? 0 : o->mg_n_null;
     h->node_blocks = blocks;
     h->ctx.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     h->ctx.profile = o->profile != 0;

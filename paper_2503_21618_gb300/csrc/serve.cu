@@ -95,6 +95,7 @@ struct Request {
     double tol = 1e-8;
     int32_t max_outer = 50;
     slrf_opts opts;
+    std::vector<double> nul;   // the options' near-null space (opts points here)
     size_t bytes = 0;
     Clock::time_point t_submit;
 };
@@ -246,6 +247,16 @@ extern "C" slrf_status slrf_server_submit(slrf_server *s, const slrf_request *r,
     q->tol = r->tol;
     q->max_outer = r->max_outer;
     q->opts = r->opts;
+    if (r->opts.mg_n_null > 0) {   // copied: the caller's array need not outlive the call
+        if (r->opts.mg_n_null > 16 || !r->opts.mg_near_null) {
+            delete q;
+            return SLRF_EINVAL;
+        }
+        q->nul.assign(r->opts.mg_near_null, r->opts.mg_near_null + (size_t)p.n * r->opts.mg_n_null);
+        q->opts.mg_near_null = q->nul.data();
+    } else {
+        q->opts.mg_near_null = nullptr;
+    }
     q->bytes = workspace_estimate(p.n, p.nnz, r->L, f.n_poles, r->opts.precision, s->sm_count,
                                   request_mg_coarse(r->opts), r->opts.krylov);
     q->t_submit = Clock::now();

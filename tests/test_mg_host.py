@@ -331,3 +331,30 @@ def test_rigid_body_cycle_for_the_shifted_systems(dump_tool, tmp_path):
         it = {k: _cocg_iterations(K, b, _vcycle(*hier[k], s)) for k in (0, 6)}
         it_j = _cocg_iterations(K, b, lambda r, dk=1.0 / K.diagonal(): dk * r)
         assert it[6] < it[0] < it_j, (s, it, it_j)
+
+
+def test_near_null_space_through_the_c_abi(api):
+    # slrf_mg_transfer / slrf_mg_describe with opts.mg_near_null: level 0's P
+    # has 6 columns per aggregate and spans B_n - w D^{-1} A B_n; invalid
+    # near-null options are rejected.
+    from workloads import rigid_body_modes
+    p = pencil_3d_elasticity(7, seed=11)
+    Bn = rigid_body_modes(p)
+    o = api.default_opts(precond=2, mg_near_null=Bn)
+    assert o.mg_n_null == 6
+    (ptr, col, val, nr, nc), rho = api.mg_transfer(p, 0, o)
+    assert nr == p.n and nc % 6 == 0
+    P = sp.csr_matrix((val, col, ptr), shape=(nr, nc))
+    A = p.A()
+    rhs = Bn - (4.0 / (3.0 * rho)) * (A @ Bn) / A.diagonal()[:, None]
+    y, *_ = np.linalg.lstsq(P.toarray(), rhs, rcond=None)
+    assert np.abs(P @ y - rhs).max() < 1e-9 * np.abs(rhs).max()
+    d = api.mg_describe(p, o)
+    assert d["levels"][1] == nc
+    assert api.mg_describe(p, api.default_opts(precond=2))["levels"][1] != nc   # translations: 3 per aggregate
+    bad = Bn.copy()
+    bad[5, 2] = np.nan
+    for opts in (api.default_opts(precond=2, mg_near_null=bad), api.default_opts(precond=2, mg_n_null=6),
+                 api.default_opts(precond=2, mg_n_null=17, mg_near_null=np.zeros((p.n, 17)))):
+        with pytest.raises(RuntimeError):
+            api.mg_transfer(p, 0, opts)
