@@ -1852,10 +1852,14 @@ size_t workspace_estimate(int64_t n, int64_t nnz, int L, int N, int precision, i
         mgb = (size_t)n * W * 2 * ts + 3 * nh * W * 2 * ts + nh * N * 2 * ts + 200 * (size_t)nnz + nc * nc * 12 +
               nc * N * 2 * ts + 16 * 4096 + 768 * 768 * 12 + 768 * (size_t)N * 2 * ts;
         // FP32 cycles ending at a level of at most mg_exact (1536) unknowns: its
-        // dense shifted inverses and their elimination work
+        // dense shifted inverses and their elimination work, and (subspace
+        // size <= 256) the inverses' bf16 split panels and the per-visit
+        // split vectors and partial sums of their tensor-core application
         if (precision == SLRF_PREC_MIXED) {
             const size_t ne = std::min<size_t>(1536, (size_t)n);
             mgb += (size_t)N * ne * ne * 8 + coarse_inverse_work_bytes((int)ne, N);
+            if (coarse_tc_fits((int)Lp))
+                mgb += coarse_tc_panel_bytes((int)ne, N) + coarse_tc_work_bytes((int)ne, N, (int)Lp);
         }
     }
     // BiCGStab keeps five more n x W blocks (r^, v, y, z, t)

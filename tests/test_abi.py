@@ -112,3 +112,33 @@ def test_slrf_design_scales_with_gamma(lib):
     f7 = api.design_poles("slrf", 3, 7.0, 1.0, 0.01)
     np.testing.assert_allclose(f7.sigma, 7.0 * f1.sigma, rtol=1e-12)
     np.testing.assert_allclose(f7.w, 7.0 * f1.w, rtol=1e-12)
+
+
+def test_request_bytes_estimate(lib):
+    # slrf_request_bytes needs no device (152 SMs assumed without one): it
+    # grows with n, L and the pole count; BiCGStab adds its five n x W blocks;
+    # a multigrid request in mixed precision also budgets the exact level's
+    # dense inverses and their three bf16 parts (each pole's 2n_l x 2n_l real
+    # form), at n_l = 1 536
+    from paper_2503_21618_gb300 import api
+    from workloads import pencil_2d_q1
+    assert lib.slrf_request_bytes(None) == -1
+    srv = api.Server.__new__(api.Server)   # request() and bytes() only: no server (no device) needed
+    srv.lib = lib
+    p, f = pencil_2d_q1(60, seed=1), api.Filter([1 + 1j, 2 + 1j], [1j, 1j])
+
+    def est(pencil, L, filt, **kw):
+        return srv.bytes(srv.request(pencil, filt, 5.0, np.zeros((pencil.n, L)), opts=api.default_opts(**kw)))
+    base = est(p, 20, f, precond=1)
+    assert base > 0
+    assert est(pencil_2d_q1(90, seed=1), 20, f, precond=1) > base
+    assert est(p, 40, f, precond=1) > base
+    assert est(p, 20, api.Filter([1 + 1j, 2 + 1j, 3 + 1j], [1j, 1j, 1j]), precond=1) > base
+    n, W = p.n, 2 * 20
+    assert est(p, 20, f, precond=1, krylov=1) - base >= 5 * n * W * 2 * 4
+    mg_fp64 = est(p, 20, f, precond=2, precision=0)
+    mg_mixed = est(p, 20, f, precond=2)
+    jac_fp64 = est(p, 20, f, precond=1, precision=0)
+    assert mg_fp64 > jac_fp64
+    ne = min(1536, n)
+    assert mg_mixed > 2 * 8 * ne * ne + 3 * (2 * ne) ** 2 * 2 * 2
